@@ -1,0 +1,455 @@
+"""Pins of the CPU oracle to facts outside itself: the paper's printed Tables 1
+and 2 (through Eq 1-3), closed-form node/byte counts, hand-built trees with
+hand-computed results, IEEE-754 single rounding, and planted mistakes that the
+checkers must catch.  CPU only."""
+import ctypes
+import os
+import random
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import treegen as tg
+from treewalk import f32_view, f64_view, half_axpy_exact, i32, node_arrays, node_walk, same_bits, u64
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+UNIT = {"KB": 1024, "MB": 1024 ** 2, "GB": 1024 ** 3}
+
+
+def load_table(name):
+    rows = []
+    for line in open(os.path.join(GOLDEN, name)):
+        if line.startswith("#") or not line.strip():
+            continue
+        a, b, v, u = line.split()
+        rows.append((int(a), int(b), v, u))
+    return rows
+
+
+def fmt(nbytes, unit):
+    return f"{nbytes / UNIT[unit]:.2f}"
+
+
+# The paper's formulas, as printed (Eq 1, Eq 2, Eq 3).
+def eq1(k, n):
+    return 24 * k + 8 * n * k
+
+
+def eq2(k, n):
+    return 24 * k + 8 * n
+
+
+def eq3(q, n, D):
+    return 12 + 8 * n if D == 0 else 24 + 8 * n + q * eq3(q, n, D - 1)
+
+
+def test_eq1_reproduces_table1():
+    rows = load_table("paper_table1_linear_datasize.txt")
+    assert len(rows) == 63
+    for n, k, v, u in rows:
+        assert fmt(eq1(k, n), u) == v, (n, k)
+
+
+def test_eq3_reproduces_table2():
+    rows = load_table("paper_table2_dense_datasize.txt")
+    assert len(rows) == 40
+    for n, q, v, u in rows:
+        assert fmt(eq3(q, n, 3), u) == v, (n, q)
+
+
+def test_oracle_count_linear_equals_table1():
+    # The oracle's byte counter over generated Linear trees (24-byte level
+    # struct, n doubles per level) reproduces the printed table cells.
+    for n, k, v, u in load_table("paper_table1_linear_datasize.txt"):
+        if n > 10 ** 5:
+            continue
+        t = tg.linear_tree(k, n, "allinit", seed=k)
+        c = oracle.count(t.schema, t.root)
+        assert c["payload_bytes"] == eq1(k, n)
+        assert fmt(c["payload_bytes"], u) == v
+        assert c["nstructs"] == k and c["levels"] == k
+        t.free()
+
+
+def test_oracle_count_linear_llinit_is_eq2():
+    for k in range(2, 11):
+        for n in (100, 1000, 12345):
+            t = tg.linear_tree(k, n, "llinit", seed=k)
+            c = oracle.count(t.schema, t.root)
+            assert c["payload_bytes"] == eq2(k, n)
+            # only the last level's A array exists: k structs + 1 array
+            assert c["nblocks"] == k + 1
+            t.free()
+
+
+def test_oracle_count_dense_equals_table2():
+    # Eq 3 counts the half-size last-level struct {int nA; double* A} as 12
+    # bytes; its real size with padding is 16, i.e. 4 more bytes per each of
+    # the q^D last-level structs.
+    D = 3
+    for n, q, v, u in load_table("paper_table2_dense_datasize.txt"):
+        if n > 1000:
+            continue
+        t = tg.dense_tree(q, n, D, seed=q)
+        c = oracle.count(t.schema, t.root)
+        assert c["payload_bytes"] == eq3(q, n, D) + 4 * q ** D
+        assert fmt(c["payload_bytes"] - 4 * q ** D, u) == v
+        assert c["per_level"] == [q ** i for i in range(D + 1)]
+        t.free()
+
+
+@pytest.mark.parametrize("levels,fanout,n", [(4, 1, 7), (3, 16, 5), (5, 3, 11), (1, 8, 3), (6, 2, 0)])
+def test_node_counts_closed_form(levels, fanout, n):
+    t = tg.node_tree(levels, fanout, n, seed=3)
+    c = oracle.count(t.schema, t.root)
+    nodes = levels if fanout == 1 else (fanout ** levels - 1) // (fanout - 1)
+    assert c["nstructs"] == nodes
+    assert c["per_level"] == [fanout ** i for i in range(levels)]
+    interior = nodes - fanout ** (levels - 1)
+    arrays = 2 * nodes if n else 0
+    assert c["nblocks"] == 1 + arrays + interior
+    assert c["payload_bytes"] == 32 * nodes + nodes * 2 * 4 * n
+    t.free()
+
+
+def test_workload_byte_totals():
+    # tiny: 4 nodes * 32 B + 4 nodes * 2 arrays * 65,536 * 4 B
+    t = tg.workload("tiny")
+    assert oracle.count(t.schema, t.root)["payload_bytes"] == 4 * 32 + 4 * 2 * 65536 * 4 == 2097280
+    t.free()
+    # deep: 64 nodes; 63 interior nodes with 2 * 1,024 floats, the leaf 2 * 2^26
+    t = tg.workload("deep")
+    c = oracle.count(t.schema, t.root)
+    assert c["payload_bytes"] == 64 * 32 + 63 * 2 * 1024 * 4 + 2 * 2 ** 26 * 4 == 537389056
+    assert c["nstructs"] == 64
+    t.free()
+
+
+# ---------------------------------------------------------------------------
+# a hand-built node tree with known addresses
+# ---------------------------------------------------------------------------
+
+class CNode(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nchild", ctypes.c_int32), ("position", ctypes.c_void_p),
+                ("velocity", ctypes.c_void_p), ("child", ctypes.c_void_p)]
+
+
+def hand_tree():
+    """root{n=2, nchild=2, pos=[1,2], vel=[3,4]} -> [c0{n=1, pos=[5], vel=[6]}, c1{n=0}]"""
+    keep = []
+    pos = (ctypes.c_float * 2)(1.0, 2.0)
+    vel = (ctypes.c_float * 2)(3.0, 4.0)
+    kids = (CNode * 2)()
+    p0 = (ctypes.c_float * 1)(5.0)
+    v0 = (ctypes.c_float * 1)(6.0)
+    kids[0] = CNode(1, 0, ctypes.addressof(p0), ctypes.addressof(v0), None)
+    kids[1] = CNode(0, 0, None, None, None)
+    root = CNode(2, 2, ctypes.addressof(pos), ctypes.addressof(vel), ctypes.addressof(kids))
+    keep += [pos, vel, kids, p0, v0, root]
+    return root, keep
+
+
+def test_deep_copy_hand_built_layout():
+    assert ctypes.sizeof(CNode) == 32
+    root, keep = hand_tree()
+    s = tg.node_schema()
+    cp = oracle.deep_copy(s, ctypes.addressof(root))
+    b = cp.base
+    # bump order: root, root.pos, root.vel, root.child[2], c0.pos, c0.vel; 16-byte starts
+    assert cp.root == b
+    assert (i32(b), i32(b + 4)) == (2, 2)
+    assert u64(b + 8) == b + 32 and u64(b + 16) == b + 48 and u64(b + 24) == b + 64
+    assert list(f32_view(b + 32, 2)) == [1.0, 2.0] and list(f32_view(b + 48, 2)) == [3.0, 4.0]
+    c0, c1 = b + 64, b + 96
+    assert (i32(c0), i32(c0 + 4)) == (1, 0)
+    assert u64(c0 + 8) == b + 128 and u64(c0 + 16) == b + 144 and u64(c0 + 24) == 0
+    assert f32_view(b + 128, 1)[0] == 5.0 and f32_view(b + 144, 1)[0] == 6.0
+    assert (i32(c1), u64(c1 + 8), u64(c1 + 16), u64(c1 + 24)) == (0, 0, 0, 0)
+    assert cp.used == 148
+    # nothing in the copy points back into the source
+    src_ptrs = {root.position, root.velocity, root.child}
+    assert not src_ptrs & {u64(b + 8), u64(b + 16), u64(b + 24)}
+
+
+def test_deep_copy_relative_pointer_base():
+    root, keep = hand_tree()
+    s = tg.node_schema()
+    base = 0x7A0000000000
+    cp = oracle.deep_copy(s, ctypes.addressof(root), ptr_base=base)
+    b = cp.base
+    assert u64(b + 8) == base + 32 and u64(b + 24) == base + 64 and u64(b + 64 + 8) == base + 128
+
+
+def test_resolve_hand_built():
+    root, keep = hand_tree()
+    s = tg.node_schema()
+    r = ctypes.addressof(root)
+    assert oracle.host_resolve(s, r, []) == r
+    assert oracle.host_resolve(s, r, [(4, 1)]) == root.child + 32
+    assert oracle.host_resolve(s, r, [(4, 0), (2, 0)]) == ctypes.cast(root.child, ctypes.POINTER(CNode))[0].position
+    assert oracle.host_resolve(s, r, [(3, 1)]) == root.velocity + 4
+    with pytest.raises(RuntimeError):
+        oracle.host_resolve(s, r, [(4, 2)])
+    with pytest.raises(RuntimeError):
+        oracle.host_resolve(s, r, [(4, 1), (2, 0)])  # c1 has no elements
+    base = 0x7A0000000000
+    cp = oracle.deep_copy(s, r, ptr_base=base)
+    img = cp.image()
+    assert oracle.image_resolve(s, img, base, []) == base
+    assert oracle.image_resolve(s, img, base, [(4, 1)]) == base + 96
+    assert oracle.image_resolve(s, img, base, [(4, 0), (2, 0)]) == base + 128
+    assert oracle.image_resolve(s, img, base, [(4, 0), (3, 0)]) == base + 144
+    assert oracle.image_resolve(s, img, base, [(2, 1)]) == base + 36
+
+
+def test_resolve_listing1_chain():
+    # simulation->atoms->traits->positions (Listing 1)
+    t = tg.listing1_tree(10, seed=4)
+    s = t.schema
+    atoms = u64(t.root + 8)
+    traits = u64(atoms + 8)
+    pos0 = u64(traits + 8)
+    assert oracle.host_resolve(s, t.root, [(1, 0), (1, 0), (1, 0)]) == pos0
+    base = 0x7B0000000000
+    cp = oracle.deep_copy(s, t.root, ptr_base=base)
+    got = oracle.image_resolve(s, cp.image(), base, [(1, 0), (1, 0), (1, 0)])
+    off = got - base
+    assert cp.image()[off:off + 80].tobytes() == ctypes.string_at(pos0, 80)
+    t.free()
+
+
+# ---------------------------------------------------------------------------
+# the leaf update: single IEEE-754 rounding, hand-computed special cases
+# ---------------------------------------------------------------------------
+
+def test_update_special_values():
+    keep = []
+    vals_p = [1.0, 0.25, -0.5, 2.0 ** -23, 1.0, 1.0 + 2.0 ** -23, -1.0, 0.75]
+    vals_v = [-2.0, 0.5, 1.0, 2.0 ** -23, 2.0 ** -23, 2.0 ** -23, -2.0 ** -23, 0.0]
+    # hand-computed: 1-1=0; 0.25+0.25; -0.5+0.5=0; 2^-23+2^-24; 1+2^-24 ties to
+    # even -> 1; (1+2^-23)+2^-24 ties to even -> 1+2^-22; -1-2^-24 -> -1 (even);
+    # 0.75+0
+    want = [0.0, 0.5, 0.0, 1.5 * 2.0 ** -23, 1.0, 1.0 + 2.0 ** -22, -1.0, 0.75]
+    n = len(vals_p)
+    pos = (ctypes.c_float * n)(*vals_p)
+    vel = (ctypes.c_float * n)(*vals_v)
+    root = CNode(n, 0, ctypes.addressof(pos), ctypes.addressof(vel), None)
+    keep += [pos, vel]
+    s = tg.node_schema()
+    oracle.update(s, ctypes.addressof(root), oracle.Op())
+    got = np.frombuffer(bytes(pos), dtype=np.float32)
+    assert list(got) == [np.float32(w) for w in want]
+    assert np.signbit(got[0]) == False and np.signbit(got[2]) == False  # RN: x + (-x) = +0
+    assert list(np.frombuffer(bytes(vel), dtype=np.float32)) == [np.float32(v) for v in vals_v]
+
+
+@pytest.mark.parametrize("levels,fanout,n", [(4, 1, 1000), (3, 5, 77), (2, 16, 257)])
+def test_update_all_is_single_rounding(levels, fanout, n):
+    t = tg.node_tree(levels, fanout, n, seed=levels * 31 + fanout)
+    s = t.schema
+    before = node_arrays(t.root)
+    cp = oracle.deep_copy(s, t.root)
+    oracle.update(s, cp.root, oracle.Op())
+    after = node_arrays(cp.root)
+    assert before.keys() == after.keys()
+    for path, (p, v) in before.items():
+        p2, v2 = after[path]
+        assert same_bits(p2, half_axpy_exact(p, v)), path
+        assert same_bits(v2, v)
+    t.free()
+
+
+def test_update_chain_touches_one_node():
+    t = tg.node_tree(3, 4, 33, seed=9)
+    s = t.schema
+    before = node_arrays(t.root)
+    cp = oracle.deep_copy(s, t.root)
+    path = [(4, 3), (4, 1)]
+    oracle.update(s, cp.root, oracle.Op(sel=oracle.SEL_CHAIN, path=path))
+    after = node_arrays(cp.root)
+    for p, (x, y) in before.items():
+        want = half_axpy_exact(x, y) if p == (3, 1) else x
+        assert same_bits(after[p][0], want), p
+    t.free()
+
+
+def test_scale_f64_is_correctly_rounded():
+    # The paper's scaling kernel (Sec. 4.1.2; Listing 2) on the Linear shape.
+    t = tg.linear_tree(3, 200, "allinit", seed=5)
+    s = t.schema
+    srcA = []
+    a = t.root
+    while a:
+        srcA.append(f64_view(u64(a + 8), 200).copy())
+        a = u64(a + 16)
+    cp = oracle.deep_copy(s, t.root)
+    oracle.update(s, cp.root, oracle.Op(kind=oracle.OP_SCALE, x_field=2, scale=1.5))
+    a = cp.root
+    for want_src in srcA:
+        got = f64_view(u64(a + 8), 200)
+        exact = [float(Fraction(float(x)) * Fraction(3, 2)) for x in want_src]
+        assert list(got) == exact
+        a = u64(a + 16)
+    t.free()
+
+
+def test_scale_listing2_chain_last_element():
+    # a0->Lnext[q-1].Lnext[q-1].Lnext[q-1].A[i] *= scale: only that A changes
+    q, n, D = 3, 17, 3
+    t = tg.dense_tree(q, n, D, seed=2)
+    s = t.schema
+    path = [(3, q - 1)] * D
+    target_src = oracle.host_resolve(s, t.root, path + [(1, 0)])
+    want = [float(Fraction(float(x)) * Fraction(5, 4)) for x in f64_view(target_src, n)]
+    cp = oracle.deep_copy(s, t.root)
+    op = oracle.Op(kind=oracle.OP_SCALE, sel=oracle.SEL_CHAIN, path=path, type=D, x_field=1, scale=1.25)
+    oracle.update(s, cp.root, op)
+    target = oracle.host_resolve(s, cp.root, path + [(1, 0)])
+    assert list(f64_view(target, n)) == want
+    # every other A is untouched: copy back only that array, then compare trees
+    t2 = tg.dense_tree(q, n, D, seed=2)
+    oracle.copy_back(s, cp.root, t2.root, op)
+    ok, msg = oracle.trees_equal(s, t2.root, cp.root)
+    assert ok, msg
+    ok, msg = oracle.trees_equal(s, t.root, t2.root)
+    assert not ok
+    t.free()
+    t2.free()
+
+
+# ---------------------------------------------------------------------------
+# copy back and the results check
+# ---------------------------------------------------------------------------
+
+def test_copy_back_writes_only_positions():
+    t = tg.node_tree(3, 3, 50, seed=12)
+    ref = tg.node_tree(3, 3, 50, seed=12)  # same seed: an untouched twin
+    s = t.schema
+    cp = oracle.deep_copy(s, t.root)
+    oracle.update(s, cp.root, oracle.Op())
+    oracle.copy_back(s, cp.root, t.root, oracle.Op())
+    a, r = node_arrays(t.root), node_arrays(ref.root)
+    for path in r:
+        assert same_bits(a[path][0], half_axpy_exact(*r[path]))
+        assert same_bits(a[path][1], r[path][1])
+    # scalars and padding untouched, host pointers untouched
+    for na, nr in zip(node_walk(t.root), node_walk(ref.root)):
+        assert na["raw"][:8] == nr["raw"][:8]
+    t.free()
+    ref.free()
+
+
+def test_trees_equal_detects_planted_differences():
+    s = tg.node_schema()
+    a = tg.node_tree(3, 3, 20, seed=7)
+    b = tg.node_tree(3, 3, 20, seed=7)
+    assert oracle.trees_equal(s, a.root, b.root)[0]
+    nodes = list(node_walk(b.root))
+    # one float in a leaf array
+    f32_view(nodes[5]["pos"], 20)[13] += np.float32(2.0 ** -20)
+    ok, msg = oracle.trees_equal(s, a.root, b.root)
+    assert not ok and "array differs" in msg
+    f32_view(nodes[5]["pos"], 20)[13] -= np.float32(2.0 ** -20)
+    assert oracle.trees_equal(s, a.root, b.root)[0]
+    # a scalar: a child count one higher than the twin's
+    cnt = ctypes.c_int32.from_address(nodes[2]["addr"])
+    cnt.value -= 1
+    ok, msg = oracle.trees_equal(s, a.root, b.root)
+    assert not ok and "struct byte" in msg
+    cnt.value += 1
+    c = tg.node_tree(3, 3, 20, seed=8)
+    assert not oracle.trees_equal(s, a.root, c.root)[0]
+    for t in (a, b, c):
+        t.free()
+
+
+def _image_setup():
+    t = tg.node_tree(3, 3, 9, seed=21)
+    base = 0x7C0000000000
+    cp = oracle.deep_copy(t.schema, t.root, ptr_base=base)
+    return t, base, cp
+
+
+def test_check_image_accepts_a_correct_copy():
+    t, base, cp = _image_setup()
+    ok, msg, seen = oracle.check_image(t.schema, t.root, cp.image(), base)
+    assert ok, msg
+    c = oracle.count(t.schema, t.root)
+    for k in ("nstructs", "nblocks", "payload_bytes", "nptr"):
+        assert seen[k] == c[k]
+    t.free()
+
+
+def _plant(img, off, value):
+    img[off:off + 8] = np.frombuffer(int(value).to_bytes(8, "little"), dtype=np.uint8)
+
+
+@pytest.mark.parametrize("mistake", ["leaf_byte", "ptr_plus16", "ptr_to_source", "shared_block",
+                                     "outside", "misaligned", "scalar", "null_with_count",
+                                     "nonnull_count0"])
+def test_check_image_catches_planted_mistakes(mistake):
+    t, base, cp = _image_setup()
+    img = cp.image().copy()
+    s = t.schema
+    rel = lambda p: p - base  # noqa: E731
+    rp = int.from_bytes(img[8:16].tobytes(), "little")      # root.position
+    rv = int.from_bytes(img[16:24].tobytes(), "little")     # root.velocity
+    rc = int.from_bytes(img[24:32].tobytes(), "little")     # root.child
+    if mistake == "leaf_byte":
+        img[rel(rv) + 5] ^= 1
+    elif mistake == "ptr_plus16":
+        _plant(img, 8, rp + 16)
+    elif mistake == "ptr_to_source":
+        _plant(img, 8, u64(t.root + 8))
+    elif mistake == "shared_block":
+        _plant(img, 16, rp)  # velocity now points at position's block
+    elif mistake == "outside":
+        _plant(img, 8, base + len(img) + 64)
+    elif mistake == "misaligned":
+        _plant(img, rel(rc) + 8, int.from_bytes(img[rel(rc) + 8:rel(rc) + 16].tobytes(), "little") + 4)
+    elif mistake == "scalar":
+        img[rel(rc) + 32 + 4] ^= 1  # child[1].nchild
+    elif mistake == "null_with_count":
+        _plant(img, rel(rc) + 16, 0)
+    elif mistake == "nonnull_count0":
+        # a leaf's child pointer must stay NULL (its count is 0)
+        leaf = rel(int.from_bytes(img[rel(rc) + 24:rel(rc) + 32].tobytes(), "little"))
+        _plant(img, leaf + 24, base)
+    ok, msg, _ = oracle.check_image(s, t.root, img, base)
+    assert not ok, mistake
+    t.free()
+
+
+def test_random_schemas_copy_and_image_agree():
+    rng = random.Random(1234)
+    for i in range(150):
+        schema, levels, rules = tg.random_schema(rng)
+        t = tg.Tree(schema, levels, rules, seed=i)
+        c = oracle.count(schema, t.root)
+        assert c["payload_bytes"] == t.payload_bytes and c["nblocks"] == t.nblocks
+        cp = oracle.deep_copy(schema, t.root)
+        ok, msg = oracle.trees_equal(schema, t.root, cp.root)
+        assert ok, msg
+        base = 0x7D0000000000
+        img = oracle.deep_copy(schema, t.root, ptr_base=base)
+        ok, msg, seen = oracle.check_image(schema, t.root, img.image(), base)
+        assert ok, msg
+        assert seen["nblocks"] == c["nblocks"]
+        t.free()
+
+
+def test_generator_is_deterministic():
+    s = tg.node_schema()
+    a = tg.workload("tiny")
+    b = tg.workload("tiny")
+    c = tg.workload("tiny", seed=99)
+    assert oracle.trees_equal(s, a.root, b.root)[0]
+    assert not oracle.trees_equal(s, a.root, c.root)[0]
+    # values are multiples of 2^-23 in [-1, 1)
+    v = node_arrays(a.root)[()][0]
+    assert v.min() >= -1.0 and v.max() < 1.0
+    assert np.all(np.ldexp(v.astype(np.float64), 23) == np.round(np.ldexp(v.astype(np.float64), 23)))
+    for t in (a, b, c):
+        t.free()
