@@ -1,0 +1,362 @@
+"""Benchmark of the deep-copy hot path on the dense workload (3 levels, fanout
+16, 273 nodes, lognormal fp32 arrays, ~338 MB), printing one JSON line.
+
+  value  device-resident step: the arena is already in HBM; one step relocates
+         every pointer (dc_relocate) and runs the leaf update through resolved
+         chains (dc_update_leaves).  GB/s = payload bytes / step time, CUDA
+         events on the launching stream, L2 flushed (512 MiB write) before each
+         step.
+  e2e    the same metric through the C ABI with host buffers: dc_deep_copy
+         (marshal + H2D + relocation), dc_update_leaves, dc_copy_back (D2H +
+         scatter into the host arrays), host clock around synchronized steps.
+  roofline  the leaf kernel: algorithmic bytes (12 B per element: read x and y,
+         write x) / its CUDA-event time, against the measured HBM copy peak.
+
+``--impl reference`` times the CPU oracle (plain recursive deep copy + update +
+copy back, one core) on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "deep-copy GB/s vs link peak; leaf kernel HBM %; batched/served speedup, p50/p99"
+WORKLOAD = "dense"
+WORKLOAD_DESC = ("dense tree: 3 levels, fanout 16 (273 nodes), node {int32 n; int32 nchild; float* position; "
+                 "float* velocity; Node* child}, array lengths lognormal(median 65,536, sigma 1.2, cap 4,194,304), "
+                 "fp32 values uniform in [-1,1), seed 2")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        dev = int(os.environ.get("LOCAL_RANK", "0"))
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                if int(c[0]) != dev:
+                    continue
+                sm.append(float(c[1]))
+                mx.append(float(c[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, c[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_cores_used():
+    return 1
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle as it stands: deep copy + update + copy back, one core."""
+    import oracle
+    import treegen as tg
+    if rank != 0:
+        return
+    t = tg.workload(WORKLOAD)
+    s = t.schema
+    payload = t.payload_bytes
+    op = oracle.Op()
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        cp = oracle.deep_copy(s, t.root)
+        oracle.update(s, cp.root, op)
+        oracle.copy_back(s, cp.root, t.root, op)
+        dt = time.perf_counter() - t0
+        del cp
+        if i >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    v = payload * len(times) / total / 1e9
+    sample = (f"{len(times)} full passes (deep copy into a fresh host arena, update every node, copy back) "
+              f"over the whole {payload / 1e6:.1f} MB workload, single thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / len(times), 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "payload_bytes": payload},
+        "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def oracle_baseline(tree, budget_s=10.0):
+    import oracle
+    s = tree.schema
+    op = oracle.Op()
+    n, t_total = 0, 0.0
+    while n < 3 or (t_total < budget_s and n < 200):
+        t0 = time.perf_counter()
+        cp = oracle.deep_copy(s, tree.root)
+        oracle.update(s, cp.root, op)
+        oracle.copy_back(s, cp.root, tree.root, op)
+        t_total += time.perf_counter() - t0
+        del cp
+        n += 1
+    v = tree.payload_bytes * n / t_total / 1e9
+    return {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} full passes (deep copy + update + copy back) over the whole workload "
+                      f"({tree.payload_bytes / 1e6:.1f} MB), {t_total:.1f} s on one host core"}
+
+
+def link_peaks(torch, nbytes=256 << 20, reps=5):
+    h = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    d = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    out = {}
+    for name, (dst, src) in {"h2d": (d, h), "d2h": (h, d)}.items():
+        best = 0.0
+        for _ in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            dst.copy_(src, non_blocking=True)
+            e1.record()
+            e1.synchronize()
+            best = max(best, nbytes / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+        out[name + "_gbs"] = round(best, 2)
+    del h, d
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the chase / UVM comparison paths")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "native" else args.warmup
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    import treegen as tg
+    import paper_1906_01128_b300 as dc
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    # each rank deep-copies its own independent tree (weak scaling, no data-path collective)
+    tree = tg.node_tree(*tg.WORKLOADS[WORKLOAD][:4], seed=tg.WORKLOADS[WORKLOAD][4] + rank)
+    s = tree.schema
+    payload = tree.payload_bytes
+    nelem = tree.nelems("Node", "position")
+    stream = torch.cuda.current_stream()
+    plan = dc.Plan(s, tree.root)
+    plan.bind()
+    info = plan.info
+    op = dc.Op()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    plan.deep_copy()
+    plan.sync()
+
+    # ---- device-resident step: relocation + leaf update --------------------
+    for _ in range(args.warmup):
+        flush.zero_()
+        plan.relocate()
+        plan.update(op)
+    barrier()
+    clocks = Clocks()
+    clocks.start()
+    launches0 = dc.kernel_launches()
+    ev = []
+    for _ in range(args.steps):
+        flush.zero_()  # L2 flush, outside the events; gives the host time to queue the step
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        plan.relocate()
+        e[1].record()
+        plan.update(op)
+        e[2].record()
+        ev.append(e)
+    barrier()
+    launches = dc.kernel_launches() - launches0
+    clk = clocks.stop()
+    plan.sync()
+    t_reloc = [a.elapsed_time(b) * 1e-3 for a, b, c in ev]
+    t_leaf = [b.elapsed_time(c) * 1e-3 for a, b, c in ev]
+    t_step = max_over_ranks(sum(x + y for x, y in zip(t_reloc, t_leaf)))
+    value = payload * world * args.steps / t_step / 1e9
+
+    hbm, peak_kind = peaks()
+    leaf_bytes = 12 * nelem
+    leaf_avg = statistics.mean(t_leaf)
+    reloc_avg = statistics.mean(t_reloc)
+    reloc_bytes = info["nblocks"] * (16 + 8) + info["nstruct_blocks"] * 8
+    roofline = {"bound": "hbm", "kernel": "leaf_kernel<float, AXPY_HALF>",
+                "achieved": round(leaf_bytes / leaf_avg / 1e9, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(leaf_bytes / leaf_avg / 1e9 / hbm, 4), "traffic": None,
+                "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
+                "algorithmic_bytes_per_launch": leaf_bytes, "avg_launch_us": round(leaf_avg * 1e6, 2)}
+
+    # ---- end to end through the C ABI with host buffers ----------------------
+    t_e2e, t_dc, t_cb = [], [], []
+    for i in range(args.warmup + max(3, args.steps // 2)):
+        barrier()
+        t0 = time.perf_counter()
+        plan.deep_copy()
+        t1 = time.perf_counter()
+        plan.update(op)
+        plan.copy_back()
+        t2 = time.perf_counter()
+        if i >= args.warmup:
+            t_e2e.append(t2 - t0)
+    # deep copy alone (marshal + H2D + relocation) against the link
+    for i in range(args.warmup + 5):
+        barrier()
+        t0 = time.perf_counter()
+        plan.deep_copy()
+        plan.sync()
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            t_dc.append(t1 - t0)
+    for i in range(args.warmup + 5):
+        barrier()
+        t0 = time.perf_counter()
+        plan.copy_back()
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            t_cb.append(t1 - t0)
+    e2e_t = max_over_ranks(statistics.mean(t_e2e))
+    e2e = {"value": round(payload * world / e2e_t / 1e9, 3), "unit": "GB/s",
+           "h2d_bytes_per_step": info["data_bytes"], "d2h_bytes_per_step": 4 * nelem,
+           "ms_per_step": round(e2e_t * 1e3, 3)}
+    link = link_peaks(torch)
+    dc_med = statistics.median(t_dc)
+    link["deep_copy_gbs"] = round(info["data_bytes"] / dc_med / 1e9, 2)
+    link["deep_copy_frac_of_h2d_peak"] = round(info["data_bytes"] / dc_med / 1e9 / link["h2d_gbs"], 4)
+    link["copy_back_gbs"] = round(4 * nelem / statistics.median(t_cb) / 1e9, 2)
+    link["copy_back_frac_of_d2h_peak"] = round(4 * nelem / statistics.median(t_cb) / 1e9 / link["d2h_gbs"], 4)
+
+    # ---- comparison paths (same GPU) -----------------------------------------
+    compare = None
+    if not args.no_compare and rank == 0:
+        compare = {}
+        t = []
+        for i in range(5):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            plan.update_chase(op)
+            e1.record()
+            e1.synchronize()
+            if i:
+                t.append(e0.elapsed_time(e1))
+        compare["chase_kernel_us"] = round(1e3 * statistics.mean(t), 2)
+        compare["resolved_leaf_kernel_us"] = round(leaf_avg * 1e6, 2)
+        u = dc.Uvm(s, tree.root)
+        first, pref = [], []
+        for i in range(3):
+            u.prefetch(False)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            u.update(op)
+            e1.record()
+            e1.synchronize()
+            first.append(e0.elapsed_time(e1))
+            u.prefetch(True)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            u.update(op)
+            e1.record()
+            e1.synchronize()
+            pref.append(e0.elapsed_time(e1))
+        compare["uvm_first_touch_kernel_ms"] = round(statistics.median(first), 3)
+        compare["uvm_prefetched_kernel_ms"] = round(statistics.median(pref), 3)
+        u.destroy()
+
+    cpu = None if (args.no_cpu or rank != 0) else oracle_baseline(tree)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * t_step / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "nodes": info["nstructs"], "blocks": info["nblocks"],
+                       "payload_bytes": payload, "arena_bytes": info["data_bytes"], "elements": nelem,
+                       "step": "dc_relocate + dc_update_leaves on the resident arena",
+                       "l2": "flushed: 512 MiB write before every timed step (outside the events)",
+                       "parallelism": f"{world} independent tree(s), one per GPU"},
+            "roofline": roofline,
+            "relocation": {"avg_launch_us": round(reloc_avg * 1e6, 2), "algorithmic_bytes": reloc_bytes,
+                           "achieved_gbs": round(reloc_bytes / reloc_avg / 1e9, 1)},
+            "e2e": e2e, "link": link, "compare": compare, "cpu_baseline": cpu, "clocks": clk,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(out))
+    plan.destroy()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

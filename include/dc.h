@@ -1,0 +1,256 @@
+/*
+ * dc.h — C ABI of the B300 deep-copy library (libdc.so).
+ *
+ * Moves a nested, pointer-linked host structure into one device arena,
+ * rebuilds every pointer so it is valid on the device, resolves pointer
+ * chains to effective device addresses, runs the leaf-array kernel through
+ * those addresses and copies the results back.  The operations follow the
+ * paper's statement of the problem: the four deep-copy steps of Fig 2 (Sec. 2),
+ * the marshalling of Algorithm 1 (Sec. 4.1.1 item 2), effective-address
+ * extraction of a pointer chain (Sec. 3), the scaling kernels of Sec. 4.1.2 and
+ * Listing 2, and the main-program flow of Algorithm 2.
+ *
+ * Conventions for every call
+ *   - Returns a dc_status and never aborts; dc_last_error() gives a message
+ *     (thread-local, valid until the next call on the same thread).
+ *   - Pointers are plain host or device addresses; sizes are bytes unless the
+ *     name says otherwise.  A dc_stream_t is a cudaStream_t (NULL = the legacy
+ *     default stream).  Calls on one plan must be ordered on one stream (or
+ *     the caller must order the streams); a plan is not thread-safe.
+ *   - Device work is asynchronous and stream-ordered.  Errors a kernel finds
+ *     (an index outside its buffers, a device-side wait that gave up, a
+ *     failed relocation check) are recorded in a device word and reported by
+ *     the next dc_sync() (or dc_copy_back()) on that plan.
+ *   - Ownership: the caller owns the host tree and must not change its shape
+ *     (pointers, counts) between dc_plan and the last call on the plan, nor
+ *     its array contents while dc_deep_copy runs.  The caller owns the device
+ *     buffer given to dc_bind_device (e.g. a torch uint8 tensor).  The library
+ *     owns the plan's tables, its pinned staging arena and managed trees;
+ *     dc_plan_destroy / dc_uvm_destroy free them.
+ */
+#ifndef DC_H
+#define DC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* dc_stream_t;
+
+typedef enum {
+  DC_OK = 0,
+  DC_EINVAL = 1,         /* bad argument, schema, path or structure */
+  DC_ENOMEM = 2,         /* host or pinned allocation failed */
+  DC_ECUDA = 3,          /* a CUDA runtime call failed (message has the CUDA error) */
+  DC_EALIAS = 4,         /* a block is reachable twice or overlaps another: not a tree */
+  DC_ECYCLE = 5,         /* a pointer leads back into one of its ancestors */
+  DC_EBUDGET = 6,        /* the bound device buffer is smaller than the plan needs */
+  DC_ETIMEOUT = 7,       /* a device-side wait gave up after its iteration limit */
+  DC_EDEVICE_BOUNDS = 8, /* a kernel found an index or offset outside its buffers */
+  DC_ESTATE = 9,         /* call out of order (no device buffer bound, no op run, ...) */
+  DC_EVERIFY = 10        /* relocation check: a slot did not hold the expected host address */
+} dc_status;
+
+/* ---- schema: C struct types described by field offsets -------------------- */
+
+typedef enum { DC_F_SCALAR = 0, DC_F_ARRAY = 1, DC_F_CHILD = 2 } dc_field_kind;
+typedef enum { DC_E_F32 = 0, DC_E_F64 = 1, DC_E_BYTES = 2 } dc_elem_kind;
+
+typedef struct {
+  int32_t kind;         /* dc_field_kind */
+  uint32_t offset;      /* byte offset of the member in its struct */
+  uint32_t elem_size;   /* SCALAR: 4 or 8 (signed integer); ARRAY: bytes per element */
+  int32_t count_field;  /* ARRAY/CHILD: index of the SCALAR field holding the
+                           element count, or -1 to use count_const */
+  uint64_t count_const; /* ARRAY/CHILD: element count when count_field == -1 */
+  int32_t child_type;   /* CHILD: index into dc_schema.types of the pointee type */
+  int32_t elem_kind;    /* ARRAY: dc_elem_kind; leaf ops need F32 or F64 */
+} dc_field;
+
+/* A struct type: `size` bytes (sizeof), alignment `align` (<= 16).  An ARRAY
+ * member is a pointer to `count` primitive elements; a CHILD member is a
+ * pointer to a contiguous array of `count` structs of child_type (count 1 for
+ * a plain struct pointer, as in Listing 1's simulation->atoms).  A pointer
+ * whose count is 0 may be anything; the copy holds NULL there.  Pointer
+ * members must sit at 8-byte aligned offsets. */
+typedef struct {
+  uint32_t size, align, nfields;
+  const dc_field* fields;
+} dc_type;
+
+typedef struct {
+  uint32_t ntypes, root_type;
+  const dc_type* types;
+} dc_schema;
+
+/* One arrow of a pointer chain: follow member `field` of the current struct
+ * and take element `index` of what it points to.  A CHILD step moves to that
+ * child struct; an ARRAY step selects an element and must be the last step. */
+typedef struct {
+  uint32_t field;
+  uint64_t index;
+} dc_step;
+
+typedef enum { DC_OP_AXPY_HALF = 0, DC_OP_SCALE = 1 } dc_op_kind;
+typedef enum { DC_SEL_ALL = 0, DC_SEL_CHAIN = 1 } dc_sel;
+
+/* A leaf-kernel request.
+ *   AXPY_HALF: x[i] = x[i] + 0.5*y[i], computed as __fadd_rn(x, __fmul_rn(0.5f, y))
+ *              for F32 arrays (one IEEE rounding per operation), likewise in F64.
+ *   SCALE:     x[i] = x[i] * scale (the paper's scaling kernel, Sec. 4.1.2 item 1
+ *              and Listing 2); scale is rounded to float for F32 arrays.
+ *   SEL_ALL:   every struct of `type` in the tree (the allinit-allused layout).
+ *   SEL_CHAIN: the one struct of `type` that `path` (CHILD steps only) reaches
+ *              from the root (the LLused layouts; Listing 2's chain).
+ * x_field / y_field are ARRAY fields of `type` with the same count and kind. */
+typedef struct {
+  int32_t kind;  /* dc_op_kind */
+  double scale;
+  int32_t sel;   /* dc_sel */
+  const dc_step* path;
+  uint32_t path_len;
+  uint32_t type;
+  uint32_t x_field, y_field;
+} dc_op;
+
+typedef struct dc_plan_s* dc_plan_t;
+typedef struct dc_uvm_s* dc_uvm_t;
+
+typedef struct {
+  uint64_t data_bytes;     /* arena data region: every block at a 16-byte aligned offset;
+                              the size of the H2D of dc_deep_copy */
+  uint64_t device_bytes;   /* bytes the buffer passed to dc_bind_device must hold:
+                              data region + block table + scratch */
+  uint64_t payload_bytes;  /* sum of block sizes without padding */
+  uint64_t nblocks;        /* root struct + non-empty arrays + non-empty child arrays */
+  uint64_t nrelocs;        /* pointer slots rewritten by the relocation (nblocks - 1) */
+  uint64_t nstructs;       /* struct instances in the tree */
+  uint64_t nstruct_blocks; /* blocks that hold structs (root + child arrays) */
+  uint64_t root_offset;    /* offset of the root struct in the data region (0) */
+} dc_plan_info;
+
+/* Plan flags (dc_plan_set_flags). */
+#define DC_PLAN_VERIFY 1u /* relocation also checks that every slot still holds the
+                             host address the plan recorded (DC_EVERIFY otherwise) */
+
+/* dc_plan — walk the host structure from `host_root` (one struct of
+ * schema->root_type) and lay out its device arena (Algorithm 1's first step,
+ * determineTotalBytes, and its allocation requests; Fig 2 step a).  Host only:
+ * touches no GPU.
+ * Layout: blocks are grouped in lanes — lane 0 holds every struct block (the
+ * root, then child arrays in depth-first order), then one lane per ARRAY field
+ * (in type, field order), each in depth-first order; every block starts on a
+ * 16-byte boundary.  Errors: DC_EINVAL (NULL pointer with a non-zero count,
+ * negative count, bad schema), DC_EALIAS / DC_ECYCLE (not a tree), DC_ENOMEM. */
+dc_status dc_plan(const dc_schema* schema, const void* host_root, dc_plan_t* out);
+dc_status dc_plan_set_flags(dc_plan_t plan, uint32_t flags);
+dc_status dc_plan_info_get(dc_plan_t plan, dc_plan_info* out);
+/* Block `i` in arena order: its host address, arena offset, byte size, lane,
+ * and its relocation entry — the struct block holding the pointer slot that
+ * refers to it (UINT32_MAX for the root) and that slot's byte offset inside
+ * it.  Any output pointer may be NULL. */
+dc_status dc_plan_block(dc_plan_t plan, uint64_t i, uint64_t* host_addr, uint64_t* offset,
+                        uint64_t* bytes, uint32_t* lane, uint32_t* parent, uint32_t* slot_off);
+/* Host threads used by marshal and copy-back scatter (0 = all online cores). */
+dc_status dc_plan_set_threads(dc_plan_t plan, uint32_t nthreads);
+dc_status dc_plan_destroy(dc_plan_t plan);
+
+/* dc_bind_device — give the plan a caller-owned device buffer of at least
+ * info.device_bytes bytes, 256-byte aligned (a torch CUDA uint8 tensor
+ * qualifies).  Uploads the block table and clears the scratch on `stream`
+ * (blocking), and allocates the plan's pinned staging arena on first use.
+ * Errors: DC_EBUDGET, DC_EINVAL (misaligned), DC_ENOMEM, DC_ECUDA. */
+dc_status dc_bind_device(dc_plan_t plan, void* dev_buffer, uint64_t bytes, dc_stream_t stream);
+
+/* dc_deep_copy — marshal every block into the pinned arena (Algorithm 1:
+ * one contiguous buffer), copy it to the device in one stream-ordered pass
+ * (Fig 2 steps b-c), then run the relocation kernel, which rebuilds every
+ * pointer slot to the device address of its target (Fig 2 step d; Algorithm
+ * 1's attach loop).  Returns once the marshal is done and the copies and the
+ * kernel are queued; the host tree may change afterwards.  Errors: DC_ESTATE
+ * (nothing bound), DC_ECUDA. */
+dc_status dc_deep_copy(dc_plan_t plan, dc_stream_t stream);
+
+/* dc_relocate — the relocation kernel of dc_deep_copy alone (Fig 2 step d):
+ * recompute every block's arena offset on the device and rewrite every pointer
+ * slot of the data region already in device memory.  For a data region that
+ * is already resident (filled by an earlier dc_deep_copy or by the caller);
+ * the result is the same whatever the slots held.  Errors: DC_ESTATE, DC_ECUDA. */
+dc_status dc_relocate(dc_plan_t plan, dc_stream_t stream);
+
+/* dc_resolve_chain — the effective device address of a pointer chain
+ * (Sec. 3: extract it once, before the compute region): the struct the CHILD
+ * steps reach, or &array[index] for a final ARRAY step.  Host only, O(path
+ * length), reads no device memory.  Errors: DC_EINVAL (bad field, index out
+ * of range, NULL link), DC_ESTATE (nothing bound).
+ * dc_resolve_offset gives the same place as an offset in the data region
+ * and needs no device buffer. */
+dc_status dc_resolve_chain(dc_plan_t plan, const dc_step* path, uint32_t len, uint64_t* dev_addr);
+dc_status dc_resolve_offset(dc_plan_t plan, const dc_step* path, uint32_t len, uint64_t* offset);
+
+/* dc_update_leaves — run the leaf kernel on the device copy through resolved
+ * addresses: the selected structs' chains are resolved on the host and the
+ * kernel streams over (x, y, n) segments with no pointer loads.  Errors:
+ * DC_EINVAL (op fields / path / counts), DC_ESTATE, DC_ECUDA. */
+dc_status dc_update_leaves(dc_plan_t plan, const dc_op* op, dc_stream_t stream);
+
+/* dc_update_chase — the same update, computed the way an unresolved chain
+ * is: every element walks root -> ... -> struct -> x/y with device loads the
+ * compiler may not hoist (Listing 2's loop body; Sec. 3).  Comparison path. */
+dc_status dc_update_chase(dc_plan_t plan, const dc_op* op, dc_stream_t stream);
+
+/* dc_verify_chain — walk `path` on the device with one thread, reading the
+ * relocated pointers, and return the address it reaches (blocking).  Lets a
+ * caller check dc_resolve_chain against the device image. */
+dc_status dc_verify_chain(dc_plan_t plan, const dc_step* path, uint32_t len, dc_stream_t stream,
+                          uint64_t* dev_addr);
+
+/* dc_copy_back — transfer back (Algorithm 2 step 5): the arrays the last
+ * dc_update_* wrote (the x arrays of the selected structs), or every ARRAY
+ * block with DC_COPY_ALL_ARRAYS, are copied device -> pinned arena -> the
+ * original host arrays.  Pointers, scalars and struct bytes on the host are
+ * never written.  Blocking: returns when the host arrays hold the results.
+ * Errors: DC_ESTATE (no op run and no flag), DC_ECUDA, plus any device error
+ * recorded by earlier kernels. */
+#define DC_COPY_ALL_ARRAYS 1u
+dc_status dc_copy_back(dc_plan_t plan, uint32_t flags, dc_stream_t stream);
+
+/* dc_sync — wait for the plan's work on `stream` and report (then clear) the
+ * device error word: DC_EDEVICE_BOUNDS, DC_ETIMEOUT or DC_EVERIFY. */
+dc_status dc_sync(dc_plan_t plan, dc_stream_t stream);
+
+/* Device address of the bound buffer's data region (for callers that want
+ * to read the device image, e.g. to check it). */
+dc_status dc_device_base(dc_plan_t plan, uint64_t* dev_base);
+
+/* ---- comparison path: Unified Virtual Memory (Sec. 2; Sec. 4.1.1 item 1) ----
+ * dc_uvm_build replicates the host tree into managed memory, one
+ * cudaMallocManaged allocation per block (as if every malloc of the
+ * application were managed); its pointers are valid on host and device with
+ * no relocation.  dc_uvm_update runs the pointer-chasing leaf kernel on it, so
+ * pages migrate on demand; dc_uvm_prefetch moves every block to the device
+ * (to_device = 1) or back to the host (0) first.  dc_uvm_copy_back copies
+ * the written arrays (all arrays with DC_COPY_ALL_ARRAYS) into the original
+ * host tree: the host reads managed memory.  dc_uvm_root gives the managed
+ * root's address. */
+dc_status dc_uvm_build(const dc_schema* schema, const void* host_root, dc_uvm_t* out);
+dc_status dc_uvm_root(dc_uvm_t uvm, uint64_t* managed_root);
+dc_status dc_uvm_prefetch(dc_uvm_t uvm, int to_device, dc_stream_t stream);
+dc_status dc_uvm_update(dc_uvm_t uvm, const dc_op* op, dc_stream_t stream);
+dc_status dc_uvm_copy_back(dc_uvm_t uvm, const void* host_root, uint32_t flags);
+dc_status dc_uvm_sync(dc_uvm_t uvm, dc_stream_t stream);
+dc_status dc_uvm_destroy(dc_uvm_t uvm);
+
+/* ---- misc ------------------------------------------------------------------ */
+const char* dc_last_error(void);
+const char* dc_status_name(dc_status s);
+/* Number of kernels this library has launched in this process (all paths). */
+uint64_t dc_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DC_H */

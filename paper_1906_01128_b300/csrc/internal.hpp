@@ -1,0 +1,226 @@
+// internal.hpp — plan tables, device-buffer layout and kernel entry points
+// shared by the host runtime (runtime.cpp, plan.cpp) and the kernels
+// (kernels.cu).  Not part of the public ABI (include/dc.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/dc.h"
+#include "pool.hpp"
+
+namespace dc {
+
+constexpr uint32_t NONE = 0xFFFFFFFFu;
+
+inline uint64_t round_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+// ---- error reporting ---------------------------------------------------------
+dc_status fail(dc_status s, const char* fmt, ...);
+dc_status cuda_fail(cudaError_t e, const char* what);
+const char* last_error();
+#define DC_CUDA(call)                                        \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return dc::cuda_fail(e_, #call);  \
+  } while (0)
+
+// ---- device-side records -----------------------------------------------------
+
+// One block of the arena, in arena order; 16 bytes so the relocation kernel
+// reads it with one vector load.
+struct BlockRec {
+  uint32_t size16;   // block bytes rounded up to 16, in units of 16 bytes
+  uint32_t parent;   // arena index of the struct block holding the pointer slot; NONE = root
+  uint32_t slot_off; // byte offset of that pointer slot inside the parent block
+  uint32_t lane;     // 0 = struct lane, else 1 + ARRAY-field lane index
+};
+static_assert(sizeof(BlockRec) == 16, "BlockRec is one 16-byte vector");
+
+// A resolved leaf segment for the streaming kernel: effective addresses of
+// x and y, the element count, and the exclusive prefix of 16-byte units
+// (ceil(n * elem_size / 16)) over the table.
+struct Segment {
+  uint64_t x, y, n, ubeg;
+};
+static_assert(sizeof(Segment) == 32, "Segment is 32 bytes");
+
+// An unresolved chain for the pointer-chasing kernel: start at `root` and
+// follow steps[step_first .. step_first + nsteps); ebeg is the exclusive
+// prefix of elements over the table.
+struct ChaseSeg {
+  uint64_t root;
+  uint32_t step_first, nsteps;
+  uint64_t n, ebeg;
+};
+static_assert(sizeof(ChaseSeg) == 32, "ChaseSeg is 32 bytes");
+
+struct ChaseStep {
+  uint32_t field_off;   // byte offset of the CHILD pointer in the current struct
+  uint32_t child_size;  // sizeof the child struct
+  uint64_t index;       // element of the child array
+};
+static_assert(sizeof(ChaseStep) == 16, "ChaseStep is 16 bytes");
+
+// Control words in device scratch.
+enum CtrlWord : uint32_t { CTRL_TILE = 0, CTRL_DONE = 1, CTRL_ERR = 2, CTRL_WORDS = 16 };
+enum DeviceErr : uint32_t { ERR_BOUNDS = 1u, ERR_TIMEOUT = 2u, ERR_VERIFY = 4u };
+
+constexpr uint32_t RELOC_THREADS = 256;
+constexpr uint32_t RELOC_ITEMS = 4;  // blocks per thread
+constexpr uint32_t RELOC_TILE = RELOC_THREADS * RELOC_ITEMS;
+constexpr uint32_t EPOCH_LIMIT = (1u << 22) - 1;
+
+// ---- kernels (kernels.cu) ------------------------------------------------------
+
+struct RelocArgs {
+  uint8_t* arena;
+  uint64_t data_bytes;
+  const BlockRec* rec;
+  const uint64_t* hostp;
+  uint64_t* soff;                  // byte offsets of struct blocks
+  unsigned long long* status;      // look-back words, one per tile
+  uint32_t* ready;                 // per tile: epoch once its struct offsets are stored
+  uint32_t* ctrl;
+  uint32_t nblocks, nstruct_blocks, ntiles, epoch, verify;
+};
+
+struct LeafArgs {
+  const Segment* seg;
+  uint32_t nseg;
+  uint64_t units;  // total 16-byte units
+  int kind;        // dc_op_kind
+  int f64;         // element type: 0 f32, 1 f64
+  double scale;
+};
+
+struct ChaseArgs {
+  const ChaseSeg* seg;
+  const ChaseStep* steps;
+  uint32_t nseg;
+  uint64_t elems;
+  uint32_t x_off, y_off;
+  int kind, f64;
+  double scale;
+};
+
+cudaError_t launch_relocate(const RelocArgs& a, cudaStream_t s, int sm_count);
+cudaError_t launch_leaf(const LeafArgs& a, cudaStream_t s, int sm_count);
+cudaError_t launch_chase(const ChaseArgs& a, cudaStream_t s, int sm_count);
+cudaError_t launch_walk(uint64_t root, const ChaseStep* steps, uint32_t nsteps, uint64_t final_add,
+                        uint64_t* out, cudaStream_t s);
+void count_launch();
+
+// ---- host plan -----------------------------------------------------------------
+
+struct HostBlock {
+  const uint8_t* host;
+  uint64_t bytes;
+  uint64_t count;     // elements (structs or array elements)
+  uint64_t off;       // arena offset
+  uint64_t ptr_first; // struct blocks: first index into Plan::ptr_target
+  uint32_t lane;
+  uint32_t type;      // struct blocks: struct type; arrays: owning struct type
+  uint32_t field;     // arrays: field index in `type`; struct blocks: NONE
+  uint32_t parent;    // arena index of the struct block with the slot; NONE = root
+  uint32_t slot_off;  // byte offset of the slot in the parent block
+  uint32_t depth;     // struct blocks: tree level of their structs
+};
+
+struct SchemaCopy {
+  std::vector<dc_type> types;
+  std::vector<std::vector<dc_field>> fields;
+  std::vector<std::vector<int32_t>> ptr_index;  // [type][field] -> pointer-field index or -1
+  std::vector<uint32_t> nptr;                   // [type] -> number of pointer fields
+  std::vector<std::vector<uint32_t>> lane_of;   // [type][field] -> lane (ARRAY fields)
+  uint32_t nlanes = 1;
+  uint32_t root_type = 0;
+};
+
+dc_status copy_schema(const dc_schema* s, SchemaCopy* out);
+
+// Layout of the caller's device buffer (byte offsets).
+struct DevLayout {
+  uint64_t data = 0, rec = 0, hostp = 0, soff = 0, status = 0, ready = 0, ctrl = 0;
+  uint64_t seg = 0, cseg = 0, steps = 0, walk = 0, total = 0;
+  uint64_t seg_cap = 0, step_cap = 0, walk_cap = 0, ntiles = 0;
+};
+
+struct OpKey {
+  int32_t kind = -1, sel = -1;
+  uint32_t type = 0, x = 0, y = 0;
+  std::vector<dc_step> path;
+  bool operator==(const OpKey& o) const;
+};
+
+}  // namespace dc
+
+struct dc_plan_s {
+  dc::SchemaCopy schema;
+  std::vector<dc::HostBlock> blocks;     // arena order
+  std::vector<uint32_t> ptr_target;      // per struct element, per pointer field: block or NONE
+  std::vector<dc::BlockRec> rec;
+  std::vector<uint64_t> hostp;
+  std::vector<uint64_t> null_slots;      // arena offsets of slots with count 0 but a non-NULL host value
+  uint64_t nstructs = 0, nstruct_blocks = 0, payload = 0, data_bytes = 0, sum_depth = 0;
+  uint32_t max_depth = 0;
+  uint32_t flags = 0;
+  uint32_t nthreads = 0;
+
+  // runtime state
+  uint8_t* dev = nullptr;
+  uint64_t dev_bytes = 0;
+  dc::DevLayout L;
+  uint8_t* pinned = nullptr;      // data-region staging arena (cudaHostAlloc)
+  uint8_t* pin_tab = nullptr;     // segment / chase table staging (cudaHostAlloc)
+  uint64_t pin_tab_bytes = 0;
+  cudaEvent_t h2d_done = nullptr; // last deep copy's transfers
+  cudaEvent_t tab_done = nullptr; // last table upload
+  uint32_t epoch = 0;
+  int sm_count = 0;
+  int device = -1;
+  dc::OpKey leaf_key, chase_key;  // ops whose tables are on the device
+  uint64_t leaf_nseg = 0, leaf_units = 0, chase_nseg = 0, chase_elems = 0;
+  std::vector<uint32_t> written;  // arrays written by the last update (arena indices)
+  std::vector<uint32_t> leaf_written, chase_written;
+  bool op_run = false;
+  std::unique_ptr<dc::Pool> pool;
+  // marshal work: pieces of blocks, grouped into transfer chunks of the data region
+  struct Piece { uint64_t off, len; const uint8_t* src; };
+  struct Chunk { uint64_t lo, hi, first, last; };
+  std::vector<Piece> pieces;
+  std::vector<Chunk> chunks;
+};
+
+struct dc_uvm_s {
+  dc_plan_s* plan = nullptr;         // host tables of the tree (no device buffer)
+  std::vector<void*> managed;        // per block (arena order)
+  uint64_t root = 0;
+  dc::ChaseSeg* dseg = nullptr;      // device tables for the chase kernel
+  dc::ChaseStep* dsteps = nullptr;
+  uint64_t seg_cap = 0, step_cap = 0;
+  std::vector<uint32_t> written;
+  dc::OpKey key;
+  uint64_t nseg = 0, elems = 0;
+  int sm_count = 0;
+  int device = -1;
+};
+
+namespace dc {
+dc_status build_plan(const dc_schema* schema, const void* host_root, dc_plan_s* p);
+// Resolve a chain over the plan tables to (block, byte offset in block, type
+// of the struct reached or NONE when the last step was an ARRAY step, element).
+dc_status resolve(const dc_plan_s* p, const dc_step* path, uint32_t len, uint32_t* block,
+                  uint64_t* within, uint32_t* type, uint64_t* elem);
+// The structs an op selects: (struct block, element) pairs.
+dc_status select_structs(const dc_plan_s* p, const dc_op* op,
+                         std::vector<std::pair<uint32_t, uint64_t>>* out);
+dc_status check_op(const dc_plan_s* p, const dc_op* op);
+// The chain of (field, index) steps from the root to struct (block, elem).
+void path_to(const dc_plan_s* p, uint32_t block, uint64_t elem, std::vector<dc_step>* out);
+}  // namespace dc

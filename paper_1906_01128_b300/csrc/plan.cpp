@@ -1,0 +1,434 @@
+// plan.cpp — the host walk of a pointer-linked structure (dc_plan).
+//
+// Algorithm 1's first step (determineTotalBytes) and its allocation requests:
+// one iterative depth-first walk over the field-offset schema records every
+// block (the root struct, each non-empty array, each non-empty child-struct
+// array) with the pointer slot that refers to it.  The blocks are then laid out
+// in lanes (all struct blocks first, then one lane per ARRAY field), each block
+// on a 16-byte boundary, which fixes the arena and the relocation table.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <unordered_map>
+
+#include "internal.hpp"
+
+namespace dc {
+
+static thread_local char g_err[1024];
+
+dc_status fail(dc_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+dc_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(DC_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+const char* last_error() { return g_err; }
+
+bool OpKey::operator==(const OpKey& o) const {
+  if (kind != o.kind || sel != o.sel || type != o.type || x != o.x || y != o.y ||
+      path.size() != o.path.size())
+    return false;
+  for (size_t i = 0; i < path.size(); i++)
+    if (path[i].field != o.path[i].field || path[i].index != o.path[i].index) return false;
+  return true;
+}
+
+dc_status copy_schema(const dc_schema* s, SchemaCopy* out) {
+  if (!s || !s->types || s->ntypes == 0 || s->root_type >= s->ntypes)
+    return fail(DC_EINVAL, "schema: missing types or bad root type");
+  out->types.assign(s->types, s->types + s->ntypes);
+  out->fields.resize(s->ntypes);
+  out->ptr_index.resize(s->ntypes);
+  out->nptr.assign(s->ntypes, 0);
+  out->lane_of.resize(s->ntypes);
+  out->root_type = s->root_type;
+  uint32_t lane = 1;
+  for (uint32_t t = 0; t < s->ntypes; t++) {
+    const dc_type& T = s->types[t];
+    if (T.size == 0 || (T.nfields && !T.fields)) return fail(DC_EINVAL, "type %u: empty", t);
+    if (T.align == 0 || T.align > 16 || (T.align & (T.align - 1)))
+      return fail(DC_EINVAL, "type %u: alignment %u is not a power of two <= 16", t, T.align);
+    out->fields[t].assign(T.fields, T.fields + T.nfields);
+    out->types[t].fields = out->fields[t].data();
+    out->ptr_index[t].assign(T.nfields, -1);
+    out->lane_of[t].assign(T.nfields, 0);
+    bool has_ptr = false;
+    for (uint32_t f = 0; f < T.nfields; f++) {
+      const dc_field& F = T.fields[f];
+      if (F.kind == DC_F_SCALAR) {
+        if (F.elem_size != 4 && F.elem_size != 8)
+          return fail(DC_EINVAL, "type %u field %u: scalar size must be 4 or 8", t, f);
+        if ((uint64_t)F.offset + F.elem_size > T.size)
+          return fail(DC_EINVAL, "type %u field %u: outside the struct", t, f);
+        continue;
+      }
+      if (F.kind != DC_F_ARRAY && F.kind != DC_F_CHILD)
+        return fail(DC_EINVAL, "type %u field %u: unknown kind %d", t, f, F.kind);
+      // the relocation writes 8-byte pointer slots: they must be naturally aligned
+      if (F.offset % 8 || (uint64_t)F.offset + 8 > T.size)
+        return fail(DC_EINVAL, "type %u field %u: pointer slot not 8-byte aligned inside the struct",
+                    t, f);
+      if (F.count_field >= 0) {
+        if ((uint32_t)F.count_field >= T.nfields || T.fields[F.count_field].kind != DC_F_SCALAR)
+          return fail(DC_EINVAL, "type %u field %u: count field is not a scalar", t, f);
+      }
+      if (F.kind == DC_F_ARRAY) {
+        if (F.elem_size == 0) return fail(DC_EINVAL, "type %u field %u: zero element size", t, f);
+        out->lane_of[t][f] = lane++;
+      } else if (F.child_type < 0 || (uint32_t)F.child_type >= s->ntypes) {
+        return fail(DC_EINVAL, "type %u field %u: bad child type", t, f);
+      }
+      out->ptr_index[t][f] = (int32_t)out->nptr[t]++;
+      has_ptr = true;
+    }
+    if (has_ptr && T.size % 8)
+      return fail(DC_EINVAL, "type %u: size %u must be a multiple of 8 (it holds pointers)", t, T.size);
+  }
+  out->nlanes = lane;
+  return DC_OK;
+}
+
+static bool read_count(const dc_type& T, const uint8_t* s, const dc_field& F, uint64_t* n) {
+  if (F.count_field < 0) {
+    *n = F.count_const;
+    return true;
+  }
+  const dc_field& C = T.fields[F.count_field];
+  int64_t v;
+  if (C.elem_size == 8) {
+    memcpy(&v, s + C.offset, 8);
+  } else {
+    int32_t w;
+    memcpy(&w, s + C.offset, 4);
+    v = w;
+  }
+  if (v < 0) return false;
+  *n = (uint64_t)v;
+  return true;
+}
+
+namespace {
+
+struct Frame {
+  uint32_t blk;    // emission index of the struct block
+  uint64_t elem;   // element of that block
+  uint32_t type;
+  uint32_t field;  // next field to descend into
+  uint64_t k;      // next element of that field's child array
+};
+
+struct Walker {
+  dc_plan_s* p;
+  const SchemaCopy& S;
+  std::vector<HostBlock> emitted;
+  std::unordered_map<uint64_t, uint32_t> starts;              // host start -> emission index
+  std::map<uint64_t, std::pair<uint64_t, uint32_t>> structs;  // struct ranges: start -> (end, id)
+  std::vector<std::pair<uint32_t, uint64_t>> null_slots;      // (emission index, slot offset)
+
+  explicit Walker(dc_plan_s* pl) : p(pl), S(pl->schema) {}
+
+  bool is_ancestor(uint32_t maybe, uint32_t blk) const {
+    for (uint32_t b = blk; b != NONE; b = emitted[b].parent)
+      if (b == maybe) return true;
+    return false;
+  }
+
+  dc_status emit(const uint8_t* host, uint64_t bytes, uint64_t count, uint32_t lane, uint32_t type,
+                 uint32_t field, uint32_t parent, uint64_t slot_off, uint32_t depth, uint32_t* id) {
+    if (emitted.size() >= (size_t)NONE - 1) return fail(DC_EINVAL, "too many blocks");
+    if (slot_off > 0xFFFFFFFFull) return fail(DC_EINVAL, "child array too large for a 32-bit slot offset");
+    if (round_up(bytes, 16) / 16 > 0xFFFFFFFFull) return fail(DC_EINVAL, "block larger than 64 GiB");
+    uint64_t a = (uint64_t)(uintptr_t)host;
+    auto hit = starts.find(a);
+    if (hit != starts.end()) {
+      if (field == NONE && is_ancestor(hit->second, parent))
+        return fail(DC_ECYCLE, "a pointer leads back to an ancestor struct block (host 0x%llx)",
+                    (unsigned long long)a);
+      return fail(DC_EALIAS, "host block 0x%llx is reached through two pointers", (unsigned long long)a);
+    }
+    if (field == NONE) {  // a struct block: it must not overlap another struct block
+      auto it = structs.upper_bound(a);
+      uint32_t other = NONE;
+      if (it != structs.end() && it->first < a + bytes) other = it->second.second;
+      if (it != structs.begin()) {
+        auto pv = std::prev(it);
+        if (pv->second.first > a) other = pv->second.second;
+      }
+      if (other != NONE) {
+        if (parent != NONE && is_ancestor(other, parent))
+          return fail(DC_ECYCLE, "a child array overlaps an ancestor struct block");
+        return fail(DC_EALIAS, "struct block at 0x%llx overlaps another", (unsigned long long)a);
+      }
+      structs.emplace(a, std::make_pair(a + bytes, (uint32_t)emitted.size()));
+    }
+    starts.emplace(a, (uint32_t)emitted.size());
+    HostBlock b{};
+    b.host = host;
+    b.bytes = bytes;
+    b.count = count;
+    b.lane = lane;
+    b.type = type;
+    b.field = field;
+    b.parent = parent;
+    b.slot_off = (uint32_t)slot_off;
+    b.depth = depth;
+    b.ptr_first = 0;
+    if (field == NONE) {
+      b.ptr_first = p->ptr_target.size();
+      p->ptr_target.resize(p->ptr_target.size() + count * S.nptr[type], NONE);
+      p->nstructs += count;
+      p->nstruct_blocks++;
+      p->sum_depth += count * depth;
+      if (depth > p->max_depth) p->max_depth = depth;
+    }
+    p->payload += bytes;
+    *id = (uint32_t)emitted.size();
+    emitted.push_back(b);
+    return DC_OK;
+  }
+
+  // Emit the blocks one struct points to (field order).
+  dc_status visit(uint32_t blk, uint64_t elem, uint32_t type) {
+    const dc_type& T = S.types[type];
+    const uint8_t* s = emitted[blk].host + elem * T.size;
+    for (uint32_t f = 0; f < T.nfields; f++) {
+      const dc_field& F = T.fields[f];
+      if (F.kind == DC_F_SCALAR) continue;
+      uint64_t n;
+      if (!read_count(T, s, F, &n)) return fail(DC_EINVAL, "negative count (type %u field %u)", type, f);
+      const uint8_t* ptr;
+      memcpy(&ptr, s + F.offset, sizeof ptr);
+      if (n == 0) {  // nothing to point at: the copy holds NULL in this slot
+        if (ptr) null_slots.push_back({blk, elem * T.size + F.offset});
+        continue;
+      }
+      if (!ptr)
+        return fail(DC_EINVAL, "NULL pointer with count %llu (type %u field %u)", (unsigned long long)n,
+                    type, f);
+      uint64_t esz = F.kind == DC_F_ARRAY ? F.elem_size : S.types[F.child_type].size;
+      if (n > UINT64_MAX / esz) return fail(DC_EINVAL, "block size overflows (type %u field %u)", type, f);
+      uint32_t id;
+      uint32_t depth = emitted[blk].depth;
+      dc_status st = F.kind == DC_F_ARRAY
+                         ? emit(ptr, n * esz, n, S.lane_of[type][f], type, f, blk,
+                                elem * T.size + F.offset, depth, &id)
+                         : emit(ptr, n * esz, n, 0, (uint32_t)F.child_type, NONE, blk,
+                                elem * T.size + F.offset, depth + 1, &id);
+      if (st) return st;
+      p->ptr_target[emitted[blk].ptr_first + elem * S.nptr[type] + S.ptr_index[type][f]] = id;
+    }
+    return DC_OK;
+  }
+
+  dc_status run(const uint8_t* root) {
+    uint32_t rt = S.root_type;
+    uint32_t rid;
+    dc_status st = emit(root, S.types[rt].size, 1, 0, rt, NONE, NONE, 0, 0, &rid);
+    if (st) return st;
+    std::vector<Frame> stack;
+    if ((st = visit(rid, 0, rt))) return st;
+    stack.push_back({rid, 0, rt, 0, 0});
+    while (!stack.empty()) {
+      Frame& fr = stack.back();
+      const dc_type& T = S.types[fr.type];
+      bool pushed = false;
+      while (fr.field < T.nfields) {
+        const dc_field& F = T.fields[fr.field];
+        if (F.kind != DC_F_CHILD) {
+          fr.field++;
+          continue;
+        }
+        uint32_t tgt = p->ptr_target[emitted[fr.blk].ptr_first + fr.elem * S.nptr[fr.type] +
+                                     S.ptr_index[fr.type][fr.field]];
+        if (tgt == NONE || fr.k >= emitted[tgt].count) {
+          fr.field++;
+          fr.k = 0;
+          continue;
+        }
+        uint64_t k = fr.k++;
+        uint32_t ct = (uint32_t)F.child_type;
+        if ((st = visit(tgt, k, ct))) return st;
+        stack.push_back({tgt, k, ct, 0, 0});
+        pushed = true;
+        break;
+      }
+      if (!pushed) stack.pop_back();
+    }
+    return DC_OK;
+  }
+};
+
+}  // namespace
+
+dc_status build_plan(const dc_schema* schema, const void* host_root, dc_plan_s* p) {
+  if (!host_root) return fail(DC_EINVAL, "host_root is NULL");
+  dc_status st = copy_schema(schema, &p->schema);
+  if (st) return st;
+  Walker w(p);
+  if ((st = w.run((const uint8_t*)host_root))) return st;
+  std::vector<HostBlock>& E = w.emitted;
+  const uint64_t nb = E.size();
+
+  // every block must be disjoint from every other (arrays included)
+  {
+    std::vector<uint32_t> by(nb);
+    for (uint64_t i = 0; i < nb; i++) by[i] = (uint32_t)i;
+    std::sort(by.begin(), by.end(), [&](uint32_t a, uint32_t b) { return E[a].host < E[b].host; });
+    for (uint64_t i = 1; i < nb; i++) {
+      const HostBlock& a = E[by[i - 1]];
+      const HostBlock& b = E[by[i]];
+      if ((uint64_t)(uintptr_t)a.host + a.bytes > (uint64_t)(uintptr_t)b.host) {
+        bool cyc = (a.field == NONE && w.is_ancestor(by[i - 1], b.parent)) ||
+                   (b.field == NONE && w.is_ancestor(by[i], a.parent));
+        return fail(cyc ? DC_ECYCLE : DC_EALIAS, "host blocks at 0x%llx and 0x%llx overlap",
+                    (unsigned long long)(uintptr_t)a.host, (unsigned long long)(uintptr_t)b.host);
+      }
+    }
+  }
+
+  // lanes: stable counting sort of the emission order
+  const uint32_t nl = p->schema.nlanes;
+  std::vector<uint64_t> lane_start(nl + 1, 0);
+  for (auto& b : E) lane_start[b.lane + 1]++;
+  for (uint32_t l = 0; l < nl; l++) lane_start[l + 1] += lane_start[l];
+  std::vector<uint32_t> new_id(nb);
+  {
+    std::vector<uint64_t> cur(lane_start.begin(), lane_start.end() - 1);
+    for (uint64_t i = 0; i < nb; i++) new_id[i] = (uint32_t)cur[E[i].lane]++;
+  }
+  p->blocks.resize(nb);
+  for (uint64_t i = 0; i < nb; i++) {
+    HostBlock b = E[i];
+    if (b.parent != NONE) b.parent = new_id[b.parent];
+    p->blocks[new_id[i]] = b;
+  }
+  for (auto& t : p->ptr_target)
+    if (t != NONE) t = new_id[t];
+  uint64_t off = 0;
+  p->rec.resize(nb);
+  p->hostp.resize(nb);
+  for (uint64_t i = 0; i < nb; i++) {
+    HostBlock& b = p->blocks[i];
+    b.off = off;
+    off += round_up(b.bytes, 16);
+    p->rec[i] = BlockRec{(uint32_t)(round_up(b.bytes, 16) / 16), b.parent, b.slot_off, b.lane};
+    p->hostp[i] = (uint64_t)(uintptr_t)b.host;
+  }
+  p->data_bytes = off;
+  p->null_slots.clear();
+  for (auto& ns : w.null_slots) p->null_slots.push_back(p->blocks[new_id[ns.first]].off + ns.second);
+  std::sort(p->null_slots.begin(), p->null_slots.end());
+  return DC_OK;
+}
+
+dc_status resolve(const dc_plan_s* p, const dc_step* path, uint32_t len, uint32_t* block,
+                  uint64_t* within, uint32_t* type, uint64_t* elem_out) {
+  if (len && !path) return fail(DC_EINVAL, "path is NULL");
+  const SchemaCopy& S = p->schema;
+  uint32_t blk = 0;  // the root struct block is arena block 0
+  uint64_t elem = 0;
+  uint32_t ti = S.root_type;
+  for (uint32_t k = 0; k < len; k++) {
+    const dc_type& T = S.types[ti];
+    if (path[k].field >= T.nfields) return fail(DC_EINVAL, "step %u: no field %u", k, path[k].field);
+    const dc_field& F = T.fields[path[k].field];
+    if (F.kind == DC_F_SCALAR) return fail(DC_EINVAL, "step %u: field %u is a scalar", k, path[k].field);
+    uint32_t tgt =
+        p->ptr_target[p->blocks[blk].ptr_first + elem * S.nptr[ti] + S.ptr_index[ti][path[k].field]];
+    if (tgt == NONE) return fail(DC_EINVAL, "step %u: pointer is empty", k);
+    if (path[k].index >= p->blocks[tgt].count)
+      return fail(DC_EINVAL, "step %u: index %llu out of range (%llu)", k,
+                  (unsigned long long)path[k].index, (unsigned long long)p->blocks[tgt].count);
+    if (F.kind == DC_F_ARRAY) {
+      if (k + 1 != len) return fail(DC_EINVAL, "step %u: an array step must be the last", k);
+      *block = tgt;
+      *within = path[k].index * F.elem_size;
+      *type = NONE;
+      if (elem_out) *elem_out = 0;
+      return DC_OK;
+    }
+    blk = tgt;
+    elem = path[k].index;
+    ti = (uint32_t)F.child_type;
+  }
+  *block = blk;
+  *within = elem * S.types[ti].size;
+  *type = ti;
+  if (elem_out) *elem_out = elem;
+  return DC_OK;
+}
+
+dc_status check_op(const dc_plan_s* p, const dc_op* op) {
+  if (!op) return fail(DC_EINVAL, "op is NULL");
+  const SchemaCopy& S = p->schema;
+  if (op->kind != DC_OP_AXPY_HALF && op->kind != DC_OP_SCALE) return fail(DC_EINVAL, "op: unknown kind");
+  if (op->sel != DC_SEL_ALL && op->sel != DC_SEL_CHAIN) return fail(DC_EINVAL, "op: unknown selection");
+  if (op->sel == DC_SEL_CHAIN && op->path_len && !op->path) return fail(DC_EINVAL, "op: path is NULL");
+  if (op->type >= S.types.size()) return fail(DC_EINVAL, "op: bad type");
+  const dc_type& T = S.types[op->type];
+  if (op->x_field >= T.nfields || T.fields[op->x_field].kind != DC_F_ARRAY)
+    return fail(DC_EINVAL, "op: x_field is not an ARRAY field");
+  const dc_field& X = T.fields[op->x_field];
+  if (!((X.elem_kind == DC_E_F32 && X.elem_size == 4) || (X.elem_kind == DC_E_F64 && X.elem_size == 8)))
+    return fail(DC_EINVAL, "op: x must be an f32 or f64 array");
+  if (op->kind == DC_OP_AXPY_HALF) {
+    if (op->y_field >= T.nfields || T.fields[op->y_field].kind != DC_F_ARRAY)
+      return fail(DC_EINVAL, "op: y_field is not an ARRAY field");
+    const dc_field& Y = T.fields[op->y_field];
+    if (Y.elem_kind != X.elem_kind || Y.elem_size != X.elem_size)
+      return fail(DC_EINVAL, "op: x and y differ in element type");
+    if (op->y_field == op->x_field) return fail(DC_EINVAL, "op: x and y are the same field");
+  }
+  return DC_OK;
+}
+
+dc_status select_structs(const dc_plan_s* p, const dc_op* op,
+                         std::vector<std::pair<uint32_t, uint64_t>>* out) {
+  out->clear();
+  if (op->sel == DC_SEL_CHAIN) {
+    uint32_t blk, ty;
+    uint64_t within, elem;
+    dc_status st = resolve(p, op->path, op->path_len, &blk, &within, &ty, &elem);
+    if (st) return st;
+    if (ty == NONE) return fail(DC_EINVAL, "op: the chain must end on a struct, not an array element");
+    if (ty != op->type)
+      return fail(DC_EINVAL, "op: the chain reaches a struct of type %u, not %u", ty, op->type);
+    out->push_back({blk, elem});
+    return DC_OK;
+  }
+  for (uint64_t b = 0; b < p->nstruct_blocks; b++) {
+    const HostBlock& B = p->blocks[b];
+    if (B.type != op->type) continue;
+    for (uint64_t e = 0; e < B.count; e++) out->push_back({(uint32_t)b, e});
+  }
+  return DC_OK;
+}
+
+void path_to(const dc_plan_s* p, uint32_t block, uint64_t elem, std::vector<dc_step>* out) {
+  out->clear();
+  const SchemaCopy& S = p->schema;
+  while (p->blocks[block].parent != NONE) {
+    const HostBlock& B = p->blocks[block];
+    const HostBlock& P = p->blocks[B.parent];
+    uint32_t psize = S.types[P.type].size;
+    uint32_t foff = B.slot_off % psize;
+    uint32_t field = 0;
+    for (uint32_t f = 0; f < S.types[P.type].nfields; f++)
+      if (S.fields[P.type][f].kind == DC_F_CHILD && S.fields[P.type][f].offset == foff) field = f;
+    out->push_back({field, elem});
+    elem = B.slot_off / psize;
+    block = B.parent;
+  }
+  std::reverse(out->begin(), out->end());
+}
+
+}  // namespace dc

@@ -1,0 +1,744 @@
+// runtime.cpp — the C ABI (include/dc.h): plan lifetime, device binding, the
+// marshal + transfer + relocation of a deep copy (Fig 2; Algorithm 1), chain
+// resolution (Sec. 3), the leaf kernels, copy back (Algorithm 2 step 5) and the
+// managed-memory comparison path.
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <thread>
+
+#include "internal.hpp"
+
+using namespace dc;
+
+static std::atomic<uint64_t> g_launches{0};
+void dc::count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+
+constexpr uint64_t PIECE_BYTES = 2ull << 20;   // largest memcpy one host thread does at once
+constexpr uint64_t CHUNK_BYTES = 32ull << 20;  // transfer granularity of the data region
+constexpr uint64_t WORD_AREA = 256;            // pinned words for small device -> host reads
+
+uint64_t align256(uint64_t x) { return round_up(x, 256); }
+
+DevLayout make_layout(const dc_plan_s* p) {
+  DevLayout L;
+  const uint64_t nb = p->blocks.size();
+  uint64_t o = align256(p->data_bytes);
+  L.rec = o;
+  o = align256(o + nb * sizeof(BlockRec));
+  L.hostp = o;
+  o = align256(o + nb * 8);
+  L.soff = o;
+  o = align256(o + std::max<uint64_t>(1, p->nstruct_blocks) * 8);
+  L.ntiles = (nb + RELOC_TILE - 1) / RELOC_TILE;
+  L.status = o;
+  o = align256(o + L.ntiles * 8);
+  L.ready = o;
+  o = align256(o + L.ntiles * 4);
+  L.ctrl = o;
+  o = align256(o + CTRL_WORDS * 4);
+  L.seg_cap = std::max<uint64_t>(1, p->nstructs);
+  L.seg = o;
+  o = align256(o + L.seg_cap * sizeof(Segment));
+  L.cseg = o;
+  o = align256(o + L.seg_cap * sizeof(ChaseSeg));
+  L.step_cap = std::max<uint64_t>(1, p->sum_depth);
+  L.steps = o;
+  o = align256(o + L.step_cap * sizeof(ChaseStep));
+  L.walk_cap = (uint64_t)p->max_depth + 2;
+  L.walk = o;
+  o = align256(o + L.walk_cap * sizeof(ChaseStep) + 16);
+  L.total = o;
+  return L;
+}
+
+// pinned table staging: [segments][chase segments][chase steps][walk steps][words]
+uint64_t tab_seg(const DevLayout& L) { (void)L; return 0; }
+uint64_t tab_cseg(const DevLayout& L) { return align256(L.seg_cap * sizeof(Segment)); }
+uint64_t tab_steps(const DevLayout& L) { return tab_cseg(L) + align256(L.seg_cap * sizeof(ChaseSeg)); }
+uint64_t tab_walk(const DevLayout& L) { return tab_steps(L) + align256(L.step_cap * sizeof(ChaseStep)); }
+uint64_t tab_words(const DevLayout& L) { return tab_walk(L) + align256(L.walk_cap * sizeof(ChaseStep)); }
+uint64_t tab_total(const DevLayout& L) { return tab_words(L) + WORD_AREA; }
+
+unsigned default_threads() {
+  unsigned hc = std::thread::hardware_concurrency();
+  if (hc == 0) hc = 1;
+  return std::min(hc, 32u);
+}
+
+Pool& pool_of(dc_plan_s* p) {
+  if (!p->pool) p->pool.reset(new Pool(p->nthreads ? p->nthreads : default_threads()));
+  return *p->pool;
+}
+
+void build_pieces(dc_plan_s* p) {
+  p->pieces.clear();
+  p->chunks.clear();
+  for (const HostBlock& b : p->blocks)
+    for (uint64_t o = 0; o < b.bytes; o += PIECE_BYTES)
+      p->pieces.push_back({b.off + o, std::min(PIECE_BYTES, b.bytes - o), b.host + o});
+  uint64_t first = 0, lo = 0;
+  for (uint64_t i = 0; i < p->pieces.size(); i++) {
+    uint64_t end = p->pieces[i].off + p->pieces[i].len;
+    bool last = i + 1 == p->pieces.size();
+    if (end - lo >= CHUNK_BYTES || last) {
+      uint64_t hi = last ? p->data_bytes : p->pieces[i + 1].off;
+      p->chunks.push_back({lo, hi, first, i + 1});
+      lo = hi;
+      first = i + 1;
+    }
+  }
+}
+
+dc_status device_error(dc_plan_s* p, cudaStream_t s) {
+  uint32_t* word = reinterpret_cast<uint32_t*>(p->pin_tab + tab_words(p->L));
+  DC_CUDA(cudaMemcpyAsync(word, p->dev + p->L.ctrl + CTRL_ERR * 4, 4, cudaMemcpyDeviceToHost, s));
+  DC_CUDA(cudaStreamSynchronize(s));
+  uint32_t e = *word;
+  if (!e) return DC_OK;
+  DC_CUDA(cudaMemsetAsync(p->dev + p->L.ctrl + CTRL_ERR * 4, 0, 4, s));
+  DC_CUDA(cudaStreamSynchronize(s));
+  if (e & ERR_BOUNDS) return fail(DC_EDEVICE_BOUNDS, "a kernel found an offset outside its buffers (0x%x)", e);
+  if (e & ERR_TIMEOUT) return fail(DC_ETIMEOUT, "a device-side wait gave up (0x%x)", e);
+  return fail(DC_EVERIFY, "relocation check: a pointer slot did not hold the recorded host address");
+}
+
+OpKey key_of(const dc_op* op) {
+  OpKey k;
+  k.kind = op->kind;
+  k.sel = op->sel;
+  k.type = op->type;
+  k.x = op->x_field;
+  k.y = op->kind == DC_OP_AXPY_HALF ? op->y_field : 0;
+  if (op->sel == DC_SEL_CHAIN) k.path.assign(op->path, op->path + op->path_len);
+  return k;
+}
+
+// x (and y) target blocks of the selected structs; structs whose x is empty are skipped.
+struct Pick {
+  uint32_t sblk;
+  uint64_t elem;
+  uint32_t bx, by;
+};
+
+dc_status pick(const dc_plan_s* p, const dc_op* op, std::vector<Pick>* out) {
+  std::vector<std::pair<uint32_t, uint64_t>> sel;
+  dc_status st = select_structs(p, op, &sel);
+  if (st) return st;
+  const SchemaCopy& S = p->schema;
+  const uint32_t np = S.nptr[op->type];
+  const int32_t ix = S.ptr_index[op->type][op->x_field];
+  const int32_t iy = op->kind == DC_OP_AXPY_HALF ? S.ptr_index[op->type][op->y_field] : -1;
+  out->clear();
+  out->reserve(sel.size());
+  for (auto& se : sel) {
+    const uint64_t base = p->blocks[se.first].ptr_first + se.second * np;
+    uint32_t bx = p->ptr_target[base + ix];
+    uint32_t by = iy >= 0 ? p->ptr_target[base + iy] : NONE;
+    if (iy >= 0) {
+      uint64_t nx = bx == NONE ? 0 : p->blocks[bx].count, ny = by == NONE ? 0 : p->blocks[by].count;
+      if (nx != ny) return fail(DC_EINVAL, "op: x has %llu elements but y has %llu", (unsigned long long)nx,
+                                (unsigned long long)ny);
+    }
+    if (bx == NONE) continue;
+    out->push_back({se.first, se.second, bx, by});
+  }
+  std::sort(out->begin(), out->end(), [&](const Pick& a, const Pick& b) { return a.bx < b.bx; });
+  return DC_OK;
+}
+
+// chase steps from the root to struct (sblk, elem), appended to `steps`
+void chain_steps(const dc_plan_s* p, uint32_t sblk, uint64_t elem, std::vector<ChaseStep>* steps) {
+  size_t start = steps->size();
+  const SchemaCopy& S = p->schema;
+  while (p->blocks[sblk].parent != NONE) {
+    const HostBlock& B = p->blocks[sblk];
+    const HostBlock& P = p->blocks[B.parent];
+    uint32_t psize = S.types[P.type].size;
+    steps->push_back({B.slot_off % psize, S.types[B.type].size, elem});
+    elem = B.slot_off / psize;
+    sblk = B.parent;
+  }
+  std::reverse(steps->begin() + start, steps->end());
+}
+
+dc_status wait_event(cudaEvent_t e) {
+  if (e) DC_CUDA(cudaEventSynchronize(e));
+  return DC_OK;
+}
+
+dc_status path_steps(const dc_plan_s* p, const dc_step* path, uint32_t len, std::vector<ChaseStep>* out) {
+  uint32_t blk, ty;
+  uint64_t within, elem;
+  dc_status st = resolve(p, path, len, &blk, &within, &ty, &elem);  // validates the chain
+  if (st) return st;
+  const SchemaCopy& S = p->schema;
+  uint32_t ti = S.root_type;
+  out->clear();
+  for (uint32_t k = 0; k < len; k++) {
+    const dc_field& F = S.fields[ti][path[k].field];
+    uint32_t sz = F.kind == DC_F_ARRAY ? F.elem_size : S.types[F.child_type].size;
+    out->push_back({F.offset, sz, path[k].index});
+    if (F.kind == DC_F_CHILD) ti = (uint32_t)F.child_type;
+  }
+  return DC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dc_last_error(void) { return last_error(); }
+
+const char* dc_status_name(dc_status s) {
+  switch (s) {
+    case DC_OK: return "DC_OK";
+    case DC_EINVAL: return "DC_EINVAL";
+    case DC_ENOMEM: return "DC_ENOMEM";
+    case DC_ECUDA: return "DC_ECUDA";
+    case DC_EALIAS: return "DC_EALIAS";
+    case DC_ECYCLE: return "DC_ECYCLE";
+    case DC_EBUDGET: return "DC_EBUDGET";
+    case DC_ETIMEOUT: return "DC_ETIMEOUT";
+    case DC_EDEVICE_BOUNDS: return "DC_EDEVICE_BOUNDS";
+    case DC_ESTATE: return "DC_ESTATE";
+    case DC_EVERIFY: return "DC_EVERIFY";
+  }
+  return "unknown";
+}
+
+uint64_t dc_kernel_launches(void) { return g_launches.load(); }
+
+dc_status dc_plan(const dc_schema* schema, const void* host_root, dc_plan_t* out) {
+  if (!out) return fail(DC_EINVAL, "out is NULL");
+  *out = nullptr;
+  dc_plan_s* p = new (std::nothrow) dc_plan_s;
+  if (!p) return fail(DC_ENOMEM, "out of host memory");
+  dc_status st;
+  try {
+    st = build_plan(schema, host_root, p);
+  } catch (const std::bad_alloc&) {
+    st = fail(DC_ENOMEM, "out of host memory while planning");
+  }
+  if (st) {
+    delete p;
+    return st;
+  }
+  p->L = make_layout(p);
+  *out = p;
+  return DC_OK;
+}
+
+dc_status dc_plan_set_flags(dc_plan_t p, uint32_t flags) {
+  if (!p) return fail(DC_EINVAL, "plan is NULL");
+  p->flags = flags;
+  return DC_OK;
+}
+
+dc_status dc_plan_set_threads(dc_plan_t p, uint32_t n) {
+  if (!p) return fail(DC_EINVAL, "plan is NULL");
+  p->nthreads = n;
+  p->pool.reset();
+  return DC_OK;
+}
+
+dc_status dc_plan_info_get(dc_plan_t p, dc_plan_info* out) {
+  if (!p || !out) return fail(DC_EINVAL, "NULL argument");
+  out->data_bytes = p->data_bytes;
+  out->device_bytes = p->L.total;
+  out->payload_bytes = p->payload;
+  out->nblocks = p->blocks.size();
+  out->nrelocs = p->blocks.size() - 1;
+  out->nstructs = p->nstructs;
+  out->nstruct_blocks = p->nstruct_blocks;
+  out->root_offset = 0;
+  return DC_OK;
+}
+
+dc_status dc_plan_block(dc_plan_t p, uint64_t i, uint64_t* host, uint64_t* off, uint64_t* bytes, uint32_t* lane,
+                        uint32_t* parent, uint32_t* slot_off) {
+  if (!p) return fail(DC_EINVAL, "plan is NULL");
+  if (i >= p->blocks.size()) return fail(DC_EINVAL, "block %llu out of range", (unsigned long long)i);
+  const HostBlock& b = p->blocks[i];
+  if (host) *host = (uint64_t)(uintptr_t)b.host;
+  if (off) *off = b.off;
+  if (bytes) *bytes = b.bytes;
+  if (lane) *lane = b.lane;
+  if (parent) *parent = b.parent;
+  if (slot_off) *slot_off = b.slot_off;
+  return DC_OK;
+}
+
+dc_status dc_plan_destroy(dc_plan_t p) {
+  if (!p) return DC_OK;
+  if (p->h2d_done) cudaEventSynchronize(p->h2d_done);
+  if (p->tab_done) cudaEventSynchronize(p->tab_done);
+  if (p->pinned) cudaFreeHost(p->pinned);
+  if (p->pin_tab) cudaFreeHost(p->pin_tab);
+  if (p->h2d_done) cudaEventDestroy(p->h2d_done);
+  if (p->tab_done) cudaEventDestroy(p->tab_done);
+  delete p;
+  return DC_OK;
+}
+
+dc_status dc_bind_device(dc_plan_t p, void* dev, uint64_t bytes, dc_stream_t stream) {
+  if (!p || !dev) return fail(DC_EINVAL, "NULL argument");
+  if ((uintptr_t)dev % 256) return fail(DC_EINVAL, "device buffer must be 256-byte aligned");
+  if (bytes < p->L.total)
+    return fail(DC_EBUDGET, "device buffer holds %llu bytes, the plan needs %llu", (unsigned long long)bytes,
+                (unsigned long long)p->L.total);
+  cudaStream_t s = stream;
+  DC_CUDA(cudaGetDevice(&p->device));
+  DC_CUDA(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device));
+  if (p->h2d_done) DC_CUDA(cudaEventSynchronize(p->h2d_done));
+  if (!p->pinned) {
+    cudaError_t e = cudaHostAlloc((void**)&p->pinned, std::max<uint64_t>(p->data_bytes, 16), cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+      p->pinned = nullptr;
+      return fail(DC_ENOMEM, "pinned arena of %llu bytes: %s", (unsigned long long)p->data_bytes,
+                  cudaGetErrorString(e));
+    }
+    // padding between blocks stays zero: the marshal writes blocks only
+    Pool& pool = pool_of(p);
+    const uint64_t n = (p->data_bytes + (64ull << 20) - 1) / (64ull << 20);
+    pool.parallel_for(n, [&](uint64_t i) {
+      uint64_t lo = i * (64ull << 20), hi = std::min<uint64_t>(p->data_bytes, lo + (64ull << 20));
+      memset(p->pinned + lo, 0, hi - lo);
+    });
+  }
+  if (!p->pin_tab || p->pin_tab_bytes < tab_total(p->L)) {
+    if (p->pin_tab) cudaFreeHost(p->pin_tab);
+    p->pin_tab_bytes = tab_total(p->L);
+    cudaError_t e = cudaHostAlloc((void**)&p->pin_tab, p->pin_tab_bytes, cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+      p->pin_tab = nullptr;
+      return fail(DC_ENOMEM, "pinned table staging: %s", cudaGetErrorString(e));
+    }
+  }
+  if (!p->h2d_done) DC_CUDA(cudaEventCreateWithFlags(&p->h2d_done, cudaEventDisableTiming));
+  if (!p->tab_done) DC_CUDA(cudaEventCreateWithFlags(&p->tab_done, cudaEventDisableTiming));
+  p->dev = (uint8_t*)dev;
+  p->dev_bytes = bytes;
+  const uint64_t nb = p->blocks.size();
+  DC_CUDA(cudaMemcpyAsync(p->dev + p->L.rec, p->rec.data(), nb * sizeof(BlockRec), cudaMemcpyHostToDevice, s));
+  DC_CUDA(cudaMemcpyAsync(p->dev + p->L.hostp, p->hostp.data(), nb * 8, cudaMemcpyHostToDevice, s));
+  DC_CUDA(cudaMemsetAsync(p->dev + p->L.soff, 0, p->L.seg - p->L.soff, s));
+  DC_CUDA(cudaStreamSynchronize(s));
+  p->epoch = 0;
+  p->leaf_key = OpKey();
+  p->chase_key = OpKey();
+  p->written.clear();
+  p->op_run = false;
+  return DC_OK;
+}
+
+dc_status dc_device_base(dc_plan_t p, uint64_t* base) {
+  if (!p || !base) return fail(DC_EINVAL, "NULL argument");
+  if (!p->dev) return fail(DC_ESTATE, "no device buffer bound");
+  *base = (uint64_t)(uintptr_t)p->dev;
+  return DC_OK;
+}
+
+dc_status dc_relocate(dc_plan_t p, dc_stream_t stream) {
+  if (!p) return fail(DC_EINVAL, "plan is NULL");
+  if (!p->dev) return fail(DC_ESTATE, "no device buffer bound");
+  cudaStream_t s = stream;
+  // Fig 2 step d: rebuild every pointer on the device
+  if (++p->epoch > EPOCH_LIMIT) {
+    DC_CUDA(cudaMemsetAsync(p->dev + p->L.status, 0, p->L.ctrl - p->L.status, s));
+    p->epoch = 1;
+  }
+  RelocArgs a;
+  a.arena = p->dev;
+  a.data_bytes = p->data_bytes;
+  a.rec = reinterpret_cast<const BlockRec*>(p->dev + p->L.rec);
+  a.hostp = reinterpret_cast<const uint64_t*>(p->dev + p->L.hostp);
+  a.soff = reinterpret_cast<uint64_t*>(p->dev + p->L.soff);
+  a.status = reinterpret_cast<unsigned long long*>(p->dev + p->L.status);
+  a.ready = reinterpret_cast<uint32_t*>(p->dev + p->L.ready);
+  a.ctrl = reinterpret_cast<uint32_t*>(p->dev + p->L.ctrl);
+  a.nblocks = (uint32_t)p->blocks.size();
+  a.nstruct_blocks = (uint32_t)p->nstruct_blocks;
+  a.ntiles = (uint32_t)p->L.ntiles;
+  a.epoch = p->epoch;
+  a.verify = (p->flags & DC_PLAN_VERIFY) ? 1u : 0u;
+  DC_CUDA(launch_relocate(a, s, p->sm_count));
+  return DC_OK;
+}
+
+dc_status dc_deep_copy(dc_plan_t p, dc_stream_t stream) {
+  if (!p) return fail(DC_EINVAL, "plan is NULL");
+  if (!p->dev) return fail(DC_ESTATE, "no device buffer bound");
+  cudaStream_t s = stream;
+  if (p->chunks.empty()) build_pieces(p);
+  // the previous deep copy's transfers read the same pinned arena
+  dc_status st = wait_event(p->h2d_done);
+  if (st) return st;
+  Pool& pool = pool_of(p);
+  size_t ns = 0;  // next NULL-slot fix-up
+  for (const auto& c : p->chunks) {
+    // Algorithm 1: every block lands at its offset in one contiguous buffer
+    if (c.last - c.first == 1 || pool.size() == 1) {
+      for (uint64_t i = c.first; i < c.last; i++)
+        memcpy(p->pinned + p->pieces[i].off, p->pieces[i].src, p->pieces[i].len);
+    } else {
+      pool.parallel_for(c.last - c.first, [&](uint64_t i) {
+        const auto& pc = p->pieces[c.first + i];
+        memcpy(p->pinned + pc.off, pc.src, pc.len);
+      });
+    }
+    while (ns < p->null_slots.size() && p->null_slots[ns] < c.hi) {
+      memset(p->pinned + p->null_slots[ns], 0, 8);
+      ns++;
+    }
+    // Fig 2 steps b-c: one stream-ordered pass over the data region
+    DC_CUDA(cudaMemcpyAsync(p->dev + c.lo, p->pinned + c.lo, c.hi - c.lo, cudaMemcpyHostToDevice, s));
+  }
+  DC_CUDA(cudaEventRecord(p->h2d_done, s));
+  return dc_relocate(p, stream);
+}
+
+dc_status dc_resolve_offset(dc_plan_t p, const dc_step* path, uint32_t len, uint64_t* offset) {
+  if (!p || !offset) return fail(DC_EINVAL, "NULL argument");
+  uint32_t blk, ty;
+  uint64_t within;
+  dc_status st = resolve(p, path, len, &blk, &within, &ty, nullptr);
+  if (st) return st;
+  *offset = p->blocks[blk].off + within;
+  return DC_OK;
+}
+
+dc_status dc_resolve_chain(dc_plan_t p, const dc_step* path, uint32_t len, uint64_t* dev_addr) {
+  if (!p || !dev_addr) return fail(DC_EINVAL, "NULL argument");
+  if (!p->dev) return fail(DC_ESTATE, "no device buffer bound");
+  uint64_t off;
+  dc_status st = dc_resolve_offset(p, path, len, &off);
+  if (st) return st;
+  *dev_addr = (uint64_t)(uintptr_t)p->dev + off;
+  return DC_OK;
+}
+
+dc_status dc_update_leaves(dc_plan_t p, const dc_op* op, dc_stream_t stream) {
+  if (!p) return fail(DC_EINVAL, "plan is NULL");
+  dc_status st = check_op(p, op);
+  if (st) return st;
+  if (!p->dev) return fail(DC_ESTATE, "no device buffer bound");
+  cudaStream_t s = stream;
+  const dc_field& X = p->schema.fields[op->type][op->x_field];
+  OpKey key = key_of(op);
+  if (!(key == p->leaf_key)) {
+    std::vector<Pick> picks;
+    if ((st = pick(p, op, &picks))) return st;
+    if ((st = wait_event(p->tab_done))) return st;
+    Segment* seg = reinterpret_cast<Segment*>(p->pin_tab + tab_seg(p->L));
+    const uint64_t base = (uint64_t)(uintptr_t)p->dev;
+    uint64_t units = 0;
+    p->leaf_written.clear();
+    for (size_t i = 0; i < picks.size(); i++) {
+      const HostBlock& bx = p->blocks[picks[i].bx];
+      seg[i].x = base + bx.off;
+      seg[i].y = picks[i].by == NONE ? 0 : base + p->blocks[picks[i].by].off;
+      seg[i].n = bx.count;
+      seg[i].ubeg = units;
+      units += (bx.count * X.elem_size + 15) / 16;
+      p->leaf_written.push_back(picks[i].bx);
+    }
+    if (!picks.empty())
+      DC_CUDA(cudaMemcpyAsync(p->dev + p->L.seg, seg, picks.size() * sizeof(Segment), cudaMemcpyHostToDevice, s));
+    DC_CUDA(cudaEventRecord(p->tab_done, s));
+    p->leaf_nseg = picks.size();
+    p->leaf_units = units;
+    p->leaf_key = key;
+  }
+  p->written = p->leaf_written;
+  p->op_run = true;
+  LeafArgs a;
+  a.seg = reinterpret_cast<const Segment*>(p->dev + p->L.seg);
+  a.nseg = (uint32_t)p->leaf_nseg;
+  a.units = p->leaf_units;
+  a.kind = op->kind;
+  a.f64 = X.elem_kind == DC_E_F64;
+  a.scale = op->scale;
+  DC_CUDA(launch_leaf(a, s, p->sm_count));
+  return DC_OK;
+}
+
+dc_status dc_update_chase(dc_plan_t p, const dc_op* op, dc_stream_t stream) {
+  if (!p) return fail(DC_EINVAL, "plan is NULL");
+  dc_status st = check_op(p, op);
+  if (st) return st;
+  if (!p->dev) return fail(DC_ESTATE, "no device buffer bound");
+  cudaStream_t s = stream;
+  const SchemaCopy& S = p->schema;
+  const dc_field& X = S.fields[op->type][op->x_field];
+  OpKey key = key_of(op);
+  if (!(key == p->chase_key)) {
+    std::vector<Pick> picks;
+    if ((st = pick(p, op, &picks))) return st;
+    if ((st = wait_event(p->tab_done))) return st;
+    ChaseSeg* seg = reinterpret_cast<ChaseSeg*>(p->pin_tab + tab_cseg(p->L));
+    ChaseStep* stp = reinterpret_cast<ChaseStep*>(p->pin_tab + tab_steps(p->L));
+    std::vector<ChaseStep> steps;
+    uint64_t elems = 0;
+    p->chase_written.clear();
+    for (size_t i = 0; i < picks.size(); i++) {
+      uint32_t first = (uint32_t)steps.size();
+      chain_steps(p, picks[i].sblk, picks[i].elem, &steps);
+      seg[i].root = (uint64_t)(uintptr_t)p->dev;
+      seg[i].step_first = first;
+      seg[i].nsteps = (uint32_t)(steps.size() - first);
+      seg[i].n = p->blocks[picks[i].bx].count;
+      seg[i].ebeg = elems;
+      elems += seg[i].n;
+      p->chase_written.push_back(picks[i].bx);
+    }
+    if (steps.size() > p->L.step_cap) return fail(DC_EINVAL, "chase table larger than planned");
+    if (!steps.empty()) memcpy(stp, steps.data(), steps.size() * sizeof(ChaseStep));
+    if (!picks.empty())
+      DC_CUDA(cudaMemcpyAsync(p->dev + p->L.cseg, seg, picks.size() * sizeof(ChaseSeg), cudaMemcpyHostToDevice, s));
+    if (!steps.empty())
+      DC_CUDA(cudaMemcpyAsync(p->dev + p->L.steps, stp, steps.size() * sizeof(ChaseStep), cudaMemcpyHostToDevice,
+                              s));
+    DC_CUDA(cudaEventRecord(p->tab_done, s));
+    p->chase_nseg = picks.size();
+    p->chase_elems = elems;
+    p->chase_key = key;
+  }
+  p->written = p->chase_written;
+  p->op_run = true;
+  ChaseArgs a;
+  a.seg = reinterpret_cast<const ChaseSeg*>(p->dev + p->L.cseg);
+  a.steps = reinterpret_cast<const ChaseStep*>(p->dev + p->L.steps);
+  a.nseg = (uint32_t)p->chase_nseg;
+  a.elems = p->chase_elems;
+  a.x_off = X.offset;
+  a.y_off = op->kind == DC_OP_AXPY_HALF ? S.fields[op->type][op->y_field].offset : 0;
+  a.kind = op->kind;
+  a.f64 = X.elem_kind == DC_E_F64;
+  a.scale = op->scale;
+  DC_CUDA(launch_chase(a, s, p->sm_count));
+  return DC_OK;
+}
+
+dc_status dc_verify_chain(dc_plan_t p, const dc_step* path, uint32_t len, dc_stream_t stream, uint64_t* dev_addr) {
+  if (!p || !dev_addr) return fail(DC_EINVAL, "NULL argument");
+  if (!p->dev) return fail(DC_ESTATE, "no device buffer bound");
+  std::vector<ChaseStep> steps;
+  dc_status st = path_steps(p, path, len, &steps);
+  if (st) return st;
+  if (steps.size() > p->L.walk_cap) return fail(DC_EINVAL, "path longer than the tree");
+  cudaStream_t s = stream;
+  if ((st = wait_event(p->tab_done))) return st;
+  ChaseStep* stp = reinterpret_cast<ChaseStep*>(p->pin_tab + tab_walk(p->L));
+  if (!steps.empty()) memcpy(stp, steps.data(), steps.size() * sizeof(ChaseStep));
+  uint8_t* dsteps = p->dev + p->L.walk;
+  uint64_t* dout = reinterpret_cast<uint64_t*>(dsteps + p->L.walk_cap * sizeof(ChaseStep));
+  if (!steps.empty())
+    DC_CUDA(cudaMemcpyAsync(dsteps, stp, steps.size() * sizeof(ChaseStep), cudaMemcpyHostToDevice, s));
+  DC_CUDA(launch_walk((uint64_t)(uintptr_t)p->dev, reinterpret_cast<const ChaseStep*>(dsteps),
+                      (uint32_t)steps.size(), 0, dout, s));
+  uint64_t* word = reinterpret_cast<uint64_t*>(p->pin_tab + tab_words(p->L) + 8);
+  DC_CUDA(cudaMemcpyAsync(word, dout, 8, cudaMemcpyDeviceToHost, s));
+  DC_CUDA(cudaStreamSynchronize(s));
+  *dev_addr = *word;
+  return DC_OK;
+}
+
+dc_status dc_copy_back(dc_plan_t p, uint32_t flags, dc_stream_t stream) {
+  if (!p) return fail(DC_EINVAL, "plan is NULL");
+  if (!p->dev) return fail(DC_ESTATE, "no device buffer bound");
+  std::vector<uint32_t> list;
+  if (flags & DC_COPY_ALL_ARRAYS) {
+    for (uint32_t b = (uint32_t)p->nstruct_blocks; b < p->blocks.size(); b++) list.push_back(b);
+  } else {
+    if (!p->op_run) return fail(DC_ESTATE, "no update has run: nothing to copy back");
+    list = p->written;
+  }
+  std::sort(list.begin(), list.end());
+  cudaStream_t s = stream;
+  // device -> pinned arena, one transfer per run of adjacent blocks
+  for (size_t i = 0; i < list.size();) {
+    uint64_t lo = p->blocks[list[i]].off, hi = lo + p->blocks[list[i]].bytes;
+    size_t j = i + 1;
+    while (j < list.size() && list[j] == list[j - 1] + 1) {
+      hi = p->blocks[list[j]].off + p->blocks[list[j]].bytes;
+      j++;
+    }
+    DC_CUDA(cudaMemcpyAsync(p->pinned + lo, p->dev + lo, hi - lo, cudaMemcpyDeviceToHost, s));
+    i = j;
+  }
+  dc_status st = device_error(p, s);  // synchronizes the stream
+  if (st) return st;
+  // pinned arena -> the original host arrays
+  std::vector<dc_plan_s::Piece> pcs;
+  for (uint32_t b : list) {
+    const HostBlock& B = p->blocks[b];
+    for (uint64_t o = 0; o < B.bytes; o += PIECE_BYTES)
+      pcs.push_back({B.off + o, std::min(PIECE_BYTES, B.bytes - o), B.host + o});
+  }
+  Pool& pool = pool_of(p);
+  if (pcs.size() <= 1 || pool.size() == 1) {
+    for (auto& pc : pcs) memcpy(const_cast<uint8_t*>(pc.src), p->pinned + pc.off, pc.len);
+  } else {
+    pool.parallel_for(pcs.size(), [&](uint64_t i) {
+      memcpy(const_cast<uint8_t*>(pcs[i].src), p->pinned + pcs[i].off, pcs[i].len);
+    });
+  }
+  return DC_OK;
+}
+
+dc_status dc_sync(dc_plan_t p, dc_stream_t stream) {
+  if (!p) return fail(DC_EINVAL, "plan is NULL");
+  if (!p->dev) return fail(DC_ESTATE, "no device buffer bound");
+  return device_error(p, stream);
+}
+
+// ---- UVM comparison path ----------------------------------------------------------
+
+dc_status dc_uvm_build(const dc_schema* schema, const void* host_root, dc_uvm_t* out) {
+  if (!out) return fail(DC_EINVAL, "out is NULL");
+  *out = nullptr;
+  dc_plan_t plan = nullptr;
+  dc_status st = dc_plan(schema, host_root, &plan);
+  if (st) return st;
+  dc_uvm_s* u = new (std::nothrow) dc_uvm_s;
+  if (!u) {
+    dc_plan_destroy(plan);
+    return fail(DC_ENOMEM, "out of host memory");
+  }
+  u->plan = plan;
+  auto cleanup = [&](dc_status s2) {
+    dc_uvm_destroy(u);
+    return s2;
+  };
+  cudaError_t e = cudaGetDevice(&u->device);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaGetDevice"));
+  e = cudaDeviceGetAttribute(&u->sm_count, cudaDevAttrMultiProcessorCount, u->device);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaDeviceGetAttribute"));
+  const uint64_t nb = plan->blocks.size();
+  u->managed.assign(nb, nullptr);
+  for (uint64_t b = 0; b < nb; b++) {  // one managed allocation per block, like a managed malloc
+    e = cudaMallocManaged(&u->managed[b], std::max<uint64_t>(plan->blocks[b].bytes, 1));
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMallocManaged"));
+    memcpy(u->managed[b], plan->blocks[b].host, plan->blocks[b].bytes);
+  }
+  for (uint64_t b = 1; b < nb; b++) {  // host pointers -> managed pointers
+    const HostBlock& B = plan->blocks[b];
+    uint64_t v = (uint64_t)(uintptr_t)u->managed[b];
+    memcpy((uint8_t*)u->managed[B.parent] + B.slot_off, &v, 8);
+  }
+  for (uint64_t off : plan->null_slots) {  // count-0 slots hold NULL
+    auto it = std::upper_bound(plan->blocks.begin(), plan->blocks.begin() + plan->nstruct_blocks, off,
+                               [](uint64_t o, const HostBlock& hb) { return o < hb.off; });
+    uint32_t b = (uint32_t)(it - plan->blocks.begin()) - 1;
+    memset((uint8_t*)u->managed[b] + (off - plan->blocks[b].off), 0, 8);
+  }
+  u->root = (uint64_t)(uintptr_t)u->managed[0];
+  u->seg_cap = std::max<uint64_t>(1, plan->nstructs);
+  u->step_cap = std::max<uint64_t>(1, plan->sum_depth);
+  e = cudaMalloc((void**)&u->dseg, u->seg_cap * sizeof(ChaseSeg));
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc"));
+  e = cudaMalloc((void**)&u->dsteps, u->step_cap * sizeof(ChaseStep));
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc"));
+  *out = u;
+  return DC_OK;
+}
+
+dc_status dc_uvm_root(dc_uvm_t u, uint64_t* root) {
+  if (!u || !root) return fail(DC_EINVAL, "NULL argument");
+  *root = u->root;
+  return DC_OK;
+}
+
+dc_status dc_uvm_prefetch(dc_uvm_t u, int to_device, dc_stream_t stream) {
+  if (!u) return fail(DC_EINVAL, "uvm is NULL");
+  cudaMemLocation loc;
+  loc.type = to_device ? cudaMemLocationTypeDevice : cudaMemLocationTypeHost;
+  loc.id = to_device ? u->device : 0;
+  for (uint64_t b = 0; b < u->managed.size(); b++)
+    DC_CUDA(cudaMemPrefetchAsync(u->managed[b], std::max<uint64_t>(u->plan->blocks[b].bytes, 1), loc, 0, stream));
+  return DC_OK;
+}
+
+dc_status dc_uvm_update(dc_uvm_t u, const dc_op* op, dc_stream_t stream) {
+  if (!u) return fail(DC_EINVAL, "uvm is NULL");
+  dc_plan_s* p = u->plan;
+  dc_status st = check_op(p, op);
+  if (st) return st;
+  const SchemaCopy& S = p->schema;
+  const dc_field& X = S.fields[op->type][op->x_field];
+  cudaStream_t s = stream;
+  OpKey key = key_of(op);
+  if (!(key == u->key)) {
+    std::vector<Pick> picks;
+    if ((st = pick(p, op, &picks))) return st;
+    std::vector<ChaseSeg> seg(picks.size());
+    std::vector<ChaseStep> steps;
+    uint64_t elems = 0;
+    u->written.clear();
+    for (size_t i = 0; i < picks.size(); i++) {
+      uint32_t first = (uint32_t)steps.size();
+      chain_steps(p, picks[i].sblk, picks[i].elem, &steps);
+      seg[i] = ChaseSeg{u->root, first, (uint32_t)(steps.size() - first), p->blocks[picks[i].bx].count, elems};
+      elems += seg[i].n;
+      u->written.push_back(picks[i].bx);
+    }
+    if (steps.size() > u->step_cap) return fail(DC_EINVAL, "chase table larger than planned");
+    if (!seg.empty()) DC_CUDA(cudaMemcpy(u->dseg, seg.data(), seg.size() * sizeof(ChaseSeg), cudaMemcpyHostToDevice));
+    if (!steps.empty())
+      DC_CUDA(cudaMemcpy(u->dsteps, steps.data(), steps.size() * sizeof(ChaseStep), cudaMemcpyHostToDevice));
+    u->nseg = seg.size();
+    u->elems = elems;
+    u->key = key;
+  }
+  ChaseArgs a;
+  a.seg = u->dseg;
+  a.steps = u->dsteps;
+  a.nseg = (uint32_t)u->nseg;
+  a.elems = u->elems;
+  a.x_off = X.offset;
+  a.y_off = op->kind == DC_OP_AXPY_HALF ? S.fields[op->type][op->y_field].offset : 0;
+  a.kind = op->kind;
+  a.f64 = X.elem_kind == DC_E_F64;
+  a.scale = op->scale;
+  DC_CUDA(launch_chase(a, s, u->sm_count));
+  return DC_OK;
+}
+
+dc_status dc_uvm_sync(dc_uvm_t u, dc_stream_t stream) {
+  if (!u) return fail(DC_EINVAL, "uvm is NULL");
+  DC_CUDA(cudaStreamSynchronize(stream));
+  return DC_OK;
+}
+
+dc_status dc_uvm_copy_back(dc_uvm_t u, const void* host_root, uint32_t flags) {
+  if (!u) return fail(DC_EINVAL, "uvm is NULL");
+  dc_plan_s* p = u->plan;
+  if (host_root != p->blocks[0].host) return fail(DC_EINVAL, "host_root is not the tree this UVM copy was built from");
+  DC_CUDA(cudaDeviceSynchronize());
+  if (flags & DC_COPY_ALL_ARRAYS) {
+    for (uint64_t b = p->nstruct_blocks; b < p->blocks.size(); b++)
+      memcpy(const_cast<uint8_t*>(p->blocks[b].host), u->managed[b], p->blocks[b].bytes);
+  } else {
+    for (uint32_t b : u->written) memcpy(const_cast<uint8_t*>(p->blocks[b].host), u->managed[b], p->blocks[b].bytes);
+  }
+  return DC_OK;
+}
+
+dc_status dc_uvm_destroy(dc_uvm_t u) {
+  if (!u) return DC_OK;
+  if (!u->managed.empty() || u->dseg || u->dsteps) cudaDeviceSynchronize();
+  for (void* m : u->managed)
+    if (m) cudaFree(m);
+  if (u->dseg) cudaFree(u->dseg);
+  if (u->dsteps) cudaFree(u->dsteps);
+  dc_plan_destroy(u->plan);
+  delete u;
+  return DC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,226 @@
+"""Host logic of libdc.so (no GPU): the exported C ABI, the planner's block and
+relocation tables, the arena layout, chain resolution and error paths.  The
+device relocation is modelled on the host from the plan's tables and checked
+with the oracle's image checker."""
+import ctypes
+import os
+import random
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+import treegen as tg
+import paper_1906_01128_b300 as dc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dc.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:dc_status|const char\*|uint64_t)\s+(dc_\w+)\s*\(", text, re.M)))
+
+
+def test_library_exports_every_declared_symbol():
+    names = declared_functions()
+    assert len(names) >= 25
+    out = subprocess.check_output(["nm", "-D", "--defined-only", dc.LIB_PATH], text=True)
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:  # and ctypes can bind each one
+        assert getattr(dc.lib, n) is not None
+    assert set(dc.SIGNATURES) | {"dc_last_error", "dc_status_name", "dc_kernel_launches"} == set(names)
+
+
+def host_image(plan, base):
+    """The arena the device holds after a deep copy, built on the host from the
+    plan's tables: every block copied to its offset, every pointer slot set to
+    base + offset of the block it refers to."""
+    info = plan.info
+    img = np.zeros(info["data_bytes"], dtype=np.uint8)
+    blocks = plan.blocks()
+    for b in blocks:
+        if b["bytes"]:
+            img[b["offset"]:b["offset"] + b["bytes"]] = np.frombuffer(
+                ctypes.string_at(b["host"], b["bytes"]), dtype=np.uint8)
+    for b in blocks:
+        if b["parent"] is not None:
+            slot = blocks[b["parent"]]["offset"] + b["slot_off"]
+            img[slot:slot + 8] = np.frombuffer((base + b["offset"]).to_bytes(8, "little"), dtype=np.uint8)
+    return img
+
+
+BASE = 0x7E0000000000
+
+
+def trees_for_tests():
+    yield tg.workload("tiny")
+    yield tg.node_tree(3, 16, tg.lognormal(300, 1.2, 5000), seed=2)
+    yield tg.node_tree(20, 1, 33, 1000, seed=3)
+    yield tg.node_tree(4, 3, tg.uniform(0, 9), seed=4)
+    yield tg.linear_tree(6, 100, "llinit", seed=5)
+    yield tg.dense_tree(3, 7, 3, seed=6)
+    yield tg.listing1_tree(50, seed=7)
+
+
+def test_plan_counts_and_layout_match_oracle():
+    for t in trees_for_tests():
+        p = dc.Plan(t.schema, t.root)
+        info, c = p.info, oracle.count(t.schema, t.root)
+        assert info["nblocks"] == c["nblocks"] and info["payload_bytes"] == c["payload_bytes"]
+        assert info["nstructs"] == c["nstructs"] and info["nrelocs"] == c["nptr"]
+        blocks = p.blocks()
+        end, lane = 0, 0
+        for i, b in enumerate(blocks):
+            assert b["offset"] % 16 == 0 and b["offset"] >= end, i
+            assert b["lane"] >= lane  # lanes are contiguous, struct lane first
+            assert (b["lane"] == 0) == (i < info["nstruct_blocks"])
+            assert (b["parent"] is None) == (i == 0)
+            if b["parent"] is not None:
+                assert b["parent"] < info["nstruct_blocks"] and b["parent"] < i
+            end, lane = b["offset"] + b["bytes"], b["lane"]
+        assert info["data_bytes"] == (end + 15) // 16 * 16 == c["padded_bytes"]
+        assert info["device_bytes"] >= info["data_bytes"]
+        p.destroy()
+        t.free()
+
+
+class CNode(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nchild", ctypes.c_int32), ("position", ctypes.c_void_p),
+                ("velocity", ctypes.c_void_p), ("child", ctypes.c_void_p)]
+
+
+def hand_tree():
+    keep = []
+    pos, vel = (ctypes.c_float * 2)(1.0, 2.0), (ctypes.c_float * 2)(3.0, 4.0)
+    p0, v0 = (ctypes.c_float * 1)(5.0), (ctypes.c_float * 1)(6.0)
+    kids = (CNode * 2)()
+    kids[0] = CNode(1, 0, ctypes.addressof(p0), ctypes.addressof(v0), None)
+    kids[1] = CNode(0, 0, None, None, None)
+    root = CNode(2, 2, ctypes.addressof(pos), ctypes.addressof(vel), ctypes.addressof(kids))
+    keep += [pos, vel, p0, v0, kids, root]
+    return root, keep
+
+
+def test_hand_tree_lane_layout():
+    # lane 0: root (32 B) @0, child array (64 B) @32; lane 1 (position):
+    # root.pos (8 B) @96, c0.pos (4 B) @112; lane 2 (velocity): @128, @144
+    root, keep = hand_tree()
+    p = dc.Plan(tg.node_schema(), ctypes.addressof(root))
+    got = [(b["offset"], b["bytes"], b["lane"], b["parent"], b["slot_off"]) for b in p.blocks()]
+    assert got == [(0, 32, 0, None, 0), (32, 64, 0, 0, 24), (96, 8, 1, 0, 8), (112, 4, 1, 1, 8),
+                   (128, 8, 2, 0, 16), (144, 4, 2, 1, 16)]
+    assert p.info["data_bytes"] == 160
+    assert p.blocks()[3]["host"] == ctypes.cast(root.child, ctypes.POINTER(CNode))[0].position
+    assert p.resolve_offset([]) == 0
+    assert p.resolve_offset([(4, 1)]) == 64
+    assert p.resolve_offset([(4, 0), (2, 0)]) == 112
+    assert p.resolve_offset([(3, 1)]) == 132
+    for bad in ([(4, 2)], [(4, 1), (2, 0)], [(0, 0)], [(2, 0), (2, 0)], [(9, 0)]):
+        with pytest.raises(dc.DcError) as e:
+            p.resolve_offset(bad)
+        assert e.value.name == "DC_EINVAL"
+
+
+def test_host_model_of_relocation_passes_the_oracle_check():
+    trees = list(trees_for_tests())
+    rng = random.Random(77)
+    for i in range(60):
+        s, levels, rules = tg.random_schema(rng)
+        trees.append(tg.Tree(s, levels, rules, seed=1000 + i))
+    for t in trees:
+        p = dc.Plan(t.schema, t.root)
+        img = host_image(p, BASE)
+        ok, msg, seen = oracle.check_image(t.schema, t.root, img, BASE)
+        assert ok, (t.name, msg)
+        p.destroy()
+        t.free()
+
+
+def test_resolve_offset_agrees_with_an_image_walk():
+    rng = random.Random(5)
+    t = tg.node_tree(4, 5, tg.uniform(1, 40), seed=11)
+    p = dc.Plan(t.schema, t.root)
+    img = host_image(p, BASE)
+    for _ in range(200):
+        depth = rng.randint(0, 3)
+        path = [(4, rng.randrange(5)) for _ in range(depth)]
+        if rng.random() < 0.5:
+            path.append((rng.choice([2, 3]), rng.randrange(1)))
+        assert BASE + p.resolve_offset(path) == oracle.image_resolve(t.schema, img, BASE, path)
+    # the Listing 1 chain simulation->atoms->traits->positions
+    t1 = tg.listing1_tree(8, seed=1)
+    p1 = dc.Plan(t1.schema, t1.root)
+    img1 = host_image(p1, BASE)
+    chain = [(1, 0), (1, 0), (3, 5)]
+    assert BASE + p1.resolve_offset(chain) == oracle.image_resolve(t1.schema, img1, BASE, chain)
+    for x in (p, p1):
+        x.destroy()
+    t.free()
+    t1.free()
+
+
+def _status(fn):
+    with pytest.raises(dc.DcError) as e:
+        fn()
+    return e.value.name
+
+
+def test_plan_rejects_non_trees_and_bad_inputs():
+    s = tg.node_schema()
+    # two pointers to one array
+    arr = (ctypes.c_float * 4)()
+    kids = (CNode * 2)()
+    kids[0] = CNode(4, 0, ctypes.addressof(arr), None, None)
+    kids[0].velocity = ctypes.addressof(arr)
+    root = CNode(0, 1, None, None, ctypes.addressof(kids))
+    assert _status(lambda: dc.Plan(s, ctypes.addressof(root))) == "DC_EALIAS"
+    # a child pointing back at its ancestor
+    loop = (CNode * 1)()
+    loop[0] = CNode(0, 1, None, None, None)
+    loop[0].child = ctypes.addressof(loop)
+    top = CNode(0, 1, None, None, ctypes.addressof(loop))
+    assert _status(lambda: dc.Plan(s, ctypes.addressof(top))) == "DC_ECYCLE"
+    # an array overlapping another one
+    big = (ctypes.c_float * 8)()
+    k2 = (CNode * 1)()
+    k2[0] = CNode(4, 0, ctypes.addressof(big), ctypes.addressof(big) + 8, None)
+    r2 = CNode(0, 1, None, None, ctypes.addressof(k2))
+    assert _status(lambda: dc.Plan(s, ctypes.addressof(r2))) == "DC_EALIAS"
+    # NULL with a count, negative count, NULL root
+    r3 = CNode(3, 0, None, None, None)
+    assert _status(lambda: dc.Plan(s, ctypes.addressof(r3))) == "DC_EINVAL"
+    r4 = CNode(-1, 0, None, None, None)
+    assert _status(lambda: dc.Plan(s, ctypes.addressof(r4))) == "DC_EINVAL"
+    assert _status(lambda: dc.Plan(s, 0)) == "DC_EINVAL"
+    # a schema with a misaligned pointer member
+    bad = tg.Schema([tg.Type("B", 16, 8, [tg.Field("n", tg.SCALAR, 0, 4),
+                                          tg.Field("a", tg.ARRAY, 4, 4, count_field=0)])])
+    assert _status(lambda: dc.Plan(bad, ctypes.addressof(r3))) == "DC_EINVAL"
+    keep = (arr, kids, root, loop, top, big, k2, r2, r3, r4)  # noqa: F841
+
+
+def test_count_zero_pointer_becomes_null_in_the_plan_image():
+    s = tg.node_schema()
+    junk = (ctypes.c_float * 2)()
+    root = CNode(0, 0, ctypes.addressof(junk), ctypes.addressof(junk), None)  # counts 0, pointers set
+    p = dc.Plan(s, ctypes.addressof(root))
+    assert p.info["nblocks"] == 1 and p.info["nrelocs"] == 0
+    keep = junk  # noqa: F841
+
+
+def test_device_calls_need_a_bound_buffer():
+    t = tg.workload("tiny")
+    p = dc.Plan(t.schema, t.root)
+    assert _status(lambda: p.deep_copy(stream=0)) == "DC_ESTATE"
+    assert _status(lambda: p.resolve([])) == "DC_ESTATE"
+    assert _status(lambda: p.update(dc.Op(), stream=0)) == "DC_ESTATE"
+    assert _status(lambda: p.copy_back(stream=0)) == "DC_ESTATE"
+    assert _status(lambda: p.update(dc.Op(x_field=0), stream=0)) == "DC_EINVAL"  # a scalar field
+    assert _status(lambda: p.update(dc.Op(y_field=2), stream=0)) == "DC_EINVAL"  # x == y
+    p.destroy()
+    t.free()

@@ -1,0 +1,273 @@
+"""Parity of the CUDA path with the CPU oracle, element by element, through the
+C ABI.  Copies, pointers and the fp32/fp64 updates must be bit-exact (0 ULP:
+the kernels use __fadd_rn/__fmul_rn, one IEEE rounding per operation, as the
+oracle does).  Covers the named workloads at full size (the sizes the
+benchmark runs), small cases that span several tiles with ragged tails, the
+paper's Linear/Dense/Listing-1 shapes, random schemas and the degenerate
+cases (empty arrays, a lone struct, tiny segments)."""
+import ctypes
+import random
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import treegen as tg
+import paper_1906_01128_b300 as dc
+
+pytestmark = pytest.mark.gpu
+
+NODE_LEAF = 4  # the node struct's child field
+
+
+def ops_pair(kind=dc.OP_AXPY_HALF, sel=dc.SEL_ALL, type_=0, x=2, y=3, scale=1.0, path=()):
+    return (dc.Op(kind, sel, type_, x, y, scale, list(path)),
+            oracle.Op(kind, sel, type_, x, y, scale, list(path)))
+
+
+def image_ok(plan, schema, root_tree):
+    ok, msg, seen = oracle.check_image(schema, root_tree, plan.image(), plan.device_base)
+    assert ok, msg
+    return seen
+
+
+def full_parity(make, op_kw=None, mode="leaf", verify=False, repeat=1):
+    """Deep copy `make()` with the CUDA path and the oracle, run the op
+    `repeat` times on both, copy back on both, compare every stage."""
+    src, ref = make(), make()
+    s = src.schema
+    plan = dc.Plan(s, src.root, flags=dc.PLAN_VERIFY if verify else 0)
+    plan.bind()
+    plan.deep_copy()
+    plan.sync()
+    seen = image_ok(plan, s, src.root)
+    c = oracle.count(s, src.root)
+    assert (seen["nblocks"], seen["payload_bytes"], seen["nstructs"]) == (c["nblocks"], c["payload_bytes"],
+                                                                         c["nstructs"])
+    if op_kw is None:
+        plan.copy_back(all_arrays=True)
+        assert oracle.trees_equal(s, src.root, ref.root)[0]
+        plan.destroy()
+        return plan
+    dop, oop = ops_pair(**op_kw)
+    cp = oracle.deep_copy(s, ref.root)
+    for _ in range(repeat):
+        (plan.update if mode == "leaf" else plan.update_chase)(dop)
+        oracle.update(s, cp.root, oop)
+    plan.sync()
+    image_ok(plan, s, cp.root)  # device arrays == the oracle's updated copy
+    plan.copy_back()
+    oracle.copy_back(s, cp.root, ref.root, oop)
+    ok, msg = oracle.trees_equal(s, src.root, ref.root)
+    assert ok, msg
+    plan.destroy()
+    src.free()
+    ref.free()
+
+
+# ---- named workloads at full size -------------------------------------------
+
+def test_tiny_all_nodes():
+    full_parity(lambda: tg.workload("tiny"), {})
+
+
+def test_tiny_chain_to_last_level():
+    full_parity(lambda: tg.workload("tiny"), dict(sel=dc.SEL_CHAIN, path=tg.leaf_path(4)))
+
+
+def test_dense_all_nodes_full_size():
+    full_parity(lambda: tg.workload("dense"), {}, verify=True)
+
+
+def test_dense_chain_listing2_path():
+    full_parity(lambda: tg.workload("dense"), dict(sel=dc.SEL_CHAIN, path=[(NODE_LEAF, 15), (NODE_LEAF, 15)]))
+
+
+def test_deep_chain_to_leaf_full_size():
+    full_parity(lambda: tg.workload("deep"), dict(sel=dc.SEL_CHAIN, path=tg.leaf_path(64)))
+
+
+def test_reloc_stress_many_tiles():
+    # 1,118,481 nodes, 2,306,868 blocks: the relocation's look-back spans ~2,250 tiles
+    full_parity(lambda: tg.workload("reloc_stress"), {}, verify=True)
+
+
+# ---- comparison paths --------------------------------------------------------
+
+def test_chase_matches_oracle_dense_all():
+    full_parity(lambda: tg.workload("dense"), {}, mode="chase")
+
+
+def test_chase_matches_oracle_deep_chain():
+    full_parity(lambda: tg.node_tree(64, 1, 1024, 1 << 18, seed=3), dict(sel=dc.SEL_CHAIN, path=tg.leaf_path(64)),
+                mode="chase")
+
+
+@pytest.mark.parametrize("prefetch", [False, True])
+def test_uvm_matches_oracle(prefetch):
+    src = tg.node_tree(3, 16, tg.lognormal(4096, 1.2, 65536), seed=2)
+    ref = tg.node_tree(3, 16, tg.lognormal(4096, 1.2, 65536), seed=2)
+    s = src.schema
+    u = dc.Uvm(s, src.root)
+    if prefetch:
+        u.prefetch(True)
+    dop, oop = ops_pair()
+    u.update(dop)
+    u.sync()
+    cp = oracle.deep_copy(s, ref.root)
+    oracle.update(s, cp.root, oop)
+    ok, msg = oracle.trees_equal(s, u.root, cp.root)  # the managed tree itself
+    assert ok, msg
+    u.copy_back()
+    oracle.copy_back(s, cp.root, ref.root, oop)
+    assert oracle.trees_equal(s, src.root, ref.root)[0]
+    u.destroy()
+
+
+def test_uvm_chain_scale_f64_linear():
+    src, ref = tg.linear_tree(8, 5000, "llinit", seed=8), tg.linear_tree(8, 5000, "llinit", seed=8)
+    s = src.schema
+    u = dc.Uvm(s, src.root)
+    kw = dict(kind=dc.OP_SCALE, sel=dc.SEL_CHAIN, x=2, scale=1.5, path=[(3, 0)] * 7)
+    dop, oop = ops_pair(**kw)
+    u.update(dop)
+    u.sync()
+    u.copy_back()
+    cp = oracle.deep_copy(s, ref.root)
+    oracle.update(s, cp.root, oop)
+    oracle.copy_back(s, cp.root, ref.root, oop)
+    assert oracle.trees_equal(s, src.root, ref.root)[0]
+    u.destroy()
+
+
+# ---- the paper's shapes --------------------------------------------------------
+
+@pytest.mark.parametrize("layout", ["allinit", "llinit"])
+def test_linear_scale_f64(layout):
+    kw = dict(kind=dc.OP_SCALE, x=2, scale=1.5)
+    if layout == "llinit":
+        kw.update(sel=dc.SEL_CHAIN, path=[(3, 0)] * 9)
+    full_parity(lambda: tg.linear_tree(10, 10 ** 5, layout, seed=10), kw)
+
+
+def test_dense_listing2_chain_scale():
+    q, D = 8, 3
+    full_parity(lambda: tg.dense_tree(q, 1000, D, seed=4),
+                dict(kind=dc.OP_SCALE, sel=dc.SEL_CHAIN, type_=D, x=1, scale=1.25, path=[(3, q - 1)] * D))
+    full_parity(lambda: tg.dense_tree(q, 1000, D, seed=4),
+                dict(kind=dc.OP_SCALE, sel=dc.SEL_CHAIN, type_=D, x=1, scale=1.25, path=[(3, q - 1)] * D),
+                mode="chase")
+
+
+def test_dense_paper_all_levels_axpy_f64():
+    # an AXPY needs two arrays: scale every level's A instead, level type by type
+    for lvl in range(4):
+        full_parity(lambda: tg.dense_tree(4, 300, 3, seed=5),
+                    dict(kind=dc.OP_SCALE, type_=lvl, x=2 if lvl < 3 else 1, scale=0.75))
+
+
+def test_listing1_chain():
+    full_parity(lambda: tg.listing1_tree(100000, seed=1),
+                dict(kind=dc.OP_SCALE, sel=dc.SEL_CHAIN, type_=2, x=1, scale=3.0, path=[(1, 0), (1, 0)]))
+
+
+# ---- ragged and degenerate cases -------------------------------------------------
+
+def test_ragged_lengths_and_empty_nodes():
+    full_parity(lambda: tg.node_tree(3, 7, tg.uniform(0, 3000), seed=12), {})
+    full_parity(lambda: tg.node_tree(3, 7, tg.uniform(0, 3000), seed=12), {}, mode="chase")
+
+
+def test_many_tiny_segments():
+    # 22,621 nodes of 1-9 elements: many segments per tile, multi-tile relocation
+    full_parity(lambda: tg.node_tree(5, 12, tg.uniform(1, 9), seed=13), {}, verify=True)
+    full_parity(lambda: tg.node_tree(5, 12, tg.uniform(1, 9), seed=13), {}, mode="chase")
+
+
+def test_lone_struct_and_empty_tree():
+    full_parity(lambda: tg.node_tree(1, 0, 0, seed=1), None)
+    full_parity(lambda: tg.node_tree(1, 0, 5, seed=1), {})
+    full_parity(lambda: tg.node_tree(4, 2, 0, seed=1), {})  # structs only, no arrays
+
+
+def test_repeated_updates_reuse_the_table():
+    full_parity(lambda: tg.node_tree(3, 5, tg.uniform(1, 999), seed=14), {}, repeat=3)
+    full_parity(lambda: tg.node_tree(3, 5, tg.uniform(1, 999), seed=14),
+                dict(kind=dc.OP_SCALE, scale=-2.0), repeat=2)
+
+
+def test_random_schemas_deep_copy_and_copy_back():
+    rng = random.Random(4242)
+    for i in range(80):
+        schema, levels, rules = tg.random_schema(rng)
+        full_parity(lambda: tg.Tree(schema, levels, rules, seed=500 + i), None)
+
+
+# ---- re-copy, resolution, relocation check ---------------------------------------
+
+def test_second_deep_copy_restores_the_image():
+    t = tg.node_tree(4, 6, tg.uniform(0, 700), seed=15)
+    p = dc.Plan(t.schema, t.root, flags=dc.PLAN_VERIFY)
+    p.bind()
+    p.deep_copy()
+    p.sync()
+    first = p.image().copy()
+    p.update(dc.Op())
+    p.deep_copy()
+    p.deep_copy()
+    p.sync()
+    assert np.array_equal(first, p.image())
+    p.destroy()
+
+
+def test_resolve_chain_matches_device_walk_and_oracle():
+    t = tg.workload("dense")
+    p = dc.Plan(t.schema, t.root)
+    p.bind()
+    p.deep_copy()
+    p.sync()
+    image_ok(p, t.schema, t.root)  # the walk below dereferences relocated pointers
+    img, base = p.image(), p.device_base
+    rng = random.Random(3)
+    paths = [[], [(NODE_LEAF, 15)], [(NODE_LEAF, 15), (NODE_LEAF, 15)], [(NODE_LEAF, 3), (NODE_LEAF, 7), (2, 0)]]
+    for _ in range(40):
+        path = [(NODE_LEAF, rng.randrange(16)) for _ in range(rng.randint(0, 2))]
+        path.append((rng.choice([2, 3]), 0))
+        paths.append(path)
+    for path in paths:
+        a = p.resolve(path)
+        assert a == p.verify_chain(path) == oracle.image_resolve(t.schema, img, base, path)
+    deep = tg.workload("deep")
+    q = dc.Plan(deep.schema, deep.root)
+    q.bind()
+    q.deep_copy()
+    q.sync()
+    image_ok(q, deep.schema, deep.root)
+    path = tg.leaf_path(64) + [(2, (1 << 26) - 1)]
+    assert q.resolve(path) == q.verify_chain(path) == oracle.image_resolve(deep.schema, q.image(), q.device_base, path)
+    p.destroy()
+    q.destroy()
+
+
+def test_kernels_are_launched_by_the_library():
+    n0 = dc.kernel_launches()
+    full_parity(lambda: tg.node_tree(2, 3, 100, seed=1), {})
+    assert dc.kernel_launches() >= n0 + 2
+
+
+def test_stream_ordering_on_a_side_stream():
+    src, ref = tg.workload("tiny"), tg.workload("tiny")
+    s = src.schema
+    st = torch.cuda.Stream()
+    p = dc.Plan(s, src.root)
+    p.bind(stream=st)
+    with torch.cuda.stream(st):
+        p.deep_copy(stream=st)
+        p.update(dc.Op(), stream=st)
+        p.copy_back(stream=st)
+    cp = oracle.deep_copy(s, ref.root)
+    oracle.update(s, cp.root, oracle.Op())
+    oracle.copy_back(s, cp.root, ref.root, oracle.Op())
+    assert oracle.trees_equal(s, src.root, ref.root)[0]
+    p.destroy()
