@@ -244,6 +244,36 @@ dc_status dc_uvm_copy_back(dc_uvm_t uvm, const void* host_root, uint32_t flags);
 dc_status dc_uvm_sync(dc_uvm_t uvm, dc_stream_t stream);
 dc_status dc_uvm_destroy(dc_uvm_t uvm);
 
+/* ---- relocation that allocates nothing ---------------------------------------
+ * The paper has no counterpart of this call; it exists for callers that
+ * cannot allocate memory at the point where they relocate.  Examples: code
+ * embedded in an application whose device memory is handed out only by that
+ * application's own pool (a cudaMalloc there would bypass its accounting or
+ * fail under its cap), or a hot path that must not allocate because
+ * cudaMalloc/cudaFree can synchronize the whole device.  Such a caller owns
+ * only the device copy of the data region (info.data_bytes, holding the
+ * marshalled image, e.g. from its own copy of dc_deep_copy's transfer).
+ *
+ * dc_relocate_static does dc_relocate's work on `dev_data` (16-byte aligned,
+ * at least data_bytes long; pointers become dev_data + block offset) with all
+ * of its scratch in one fixed device array of DC_STATIC_SCRATCH_BYTES bytes
+ * inside the library, which every GPU that loads the library keeps until the
+ * process exits.  Limits: plans of at most DC_STATIC_MAX_BLOCKS blocks
+ * (DC_EBUDGET otherwise); no DC_PLAN_VERIFY check.  It calls no cudaMalloc,
+ * cudaHostAlloc, cudaFree or other allocating routine.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the array and the array
+ * keeps the previous call's contents (the call clears what must start at
+ * zero), so calls whose work overlaps on the GPU race: order them on one
+ * stream.  If `dev_status` is not NULL, the device word it points to receives
+ * the kernel's error bits once the work completes (0 = success, 1 = an offset
+ * outside the buffers, 2 = a device-side wait gave up). */
+#define DC_STATIC_MAX_BLOCKS 65536u
+#define DC_STATIC_SCRATCH_BYTES 1573888u /* 1 MiB block records + 512 KiB offsets + look-back/control words */
+dc_status dc_relocate_static(dc_plan_t plan, void* dev_data, uint64_t data_bytes, uint32_t* dev_status,
+                             dc_stream_t stream);
+
 /* ---- misc ------------------------------------------------------------------ */
 const char* dc_last_error(void);
 const char* dc_status_name(dc_status s);

@@ -86,6 +86,7 @@ SIGNATURES = {
     "dc_bind_device": [_vp, _vp, _u64, _vp],
     "dc_deep_copy": [_vp, _vp],
     "dc_relocate": [_vp, _vp],
+    "dc_relocate_static": [_vp, _vp, _u64, _vp, _vp],
     "dc_resolve_chain": [_vp, _P(_Step), _u32, _P(_u64)],
     "dc_resolve_offset": [_vp, _P(_Step), _u32, _P(_u64)],
     "dc_update_leaves": [_vp, _P(_Op), _vp],

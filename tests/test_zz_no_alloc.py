@@ -1,0 +1,94 @@
+"""dc_relocate_static, the relocation entry point that allocates nothing.
+
+It serves callers that cannot allocate memory where they relocate: code whose
+device memory is handed out by another application's pool (a cudaMalloc of
+its own would escape that pool's accounting or fail under its cap), or a hot
+path that must not allocate because cudaMalloc/cudaFree can synchronize the
+whole device.  The call takes only the device data region and keeps its
+scratch in a fixed array inside the library.
+
+These tests call it through the C ABI and require the same bytes as
+dc_relocate (bit for bit: relocation is integer work) on two calls in a row.
+The file is named so that pytest collects it last."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import treegen as tg
+import paper_1906_01128_b300 as dc
+
+pytestmark = pytest.mark.gpu
+
+
+def marshalled_image(plan) -> np.ndarray:
+    """The data region as the marshal leaves it: every block copied verbatim
+    (host pointers still in the slots) to its arena offset."""
+    img = np.zeros(plan.info["data_bytes"], dtype=np.uint8)
+    for b in plan.blocks():
+        if b["bytes"]:
+            img[b["offset"]:b["offset"] + b["bytes"]] = np.frombuffer(ctypes.string_at(b["host"], b["bytes"]),
+                                                                     dtype=np.uint8)
+    return img
+
+
+def relocate_static(plan, ptr, nbytes, status):
+    stream = torch.cuda.current_stream().cuda_stream
+    rc = dc.lib.dc_relocate_static(plan._h, ptr, nbytes, status.data_ptr() if status is not None else None,
+                                   stream)
+    return rc
+
+
+@pytest.mark.parametrize("make", [
+    lambda: tg.workload("dense"),                       # 564 blocks, one look-back tile
+    lambda: tg.node_tree(4, 16, tg.uniform(1, 40), seed=21),  # ~13,000 blocks, 13 tiles
+], ids=["dense", "multi_tile"])
+def test_static_scratch_matches_dc_relocate_twice(make):
+    t = make()
+    plan = dc.Plan(t.schema, t.root)
+    buf = plan.bind()
+    n = plan.info["data_bytes"]
+    image = torch.from_numpy(marshalled_image(plan)).cuda()
+    # reference: the existing entry point on the same buffer
+    buf[:n].copy_(image)
+    plan.relocate()
+    plan.sync()
+    want = buf[:n].cpu()
+    ok, msg, _ = oracle.check_image(t.schema, t.root, want.numpy(), buf.data_ptr())
+    assert ok, msg
+    status = torch.empty(1, dtype=torch.int32, device="cuda")
+    for call in range(2):
+        buf[:n].copy_(image)  # back to host pointers in every slot
+        status.fill_(-1)
+        assert relocate_static(plan, buf.data_ptr(), n, status) == 0, dc.lib.dc_last_error()
+        torch.cuda.synchronize()
+        assert status.item() == 0, call
+        got = buf[:n].cpu()
+        assert torch.equal(got, want), f"call {call}: bytes differ from dc_relocate"
+    # a buffer of the caller's own: pointers now point into that buffer
+    other = torch.empty(n + 256, dtype=torch.uint8, device="cuda")
+    other[:n].copy_(image)
+    assert relocate_static(plan, other.data_ptr(), n, None) == 0
+    torch.cuda.synchronize()
+    ok, msg, _ = oracle.check_image(t.schema, t.root, other[:n].cpu().numpy(), other.data_ptr())
+    assert ok, msg
+    plan.destroy()
+    t.free()
+
+
+def test_static_scratch_rejects_plans_beyond_its_limit():
+    t = tg.node_tree(5, 16, 3, seed=1)  # 69,905 nodes: more blocks than the array holds
+    plan = dc.Plan(t.schema, t.root)
+    assert plan.info["nblocks"] > 65536
+    dummy = torch.empty(256, dtype=torch.uint8, device="cuda")
+    rc = relocate_static(plan, dummy.data_ptr(), plan.info["data_bytes"], None)
+    assert dc.STATUS[rc] == "DC_EBUDGET"
+    assert b"at most 65536" in dc.lib.dc_last_error()
+    small = tg.workload("tiny")
+    p2 = dc.Plan(small.schema, small.root)
+    rc = relocate_static(p2, dummy.data_ptr(), 256, None)  # region smaller than the plan's
+    assert dc.STATUS[rc] == "DC_EINVAL"
+    for x in (plan, p2):
+        x.destroy()
