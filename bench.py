@@ -29,10 +29,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "deep-copy GB/s vs link peak; leaf kernel HBM %; batched/served speedup, p50/p99"
-WORKLOAD = "dense"
-WORKLOAD_DESC = ("dense tree: 3 levels, fanout 16 (273 nodes), node {int32 n; int32 nchild; float* position; "
-                 "float* velocity; Node* child}, array lengths lognormal(median 65,536, sigma 1.2, cap 4,194,304), "
-                 "fp32 values uniform in [-1,1), seed 2")
+NODE = "node {int32 n; int32 nchild; float* position; float* velocity; Node* child}"
+WORKLOADS = {
+    "dense": ("dense tree: 3 levels, fanout 16 (273 nodes), " + NODE + ", array lengths lognormal(median 65,536, "
+              "sigma 1.2, cap 4,194,304), fp32 values uniform in [-1,1), seed 2"),
+    "tiny": "tiny chain: 4 levels, fanout 1, " + NODE + ", 65,536 fp32 per array, seed 1",
+    "deep": ("deep chain: 64 levels, fanout 1, " + NODE + ", 1,024 fp32 per interior array, 2^26 at the leaf, "
+             "update through the 63-step chain to the leaf, seed 3"),
+    "reloc_stress": ("pointer-heavy tree: 6 levels, fanout 16 (1,118,481 nodes), " + NODE + ", 10 fp32 per array "
+                     "(the paper's n = 10 Dense case), seed 6"),
+}
 
 
 def peaks():
@@ -51,7 +57,7 @@ class Clocks:
         self.proc = None
         self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks.csv")
 
-    def start(self):
+    def start(self, wait_s: float = 5.0):
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
@@ -59,7 +65,10 @@ class Clocks:
                 ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+                 "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
+            t0 = time.time()  # the timed region starts once the sampler is producing
+            while time.time() - t0 < wait_s and os.path.getsize(self.path) == 0:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
 
@@ -100,10 +109,10 @@ def run_reference(args, rank, world):
     import treegen as tg
     if rank != 0:
         return
-    t = tg.workload(WORKLOAD)
+    t = tg.workload(args.workload)
     s = t.schema
     payload = t.payload_bytes
-    op = oracle.Op()
+    op = oracle_op(args.workload)
     times = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -122,16 +131,24 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / len(times), 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "payload_bytes": payload},
+        "config": {"workload": WORKLOADS[args.workload], "payload_bytes": payload},
         "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
 
-def oracle_baseline(tree, budget_s=10.0):
+def oracle_op(workload):
+    import oracle
+    import treegen as tg
+    if workload == "deep":
+        return oracle.Op(sel=oracle.SEL_CHAIN, path=tg.leaf_path(64))
+    return oracle.Op()
+
+
+def oracle_baseline(tree, workload, budget_s=10.0):
     import oracle
     s = tree.schema
-    op = oracle.Op()
+    op = oracle_op(workload)
     n, t_total = 0, 0.0
     while n < 3 or (t_total < budget_s and n < 200):
         t0 = time.perf_counter()
@@ -171,6 +188,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="dense", choices=sorted(WORKLOADS))
     ap.add_argument("--no-compare", action="store_true", help="skip the chase / UVM comparison paths")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     args = ap.parse_args()
@@ -191,7 +209,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
     # each rank deep-copies its own independent tree (weak scaling, no data-path collective)
-    tree = tg.node_tree(*tg.WORKLOADS[WORKLOAD][:4], seed=tg.WORKLOADS[WORKLOAD][4] + rank)
+    tree = tg.node_tree(*tg.WORKLOADS[args.workload][:4], seed=tg.WORKLOADS[args.workload][4] + rank)
     s = tree.schema
     payload = tree.payload_bytes
     nelem = tree.nelems("Node", "position")
@@ -199,7 +217,11 @@ def main():
     plan = dc.Plan(s, tree.root)
     plan.bind()
     info = plan.info
-    op = dc.Op()
+    if args.workload == "deep":  # only the leaf carries the long arrays: update through its chain
+        op = dc.Op(sel=dc.SEL_CHAIN, path=tg.leaf_path(64))
+        nelem = 1 << 26
+    else:
+        op = dc.Op()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
 
     def barrier():
@@ -217,14 +239,14 @@ def main():
     plan.deep_copy()
     plan.sync()
 
+    clocks = Clocks()
+    clocks.start()
     # ---- device-resident step: relocation + leaf update --------------------
     for _ in range(args.warmup):
         flush.zero_()
         plan.relocate()
         plan.update(op)
     barrier()
-    clocks = Clocks()
-    clocks.start()
     launches0 = dc.kernel_launches()
     ev = []
     for _ in range(args.steps):
@@ -238,7 +260,6 @@ def main():
         ev.append(e)
     barrier()
     launches = dc.kernel_launches() - launches0
-    clk = clocks.stop()
     plan.sync()
     t_reloc = [a.elapsed_time(b) * 1e-3 for a, b, c in ev]
     t_leaf = [b.elapsed_time(c) * 1e-3 for a, b, c in ev]
@@ -284,6 +305,7 @@ def main():
         t1 = time.perf_counter()
         if i >= args.warmup:
             t_cb.append(t1 - t0)
+    clk = clocks.stop()
     e2e_t = max_over_ranks(statistics.mean(t_e2e))
     e2e = {"value": round(payload * world / e2e_t / 1e9, 3), "unit": "GB/s",
            "h2d_bytes_per_step": info["data_bytes"], "d2h_bytes_per_step": 4 * nelem,
@@ -334,14 +356,14 @@ def main():
         compare["uvm_prefetched_kernel_ms"] = round(statistics.median(pref), 3)
         u.destroy()
 
-    cpu = None if (args.no_cpu or rank != 0) else oracle_baseline(tree)
+    cpu = None if (args.no_cpu or rank != 0) else oracle_baseline(tree, args.workload)
 
     if rank == 0:
         out = {
             "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(1e3 * t_step / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC, "nodes": info["nstructs"], "blocks": info["nblocks"],
+            "config": {"workload": WORKLOADS[args.workload], "nodes": info["nstructs"], "blocks": info["nblocks"],
                        "payload_bytes": payload, "arena_bytes": info["data_bytes"], "elements": nelem,
                        "step": "dc_relocate + dc_update_leaves on the resident arena",
                        "l2": "flushed: 512 MiB write before every timed step (outside the events)",
