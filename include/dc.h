@@ -22,8 +22,9 @@
  *     failed relocation check) are recorded in a device word and reported by
  *     the next dc_sync() (or dc_copy_back()) on that plan.
  *   - Ownership: the caller owns the host tree and must not change its shape
- *     (pointers, counts) between dc_plan and the last call on the plan, nor
- *     its array contents while dc_deep_copy runs.  The caller owns the device
+ *     (pointers, counts) or free it before dc_plan_destroy, nor write its
+ *     arrays while a dc_deep_copy is in flight (until dc_sync, or any later
+ *     blocking call on the same stream).  The caller owns the device
  *     buffer given to dc_bind_device (e.g. a torch uint8 tensor).  The library
  *     owns the plan's tables, its pinned staging arena and managed trees;
  *     dc_plan_destroy / dc_uvm_destroy free them.
@@ -132,9 +133,15 @@ typedef struct {
   uint64_t root_offset;    /* offset of the root struct in the data region (0) */
 } dc_plan_info;
 
-/* Plan flags (dc_plan_set_flags). */
+/* Plan flags (dc_plan_set_flags, before dc_bind_device). */
 #define DC_PLAN_VERIFY 1u /* relocation also checks that every slot still holds the
                              host address the plan recorded (DC_EVERIFY otherwise) */
+#define DC_PLAN_STAGED 2u /* move every block through the pinned arena; by default
+                             arrays of DC_DIRECT_MIN_BYTES or more are transferred
+                             straight from / to their own host pages, which
+                             dc_bind_device page-locks (cudaHostRegister) until
+                             dc_plan_destroy */
+#define DC_DIRECT_MIN_BYTES (256u << 10)
 
 /* dc_plan — walk the host structure from `host_root` (one struct of
  * schema->root_type) and lay out its device arena (Algorithm 1's first step,
@@ -165,13 +172,16 @@ dc_status dc_plan_destroy(dc_plan_t plan);
  * Errors: DC_EBUDGET, DC_EINVAL (misaligned), DC_ENOMEM, DC_ECUDA. */
 dc_status dc_bind_device(dc_plan_t plan, void* dev_buffer, uint64_t bytes, dc_stream_t stream);
 
-/* dc_deep_copy — marshal every block into the pinned arena (Algorithm 1:
- * one contiguous buffer), copy it to the device in one stream-ordered pass
- * (Fig 2 steps b-c), then run the relocation kernel, which rebuilds every
- * pointer slot to the device address of its target (Fig 2 step d; Algorithm
- * 1's attach loop).  Returns once the marshal is done and the copies and the
- * kernel are queued; the host tree may change afterwards.  Errors: DC_ESTATE
- * (nothing bound), DC_ECUDA. */
+/* dc_deep_copy — move the tree into the arena (Fig 2 steps b-c), then run
+ * the relocation kernel, which rebuilds every pointer slot to the device
+ * address of its target (Fig 2 step d; Algorithm 1's attach loop).  Struct
+ * blocks and small arrays are marshalled into the pinned arena (Algorithm 1:
+ * one contiguous buffer) and sent in chunks overlapped with the marshal;
+ * large arrays go by DMA straight from their host pages into their arena
+ * slot, one transfer per array (the paper's pointerchain transfer scheme,
+ * Sec. 4.1.1 item 3), unless the plan has DC_PLAN_STAGED.  Returns once the
+ * copies and the kernel are queued; large arrays are read by the DMA until the
+ * stream gets there.  Errors: DC_ESTATE (nothing bound), DC_ECUDA. */
 dc_status dc_deep_copy(dc_plan_t plan, dc_stream_t stream);
 
 /* dc_relocate — the relocation kernel of dc_deep_copy alone (Fig 2 step d):

@@ -72,7 +72,7 @@ enum CtrlWord : uint32_t { CTRL_TILE = 0, CTRL_DONE = 1, CTRL_ERR = 2, CTRL_WORD
 enum DeviceErr : uint32_t { ERR_BOUNDS = 1u, ERR_TIMEOUT = 2u, ERR_VERIFY = 4u };
 
 constexpr uint32_t RELOC_THREADS = 256;
-constexpr uint32_t RELOC_ITEMS = 4;  // blocks per thread
+constexpr uint32_t RELOC_ITEMS = 8;  // blocks per thread
 constexpr uint32_t RELOC_TILE = RELOC_THREADS * RELOC_ITEMS;
 constexpr uint32_t EPOCH_LIMIT = (1u << 22) - 1;
 
@@ -90,8 +90,13 @@ struct RelocArgs {
   uint32_t nblocks, nstruct_blocks, ntiles, epoch, verify;
 };
 
+constexpr uint32_t LEAF_THREADS = 256;
+constexpr uint32_t LEAF_UNROLL = 4;
+constexpr uint32_t LEAF_TILE = LEAF_THREADS * LEAF_UNROLL;  // 16-byte units per tile
+
 struct LeafArgs {
   const Segment* seg;
+  const uint32_t* tile_seg;  // per tile: the segment holding its first unit; one extra entry = nseg - 1
   uint32_t nseg;
   uint64_t units;  // total 16-byte units
   int kind;        // dc_op_kind
@@ -147,8 +152,8 @@ dc_status copy_schema(const dc_schema* s, SchemaCopy* out);
 // Layout of the caller's device buffer (byte offsets).
 struct DevLayout {
   uint64_t data = 0, rec = 0, hostp = 0, soff = 0, status = 0, ready = 0, ctrl = 0;
-  uint64_t seg = 0, cseg = 0, steps = 0, walk = 0, total = 0;
-  uint64_t seg_cap = 0, step_cap = 0, walk_cap = 0, ntiles = 0;
+  uint64_t seg = 0, tseg = 0, cseg = 0, steps = 0, walk = 0, total = 0;
+  uint64_t seg_cap = 0, tseg_cap = 0, step_cap = 0, walk_cap = 0, ntiles = 0;
 };
 
 struct OpKey {
@@ -190,11 +195,27 @@ struct dc_plan_s {
   std::vector<uint32_t> leaf_written, chase_written;
   bool op_run = false;
   std::unique_ptr<dc::Pool> pool;
-  // marshal work: pieces of blocks, grouped into transfer chunks of the data region
-  struct Piece { uint64_t off, len; const uint8_t* src; };
-  struct Chunk { uint64_t lo, hi, first, last; };
-  std::vector<Piece> pieces;
-  std::vector<Chunk> chunks;
+  // transfer plan, built at the first bind: large arrays move by DMA straight
+  // between their (registered) host pages and the arena; everything else is
+  // marshalled into the pinned arena in pieces, handed out to host threads in
+  // units, and sent in chunks of staged runs
+  struct Piece { uint64_t off, len; uint8_t* host; };
+  struct Unit { uint64_t first, last; };  // pieces [first, last)
+  struct Copy { uint64_t lo, hi; };       // a run of the data region
+  struct Chunk { uint64_t ufirst, ulast, cfirst, clast; };
+  struct Moves {                          // what one transfer direction moves
+    std::vector<uint32_t> direct;         // blocks copied straight to / from host memory
+    std::vector<Piece> pieces;            // staged blocks, in pieces
+    std::vector<Unit> units;
+    std::vector<Copy> copies;             // staged runs (clipped to chunks)
+    std::vector<Chunk> chunks;
+  };
+  bool transfers_ready = false;
+  std::vector<uint8_t> direct;            // per block
+  std::vector<std::pair<void*, uint64_t>> registered;  // host spans this plan registered
+  Moves h2d;                              // everything, for dc_deep_copy
+  std::vector<uint32_t> back_key;         // the block list `back` was built for
+  Moves back;                             // the last copy-back's blocks
 };
 
 struct dc_uvm_s {

@@ -64,6 +64,50 @@ __device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, uint32_t lane) {
   return v;
 }
 
+// Warp 0 of a CTA: publish this tile's aggregate, then look back over the
+// predecessors 32 at a time until a tile with an inclusive prefix is found
+// (decoupled look-back).  Returns the exclusive prefix (lane 0 publishes the
+// inclusive one).  Every wait is bounded; on a timeout the error word is set.
+__device__ uint64_t look_back(const RelocArgs& a, uint32_t t, uint64_t tile_sum, uint32_t lane) {
+  uint32_t* err = &a.ctrl[CTRL_ERR];
+  if (t == 0) {
+    if (lane == 0) st_release(&a.status[0], pack(a.epoch, FLAG_PREFIX, tile_sum));
+    return 0;
+  }
+  if (lane == 0) st_release(&a.status[t], pack(a.epoch, FLAG_AGG, tile_sum));
+  uint64_t prefix = 0;
+  int64_t top = (int64_t)t - 1;  // window: predecessors top, top-1, ..., top-31
+  uint32_t spins = 0;
+  while (top >= 0) {
+    const int64_t j = top - (int64_t)lane;
+    uint32_t fl = FLAG_PREFIX;  // before tile 0: an empty prefix
+    uint64_t v = 0;
+    if (j >= 0) {
+      unsigned long long w = ld_acquire(&a.status[j]);
+      fl = ((uint32_t)(w >> 42) == a.epoch) ? (uint32_t)(w >> 40) & 3u : 0u;
+      v = w & ((1ull << 40) - 1);
+    }
+    if (__any_sync(0xffffffffu, fl == 0)) {
+      if (++spins > SPIN_LIMIT || (ld_relaxed(err) & ERR_TIMEOUT)) {
+        if (lane == 0) atomicOr(err, ERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(32);
+      continue;
+    }
+    const uint32_t pmask = __ballot_sync(0xffffffffu, fl == FLAG_PREFIX);
+    const uint32_t stop = pmask ? (uint32_t)(__ffs(pmask) - 1) : 31u;  // closest prefix in the window
+    uint64_t part = lane <= stop ? v : 0;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) part += __shfl_xor_sync(0xffffffffu, part, d);
+    prefix += part;
+    if (pmask) break;
+    top -= 32;
+  }
+  if (lane == 0) st_release(&a.status[t], pack(a.epoch, FLAG_PREFIX, prefix + tile_sum));
+  return prefix;
+}
+
 __global__ void __launch_bounds__(RELOC_THREADS) relocate_kernel(RelocArgs a) {
   constexpr uint32_t NW = RELOC_THREADS / 32;
   __shared__ uint64_t s_off[RELOC_TILE];
@@ -72,6 +116,7 @@ __global__ void __launch_bounds__(RELOC_THREADS) relocate_kernel(RelocArgs a) {
   __shared__ uint32_t s_tile;
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t* err = &a.ctrl[CTRL_ERR];
+  uint32_t ready_tile = NONE;  // last parent tile this thread saw ready
 
   for (;;) {
     if (tid == 0) s_tile = atomicAdd(&a.ctrl[CTRL_TILE], 1u);
@@ -102,40 +147,12 @@ __global__ void __launch_bounds__(RELOC_THREADS) relocate_kernel(RelocArgs a) {
       uint64_t w = lane < NW ? s_warp[lane] : 0;
       w = warp_incl_scan(w, lane);
       if (lane < NW) s_warp[lane] = w;
+      __syncwarp();
+      const uint64_t pre = look_back(a, t, __shfl_sync(0xffffffffu, w, NW - 1), lane);
+      if (lane == 0) s_prefix = pre;
     }
     __syncthreads();
-    const uint64_t tile_sum = s_warp[NW - 1];
-    uint64_t excl = (warp ? s_warp[warp - 1] : 0) + incl - local;
-
-    // decoupled look-back across tiles
-    if (tid == 0) {
-      uint64_t prefix = 0;
-      if (t == 0) {
-        st_release(&a.status[0], pack(a.epoch, FLAG_PREFIX, tile_sum));
-      } else {
-        st_release(&a.status[t], pack(a.epoch, FLAG_AGG, tile_sum));
-        int64_t j = (int64_t)t - 1;
-        uint32_t spins = 0;
-        while (j >= 0) {
-          unsigned long long w = ld_acquire(&a.status[j]);
-          uint32_t ep = (uint32_t)(w >> 42), fl = (uint32_t)(w >> 40) & 3u;
-          if (ep != a.epoch || fl == 0) {
-            if (++spins > SPIN_LIMIT || (ld_relaxed(err) & ERR_TIMEOUT)) {
-              atomicOr(err, ERR_TIMEOUT);
-              break;
-            }
-            __nanosleep(64);
-            continue;
-          }
-          prefix += w & ((1ull << 40) - 1);
-          if (fl == FLAG_PREFIX) break;
-          j--;
-        }
-        st_release(&a.status[t], pack(a.epoch, FLAG_PREFIX, prefix + tile_sum));
-      }
-      s_prefix = prefix;
-    }
-    __syncthreads();
+    const uint64_t excl = (warp ? s_warp[warp - 1] : 0) + incl - local;
 
     // byte offsets of this thread's blocks; struct blocks publish theirs
     uint64_t o16 = s_prefix + excl;
@@ -169,17 +186,20 @@ __global__ void __launch_bounds__(RELOC_THREADS) relocate_kernel(RelocArgs a) {
         poff = s_off[p - base];
       } else {
         const uint32_t pt = p / RELOC_TILE;
-        uint32_t spins = 0;
-        bool ok = true;
-        while (ld_acquire(&a.ready[pt]) != a.epoch) {
-          if (++spins > SPIN_LIMIT || (ld_relaxed(err) & ERR_TIMEOUT)) {
-            atomicOr(err, ERR_TIMEOUT);
-            ok = false;
-            break;
+        if (pt != ready_tile) {
+          uint32_t spins = 0;
+          bool ok = true;
+          while (ld_acquire(&a.ready[pt]) != a.epoch) {
+            if (++spins > SPIN_LIMIT || (ld_relaxed(err) & ERR_TIMEOUT)) {
+              atomicOr(err, ERR_TIMEOUT);
+              ok = false;
+              break;
+            }
+            __nanosleep(32);
           }
-          __nanosleep(64);
+          if (!ok) continue;
+          ready_tile = pt;
         }
-        if (!ok) continue;
         poff = *(volatile const uint64_t*)&a.soff[p];
       }
       uint64_t slot = poff + r[k].slot_off;
@@ -206,10 +226,6 @@ __global__ void __launch_bounds__(RELOC_THREADS) relocate_kernel(RelocArgs a) {
 }
 
 // ---- leaf update over resolved segments -------------------------------------
-
-constexpr uint32_t LEAF_THREADS = 256;
-constexpr uint32_t LEAF_UNROLL = 4;
-constexpr uint32_t LEAF_TILE = LEAF_THREADS * LEAF_UNROLL;  // 16-byte units per tile
 
 template <typename T>
 struct V16;
@@ -256,35 +272,30 @@ template <typename T, int KIND>
 __global__ void __launch_bounds__(LEAF_THREADS) leaf_kernel(LeafArgs a) {
   using VT = typename V16<T>::type;
   constexpr int EPU = V16<T>::N;
-  __shared__ uint32_t s_lo, s_hi;
   const T sc = (T)a.scale;
   const Segment* seg = a.seg;
-  auto ub = [&](uint32_t s) { return seg[s].ubeg; };
-  for (uint64_t u0 = (uint64_t)blockIdx.x * LEAF_TILE; u0 < a.units; u0 += (uint64_t)gridDim.x * LEAF_TILE) {
-    if (threadIdx.x == 0) {
-      uint64_t last = min(u0 + LEAF_TILE, a.units) - 1;
-      s_lo = search(0, a.nseg - 1, u0, ub);
-      s_hi = search(s_lo, a.nseg - 1, last, ub);
-    }
-    __syncthreads();
-    const uint32_t lo = s_lo, hi = s_hi;
+  auto ub = [&](uint32_t s) { return __ldg(&seg[s].ubeg); };
+  for (uint64_t t = blockIdx.x; t * LEAF_TILE < a.units; t += gridDim.x) {
+    const uint64_t u0 = t * LEAF_TILE;
+    // the tile's segments are [lo, hi]; most tiles lie inside one segment
+    const uint32_t lo = __ldg(&a.tile_seg[t]), hi = __ldg(&a.tile_seg[t + 1]);
     VT xv[LEAF_UNROLL], yv[LEAF_UNROLL];
     VT* xp[LEAF_UNROLL];
     const VT* yp[LEAF_UNROLL];
-    uint32_t tail[LEAF_UNROLL];  // elements of a partial unit; EPU = full vector
+    uint32_t tail[LEAF_UNROLL];  // elements of this unit; EPU = a full vector
 #pragma unroll
     for (uint32_t k = 0; k < LEAF_UNROLL; k++) {
-      uint64_t u = u0 + threadIdx.x + k * LEAF_THREADS;
+      const uint64_t u = u0 + threadIdx.x + k * LEAF_THREADS;
       tail[k] = 0;
       xp[k] = nullptr;
       yp[k] = nullptr;
       if (u >= a.units) continue;
-      uint32_t s = lo == hi ? lo : search(lo, hi, u, ub);
+      const uint32_t s = lo == hi ? lo : search(lo, hi, u, ub);
       const Segment g = seg[s];
-      uint64_t e0 = (u - g.ubeg) * EPU;
+      const uint64_t e0 = (u - g.ubeg) * EPU;
       xp[k] = reinterpret_cast<VT*>(g.x + e0 * sizeof(T));
       yp[k] = reinterpret_cast<const VT*>(g.y + e0 * sizeof(T));
-      uint64_t left = g.n - e0;
+      const uint64_t left = g.n - e0;
       tail[k] = left >= (uint64_t)EPU ? EPU : (uint32_t)left;
     }
 #pragma unroll
@@ -308,7 +319,6 @@ __global__ void __launch_bounds__(LEAF_THREADS) leaf_kernel(LeafArgs a) {
         for (uint32_t i = 0; i < tail[k]; i++) x[i] = apply<T, KIND>(x[i], KIND == DC_OP_AXPY_HALF ? y[i] : T(0), sc);
       }
     }
-    __syncthreads();
   }
 }
 

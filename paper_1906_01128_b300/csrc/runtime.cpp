@@ -44,6 +44,10 @@ DevLayout make_layout(const dc_plan_s* p) {
   L.seg_cap = std::max<uint64_t>(1, p->nstructs);
   L.seg = o;
   o = align256(o + L.seg_cap * sizeof(Segment));
+  // every segment has at least one 16-byte unit and lives in the data region
+  L.tseg_cap = p->data_bytes / 16 / LEAF_TILE + 2;
+  L.tseg = o;
+  o = align256(o + L.tseg_cap * 4);
   L.cseg = o;
   o = align256(o + L.seg_cap * sizeof(ChaseSeg));
   L.step_cap = std::max<uint64_t>(1, p->sum_depth);
@@ -56,9 +60,10 @@ DevLayout make_layout(const dc_plan_s* p) {
   return L;
 }
 
-// pinned table staging: [segments][chase segments][chase steps][walk steps][words]
+// pinned table staging: [segments][tile table][chase segments][chase steps][walk steps][words]
 uint64_t tab_seg(const DevLayout& L) { (void)L; return 0; }
-uint64_t tab_cseg(const DevLayout& L) { return align256(L.seg_cap * sizeof(Segment)); }
+uint64_t tab_tseg(const DevLayout& L) { return align256(L.seg_cap * sizeof(Segment)); }
+uint64_t tab_cseg(const DevLayout& L) { return tab_tseg(L) + align256(L.tseg_cap * 4); }
 uint64_t tab_steps(const DevLayout& L) { return tab_cseg(L) + align256(L.seg_cap * sizeof(ChaseSeg)); }
 uint64_t tab_walk(const DevLayout& L) { return tab_steps(L) + align256(L.step_cap * sizeof(ChaseStep)); }
 uint64_t tab_words(const DevLayout& L) { return tab_walk(L) + align256(L.walk_cap * sizeof(ChaseStep)); }
@@ -75,22 +80,116 @@ Pool& pool_of(dc_plan_s* p) {
   return *p->pool;
 }
 
-void build_pieces(dc_plan_s* p) {
-  p->pieces.clear();
-  p->chunks.clear();
-  for (const HostBlock& b : p->blocks)
-    for (uint64_t o = 0; o < b.bytes; o += PIECE_BYTES)
-      p->pieces.push_back({b.off + o, std::min(PIECE_BYTES, b.bytes - o), b.host + o});
-  uint64_t first = 0, lo = 0;
-  for (uint64_t i = 0; i < p->pieces.size(); i++) {
-    uint64_t end = p->pieces[i].off + p->pieces[i].len;
-    bool last = i + 1 == p->pieces.size();
-    if (end - lo >= CHUNK_BYTES || last) {
-      uint64_t hi = last ? p->data_bytes : p->pieces[i + 1].off;
-      p->chunks.push_back({lo, hi, first, i + 1});
-      lo = hi;
-      first = i + 1;
+constexpr uint64_t UNIT_BYTES = 1ull << 20;  // host work handed out at once
+constexpr uint64_t UNIT_PIECES = 4096;
+
+// Pieces, work units, staged runs and chunks for moving `list` (arena indices,
+// ascending).  Blocks marked direct are listed apart and moved by their own DMA.
+void plan_moves(const dc_plan_s* p, const std::vector<uint32_t>& list, dc_plan_s::Moves* m) {
+  *m = dc_plan_s::Moves();
+  for (size_t i = 0; i < list.size(); i++) {
+    const HostBlock& B = p->blocks[list[i]];
+    if (p->direct[list[i]]) {
+      m->direct.push_back(list[i]);
+      continue;
     }
+    for (uint64_t o = 0; o < B.bytes; o += PIECE_BYTES)
+      m->pieces.push_back({B.off + o, std::min(PIECE_BYTES, B.bytes - o), const_cast<uint8_t*>(B.host) + o});
+  }
+  for (uint64_t i = 0; i < m->pieces.size();) {  // units of ~1 MiB or 4096 pieces
+    uint64_t j = i, bytes = 0;
+    while (j < m->pieces.size() && bytes < UNIT_BYTES && j - i < UNIT_PIECES) bytes += m->pieces[j++].len;
+    m->units.push_back({i, j});
+    i = j;
+  }
+  // staged runs: adjacent staged blocks of the list travel as one copy
+  std::vector<dc_plan_s::Copy> runs;
+  for (size_t i = 0; i < list.size();) {
+    if (p->direct[list[i]]) {
+      i++;
+      continue;
+    }
+    uint64_t lo = p->blocks[list[i]].off, hi = lo + p->blocks[list[i]].bytes;
+    size_t j = i + 1;
+    while (j < list.size() && list[j] == list[j - 1] + 1 && !p->direct[list[j]]) {
+      hi = p->blocks[list[j]].off + p->blocks[list[j]].bytes;
+      j++;
+    }
+    if (hi > lo) runs.push_back({lo, hi});
+    i = j;
+  }
+  // chunks of ~CHUNK_BYTES of staged data: marshal a chunk, send it, go on
+  size_t r = 0;
+  for (uint64_t u = 0; u < m->units.size();) {
+    uint64_t v = u, bytes = 0;
+    while (v < m->units.size() && bytes < CHUNK_BYTES) {
+      for (uint64_t k = m->units[v].first; k < m->units[v].last; k++) bytes += m->pieces[k].len;
+      v++;
+    }
+    const uint64_t lo = m->pieces[m->units[u].first].off;
+    const uint64_t hi = v < m->units.size() ? m->pieces[m->units[v].first].off : ~0ull;
+    const uint64_t cfirst = m->copies.size();
+    while (r < runs.size() && runs[r].lo < hi) {
+      const uint64_t a = std::max(runs[r].lo, lo), b = std::min(runs[r].hi, hi);
+      if (b > a) m->copies.push_back({a, b});
+      if (runs[r].hi <= hi) r++;
+      else break;
+    }
+    m->chunks.push_back({u, v, cfirst, m->copies.size()});
+    u = v;
+  }
+}
+
+// Decide which arrays move by direct DMA and page-lock their host spans.
+void plan_transfers(dc_plan_s* p) {
+  const uint64_t nb = p->blocks.size();
+  p->direct.assign(nb, 0);
+  if (!(p->flags & DC_PLAN_STAGED)) {
+    const uint64_t page = 4096;
+    std::vector<uint32_t> cand;
+    for (uint32_t b = 0; b < nb; b++)
+      if (p->blocks[b].lane != 0 && p->blocks[b].bytes >= DC_DIRECT_MIN_BYTES) cand.push_back(b);
+    std::sort(cand.begin(), cand.end(), [&](uint32_t a, uint32_t b) { return p->blocks[a].host < p->blocks[b].host; });
+    for (size_t i = 0; i < cand.size();) {  // merge overlapping page spans, register each once
+      uintptr_t lo = (uintptr_t)p->blocks[cand[i]].host / page * page;
+      uintptr_t hi = round_up((uintptr_t)p->blocks[cand[i]].host + p->blocks[cand[i]].bytes, page);
+      size_t j = i + 1;
+      while (j < cand.size() && (uintptr_t)p->blocks[cand[j]].host / page * page <= hi) {
+        hi = std::max<uintptr_t>(hi, round_up((uintptr_t)p->blocks[cand[j]].host + p->blocks[cand[j]].bytes, page));
+        j++;
+      }
+      // only spans this plan page-locks itself move directly; anything else
+      // (already registered elsewhere, or refused) is staged
+      cudaError_t e = cudaHostRegister((void*)lo, hi - lo, cudaHostRegisterDefault);
+      if (e == cudaSuccess) {
+        p->registered.push_back({(void*)lo, hi - lo});
+        for (size_t k = i; k < j; k++) p->direct[cand[k]] = 1;
+      } else {
+        cudaGetLastError();  // not a sticky error: clear it
+      }
+      i = j;
+    }
+  }
+  std::vector<uint32_t> all(nb);
+  for (uint32_t b = 0; b < nb; b++) all[b] = b;
+  plan_moves(p, all, &p->h2d);
+  p->transfers_ready = true;
+}
+
+void marshal_units(dc_plan_s* p, Pool& pool, const dc_plan_s::Moves& m, uint64_t ufirst, uint64_t ulast, bool to_arena) {
+  auto unit = [&](uint64_t u) {
+    for (uint64_t k = m.units[u].first; k < m.units[u].last; k++) {
+      const auto& pc = m.pieces[k];
+      if (to_arena)
+        memcpy(p->pinned + pc.off, pc.host, pc.len);
+      else
+        memcpy(pc.host, p->pinned + pc.off, pc.len);
+    }
+  };
+  if (ulast - ufirst == 1 || pool.size() == 1) {
+    for (uint64_t u = ufirst; u < ulast; u++) unit(u);
+  } else {
+    pool.parallel_for(ulast - ufirst, [&](uint64_t i) { unit(ufirst + i); });
   }
 }
 
@@ -279,6 +378,7 @@ dc_status dc_plan_destroy(dc_plan_t p) {
   if (p->tab_done) cudaEventSynchronize(p->tab_done);
   if (p->pinned) cudaFreeHost(p->pinned);
   if (p->pin_tab) cudaFreeHost(p->pin_tab);
+  for (auto& r : p->registered) cudaHostUnregister(r.first);
   if (p->h2d_done) cudaEventDestroy(p->h2d_done);
   if (p->tab_done) cudaEventDestroy(p->tab_done);
   delete p;
@@ -319,6 +419,7 @@ dc_status dc_bind_device(dc_plan_t p, void* dev, uint64_t bytes, dc_stream_t str
       return fail(DC_ENOMEM, "pinned table staging: %s", cudaGetErrorString(e));
     }
   }
+  if (!p->transfers_ready) plan_transfers(p);
   if (!p->h2d_done) DC_CUDA(cudaEventCreateWithFlags(&p->h2d_done, cudaEventDisableTiming));
   if (!p->tab_done) DC_CUDA(cudaEventCreateWithFlags(&p->tab_done, cudaEventDisableTiming));
   p->dev = (uint8_t*)dev;
@@ -374,29 +475,26 @@ dc_status dc_deep_copy(dc_plan_t p, dc_stream_t stream) {
   if (!p) return fail(DC_EINVAL, "plan is NULL");
   if (!p->dev) return fail(DC_ESTATE, "no device buffer bound");
   cudaStream_t s = stream;
-  if (p->chunks.empty()) build_pieces(p);
   // the previous deep copy's transfers read the same pinned arena
   dc_status st = wait_event(p->h2d_done);
   if (st) return st;
+  const dc_plan_s::Moves& m = p->h2d;
+  // large arrays: one DMA each, straight from the caller's (registered) pages
+  for (uint32_t b : m.direct)
+    DC_CUDA(cudaMemcpyAsync(p->dev + p->blocks[b].off, p->blocks[b].host, p->blocks[b].bytes, cudaMemcpyHostToDevice, s));
+  // everything else: Algorithm 1's contiguous buffer, marshalled and sent chunk by chunk
   Pool& pool = pool_of(p);
   size_t ns = 0;  // next NULL-slot fix-up
-  for (const auto& c : p->chunks) {
-    // Algorithm 1: every block lands at its offset in one contiguous buffer
-    if (c.last - c.first == 1 || pool.size() == 1) {
-      for (uint64_t i = c.first; i < c.last; i++)
-        memcpy(p->pinned + p->pieces[i].off, p->pieces[i].src, p->pieces[i].len);
-    } else {
-      pool.parallel_for(c.last - c.first, [&](uint64_t i) {
-        const auto& pc = p->pieces[c.first + i];
-        memcpy(p->pinned + pc.off, pc.src, pc.len);
-      });
-    }
-    while (ns < p->null_slots.size() && p->null_slots[ns] < c.hi) {
+  for (const auto& c : m.chunks) {
+    marshal_units(p, pool, m, c.ufirst, c.ulast, true);
+    const uint64_t hi = c.clast > c.cfirst ? m.copies[c.clast - 1].hi : 0;
+    while (ns < p->null_slots.size() && p->null_slots[ns] < hi) {
       memset(p->pinned + p->null_slots[ns], 0, 8);
       ns++;
     }
-    // Fig 2 steps b-c: one stream-ordered pass over the data region
-    DC_CUDA(cudaMemcpyAsync(p->dev + c.lo, p->pinned + c.lo, c.hi - c.lo, cudaMemcpyHostToDevice, s));
+    for (uint64_t k = c.cfirst; k < c.clast; k++)
+      DC_CUDA(cudaMemcpyAsync(p->dev + m.copies[k].lo, p->pinned + m.copies[k].lo, m.copies[k].hi - m.copies[k].lo,
+                              cudaMemcpyHostToDevice, s));
   }
   DC_CUDA(cudaEventRecord(p->h2d_done, s));
   return dc_relocate(p, stream);
@@ -447,8 +545,20 @@ dc_status dc_update_leaves(dc_plan_t p, const dc_op* op, dc_stream_t stream) {
       units += (bx.count * X.elem_size + 15) / 16;
       p->leaf_written.push_back(picks[i].bx);
     }
-    if (!picks.empty())
+    // tile -> segment holding the tile's first unit (two-pointer walk)
+    uint32_t* tseg = reinterpret_cast<uint32_t*>(p->pin_tab + tab_tseg(p->L));
+    const uint64_t ntiles = (units + LEAF_TILE - 1) / LEAF_TILE;
+    if (ntiles + 1 > p->L.tseg_cap) return fail(DC_EINVAL, "tile table larger than planned");
+    for (uint64_t t = 0, sg = 0; t < ntiles; t++) {
+      const uint64_t u = t * LEAF_TILE;
+      while (sg + 1 < picks.size() && seg[sg + 1].ubeg <= u) sg++;
+      tseg[t] = (uint32_t)sg;
+    }
+    tseg[ntiles] = picks.empty() ? 0 : (uint32_t)(picks.size() - 1);
+    if (!picks.empty()) {
       DC_CUDA(cudaMemcpyAsync(p->dev + p->L.seg, seg, picks.size() * sizeof(Segment), cudaMemcpyHostToDevice, s));
+      DC_CUDA(cudaMemcpyAsync(p->dev + p->L.tseg, tseg, (ntiles + 1) * 4, cudaMemcpyHostToDevice, s));
+    }
     DC_CUDA(cudaEventRecord(p->tab_done, s));
     p->leaf_nseg = picks.size();
     p->leaf_units = units;
@@ -458,6 +568,7 @@ dc_status dc_update_leaves(dc_plan_t p, const dc_op* op, dc_stream_t stream) {
   p->op_run = true;
   LeafArgs a;
   a.seg = reinterpret_cast<const Segment*>(p->dev + p->L.seg);
+  a.tile_seg = reinterpret_cast<const uint32_t*>(p->dev + p->L.tseg);
   a.nseg = (uint32_t)p->leaf_nseg;
   a.units = p->leaf_units;
   a.kind = op->kind;
@@ -559,35 +670,21 @@ dc_status dc_copy_back(dc_plan_t p, uint32_t flags, dc_stream_t stream) {
     list = p->written;
   }
   std::sort(list.begin(), list.end());
-  cudaStream_t s = stream;
-  // device -> pinned arena, one transfer per run of adjacent blocks
-  for (size_t i = 0; i < list.size();) {
-    uint64_t lo = p->blocks[list[i]].off, hi = lo + p->blocks[list[i]].bytes;
-    size_t j = i + 1;
-    while (j < list.size() && list[j] == list[j - 1] + 1) {
-      hi = p->blocks[list[j]].off + p->blocks[list[j]].bytes;
-      j++;
-    }
-    DC_CUDA(cudaMemcpyAsync(p->pinned + lo, p->dev + lo, hi - lo, cudaMemcpyDeviceToHost, s));
-    i = j;
+  if (list != p->back_key) {
+    plan_moves(p, list, &p->back);
+    p->back_key = list;
   }
+  const dc_plan_s::Moves& m = p->back;
+  cudaStream_t s = stream;
+  // large arrays straight into the caller's pages; the rest via the pinned arena
+  for (uint32_t b : m.direct)
+    DC_CUDA(cudaMemcpyAsync(const_cast<uint8_t*>(p->blocks[b].host), p->dev + p->blocks[b].off, p->blocks[b].bytes,
+                            cudaMemcpyDeviceToHost, s));
+  for (const auto& c : m.copies)
+    DC_CUDA(cudaMemcpyAsync(p->pinned + c.lo, p->dev + c.lo, c.hi - c.lo, cudaMemcpyDeviceToHost, s));
   dc_status st = device_error(p, s);  // synchronizes the stream
   if (st) return st;
-  // pinned arena -> the original host arrays
-  std::vector<dc_plan_s::Piece> pcs;
-  for (uint32_t b : list) {
-    const HostBlock& B = p->blocks[b];
-    for (uint64_t o = 0; o < B.bytes; o += PIECE_BYTES)
-      pcs.push_back({B.off + o, std::min(PIECE_BYTES, B.bytes - o), B.host + o});
-  }
-  Pool& pool = pool_of(p);
-  if (pcs.size() <= 1 || pool.size() == 1) {
-    for (auto& pc : pcs) memcpy(const_cast<uint8_t*>(pc.src), p->pinned + pc.off, pc.len);
-  } else {
-    pool.parallel_for(pcs.size(), [&](uint64_t i) {
-      memcpy(const_cast<uint8_t*>(pcs[i].src), p->pinned + pcs[i].off, pcs[i].len);
-    });
-  }
+  if (!m.units.empty()) marshal_units(p, pool_of(p), m, 0, m.units.size(), false);
   return DC_OK;
 }
 

@@ -14,7 +14,8 @@ using namespace dc;
 namespace {
 
 constexpr uint64_t MAX_BLOCKS = DC_STATIC_MAX_BLOCKS;
-constexpr uint64_t MAX_TILES = (MAX_BLOCKS + RELOC_TILE - 1) / RELOC_TILE;
+constexpr uint64_t MAX_TILES = 64;  // look-back words reserved; enough for any tile of >= 1024 blocks
+static_assert(MAX_BLOCKS <= MAX_TILES * RELOC_TILE, "look-back words cover every tile");
 constexpr uint64_t al256(uint64_t x) { return (x + 255) / 256 * 256; }
 // byte layout of the array
 constexpr uint64_t OFF_REC = 0;                                   // 16 B per block

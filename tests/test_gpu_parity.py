@@ -32,12 +32,12 @@ def image_ok(plan, schema, root_tree):
     return seen
 
 
-def full_parity(make, op_kw=None, mode="leaf", verify=False, repeat=1):
+def full_parity(make, op_kw=None, mode="leaf", verify=False, repeat=1, flags=0):
     """Deep copy `make()` with the CUDA path and the oracle, run the op
     `repeat` times on both, copy back on both, compare every stage."""
     src, ref = make(), make()
     s = src.schema
-    plan = dc.Plan(s, src.root, flags=dc.PLAN_VERIFY if verify else 0)
+    plan = dc.Plan(s, src.root, flags=(dc.PLAN_VERIFY if verify else 0) | flags)
     plan.bind()
     plan.deep_copy()
     plan.sync()
@@ -78,6 +78,18 @@ def test_tiny_chain_to_last_level():
 
 def test_dense_all_nodes_full_size():
     full_parity(lambda: tg.workload("dense"), {}, verify=True)
+
+
+def test_dense_all_nodes_staged_transfers():
+    # every block through the pinned arena (no direct DMA from host pages)
+    full_parity(lambda: tg.workload("dense"), {}, flags=dc.PLAN_STAGED)
+    full_parity(lambda: tg.workload("deep"), dict(sel=dc.SEL_CHAIN, path=tg.leaf_path(64)), flags=dc.PLAN_STAGED)
+
+
+def test_copy_back_all_arrays_mixed_direct_and_staged():
+    # lengths around the direct-transfer threshold (65,536 fp32 = 256 KiB)
+    full_parity(lambda: tg.node_tree(3, 9, tg.uniform(60000, 70000), seed=31), None)
+    full_parity(lambda: tg.node_tree(3, 9, tg.uniform(60000, 70000), seed=31), {})
 
 
 def test_dense_chain_listing2_path():
