@@ -7,8 +7,9 @@
          events on the launching stream, L2 flushed (512 MiB write) before each
          step.
   e2e    the same metric through the C ABI with host buffers: dc_deep_copy
-         (marshal + H2D + relocation), dc_update_leaves, dc_copy_back (D2H +
-         scatter into the host arrays), host clock around synchronized steps.
+         (transfer + relocation), dc_update_leaves, dc_copy_back (back into the
+         host arrays), host clock around synchronized steps; reported for a plan
+         with DC_PLAN_MAP_HOST (e2e) and for the default staged plan (e2e_staged).
   roofline  the leaf kernel: algorithmic bytes (12 B per element: read x and y,
          write x) / its CUDA-event time, against the measured HBM copy peak.
 
@@ -278,44 +279,55 @@ def main():
                 "algorithmic_bytes_per_launch": leaf_bytes, "avg_launch_us": round(leaf_avg * 1e6, 2)}
 
     # ---- end to end through the C ABI with host buffers ----------------------
-    t_e2e, t_dc, t_cb = [], [], []
-    for i in range(args.warmup + max(3, args.steps // 2)):
-        barrier()
-        t0 = time.perf_counter()
-        plan.deep_copy()
-        t1 = time.perf_counter()
-        plan.update(op)
-        plan.copy_back()
-        t2 = time.perf_counter()
-        if i >= args.warmup:
-            t_e2e.append(t2 - t0)
-    # deep copy alone (marshal + H2D + relocation) against the link
-    for i in range(args.warmup + 5):
-        barrier()
-        t0 = time.perf_counter()
-        plan.deep_copy()
-        plan.sync()
-        t1 = time.perf_counter()
-        if i >= args.warmup:
-            t_dc.append(t1 - t0)
-    for i in range(args.warmup + 5):
-        barrier()
-        t0 = time.perf_counter()
-        plan.copy_back()
-        t1 = time.perf_counter()
-        if i >= args.warmup:
-            t_cb.append(t1 - t0)
+    def measure_e2e(pl):
+        t_e2e, t_dc, t_cb = [], [], []
+        for i in range(args.warmup + max(3, args.steps // 2)):
+            barrier()
+            t0 = time.perf_counter()
+            pl.deep_copy()
+            pl.update(op)
+            pl.copy_back()
+            t1 = time.perf_counter()
+            if i >= args.warmup:
+                t_e2e.append(t1 - t0)
+        for i in range(args.warmup + 5):  # deep copy alone (transfer + relocation) against the link
+            barrier()
+            t0 = time.perf_counter()
+            pl.deep_copy()
+            pl.sync()
+            t1 = time.perf_counter()
+            if i >= args.warmup:
+                t_dc.append(t1 - t0)
+        for i in range(args.warmup + 5):
+            barrier()
+            t0 = time.perf_counter()
+            pl.copy_back()
+            t1 = time.perf_counter()
+            if i >= args.warmup:
+                t_cb.append(t1 - t0)
+        e2e_t = max_over_ranks(statistics.mean(t_e2e))
+        return {"value": round(payload * world / e2e_t / 1e9, 3), "unit": "GB/s",
+                "h2d_bytes_per_step": info["data_bytes"], "d2h_bytes_per_step": 4 * nelem,
+                "ms_per_step": round(e2e_t * 1e3, 3),
+                "deep_copy_gbs": round(info["data_bytes"] / statistics.median(t_dc) / 1e9, 2),
+                "copy_back_gbs": round(4 * nelem / statistics.median(t_cb) / 1e9, 2)}
+
+    e2e_staged = measure_e2e(plan)
+    plan_m = dc.Plan(s, tree.root, flags=dc.PLAN_MAP_HOST)
+    plan_m.bind()
+    plan_m.deep_copy()
+    plan_m.update(op)
+    plan_m.sync()
+    e2e_mapped = measure_e2e(plan_m)
+    plan_m.destroy()
+    del plan_m
     clk = clocks.stop()
-    e2e_t = max_over_ranks(statistics.mean(t_e2e))
-    e2e = {"value": round(payload * world / e2e_t / 1e9, 3), "unit": "GB/s",
-           "h2d_bytes_per_step": info["data_bytes"], "d2h_bytes_per_step": 4 * nelem,
-           "ms_per_step": round(e2e_t * 1e3, 3)}
+    e2e = dict(e2e_mapped)
+    e2e["api"] = "dc_deep_copy + dc_update_leaves + dc_copy_back, plan flag DC_PLAN_MAP_HOST"
     link = link_peaks(torch)
-    dc_med = statistics.median(t_dc)
-    link["deep_copy_gbs"] = round(info["data_bytes"] / dc_med / 1e9, 2)
-    link["deep_copy_frac_of_h2d_peak"] = round(info["data_bytes"] / dc_med / 1e9 / link["h2d_gbs"], 4)
-    link["copy_back_gbs"] = round(4 * nelem / statistics.median(t_cb) / 1e9, 2)
-    link["copy_back_frac_of_d2h_peak"] = round(4 * nelem / statistics.median(t_cb) / 1e9 / link["d2h_gbs"], 4)
+    for mode, r in (("staged", e2e_staged), ("map_host", e2e_mapped)):
+        link[f"deep_copy_frac_of_h2d_peak_{mode}"] = round(r["deep_copy_gbs"] / link["h2d_gbs"], 4)
+        link[f"copy_back_frac_of_d2h_peak_{mode}"] = round(r["copy_back_gbs"] / link["d2h_gbs"], 4)
 
     # ---- comparison paths (same GPU) -----------------------------------------
     compare = None
@@ -371,7 +383,8 @@ def main():
             "roofline": roofline,
             "relocation": {"avg_launch_us": round(reloc_avg * 1e6, 2), "algorithmic_bytes": reloc_bytes,
                            "achieved_gbs": round(reloc_bytes / reloc_avg / 1e9, 1)},
-            "e2e": e2e, "link": link, "compare": compare, "cpu_baseline": cpu, "clocks": clk,
+            "e2e": e2e, "e2e_staged": e2e_staged, "link": link, "compare": compare, "cpu_baseline": cpu,
+            "clocks": clk,
             "gpu_launches": launches,
         }
         print(json.dumps(out))

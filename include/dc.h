@@ -136,12 +136,16 @@ typedef struct {
 /* Plan flags (dc_plan_set_flags, before dc_bind_device). */
 #define DC_PLAN_VERIFY 1u /* relocation also checks that every slot still holds the
                              host address the plan recorded (DC_EVERIFY otherwise) */
-#define DC_PLAN_STAGED 2u /* move every block through the pinned arena; by default
-                             arrays of DC_DIRECT_MIN_BYTES or more are transferred
-                             straight from / to their own host pages, which
-                             dc_bind_device page-locks (cudaHostRegister) until
-                             dc_plan_destroy */
-#define DC_DIRECT_MIN_BYTES (256u << 10)
+#define DC_PLAN_MAP_HOST 2u /* move the whole pages inside each array of at least
+                             DC_MAP_MIN_BYTES straight between the caller's memory and
+                             the arena (one kernel launch for all of them) instead of
+                             through the pinned arena.  dc_bind_device page-locks and
+                             maps those pages in place (cudaHostRegister) until
+                             dc_plan_destroy; only pages wholly inside an array are
+                             touched.  While they are registered, a cudaMemcpy by the
+                             caller that starts inside such a page range and runs past
+                             its end fails. */
+#define DC_MAP_MIN_BYTES (64u << 10)
 
 /* dc_plan — walk the host structure from `host_root` (one struct of
  * schema->root_type) and lay out its device arena (Algorithm 1's first step,
@@ -174,14 +178,16 @@ dc_status dc_bind_device(dc_plan_t plan, void* dev_buffer, uint64_t bytes, dc_st
 
 /* dc_deep_copy — move the tree into the arena (Fig 2 steps b-c), then run
  * the relocation kernel, which rebuilds every pointer slot to the device
- * address of its target (Fig 2 step d; Algorithm 1's attach loop).  Struct
- * blocks and small arrays are marshalled into the pinned arena (Algorithm 1:
- * one contiguous buffer) and sent in chunks overlapped with the marshal;
- * large arrays go by DMA straight from their host pages into their arena
- * slot, one transfer per array (the paper's pointerchain transfer scheme,
- * Sec. 4.1.1 item 3), unless the plan has DC_PLAN_STAGED.  Returns once the
- * copies and the kernel are queued; large arrays are read by the DMA until the
- * stream gets there.  Errors: DC_ESTATE (nothing bound), DC_ECUDA. */
+ * address of its target (Fig 2 step d; Algorithm 1's attach loop).  By
+ * default every block is marshalled into the pinned arena (Algorithm 1: one
+ * contiguous buffer) by host threads and sent by DMA chunk by chunk while the
+ * marshal goes on; with DC_PLAN_MAP_HOST the interiors of large arrays are
+ * read straight from the caller's pages by one kernel launch (one transfer
+ * per effective-address array, as in the paper's pointerchain scheme,
+ * Sec. 4.1.1 item 3) while the rest is marshalled.  Returns once the copies
+ * and the kernel are queued; with DC_PLAN_MAP_HOST the caller's arrays are
+ * read until the stream gets there.  Errors: DC_ESTATE (nothing bound),
+ * DC_ECUDA. */
 dc_status dc_deep_copy(dc_plan_t plan, dc_stream_t stream);
 
 /* dc_relocate — the relocation kernel of dc_deep_copy alone (Fig 2 step d):

@@ -29,7 +29,7 @@ LIB_PATH = os.path.join(_HERE, "libdc.so")
 OP_AXPY_HALF, OP_SCALE = 0, 1
 SEL_ALL, SEL_CHAIN = 0, 1
 PLAN_VERIFY = 1
-PLAN_STAGED = 2
+PLAN_MAP_HOST = 2
 COPY_ALL_ARRAYS = 1
 
 STATUS = {0: "DC_OK", 1: "DC_EINVAL", 2: "DC_ENOMEM", 3: "DC_ECUDA", 4: "DC_EALIAS", 5: "DC_ECYCLE",

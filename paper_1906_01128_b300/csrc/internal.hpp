@@ -104,6 +104,21 @@ struct LeafArgs {
   double scale;
 };
 
+// One block to move between host and device memory: src and dst are device-
+// visible addresses (a mapped host page or the arena); ubeg is the exclusive
+// prefix of 16-byte units over the table.
+struct MoveDesc {
+  uint64_t src, dst, bytes, ubeg;
+};
+static_assert(sizeof(MoveDesc) == 32, "MoveDesc is 32 bytes");
+
+struct MoveArgs {
+  const MoveDesc* d;
+  const uint32_t* tile_desc;  // per tile of LEAF_TILE units: its first descriptor; one extra entry
+  uint32_t nd;
+  uint64_t units;
+};
+
 struct ChaseArgs {
   const ChaseSeg* seg;
   const ChaseStep* steps;
@@ -117,6 +132,7 @@ struct ChaseArgs {
 cudaError_t launch_relocate(const RelocArgs& a, cudaStream_t s, int sm_count);
 cudaError_t launch_leaf(const LeafArgs& a, cudaStream_t s, int sm_count);
 cudaError_t launch_chase(const ChaseArgs& a, cudaStream_t s, int sm_count);
+cudaError_t launch_move(const MoveArgs& a, cudaStream_t s, int sm_count);
 cudaError_t launch_walk(uint64_t root, const ChaseStep* steps, uint32_t nsteps, uint64_t final_add,
                         uint64_t* out, cudaStream_t s);
 void count_launch();
@@ -153,7 +169,8 @@ dc_status copy_schema(const dc_schema* s, SchemaCopy* out);
 struct DevLayout {
   uint64_t data = 0, rec = 0, hostp = 0, soff = 0, status = 0, ready = 0, ctrl = 0;
   uint64_t seg = 0, tseg = 0, cseg = 0, steps = 0, walk = 0, total = 0;
-  uint64_t seg_cap = 0, tseg_cap = 0, step_cap = 0, walk_cap = 0, ntiles = 0;
+  uint64_t mva = 0, mvat = 0, mvb = 0, mvbt = 0, bk = 0, bkt = 0;  // move tables + their tile tables
+  uint64_t seg_cap = 0, tseg_cap = 0, step_cap = 0, walk_cap = 0, ntiles = 0, tab_cap = 0;
 };
 
 struct OpKey {
@@ -195,27 +212,29 @@ struct dc_plan_s {
   std::vector<uint32_t> leaf_written, chase_written;
   bool op_run = false;
   std::unique_ptr<dc::Pool> pool;
-  // transfer plan, built at the first bind: large arrays move by DMA straight
-  // between their (registered) host pages and the arena; everything else is
-  // marshalled into the pinned arena in pieces, handed out to host threads in
-  // units, and sent in chunks of staged runs
-  struct Piece { uint64_t off, len; uint8_t* host; };
-  struct Unit { uint64_t first, last; };  // pieces [first, last)
-  struct Copy { uint64_t lo, hi; };       // a run of the data region
+  // transfers (transfer.cpp), planned at the first bind
+  struct Frag { uint64_t off, len; uint8_t* host; };  // staged bytes: arena offset, length, host address
+  struct Unit { uint64_t first, last; };              // pieces [first, last), one host thread at a time
+  struct Copy { uint64_t lo, hi; };                   // a range of the data region
   struct Chunk { uint64_t ufirst, ulast, cfirst, clast; };
-  struct Moves {                          // what one transfer direction moves
-    std::vector<uint32_t> direct;         // blocks copied straight to / from host memory
-    std::vector<Piece> pieces;            // staged blocks, in pieces
+  struct Moves {
+    std::vector<Frag> frags;          // staged bytes, arena order
+    std::vector<Frag> pieces;         // frags split for host threads
     std::vector<Unit> units;
-    std::vector<Copy> copies;             // staged runs (clipped to chunks)
+    std::vector<Copy> runs;           // frags separated only by padding, merged
+    std::vector<Copy> copies;         // runs clipped to chunks (DMA)
     std::vector<Chunk> chunks;
+    std::vector<uint32_t> interiors;  // blocks whose interior moves through mapped caller pages
   };
   bool transfers_ready = false;
-  std::vector<uint8_t> direct;            // per block
-  std::vector<std::pair<void*, uint64_t>> registered;  // host spans this plan registered
-  Moves h2d;                              // everything, for dc_deep_copy
-  std::vector<uint32_t> back_key;         // the block list `back` was built for
-  Moves back;                             // the last copy-back's blocks
+  uint8_t* pinned_dev = nullptr;      // device view of the (mapped) pinned arena
+  std::vector<uint64_t> ilo, ihi, idev;  // per block: mapped interior host range, its device address
+  std::vector<std::pair<void*, uint64_t>> registered;  // caller pages this plan page-locked
+  Moves h2d;
+  uint64_t h2d_int_nd = 0, h2d_int_units = 0, h2d_frag_nd = 0, h2d_frag_units = 0;
+  std::vector<uint32_t> back_key;     // the block list `back` was built for
+  Moves back;
+  uint64_t bk_nd = 0, bk_units = 0;
 };
 
 struct dc_uvm_s {
@@ -242,6 +261,17 @@ dc_status resolve(const dc_plan_s* p, const dc_step* path, uint32_t len, uint32_
 dc_status select_structs(const dc_plan_s* p, const dc_op* op,
                          std::vector<std::pair<uint32_t, uint64_t>>* out);
 dc_status check_op(const dc_plan_s* p, const dc_op* op);
+// transfer.cpp
+uint64_t interior_bytes(const HostBlock& b);
+void plan_moves(const dc_plan_s* p, const std::vector<uint32_t>& list, dc_plan_s::Moves* m);
+void plan_transfers(dc_plan_s* p);
+void release_transfers(dc_plan_s* p);
+dc_status upload_h2d_tables(dc_plan_s* p, cudaStream_t s);
+dc_status transfer_to_device(dc_plan_s* p, cudaStream_t s);
+dc_status transfer_back(dc_plan_s* p, const std::vector<uint32_t>& list, cudaStream_t s);
+// runtime.cpp
+dc_status device_error(dc_plan_s* p, cudaStream_t s);
+Pool& pool_of(dc_plan_s* p);
 // The chain of (field, index) steps from the root to struct (block, elem).
 void path_to(const dc_plan_s* p, uint32_t block, uint64_t elem, std::vector<dc_step>* out);
 }  // namespace dc

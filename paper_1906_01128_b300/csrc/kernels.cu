@@ -12,6 +12,10 @@
 //   chase_kernel     the same update with every element walking its pointer
 //                    chain from the root (Listing 2's loop body), with loads
 //                    that may not be hoisted out of the element loop.
+//   move_kernel      moves whole blocks between mapped host pages and the
+//                    arena in 16-byte units (the deep copy's transfer and the
+//                    copy back, one launch for every block instead of one DMA
+//                    per block).
 //   walk_kernel      one thread follows a chain and reports the address.
 #include <cuda_runtime.h>
 
@@ -322,6 +326,55 @@ __global__ void __launch_bounds__(LEAF_THREADS) leaf_kernel(LeafArgs a) {
   }
 }
 
+// ---- block moves between host and device ------------------------------------
+
+// Copy n (<= 16) bytes with the widest access both addresses allow; never
+// touches a byte outside [src, src + n) or [dst, dst + n).
+__device__ __forceinline__ void move_partial(uint64_t src, uint64_t dst, uint32_t n) {
+  const uint64_t al = src | dst;
+  if ((al & 7) == 0 && (n & 7) == 0) {
+    for (uint32_t i = 0; i < n; i += 8) *reinterpret_cast<uint64_t*>(dst + i) = *reinterpret_cast<const uint64_t*>(src + i);
+  } else if ((al & 3) == 0 && (n & 3) == 0) {
+    for (uint32_t i = 0; i < n; i += 4) *reinterpret_cast<uint32_t*>(dst + i) = *reinterpret_cast<const uint32_t*>(src + i);
+  } else {
+    for (uint32_t i = 0; i < n; i++) *reinterpret_cast<uint8_t*>(dst + i) = *reinterpret_cast<const uint8_t*>(src + i);
+  }
+}
+
+__global__ void __launch_bounds__(LEAF_THREADS) move_kernel(MoveArgs a) {
+  const MoveDesc* d = a.d;
+  auto ub = [&](uint32_t i) { return __ldg(&d[i].ubeg); };
+  for (uint64_t t = blockIdx.x; t * LEAF_TILE < a.units; t += gridDim.x) {
+    const uint64_t u0 = t * LEAF_TILE;
+    const uint32_t lo = __ldg(&a.tile_desc[t]), hi = __ldg(&a.tile_desc[t + 1]);
+    uint4 v[LEAF_UNROLL];
+    uint64_t dst[LEAF_UNROLL];
+    bool full[LEAF_UNROLL];
+#pragma unroll
+    for (uint32_t k = 0; k < LEAF_UNROLL; k++) {  // issue every load first
+      const uint64_t u = u0 + threadIdx.x + k * LEAF_THREADS;
+      full[k] = false;
+      dst[k] = 0;
+      if (u >= a.units) continue;
+      const uint32_t s = lo == hi ? lo : search(lo, hi, u, ub);
+      const MoveDesc g = d[s];
+      const uint64_t off = (u - g.ubeg) * 16;
+      const uint64_t left = g.bytes - off;
+      const uint64_t src = g.src + off;
+      dst[k] = g.dst + off;
+      if (left >= 16 && ((src | dst[k]) & 15) == 0) {
+        v[k] = *reinterpret_cast<const uint4*>(src);
+        full[k] = true;
+      } else {
+        move_partial(src, dst[k], left >= 16 ? 16u : (uint32_t)left);
+      }
+    }
+#pragma unroll
+    for (uint32_t k = 0; k < LEAF_UNROLL; k++)
+      if (full[k]) *reinterpret_cast<uint4*>(dst[k]) = v[k];
+  }
+}
+
 // ---- per-element pointer chase ---------------------------------------------
 
 // A load the compiler must issue every time it appears (no hoisting or reuse).
@@ -426,6 +479,16 @@ cudaError_t launch_chase(const ChaseArgs& a, cudaStream_t s, int sm_count) {
     a.kind == DC_OP_AXPY_HALF ? go(chase_kernel<double, DC_OP_AXPY_HALF>) : go(chase_kernel<double, DC_OP_SCALE>);
   else
     a.kind == DC_OP_AXPY_HALF ? go(chase_kernel<float, DC_OP_AXPY_HALF>) : go(chase_kernel<float, DC_OP_SCALE>);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_move(const MoveArgs& a, cudaStream_t s, int sm_count) {
+  if (a.units == 0 || a.nd == 0) return cudaSuccess;
+  static int occ = occupancy(move_kernel, LEAF_THREADS, 0);
+  uint64_t tiles = (a.units + LEAF_TILE - 1) / LEAF_TILE;
+  uint32_t grid = (uint32_t)std::min<uint64_t>(tiles, (uint64_t)sm_count * occ);
+  move_kernel<<<grid, LEAF_THREADS, 0, s>>>(a);
   count_launch();
   return cudaGetLastError();
 }

@@ -18,8 +18,6 @@ void dc::count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 namespace {
 
-constexpr uint64_t PIECE_BYTES = 2ull << 20;   // largest memcpy one host thread does at once
-constexpr uint64_t CHUNK_BYTES = 32ull << 20;  // transfer granularity of the data region
 constexpr uint64_t WORD_AREA = 256;            // pinned words for small device -> host reads
 
 uint64_t align256(uint64_t x) { return round_up(x, 256); }
@@ -53,6 +51,15 @@ DevLayout make_layout(const dc_plan_s* p) {
   L.step_cap = std::max<uint64_t>(1, p->sum_depth);
   L.steps = o;
   o = align256(o + L.step_cap * sizeof(ChaseStep));
+  // move tables: at most one descriptor per block plus two per array interior
+  uint64_t interiors = 0;
+  for (const auto& b : p->blocks) interiors += interior_bytes(b) ? 1 : 0;
+  L.tab_cap = nb + 2 * interiors;
+  for (uint64_t* t : {&L.mva, &L.mvat, &L.mvb, &L.mvbt, &L.bk, &L.bkt}) {
+    *t = o;
+    bool tiles = (t == &L.mvat || t == &L.mvbt || t == &L.bkt);
+    o = align256(o + (tiles ? L.tseg_cap * 4 : L.tab_cap * sizeof(MoveDesc)));
+  }
   L.walk_cap = (uint64_t)p->max_depth + 2;
   L.walk = o;
   o = align256(o + L.walk_cap * sizeof(ChaseStep) + 16);
@@ -75,125 +82,18 @@ unsigned default_threads() {
   return std::min(hc, 32u);
 }
 
-Pool& pool_of(dc_plan_s* p) {
+}  // namespace
+
+Pool& dc::pool_of(dc_plan_s* p) {
   if (!p->pool) p->pool.reset(new Pool(p->nthreads ? p->nthreads : default_threads()));
   return *p->pool;
 }
 
-constexpr uint64_t UNIT_BYTES = 1ull << 20;  // host work handed out at once
-constexpr uint64_t UNIT_PIECES = 4096;
+namespace {
 
-// Pieces, work units, staged runs and chunks for moving `list` (arena indices,
-// ascending).  Blocks marked direct are listed apart and moved by their own DMA.
-void plan_moves(const dc_plan_s* p, const std::vector<uint32_t>& list, dc_plan_s::Moves* m) {
-  *m = dc_plan_s::Moves();
-  for (size_t i = 0; i < list.size(); i++) {
-    const HostBlock& B = p->blocks[list[i]];
-    if (p->direct[list[i]]) {
-      m->direct.push_back(list[i]);
-      continue;
-    }
-    for (uint64_t o = 0; o < B.bytes; o += PIECE_BYTES)
-      m->pieces.push_back({B.off + o, std::min(PIECE_BYTES, B.bytes - o), const_cast<uint8_t*>(B.host) + o});
-  }
-  for (uint64_t i = 0; i < m->pieces.size();) {  // units of ~1 MiB or 4096 pieces
-    uint64_t j = i, bytes = 0;
-    while (j < m->pieces.size() && bytes < UNIT_BYTES && j - i < UNIT_PIECES) bytes += m->pieces[j++].len;
-    m->units.push_back({i, j});
-    i = j;
-  }
-  // staged runs: adjacent staged blocks of the list travel as one copy
-  std::vector<dc_plan_s::Copy> runs;
-  for (size_t i = 0; i < list.size();) {
-    if (p->direct[list[i]]) {
-      i++;
-      continue;
-    }
-    uint64_t lo = p->blocks[list[i]].off, hi = lo + p->blocks[list[i]].bytes;
-    size_t j = i + 1;
-    while (j < list.size() && list[j] == list[j - 1] + 1 && !p->direct[list[j]]) {
-      hi = p->blocks[list[j]].off + p->blocks[list[j]].bytes;
-      j++;
-    }
-    if (hi > lo) runs.push_back({lo, hi});
-    i = j;
-  }
-  // chunks of ~CHUNK_BYTES of staged data: marshal a chunk, send it, go on
-  size_t r = 0;
-  for (uint64_t u = 0; u < m->units.size();) {
-    uint64_t v = u, bytes = 0;
-    while (v < m->units.size() && bytes < CHUNK_BYTES) {
-      for (uint64_t k = m->units[v].first; k < m->units[v].last; k++) bytes += m->pieces[k].len;
-      v++;
-    }
-    const uint64_t lo = m->pieces[m->units[u].first].off;
-    const uint64_t hi = v < m->units.size() ? m->pieces[m->units[v].first].off : ~0ull;
-    const uint64_t cfirst = m->copies.size();
-    while (r < runs.size() && runs[r].lo < hi) {
-      const uint64_t a = std::max(runs[r].lo, lo), b = std::min(runs[r].hi, hi);
-      if (b > a) m->copies.push_back({a, b});
-      if (runs[r].hi <= hi) r++;
-      else break;
-    }
-    m->chunks.push_back({u, v, cfirst, m->copies.size()});
-    u = v;
-  }
-}
+}  // namespace
 
-// Decide which arrays move by direct DMA and page-lock their host spans.
-void plan_transfers(dc_plan_s* p) {
-  const uint64_t nb = p->blocks.size();
-  p->direct.assign(nb, 0);
-  if (!(p->flags & DC_PLAN_STAGED)) {
-    const uint64_t page = 4096;
-    std::vector<uint32_t> cand;
-    for (uint32_t b = 0; b < nb; b++)
-      if (p->blocks[b].lane != 0 && p->blocks[b].bytes >= DC_DIRECT_MIN_BYTES) cand.push_back(b);
-    std::sort(cand.begin(), cand.end(), [&](uint32_t a, uint32_t b) { return p->blocks[a].host < p->blocks[b].host; });
-    for (size_t i = 0; i < cand.size();) {  // merge overlapping page spans, register each once
-      uintptr_t lo = (uintptr_t)p->blocks[cand[i]].host / page * page;
-      uintptr_t hi = round_up((uintptr_t)p->blocks[cand[i]].host + p->blocks[cand[i]].bytes, page);
-      size_t j = i + 1;
-      while (j < cand.size() && (uintptr_t)p->blocks[cand[j]].host / page * page <= hi) {
-        hi = std::max<uintptr_t>(hi, round_up((uintptr_t)p->blocks[cand[j]].host + p->blocks[cand[j]].bytes, page));
-        j++;
-      }
-      // only spans this plan page-locks itself move directly; anything else
-      // (already registered elsewhere, or refused) is staged
-      cudaError_t e = cudaHostRegister((void*)lo, hi - lo, cudaHostRegisterDefault);
-      if (e == cudaSuccess) {
-        p->registered.push_back({(void*)lo, hi - lo});
-        for (size_t k = i; k < j; k++) p->direct[cand[k]] = 1;
-      } else {
-        cudaGetLastError();  // not a sticky error: clear it
-      }
-      i = j;
-    }
-  }
-  std::vector<uint32_t> all(nb);
-  for (uint32_t b = 0; b < nb; b++) all[b] = b;
-  plan_moves(p, all, &p->h2d);
-  p->transfers_ready = true;
-}
-
-void marshal_units(dc_plan_s* p, Pool& pool, const dc_plan_s::Moves& m, uint64_t ufirst, uint64_t ulast, bool to_arena) {
-  auto unit = [&](uint64_t u) {
-    for (uint64_t k = m.units[u].first; k < m.units[u].last; k++) {
-      const auto& pc = m.pieces[k];
-      if (to_arena)
-        memcpy(p->pinned + pc.off, pc.host, pc.len);
-      else
-        memcpy(pc.host, p->pinned + pc.off, pc.len);
-    }
-  };
-  if (ulast - ufirst == 1 || pool.size() == 1) {
-    for (uint64_t u = ufirst; u < ulast; u++) unit(u);
-  } else {
-    pool.parallel_for(ulast - ufirst, [&](uint64_t i) { unit(ufirst + i); });
-  }
-}
-
-dc_status device_error(dc_plan_s* p, cudaStream_t s) {
+dc_status dc::device_error(dc_plan_s* p, cudaStream_t s) {
   uint32_t* word = reinterpret_cast<uint32_t*>(p->pin_tab + tab_words(p->L));
   DC_CUDA(cudaMemcpyAsync(word, p->dev + p->L.ctrl + CTRL_ERR * 4, 4, cudaMemcpyDeviceToHost, s));
   DC_CUDA(cudaStreamSynchronize(s));
@@ -205,6 +105,8 @@ dc_status device_error(dc_plan_s* p, cudaStream_t s) {
   if (e & ERR_TIMEOUT) return fail(DC_ETIMEOUT, "a device-side wait gave up (0x%x)", e);
   return fail(DC_EVERIFY, "relocation check: a pointer slot did not hold the recorded host address");
 }
+
+namespace {
 
 OpKey key_of(const dc_op* op) {
   OpKey k;
@@ -378,7 +280,7 @@ dc_status dc_plan_destroy(dc_plan_t p) {
   if (p->tab_done) cudaEventSynchronize(p->tab_done);
   if (p->pinned) cudaFreeHost(p->pinned);
   if (p->pin_tab) cudaFreeHost(p->pin_tab);
-  for (auto& r : p->registered) cudaHostUnregister(r.first);
+  release_transfers(p);
   if (p->h2d_done) cudaEventDestroy(p->h2d_done);
   if (p->tab_done) cudaEventDestroy(p->tab_done);
   delete p;
@@ -396,12 +298,13 @@ dc_status dc_bind_device(dc_plan_t p, void* dev, uint64_t bytes, dc_stream_t str
   DC_CUDA(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device));
   if (p->h2d_done) DC_CUDA(cudaEventSynchronize(p->h2d_done));
   if (!p->pinned) {
-    cudaError_t e = cudaHostAlloc((void**)&p->pinned, std::max<uint64_t>(p->data_bytes, 16), cudaHostAllocDefault);
+    cudaError_t e = cudaHostAlloc((void**)&p->pinned, std::max<uint64_t>(p->data_bytes, 16), cudaHostAllocMapped);
     if (e != cudaSuccess) {
       p->pinned = nullptr;
       return fail(DC_ENOMEM, "pinned arena of %llu bytes: %s", (unsigned long long)p->data_bytes,
                   cudaGetErrorString(e));
     }
+    DC_CUDA(cudaHostGetDevicePointer((void**)&p->pinned_dev, p->pinned, 0));
     // padding between blocks stays zero: the marshal writes blocks only
     Pool& pool = pool_of(p);
     const uint64_t n = (p->data_bytes + (64ull << 20) - 1) / (64ull << 20);
@@ -410,6 +313,7 @@ dc_status dc_bind_device(dc_plan_t p, void* dev, uint64_t bytes, dc_stream_t str
       memset(p->pinned + lo, 0, hi - lo);
     });
   }
+  if (!p->transfers_ready) plan_transfers(p);
   if (!p->pin_tab || p->pin_tab_bytes < tab_total(p->L)) {
     if (p->pin_tab) cudaFreeHost(p->pin_tab);
     p->pin_tab_bytes = tab_total(p->L);
@@ -419,7 +323,6 @@ dc_status dc_bind_device(dc_plan_t p, void* dev, uint64_t bytes, dc_stream_t str
       return fail(DC_ENOMEM, "pinned table staging: %s", cudaGetErrorString(e));
     }
   }
-  if (!p->transfers_ready) plan_transfers(p);
   if (!p->h2d_done) DC_CUDA(cudaEventCreateWithFlags(&p->h2d_done, cudaEventDisableTiming));
   if (!p->tab_done) DC_CUDA(cudaEventCreateWithFlags(&p->tab_done, cudaEventDisableTiming));
   p->dev = (uint8_t*)dev;
@@ -428,7 +331,13 @@ dc_status dc_bind_device(dc_plan_t p, void* dev, uint64_t bytes, dc_stream_t str
   DC_CUDA(cudaMemcpyAsync(p->dev + p->L.rec, p->rec.data(), nb * sizeof(BlockRec), cudaMemcpyHostToDevice, s));
   DC_CUDA(cudaMemcpyAsync(p->dev + p->L.hostp, p->hostp.data(), nb * 8, cudaMemcpyHostToDevice, s));
   DC_CUDA(cudaMemsetAsync(p->dev + p->L.soff, 0, p->L.seg - p->L.soff, s));
+  {
+    dc_status st = upload_h2d_tables(p, s);
+    if (st) return st;
+  }
   DC_CUDA(cudaStreamSynchronize(s));
+  p->back_key.clear();
+  p->bk_nd = 0;
   p->epoch = 0;
   p->leaf_key = OpKey();
   p->chase_key = OpKey();
@@ -478,24 +387,8 @@ dc_status dc_deep_copy(dc_plan_t p, dc_stream_t stream) {
   // the previous deep copy's transfers read the same pinned arena
   dc_status st = wait_event(p->h2d_done);
   if (st) return st;
-  const dc_plan_s::Moves& m = p->h2d;
-  // large arrays: one DMA each, straight from the caller's (registered) pages
-  for (uint32_t b : m.direct)
-    DC_CUDA(cudaMemcpyAsync(p->dev + p->blocks[b].off, p->blocks[b].host, p->blocks[b].bytes, cudaMemcpyHostToDevice, s));
-  // everything else: Algorithm 1's contiguous buffer, marshalled and sent chunk by chunk
-  Pool& pool = pool_of(p);
-  size_t ns = 0;  // next NULL-slot fix-up
-  for (const auto& c : m.chunks) {
-    marshal_units(p, pool, m, c.ufirst, c.ulast, true);
-    const uint64_t hi = c.clast > c.cfirst ? m.copies[c.clast - 1].hi : 0;
-    while (ns < p->null_slots.size() && p->null_slots[ns] < hi) {
-      memset(p->pinned + p->null_slots[ns], 0, 8);
-      ns++;
-    }
-    for (uint64_t k = c.cfirst; k < c.clast; k++)
-      DC_CUDA(cudaMemcpyAsync(p->dev + m.copies[k].lo, p->pinned + m.copies[k].lo, m.copies[k].hi - m.copies[k].lo,
-                              cudaMemcpyHostToDevice, s));
-  }
+  pool_of(p);
+  if ((st = transfer_to_device(p, s))) return st;
   DC_CUDA(cudaEventRecord(p->h2d_done, s));
   return dc_relocate(p, stream);
 }
@@ -670,22 +563,8 @@ dc_status dc_copy_back(dc_plan_t p, uint32_t flags, dc_stream_t stream) {
     list = p->written;
   }
   std::sort(list.begin(), list.end());
-  if (list != p->back_key) {
-    plan_moves(p, list, &p->back);
-    p->back_key = list;
-  }
-  const dc_plan_s::Moves& m = p->back;
-  cudaStream_t s = stream;
-  // large arrays straight into the caller's pages; the rest via the pinned arena
-  for (uint32_t b : m.direct)
-    DC_CUDA(cudaMemcpyAsync(const_cast<uint8_t*>(p->blocks[b].host), p->dev + p->blocks[b].off, p->blocks[b].bytes,
-                            cudaMemcpyDeviceToHost, s));
-  for (const auto& c : m.copies)
-    DC_CUDA(cudaMemcpyAsync(p->pinned + c.lo, p->dev + c.lo, c.hi - c.lo, cudaMemcpyDeviceToHost, s));
-  dc_status st = device_error(p, s);  // synchronizes the stream
-  if (st) return st;
-  if (!m.units.empty()) marshal_units(p, pool_of(p), m, 0, m.units.size(), false);
-  return DC_OK;
+  pool_of(p);
+  return transfer_back(p, list, stream);
 }
 
 dc_status dc_sync(dc_plan_t p, dc_stream_t stream) {

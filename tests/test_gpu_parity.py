@@ -80,16 +80,32 @@ def test_dense_all_nodes_full_size():
     full_parity(lambda: tg.workload("dense"), {}, verify=True)
 
 
-def test_dense_all_nodes_staged_transfers():
-    # every block through the pinned arena (no direct DMA from host pages)
-    full_parity(lambda: tg.workload("dense"), {}, flags=dc.PLAN_STAGED)
-    full_parity(lambda: tg.workload("deep"), dict(sel=dc.SEL_CHAIN, path=tg.leaf_path(64)), flags=dc.PLAN_STAGED)
+def test_dense_all_nodes_mapped_host_pages():
+    # array interiors moved straight from / to the caller's page-locked pages
+    full_parity(lambda: tg.workload("dense"), {}, flags=dc.PLAN_MAP_HOST)
+    full_parity(lambda: tg.workload("deep"), dict(sel=dc.SEL_CHAIN, path=tg.leaf_path(64)), flags=dc.PLAN_MAP_HOST)
 
 
-def test_copy_back_all_arrays_mixed_direct_and_staged():
-    # lengths around the direct-transfer threshold (65,536 fp32 = 256 KiB)
-    full_parity(lambda: tg.node_tree(3, 9, tg.uniform(60000, 70000), seed=31), None)
-    full_parity(lambda: tg.node_tree(3, 9, tg.uniform(60000, 70000), seed=31), {})
+@pytest.mark.parametrize("flags", [0, dc.PLAN_MAP_HOST])
+def test_lengths_around_the_mapping_threshold(flags):
+    # 16,000-17,000 fp32 per array: interiors of 0-2 pages above 64 KiB, heads and tails staged
+    full_parity(lambda: tg.node_tree(3, 9, tg.uniform(16000, 17000), seed=31), None, flags=flags)
+    full_parity(lambda: tg.node_tree(3, 9, tg.uniform(16000, 17000), seed=31), {}, flags=flags)
+    full_parity(lambda: tg.node_tree(3, 9, tg.uniform(60000, 70000), seed=31), {}, flags=flags)
+
+
+def test_mapped_pages_do_not_break_callers_copies():
+    # while a MAP_HOST plan is bound, ordinary torch copies from other host memory work
+    t = tg.workload("tiny")
+    p = dc.Plan(t.schema, t.root, flags=dc.PLAN_MAP_HOST)
+    p.bind()
+    p.deep_copy()
+    p.sync()
+    for n in (1000, 100000, 3000000):
+        x = torch.arange(n, dtype=torch.float32)
+        assert torch.equal(x.cuda().cpu(), x)
+    p.destroy()
+    t.free()
 
 
 def test_dense_chain_listing2_path():
@@ -195,6 +211,37 @@ def test_many_tiny_segments():
     # 22,621 nodes of 1-9 elements: many segments per tile, multi-tile relocation
     full_parity(lambda: tg.node_tree(5, 12, tg.uniform(1, 9), seed=13), {}, verify=True)
     full_parity(lambda: tg.node_tree(5, 12, tg.uniform(1, 9), seed=13), {}, mode="chase")
+
+
+class CNode(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nchild", ctypes.c_int32), ("position", ctypes.c_void_p),
+                ("velocity", ctypes.c_void_p), ("child", ctypes.c_void_p)]
+
+
+class HandTree:
+    """root {n = 0 but position/velocity set to junk} -> 3 children with data:
+    the root's slots must come out NULL; its block takes the staged path while
+    the others move through mapped host pages."""
+
+    def __init__(self):
+        self.schema = tg.node_schema()
+        self.junk = (ctypes.c_float * 4)()
+        self.arrs = [(ctypes.c_float * 1000)(*[float(i % 97) / 128 for i in range(1000)]) for _ in range(6)]
+        self.kids = (CNode * 3)()
+        for j in range(3):
+            self.kids[j] = CNode(1000 - j, 0, ctypes.addressof(self.arrs[2 * j]), ctypes.addressof(self.arrs[2 * j + 1]),
+                                 None)
+        self.node = CNode(0, 3, ctypes.addressof(self.junk), ctypes.addressof(self.junk), ctypes.addressof(self.kids))
+        self.root = ctypes.addressof(self.node)
+
+    def free(self):
+        pass
+
+
+@pytest.mark.parametrize("flags", [0, dc.PLAN_MAP_HOST])
+def test_count_zero_slot_is_nulled_on_the_device(flags):
+    full_parity(HandTree, {}, flags=flags)
+    full_parity(HandTree, None, flags=flags)
 
 
 def test_lone_struct_and_empty_tree():
