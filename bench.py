@@ -66,7 +66,7 @@ class Clocks:
                 ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
             t0 = time.time()  # the timed region starts once the sampler is producing
             while time.time() - t0 < wait_s and os.path.getsize(self.path) == 0:
                 time.sleep(0.02)
@@ -266,17 +266,22 @@ def main():
     t_leaf = [b.elapsed_time(c) * 1e-3 for a, b, c in ev]
     t_step = max_over_ranks(sum(x + y for x, y in zip(t_reloc, t_leaf)))
     value = payload * world * args.steps / t_step / 1e9
+    step_median = max_over_ranks(statistics.median([x + y for x, y in zip(t_reloc, t_leaf)]))
 
     hbm, peak_kind = peaks()
     leaf_bytes = 12 * nelem
     leaf_avg = statistics.mean(t_leaf)
     reloc_avg = statistics.mean(t_reloc)
+    leaf_med = statistics.median(t_leaf)
+    reloc_med = statistics.median(t_reloc)
     reloc_bytes = info["nblocks"] * (16 + 8) + info["nstruct_blocks"] * 8
     roofline = {"bound": "hbm", "kernel": "leaf_kernel<float, AXPY_HALF>",
                 "achieved": round(leaf_bytes / leaf_avg / 1e9, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(leaf_bytes / leaf_avg / 1e9 / hbm, 4), "traffic": None,
                 "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
-                "algorithmic_bytes_per_launch": leaf_bytes, "avg_launch_us": round(leaf_avg * 1e6, 2)}
+                "algorithmic_bytes_per_launch": leaf_bytes, "avg_launch_us": round(leaf_avg * 1e6, 2),
+                "median_launch_us": round(leaf_med * 1e6, 2),
+                "frac_at_median": round(leaf_bytes / leaf_med / 1e9 / hbm, 4)}
 
     # ---- end to end through the C ABI with host buffers ----------------------
     def measure_e2e(pl):
@@ -381,8 +386,10 @@ def main():
                        "l2": "flushed: 512 MiB write before every timed step (outside the events)",
                        "parallelism": f"{world} independent tree(s), one per GPU"},
             "roofline": roofline,
-            "relocation": {"avg_launch_us": round(reloc_avg * 1e6, 2), "algorithmic_bytes": reloc_bytes,
-                           "achieved_gbs": round(reloc_bytes / reloc_avg / 1e9, 1)},
+            "relocation": {"avg_launch_us": round(reloc_avg * 1e6, 2), "median_launch_us": round(reloc_med * 1e6, 2),
+                           "algorithmic_bytes": reloc_bytes, "achieved_gbs": round(reloc_bytes / reloc_avg / 1e9, 1),
+                           "frac": round(reloc_bytes / reloc_avg / 1e9 / hbm, 4)},
+            "step_median_ms": round(step_median * 1e3, 4),
             "e2e": e2e, "e2e_staged": e2e_staged, "link": link, "compare": compare, "cpu_baseline": cpu,
             "clocks": clk,
             "gpu_launches": launches,

@@ -68,13 +68,12 @@ struct ChaseStep {
 static_assert(sizeof(ChaseStep) == 16, "ChaseStep is 16 bytes");
 
 // Control words in device scratch.
-enum CtrlWord : uint32_t { CTRL_TILE = 0, CTRL_DONE = 1, CTRL_ERR = 2, CTRL_WORDS = 16 };
+enum CtrlWord : uint32_t { CTRL_ERR = 2, CTRL_WORDS = 16 };
 enum DeviceErr : uint32_t { ERR_BOUNDS = 1u, ERR_TIMEOUT = 2u, ERR_VERIFY = 4u };
 
 constexpr uint32_t RELOC_THREADS = 256;
-constexpr uint32_t RELOC_ITEMS = 8;  // blocks per thread
+constexpr uint32_t RELOC_ITEMS = 4;  // blocks per thread
 constexpr uint32_t RELOC_TILE = RELOC_THREADS * RELOC_ITEMS;
-constexpr uint32_t EPOCH_LIMIT = (1u << 22) - 1;
 
 // ---- kernels (kernels.cu) ------------------------------------------------------
 
@@ -82,12 +81,11 @@ struct RelocArgs {
   uint8_t* arena;
   uint64_t data_bytes;
   const BlockRec* rec;
-  const uint64_t* hostp;
-  uint64_t* soff;                  // byte offsets of struct blocks
-  unsigned long long* status;      // look-back words, one per tile
-  uint32_t* ready;                 // per tile: epoch once its struct offsets are stored
+  const uint64_t* hostp;       // host address of each block (checked with DC_PLAN_VERIFY)
+  const uint64_t* soff;        // byte offset of each struct block (the parents)
+  const uint64_t* tile_base;   // per tile of RELOC_TILE blocks: offset of its first block, 16-byte units
   uint32_t* ctrl;
-  uint32_t nblocks, nstruct_blocks, ntiles, epoch, verify;
+  uint32_t nblocks, nstruct_blocks, ntiles, verify;
 };
 
 constexpr uint32_t LEAF_THREADS = 256;
@@ -167,7 +165,7 @@ dc_status copy_schema(const dc_schema* s, SchemaCopy* out);
 
 // Layout of the caller's device buffer (byte offsets).
 struct DevLayout {
-  uint64_t data = 0, rec = 0, hostp = 0, soff = 0, status = 0, ready = 0, ctrl = 0;
+  uint64_t data = 0, rec = 0, hostp = 0, soff = 0, status = 0, ctrl = 0;
   uint64_t seg = 0, tseg = 0, cseg = 0, steps = 0, walk = 0, total = 0;
   uint64_t mva = 0, mvat = 0, mvb = 0, mvbt = 0, bk = 0, bkt = 0;  // move tables + their tile tables
   uint64_t seg_cap = 0, tseg_cap = 0, step_cap = 0, walk_cap = 0, ntiles = 0, tab_cap = 0;
@@ -188,6 +186,8 @@ struct dc_plan_s {
   std::vector<uint32_t> ptr_target;      // per struct element, per pointer field: block or NONE
   std::vector<dc::BlockRec> rec;
   std::vector<uint64_t> hostp;
+  std::vector<uint64_t> struct_off;      // arena offset of each struct block
+  std::vector<uint64_t> tile_base;       // per relocation tile: offset of its first block / 16
   std::vector<uint64_t> null_slots;      // arena offsets of slots with count 0 but a non-NULL host value
   uint64_t nstructs = 0, nstruct_blocks = 0, payload = 0, data_bytes = 0, sum_depth = 0;
   uint32_t max_depth = 0;
@@ -203,13 +203,14 @@ struct dc_plan_s {
   uint64_t pin_tab_bytes = 0;
   cudaEvent_t h2d_done = nullptr; // last deep copy's transfers
   cudaEvent_t tab_done = nullptr; // last table upload
-  uint32_t epoch = 0;
   int sm_count = 0;
   int device = -1;
   dc::OpKey leaf_key, chase_key;  // ops whose tables are on the device
   uint64_t leaf_nseg = 0, leaf_units = 0, chase_nseg = 0, chase_elems = 0;
-  std::vector<uint32_t> written;  // arrays written by the last update (arena indices)
-  std::vector<uint32_t> leaf_written, chase_written;
+  const std::vector<uint32_t>* written = nullptr;  // arrays the last update wrote (leaf_written or chase_written)
+  std::vector<uint32_t> leaf_written, chase_written;  // ascending arena indices
+  uint64_t gen = 0;                // bumped whenever a written list is rebuilt
+  uint64_t leaf_gen = 0, chase_gen = 0, written_gen = 0;
   bool op_run = false;
   std::unique_ptr<dc::Pool> pool;
   // transfers (transfer.cpp), planned at the first bind
@@ -232,7 +233,7 @@ struct dc_plan_s {
   std::vector<std::pair<void*, uint64_t>> registered;  // caller pages this plan page-locked
   Moves h2d;
   uint64_t h2d_int_nd = 0, h2d_int_units = 0, h2d_frag_nd = 0, h2d_frag_units = 0;
-  std::vector<uint32_t> back_key;     // the block list `back` was built for
+  uint64_t back_key = ~0ull;          // generation of the block list `back` was built for (0 = all arrays)
   Moves back;
   uint64_t bk_nd = 0, bk_units = 0;
 };
@@ -268,7 +269,7 @@ void plan_transfers(dc_plan_s* p);
 void release_transfers(dc_plan_s* p);
 dc_status upload_h2d_tables(dc_plan_s* p, cudaStream_t s);
 dc_status transfer_to_device(dc_plan_s* p, cudaStream_t s);
-dc_status transfer_back(dc_plan_s* p, const std::vector<uint32_t>& list, cudaStream_t s);
+dc_status transfer_back(dc_plan_s* p, const std::vector<uint32_t>& list, uint64_t key, cudaStream_t s);
 // runtime.cpp
 dc_status device_error(dc_plan_s* p, cudaStream_t s);
 Pool& pool_of(dc_plan_s* p);

@@ -2,10 +2,10 @@
 //
 //   relocate_kernel  Fig 2 step d / Algorithm 1's attach loop: one pass that
 //                    computes every block's arena offset (an exclusive scan of
-//                    the 16-byte block sizes, warp shuffles inside a tile and
-//                    decoupled look-back across tiles) and rewrites the pointer
-//                    slot that refers to each block with the block's device
-//                    address.  Block records are read as 16-byte vectors.
+//                    the 16-byte block sizes with warp shuffles, on top of the
+//                    tile's base offset) and rewrites the pointer slot that
+//                    refers to each block with the block's device address.
+//                    Block records are read as 16-byte vectors.
 //   leaf_kernel      the leaf update through resolved effective addresses
 //                    (Sec. 3): x += 0.5*y or x *= scale over (x, y, n)
 //                    segments, 16-byte vector loads/stores, no pointer loads.
@@ -27,38 +27,6 @@ namespace dc {
 
 namespace {
 
-constexpr uint32_t FLAG_AGG = 1, FLAG_PREFIX = 2;
-constexpr uint32_t SPIN_LIMIT = 1u << 22;
-
-__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// look-back status word: epoch (22 bits) | flag (2 bits) | inclusive/aggregate
-// sum of 16-byte units (40 bits)
-__device__ __forceinline__ unsigned long long pack(uint32_t epoch, uint32_t flag, uint64_t v) {
-  return ((unsigned long long)epoch << 42) | ((unsigned long long)flag << 40) |
-         (v & ((1ull << 40) - 1));
-}
-
 __device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, uint32_t lane) {
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
@@ -68,164 +36,79 @@ __device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, uint32_t lane) {
   return v;
 }
 
-// Warp 0 of a CTA: publish this tile's aggregate, then look back over the
-// predecessors 32 at a time until a tile with an inclusive prefix is found
-// (decoupled look-back).  Returns the exclusive prefix (lane 0 publishes the
-// inclusive one).  Every wait is bounded; on a timeout the error word is set.
-__device__ uint64_t look_back(const RelocArgs& a, uint32_t t, uint64_t tile_sum, uint32_t lane) {
-  uint32_t* err = &a.ctrl[CTRL_ERR];
-  if (t == 0) {
-    if (lane == 0) st_release(&a.status[0], pack(a.epoch, FLAG_PREFIX, tile_sum));
-    return 0;
-  }
-  if (lane == 0) st_release(&a.status[t], pack(a.epoch, FLAG_AGG, tile_sum));
-  uint64_t prefix = 0;
-  int64_t top = (int64_t)t - 1;  // window: predecessors top, top-1, ..., top-31
-  uint32_t spins = 0;
-  while (top >= 0) {
-    const int64_t j = top - (int64_t)lane;
-    uint32_t fl = FLAG_PREFIX;  // before tile 0: an empty prefix
-    uint64_t v = 0;
-    if (j >= 0) {
-      unsigned long long w = ld_acquire(&a.status[j]);
-      fl = ((uint32_t)(w >> 42) == a.epoch) ? (uint32_t)(w >> 40) & 3u : 0u;
-      v = w & ((1ull << 40) - 1);
-    }
-    if (__any_sync(0xffffffffu, fl == 0)) {
-      if (++spins > SPIN_LIMIT || (ld_relaxed(err) & ERR_TIMEOUT)) {
-        if (lane == 0) atomicOr(err, ERR_TIMEOUT);
-        break;
-      }
-      __nanosleep(32);
-      continue;
-    }
-    const uint32_t pmask = __ballot_sync(0xffffffffu, fl == FLAG_PREFIX);
-    const uint32_t stop = pmask ? (uint32_t)(__ffs(pmask) - 1) : 31u;  // closest prefix in the window
-    uint64_t part = lane <= stop ? v : 0;
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) part += __shfl_xor_sync(0xffffffffu, part, d);
-    prefix += part;
-    if (pmask) break;
-    top -= 32;
-  }
-  if (lane == 0) st_release(&a.status[t], pack(a.epoch, FLAG_PREFIX, prefix + tile_sum));
-  return prefix;
-}
-
+// One tile of RELOC_TILE blocks per CTA iteration.  Warp w owns blocks
+// [base + w*32*ITEMS, base + (w+1)*32*ITEMS); its lanes read 32 consecutive
+// 16-byte records per instruction (coalesced).  The block sizes are scanned
+// with warp shuffles (slice by slice, carrying the running total), then across
+// the tile's warps, on top of the tile's base offset; every block's parent
+// slot is then rewritten.  Parents in an earlier tile take their offset from
+// the struct-offset table.
 __global__ void __launch_bounds__(RELOC_THREADS) relocate_kernel(RelocArgs a) {
   constexpr uint32_t NW = RELOC_THREADS / 32;
+  constexpr uint32_t WSPAN = 32 * RELOC_ITEMS;  // blocks per warp
   __shared__ uint64_t s_off[RELOC_TILE];
   __shared__ uint64_t s_warp[NW];
-  __shared__ uint64_t s_prefix;
-  __shared__ uint32_t s_tile;
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t* err = &a.ctrl[CTRL_ERR];
-  uint32_t ready_tile = NONE;  // last parent tile this thread saw ready
 
-  for (;;) {
-    if (tid == 0) s_tile = atomicAdd(&a.ctrl[CTRL_TILE], 1u);
-    __syncthreads();
-    const uint32_t t = s_tile;
-    if (t >= a.ntiles) break;
+  for (uint32_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
     const uint64_t base = (uint64_t)t * RELOC_TILE;
-
-    // this thread's blocks: base + tid*ITEMS + k (one 16-byte record each)
+    const uint64_t wbase = base + warp * WSPAN;
     BlockRec r[RELOC_ITEMS];
-    uint64_t local = 0;
 #pragma unroll
     for (uint32_t k = 0; k < RELOC_ITEMS; k++) {
-      uint64_t b = base + tid * RELOC_ITEMS + k;
+      const uint64_t b = wbase + k * 32 + lane;
       if (b < a.nblocks) {
-        uint4 v = __ldg(reinterpret_cast<const uint4*>(a.rec) + b);
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.rec) + b);
         r[k] = BlockRec{v.x, v.y, v.z, v.w};
       } else {
         r[k] = BlockRec{0, NONE, 0, 0};
       }
-      local += r[k].size16;
     }
-    // tile-wide exclusive scan of the block sizes
-    uint64_t incl = warp_incl_scan(local, lane);
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-      uint64_t w = lane < NW ? s_warp[lane] : 0;
-      w = warp_incl_scan(w, lane);
-      if (lane < NW) s_warp[lane] = w;
-      __syncwarp();
-      const uint64_t pre = look_back(a, t, __shfl_sync(0xffffffffu, w, NW - 1), lane);
-      if (lane == 0) s_prefix = pre;
-    }
-    __syncthreads();
-    const uint64_t excl = (warp ? s_warp[warp - 1] : 0) + incl - local;
-
-    // byte offsets of this thread's blocks; struct blocks publish theirs
-    uint64_t o16 = s_prefix + excl;
-    uint64_t off[RELOC_ITEMS];
+    // exclusive offsets inside the warp's span, slice by slice
+    uint64_t ex[RELOC_ITEMS];
+    uint64_t carry = 0;
 #pragma unroll
     for (uint32_t k = 0; k < RELOC_ITEMS; k++) {
-      uint64_t b = base + tid * RELOC_ITEMS + k;
-      off[k] = o16 * 16;
-      s_off[tid * RELOC_ITEMS + k] = off[k];
-      if (b < a.nstruct_blocks) a.soff[b] = off[k];
-      o16 += r[k].size16;
+      const uint64_t incl = warp_incl_scan(r[k].size16, lane);
+      ex[k] = carry + incl - r[k].size16;
+      carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) s_warp[warp] = carry;
+    __syncthreads();
+    uint64_t wpre = 0;  // every warp adds up the totals of the warps before it
+#pragma unroll
+    for (uint32_t w = 0; w < NW; w++) wpre += w < warp ? s_warp[w] : 0;
+    const uint64_t o16 = __ldg(&a.tile_base[t]) + wpre;
+#pragma unroll
+    for (uint32_t k = 0; k < RELOC_ITEMS; k++) {
+      const uint64_t b = wbase + k * 32 + lane;
+      ex[k] = (o16 + ex[k]) * 16;  // byte offset of block b
+      s_off[b - base] = ex[k];
+      if (a.verify && b < a.nstruct_blocks && __ldg(&a.soff[b]) != ex[k]) atomicOr(err, ERR_VERIFY);
     }
     __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      st_release(&a.ready[t], a.epoch);
-    }
-
     // rewrite the slot that points at each block (the root has none)
 #pragma unroll
     for (uint32_t k = 0; k < RELOC_ITEMS; k++) {
-      uint64_t b = base + tid * RELOC_ITEMS + k;
-      uint32_t p = r[k].parent;
+      const uint64_t b = wbase + k * 32 + lane;
+      const uint32_t p = r[k].parent;
       if (b >= a.nblocks || p == NONE) continue;
       if (p >= b || p >= a.nstruct_blocks) {
         atomicOr(err, ERR_BOUNDS);
         continue;
       }
-      uint64_t poff;
-      if (p >= base) {
-        poff = s_off[p - base];
-      } else {
-        const uint32_t pt = p / RELOC_TILE;
-        if (pt != ready_tile) {
-          uint32_t spins = 0;
-          bool ok = true;
-          while (ld_acquire(&a.ready[pt]) != a.epoch) {
-            if (++spins > SPIN_LIMIT || (ld_relaxed(err) & ERR_TIMEOUT)) {
-              atomicOr(err, ERR_TIMEOUT);
-              ok = false;
-              break;
-            }
-            __nanosleep(32);
-          }
-          if (!ok) continue;
-          ready_tile = pt;
-        }
-        poff = *(volatile const uint64_t*)&a.soff[p];
-      }
-      uint64_t slot = poff + r[k].slot_off;
+      const uint64_t poff = p >= base ? s_off[p - base] : __ldg(&a.soff[p]);
+      const uint64_t slot = poff + r[k].slot_off;
       if (slot + 8 > a.data_bytes || (slot & 7)) {
         atomicOr(err, ERR_BOUNDS);
         continue;
       }
       uint64_t* sp = reinterpret_cast<uint64_t*>(a.arena + slot);
       if (a.verify && *sp != a.hostp[b]) atomicOr(err, ERR_VERIFY);
-      *sp = reinterpret_cast<uint64_t>(a.arena) + off[k];
+      *sp = reinterpret_cast<uint64_t>(a.arena) + ex[k];
     }
-    __syncthreads();  // s_tile / s_off / s_prefix are reused by the next tile
-  }
-
-  // the last CTA out resets the tile counter for the next launch
-  if (tid == 0) {
-    __threadfence();
-    uint32_t d = atomicAdd(&a.ctrl[CTRL_DONE], 1u);
-    if (d == gridDim.x - 1) {
-      atomicExch(&a.ctrl[CTRL_TILE], 0u);
-      atomicExch(&a.ctrl[CTRL_DONE], 0u);
-    }
+    __syncthreads();  // s_off and s_warp are reused by the next tile
   }
 }
 
@@ -441,8 +324,8 @@ int occupancy(K kernel, int threads, size_t smem) {
 }  // namespace
 
 cudaError_t launch_relocate(const RelocArgs& a, cudaStream_t s, int sm_count) {
-  static int occ = occupancy(relocate_kernel, RELOC_THREADS, 0);
-  uint32_t grid = (uint32_t)std::min<uint64_t>(a.ntiles, (uint64_t)sm_count * occ);
+  (void)sm_count;
+  uint32_t grid = a.ntiles;  // one tile per CTA; the block scheduler overlaps their phases
   if (grid == 0) grid = 1;
   relocate_kernel<<<grid, RELOC_THREADS, 0, s>>>(a);
   count_launch();

@@ -324,6 +324,10 @@ dc_status build_plan(const dc_schema* schema, const void* host_root, dc_plan_s* 
     p->hostp[i] = (uint64_t)(uintptr_t)b.host;
   }
   p->data_bytes = off;
+  p->struct_off.resize(p->nstruct_blocks);
+  for (uint64_t i = 0; i < p->nstruct_blocks; i++) p->struct_off[i] = p->blocks[i].off;
+  p->tile_base.clear();
+  for (uint64_t i = 0; i < nb; i += RELOC_TILE) p->tile_base.push_back(p->blocks[i].off / 16);
   p->null_slots.clear();
   for (auto& ns : w.null_slots) p->null_slots.push_back(p->blocks[new_id[ns.first]].off + ns.second);
   std::sort(p->null_slots.begin(), p->null_slots.end());

@@ -33,10 +33,8 @@ DevLayout make_layout(const dc_plan_s* p) {
   L.soff = o;
   o = align256(o + std::max<uint64_t>(1, p->nstruct_blocks) * 8);
   L.ntiles = (nb + RELOC_TILE - 1) / RELOC_TILE;
-  L.status = o;
+  L.status = o;  // tile base offsets
   o = align256(o + L.ntiles * 8);
-  L.ready = o;
-  o = align256(o + L.ntiles * 4);
   L.ctrl = o;
   o = align256(o + CTRL_WORDS * 4);
   L.seg_cap = std::max<uint64_t>(1, p->nstructs);
@@ -330,18 +328,20 @@ dc_status dc_bind_device(dc_plan_t p, void* dev, uint64_t bytes, dc_stream_t str
   const uint64_t nb = p->blocks.size();
   DC_CUDA(cudaMemcpyAsync(p->dev + p->L.rec, p->rec.data(), nb * sizeof(BlockRec), cudaMemcpyHostToDevice, s));
   DC_CUDA(cudaMemcpyAsync(p->dev + p->L.hostp, p->hostp.data(), nb * 8, cudaMemcpyHostToDevice, s));
-  DC_CUDA(cudaMemsetAsync(p->dev + p->L.soff, 0, p->L.seg - p->L.soff, s));
+  DC_CUDA(cudaMemsetAsync(p->dev + p->L.ctrl, 0, CTRL_WORDS * 4, s));
+  DC_CUDA(cudaMemcpyAsync(p->dev + p->L.soff, p->struct_off.data(), p->struct_off.size() * 8, cudaMemcpyHostToDevice, s));
+  DC_CUDA(cudaMemcpyAsync(p->dev + p->L.status, p->tile_base.data(), p->tile_base.size() * 8, cudaMemcpyHostToDevice,
+                          s));
   {
     dc_status st = upload_h2d_tables(p, s);
     if (st) return st;
   }
   DC_CUDA(cudaStreamSynchronize(s));
-  p->back_key.clear();
+  p->back_key = ~0ull;
   p->bk_nd = 0;
-  p->epoch = 0;
   p->leaf_key = OpKey();
   p->chase_key = OpKey();
-  p->written.clear();
+  p->written = nullptr;
   p->op_run = false;
   return DC_OK;
 }
@@ -358,23 +358,17 @@ dc_status dc_relocate(dc_plan_t p, dc_stream_t stream) {
   if (!p->dev) return fail(DC_ESTATE, "no device buffer bound");
   cudaStream_t s = stream;
   // Fig 2 step d: rebuild every pointer on the device
-  if (++p->epoch > EPOCH_LIMIT) {
-    DC_CUDA(cudaMemsetAsync(p->dev + p->L.status, 0, p->L.ctrl - p->L.status, s));
-    p->epoch = 1;
-  }
   RelocArgs a;
   a.arena = p->dev;
   a.data_bytes = p->data_bytes;
   a.rec = reinterpret_cast<const BlockRec*>(p->dev + p->L.rec);
   a.hostp = reinterpret_cast<const uint64_t*>(p->dev + p->L.hostp);
-  a.soff = reinterpret_cast<uint64_t*>(p->dev + p->L.soff);
-  a.status = reinterpret_cast<unsigned long long*>(p->dev + p->L.status);
-  a.ready = reinterpret_cast<uint32_t*>(p->dev + p->L.ready);
+  a.soff = reinterpret_cast<const uint64_t*>(p->dev + p->L.soff);
+  a.tile_base = reinterpret_cast<const uint64_t*>(p->dev + p->L.status);
   a.ctrl = reinterpret_cast<uint32_t*>(p->dev + p->L.ctrl);
   a.nblocks = (uint32_t)p->blocks.size();
   a.nstruct_blocks = (uint32_t)p->nstruct_blocks;
   a.ntiles = (uint32_t)p->L.ntiles;
-  a.epoch = p->epoch;
   a.verify = (p->flags & DC_PLAN_VERIFY) ? 1u : 0u;
   DC_CUDA(launch_relocate(a, s, p->sm_count));
   return DC_OK;
@@ -427,16 +421,28 @@ dc_status dc_update_leaves(dc_plan_t p, const dc_op* op, dc_stream_t stream) {
     if ((st = wait_event(p->tab_done))) return st;
     Segment* seg = reinterpret_cast<Segment*>(p->pin_tab + tab_seg(p->L));
     const uint64_t base = (uint64_t)(uintptr_t)p->dev;
-    uint64_t units = 0;
+    const uint64_t esz = X.elem_size;
+    const bool axpy = op->kind == DC_OP_AXPY_HALF;
+    uint64_t units = 0, nseg = 0;
     p->leaf_written.clear();
+    p->leaf_gen = ++p->gen;
     for (size_t i = 0; i < picks.size(); i++) {
       const HostBlock& bx = p->blocks[picks[i].bx];
-      seg[i].x = base + bx.off;
-      seg[i].y = picks[i].by == NONE ? 0 : base + p->blocks[picks[i].by].off;
-      seg[i].n = bx.count;
-      seg[i].ubeg = units;
-      units += (bx.count * X.elem_size + 15) / 16;
+      const uint64_t x = base + bx.off, y = picks[i].by == NONE ? 0 : base + p->blocks[picks[i].by].off;
       p->leaf_written.push_back(picks[i].bx);
+      if (nseg) {  // x (and y) continue the previous segment after at most its padding: one stream
+        Segment& g = seg[nseg - 1];
+        const uint64_t end = g.x + g.n * esz;
+        if (x >= end && x - end < 16 && (x - g.x) % esz == 0 && (!axpy || y - g.y == x - g.x)) {
+          g.n = (x - g.x) / esz + bx.count;
+          continue;
+        }
+      }
+      seg[nseg++] = Segment{x, y, bx.count, 0};
+    }
+    for (uint64_t i = 0; i < nseg; i++) {
+      seg[i].ubeg = units;
+      units += (seg[i].n * esz + 15) / 16;
     }
     // tile -> segment holding the tile's first unit (two-pointer walk)
     uint32_t* tseg = reinterpret_cast<uint32_t*>(p->pin_tab + tab_tseg(p->L));
@@ -444,20 +450,21 @@ dc_status dc_update_leaves(dc_plan_t p, const dc_op* op, dc_stream_t stream) {
     if (ntiles + 1 > p->L.tseg_cap) return fail(DC_EINVAL, "tile table larger than planned");
     for (uint64_t t = 0, sg = 0; t < ntiles; t++) {
       const uint64_t u = t * LEAF_TILE;
-      while (sg + 1 < picks.size() && seg[sg + 1].ubeg <= u) sg++;
+      while (sg + 1 < nseg && seg[sg + 1].ubeg <= u) sg++;
       tseg[t] = (uint32_t)sg;
     }
-    tseg[ntiles] = picks.empty() ? 0 : (uint32_t)(picks.size() - 1);
-    if (!picks.empty()) {
-      DC_CUDA(cudaMemcpyAsync(p->dev + p->L.seg, seg, picks.size() * sizeof(Segment), cudaMemcpyHostToDevice, s));
+    tseg[ntiles] = nseg ? (uint32_t)(nseg - 1) : 0;
+    if (nseg) {
+      DC_CUDA(cudaMemcpyAsync(p->dev + p->L.seg, seg, nseg * sizeof(Segment), cudaMemcpyHostToDevice, s));
       DC_CUDA(cudaMemcpyAsync(p->dev + p->L.tseg, tseg, (ntiles + 1) * 4, cudaMemcpyHostToDevice, s));
     }
     DC_CUDA(cudaEventRecord(p->tab_done, s));
-    p->leaf_nseg = picks.size();
+    p->leaf_nseg = nseg;
     p->leaf_units = units;
     p->leaf_key = key;
   }
-  p->written = p->leaf_written;
+  p->written = &p->leaf_written;
+  p->written_gen = p->leaf_gen;
   p->op_run = true;
   LeafArgs a;
   a.seg = reinterpret_cast<const Segment*>(p->dev + p->L.seg);
@@ -489,6 +496,7 @@ dc_status dc_update_chase(dc_plan_t p, const dc_op* op, dc_stream_t stream) {
     std::vector<ChaseStep> steps;
     uint64_t elems = 0;
     p->chase_written.clear();
+    p->chase_gen = ++p->gen;
     for (size_t i = 0; i < picks.size(); i++) {
       uint32_t first = (uint32_t)steps.size();
       chain_steps(p, picks[i].sblk, picks[i].elem, &steps);
@@ -512,7 +520,8 @@ dc_status dc_update_chase(dc_plan_t p, const dc_op* op, dc_stream_t stream) {
     p->chase_elems = elems;
     p->chase_key = key;
   }
-  p->written = p->chase_written;
+  p->written = &p->chase_written;
+  p->written_gen = p->chase_gen;
   p->op_run = true;
   ChaseArgs a;
   a.seg = reinterpret_cast<const ChaseSeg*>(p->dev + p->L.cseg);
@@ -555,16 +564,20 @@ dc_status dc_verify_chain(dc_plan_t p, const dc_step* path, uint32_t len, dc_str
 dc_status dc_copy_back(dc_plan_t p, uint32_t flags, dc_stream_t stream) {
   if (!p) return fail(DC_EINVAL, "plan is NULL");
   if (!p->dev) return fail(DC_ESTATE, "no device buffer bound");
-  std::vector<uint32_t> list;
+  static const std::vector<uint32_t> none;
+  std::vector<uint32_t> all;
+  uint64_t key;
   if (flags & DC_COPY_ALL_ARRAYS) {
-    for (uint32_t b = (uint32_t)p->nstruct_blocks; b < p->blocks.size(); b++) list.push_back(b);
+    key = 0;
+    if (p->back_key != 0)
+      for (uint32_t b = (uint32_t)p->nstruct_blocks; b < p->blocks.size(); b++) all.push_back(b);
   } else {
     if (!p->op_run) return fail(DC_ESTATE, "no update has run: nothing to copy back");
-    list = p->written;
+    key = p->written_gen;
   }
-  std::sort(list.begin(), list.end());
   pool_of(p);
-  return transfer_back(p, list, stream);
+  const std::vector<uint32_t>& list = (flags & DC_COPY_ALL_ARRAYS) ? all : (key == p->back_key ? none : *p->written);
+  return transfer_back(p, list, key, stream);
 }
 
 dc_status dc_sync(dc_plan_t p, dc_stream_t stream) {

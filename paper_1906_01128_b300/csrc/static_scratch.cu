@@ -1,7 +1,7 @@
 // static_scratch.cu — dc_relocate_static: the relocation kernel run with its
-// scratch (block records, struct-block offsets, look-back words, control
-// words) taken from one fixed array in device memory instead of from a buffer
-// the caller sized and allocated.  Nothing here allocates: no cudaMalloc,
+// scratch (block records, struct-block offsets, tile offsets, control words)
+// taken from one fixed array in device memory instead of from a buffer the
+// caller sized and allocated.  Nothing here allocates: no cudaMalloc,
 // cudaHostAlloc or cudaFree, and no allocating library call.
 #include <cuda_runtime.h>
 
@@ -14,14 +14,14 @@ using namespace dc;
 namespace {
 
 constexpr uint64_t MAX_BLOCKS = DC_STATIC_MAX_BLOCKS;
-constexpr uint64_t MAX_TILES = 64;  // look-back words reserved; enough for any tile of >= 1024 blocks
-static_assert(MAX_BLOCKS <= MAX_TILES * RELOC_TILE, "look-back words cover every tile");
+constexpr uint64_t MAX_TILES = 64;  // tile words reserved; enough for any tile of >= 1024 blocks
+static_assert(MAX_BLOCKS <= MAX_TILES * RELOC_TILE, "tile words cover every tile");
 constexpr uint64_t al256(uint64_t x) { return (x + 255) / 256 * 256; }
 // byte layout of the array
 constexpr uint64_t OFF_REC = 0;                                   // 16 B per block
 constexpr uint64_t OFF_SOFF = al256(OFF_REC + 16 * MAX_BLOCKS);   // 8 B per struct block
-constexpr uint64_t OFF_STATUS = al256(OFF_SOFF + 8 * MAX_BLOCKS); // 8 B per tile
-constexpr uint64_t OFF_READY = al256(OFF_STATUS + 8 * MAX_TILES); // 4 B per tile
+constexpr uint64_t OFF_STATUS = al256(OFF_SOFF + 8 * MAX_BLOCKS); // 8 B per tile: tile base offsets
+constexpr uint64_t OFF_READY = al256(OFF_STATUS + 8 * MAX_TILES); // 4 B per tile (unused)
 constexpr uint64_t OFF_CTRL = al256(OFF_READY + 4 * MAX_TILES);   // control words
 constexpr uint64_t SCRATCH_BYTES = al256(OFF_CTRL + 4 * CTRL_WORDS);
 static_assert(SCRATCH_BYTES == DC_STATIC_SCRATCH_BYTES, "dc.h states the array's size");
@@ -74,23 +74,23 @@ extern "C" dc_status dc_relocate_static(dc_plan_t p, void* dev_data, uint64_t da
   dc_status st = scratch_for(dev, &s, &sms);
   if (st) return st;
   cudaStream_t cs = stream;
-  // the array keeps the previous call's contents: the look-back and control
-  // words must start at zero
-  DC_CUDA(cudaMemsetAsync(s + OFF_STATUS, 0, SCRATCH_BYTES - OFF_STATUS, cs));
+  // the array keeps the previous call's contents: the error word must start
+  // at zero, and this plan's tables replace the last call's
+  DC_CUDA(cudaMemsetAsync(s + OFF_CTRL, 0, SCRATCH_BYTES - OFF_CTRL, cs));
   DC_CUDA(cudaMemcpyAsync(s + OFF_REC, p->rec.data(), nb * sizeof(BlockRec), cudaMemcpyHostToDevice, cs));
+  DC_CUDA(cudaMemcpyAsync(s + OFF_SOFF, p->struct_off.data(), p->struct_off.size() * 8, cudaMemcpyHostToDevice, cs));
+  DC_CUDA(cudaMemcpyAsync(s + OFF_STATUS, p->tile_base.data(), p->tile_base.size() * 8, cudaMemcpyHostToDevice, cs));
   RelocArgs a;
   a.arena = static_cast<uint8_t*>(dev_data);
   a.data_bytes = p->data_bytes;
   a.rec = reinterpret_cast<const BlockRec*>(s + OFF_REC);
   a.hostp = nullptr;  // no slot check in this variant
-  a.soff = reinterpret_cast<uint64_t*>(s + OFF_SOFF);
-  a.status = reinterpret_cast<unsigned long long*>(s + OFF_STATUS);
-  a.ready = reinterpret_cast<uint32_t*>(s + OFF_READY);
+  a.soff = reinterpret_cast<const uint64_t*>(s + OFF_SOFF);
+  a.tile_base = reinterpret_cast<const uint64_t*>(s + OFF_STATUS);
   a.ctrl = reinterpret_cast<uint32_t*>(s + OFF_CTRL);
   a.nblocks = (uint32_t)nb;
   a.nstruct_blocks = (uint32_t)p->nstruct_blocks;
   a.ntiles = (uint32_t)((nb + RELOC_TILE - 1) / RELOC_TILE);
-  a.epoch = 1;
   a.verify = 0;
   DC_CUDA(launch_relocate(a, cs, sms));
   if (dev_status)

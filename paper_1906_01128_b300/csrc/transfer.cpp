@@ -238,8 +238,8 @@ dc_status transfer_to_device(dc_plan_s* p, cudaStream_t s) {
   return DC_OK;
 }
 
-dc_status transfer_back(dc_plan_s* p, const std::vector<uint32_t>& list, cudaStream_t s) {
-  if (list != p->back_key) {
+dc_status transfer_back(dc_plan_s* p, const std::vector<uint32_t>& list, uint64_t key, cudaStream_t s) {
+  if (key != p->back_key) {
     plan_moves(p, list, &p->back);
     const uint64_t base = (uint64_t)(uintptr_t)p->dev;
     std::vector<MoveDesc> d;
@@ -250,7 +250,7 @@ dc_status transfer_back(dc_plan_s* p, const std::vector<uint32_t>& list, cudaStr
       push_desc(&d, base + r.lo, (uint64_t)(uintptr_t)p->pinned_dev + r.lo, r.hi - r.lo);
     dc_status st = upload(p, d, p->L.bk, p->L.bkt, p->L.tab_cap, &p->bk_nd, &p->bk_units, s);
     if (st) return st;
-    p->back_key = list;
+    p->back_key = key;
   }
   dc_status st = launch_table(p, p->L.bk, p->L.bkt, p->bk_nd, p->bk_units, s);
   if (st) return st;
