@@ -100,8 +100,25 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_cores_used():
-    return 1
+def rank_seed(workload: str, rank: int) -> int:
+    """Each rank deep-copies its own independent tree of the workload: the
+    workload's seed shifted by the rank (weak scaling, no shared data)."""
+    import treegen as tg
+    return tg.WORKLOADS[workload][4] + rank
+
+
+def aggregate(payload_bytes: int, steps: int, t_local: float, world: int, dist=None):
+    """Whole-job throughput: bytes all ranks moved / the slowest rank's time.
+    Returns (GB/s, max time)."""
+    t = t_local
+    if world > 1:
+        import torch
+        x = torch.tensor([t_local], dtype=torch.float64)
+        dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+        x = x.to(dev)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t = float(x.item())
+    return payload_bytes * world * steps / t / 1e9, t
 
 
 def run_reference(args, rank, world):
@@ -210,7 +227,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
     # each rank deep-copies its own independent tree (weak scaling, no data-path collective)
-    tree = tg.node_tree(*tg.WORKLOADS[args.workload][:4], seed=tg.WORKLOADS[args.workload][4] + rank)
+    tree = tg.node_tree(*tg.WORKLOADS[args.workload][:4], seed=rank_seed(args.workload, rank))
     s = tree.schema
     payload = tree.payload_bytes
     nelem = tree.nelems("Node", "position")
@@ -264,8 +281,8 @@ def main():
     plan.sync()
     t_reloc = [a.elapsed_time(b) * 1e-3 for a, b, c in ev]
     t_leaf = [b.elapsed_time(c) * 1e-3 for a, b, c in ev]
-    t_step = max_over_ranks(sum(x + y for x, y in zip(t_reloc, t_leaf)))
-    value = payload * world * args.steps / t_step / 1e9
+    value, t_step = aggregate(payload, args.steps, sum(x + y for x, y in zip(t_reloc, t_leaf)), world,
+                              dist if world > 1 else None)
     step_median = max_over_ranks(statistics.median([x + y for x, y in zip(t_reloc, t_leaf)]))
 
     hbm, peak_kind = peaks()
