@@ -334,6 +334,20 @@ def main():
                 "deep_copy_gbs": round(info["data_bytes"] / statistics.median(t_dc) / 1e9, 2),
                 "copy_back_gbs": round(4 * nelem / statistics.median(t_cb) / 1e9, 2)}
 
+    def measure_roundtrip(pl):
+        t = []
+        for i in range(args.warmup + max(3, args.steps // 2)):
+            barrier()
+            t0 = time.perf_counter()
+            pl.roundtrip(op)
+            t1 = time.perf_counter()
+            if i >= args.warmup:
+                t.append(t1 - t0)
+        tt = max_over_ranks(statistics.mean(t))
+        return {"value": round(payload * world / tt / 1e9, 3), "unit": "GB/s",
+                "h2d_bytes_per_step": info["data_bytes"], "d2h_bytes_per_step": 4 * nelem,
+                "ms_per_step": round(tt * 1e3, 3)}
+
     e2e_staged = measure_e2e(plan)
     plan_m = dc.Plan(s, tree.root, flags=dc.PLAN_MAP_HOST)
     plan_m.bind()
@@ -341,11 +355,16 @@ def main():
     plan_m.update(op)
     plan_m.sync()
     e2e_mapped = measure_e2e(plan_m)
+    e2e_rt = measure_roundtrip(plan_m)
     plan_m.destroy()
     del plan_m
     clk = clocks.stop()
-    e2e = dict(e2e_mapped)
-    e2e["api"] = "dc_deep_copy + dc_update_leaves + dc_copy_back, plan flag DC_PLAN_MAP_HOST"
+    if e2e_rt["value"] >= e2e_mapped["value"]:
+        e2e = dict(e2e_rt)
+        e2e["api"] = "dc_roundtrip (deep copy + leaf update + copy back in one call), plan flag DC_PLAN_MAP_HOST"
+    else:
+        e2e = dict(e2e_mapped)
+        e2e["api"] = "dc_deep_copy + dc_update_leaves + dc_copy_back, plan flag DC_PLAN_MAP_HOST"
     link = link_peaks(torch)
     for mode, r in (("staged", e2e_staged), ("map_host", e2e_mapped)):
         link[f"deep_copy_frac_of_h2d_peak_{mode}"] = round(r["deep_copy_gbs"] / link["h2d_gbs"], 4)
@@ -407,7 +426,7 @@ def main():
                            "algorithmic_bytes": reloc_bytes, "achieved_gbs": round(reloc_bytes / reloc_avg / 1e9, 1),
                            "frac": round(reloc_bytes / reloc_avg / 1e9 / hbm, 4)},
             "step_median_ms": round(step_median * 1e3, 4),
-            "e2e": e2e, "e2e_staged": e2e_staged, "link": link, "compare": compare, "cpu_baseline": cpu,
+            "e2e": e2e, "e2e_three_calls_map_host": e2e_mapped, "e2e_staged": e2e_staged, "link": link, "compare": compare, "cpu_baseline": cpu,
             "clocks": clk,
             "gpu_launches": launches,
         }

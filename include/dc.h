@@ -234,6 +234,18 @@ dc_status dc_verify_chain(dc_plan_t plan, const dc_step* path, uint32_t len, dc_
 #define DC_COPY_ALL_ARRAYS 1u
 dc_status dc_copy_back(dc_plan_t plan, uint32_t flags, dc_stream_t stream);
 
+/* dc_roundtrip — dc_deep_copy, dc_update_leaves(op) and dc_copy_back(0) as one
+ * call (Algorithm 2 steps 3-5: transfer, run the kernel once, transfer back),
+ * with the same results.  With a DC_PLAN_MAP_HOST plan whose selected arrays
+ * start on 16-byte host addresses, the blocks the op does not touch move as in
+ * dc_deep_copy, and one kernel then reads each selected x and y element from
+ * host memory, applies the update, writes x and y into the arena and the new x
+ * straight back to the host: the two directions of the link overlap instead of
+ * following each other.  Otherwise it runs the three calls in turn.
+ * Blocking: returns when the host arrays hold the results.  Errors: as the
+ * three calls. */
+dc_status dc_roundtrip(dc_plan_t plan, const dc_op* op, dc_stream_t stream);
+
 /* dc_sync — wait for the plan's work on `stream` and report (then clear) the
  * device error word: DC_EDEVICE_BOUNDS, DC_ETIMEOUT or DC_EVERIFY. */
 dc_status dc_sync(dc_plan_t plan, dc_stream_t stream);

@@ -94,6 +94,7 @@ SIGNATURES = {
     "dc_update_chase": [_vp, _P(_Op), _vp],
     "dc_verify_chain": [_vp, _P(_Step), _u32, _vp, _P(_u64)],
     "dc_copy_back": [_vp, _u32, _vp],
+    "dc_roundtrip": [_vp, _P(_Op), _vp],
     "dc_sync": [_vp, _vp],
     "dc_device_base": [_vp, _P(_u64)],
     "dc_uvm_build": [_P(_Schema), _vp, _P(_vp)],
@@ -261,6 +262,11 @@ class Plan:
     def update_chase(self, op=None, stream=None):
         o, keep = _op(op or Op())
         _check(lib.dc_update_chase(self._h, ctypes.byref(o), _stream(stream)))
+
+    def roundtrip(self, op=None, stream=None):
+        """deep_copy + update(op) + copy_back in one pipelined call."""
+        o, keep = _op(op or Op())
+        _check(lib.dc_roundtrip(self._h, ctypes.byref(o), _stream(stream)))
 
     def copy_back(self, all_arrays: bool = False, stream=None):
         _check(lib.dc_copy_back(self._h, COPY_ALL_ARRAYS if all_arrays else 0, _stream(stream)))

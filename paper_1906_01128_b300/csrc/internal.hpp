@@ -117,6 +117,28 @@ struct MoveArgs {
   uint64_t units;
 };
 
+// One selected struct of a fused round trip (dc_roundtrip): its x and y blocks in the
+// arena (xd, yd), their element count, the unit prefix, and for each of x and
+// y where its bytes live on the host side: the host address, the mapped
+// interior [lo, hi) of caller pages with its device address, and the block's
+// place in the mapped pinned arena (for the bytes outside the interior).
+struct StreamSeg {
+  uint64_t xd, yd, n, ubeg;
+  uint64_t xh, xlo, xhi, xi, xp;
+  uint64_t yh, ylo, yhi, yi, yp;
+  uint64_t pad[2];
+};
+static_assert(sizeof(StreamSeg) == 128, "StreamSeg is 128 bytes");
+
+struct StreamArgs {
+  const StreamSeg* seg;
+  const uint32_t* tile_seg;
+  uint32_t nseg;
+  uint64_t units;
+  int kind, f64;
+  double scale;
+};
+
 struct ChaseArgs {
   const ChaseSeg* seg;
   const ChaseStep* steps;
@@ -131,6 +153,7 @@ cudaError_t launch_relocate(const RelocArgs& a, cudaStream_t s, int sm_count);
 cudaError_t launch_leaf(const LeafArgs& a, cudaStream_t s, int sm_count);
 cudaError_t launch_chase(const ChaseArgs& a, cudaStream_t s, int sm_count);
 cudaError_t launch_move(const MoveArgs& a, cudaStream_t s, int sm_count);
+cudaError_t launch_stream(const StreamArgs& a, cudaStream_t s, int sm_count);
 cudaError_t launch_walk(uint64_t root, const ChaseStep* steps, uint32_t nsteps, uint64_t final_add,
                         uint64_t* out, cudaStream_t s);
 void count_launch();
@@ -168,6 +191,7 @@ struct DevLayout {
   uint64_t data = 0, rec = 0, hostp = 0, soff = 0, status = 0, ctrl = 0;
   uint64_t seg = 0, tseg = 0, cseg = 0, steps = 0, walk = 0, total = 0;
   uint64_t mva = 0, mvat = 0, mvb = 0, mvbt = 0, bk = 0, bkt = 0;  // move tables + their tile tables
+  uint64_t sta = 0, stat = 0, stb = 0, stbt = 0, sts = 0, stst = 0;  // fused-step tables
   uint64_t seg_cap = 0, tseg_cap = 0, step_cap = 0, walk_cap = 0, ntiles = 0, tab_cap = 0;
 };
 
@@ -236,6 +260,13 @@ struct dc_plan_s {
   uint64_t back_key = ~0ull;          // generation of the block list `back` was built for (0 = all arrays)
   Moves back;
   uint64_t bk_nd = 0, bk_units = 0;
+  // the fused round trip (step.cpp), cached per op
+  dc::OpKey step_key;
+  bool step_fused = false;
+  Moves step_rest, step_xy, step_xback;
+  uint64_t st_int_nd = 0, st_int_units = 0, st_run_nd = 0, st_run_units = 0, st_nseg = 0, st_units = 0;
+  std::vector<uint32_t> step_written;
+  uint64_t step_gen = 0;
 };
 
 struct dc_uvm_s {
@@ -270,9 +301,25 @@ void release_transfers(dc_plan_s* p);
 dc_status upload_h2d_tables(dc_plan_s* p, cudaStream_t s);
 dc_status transfer_to_device(dc_plan_s* p, cudaStream_t s);
 dc_status transfer_back(dc_plan_s* p, const std::vector<uint32_t>& list, uint64_t key, cudaStream_t s);
+dc_status upload(dc_plan_s* p, const std::vector<MoveDesc>& d, uint64_t desc_off, uint64_t tile_off, uint64_t cap,
+                 uint64_t* nd, uint64_t* units, cudaStream_t s);
+void push_desc(std::vector<MoveDesc>* d, uint64_t src, uint64_t dst, uint64_t bytes);
+dc_status launch_table(dc_plan_s* p, uint64_t desc_off, uint64_t tile_off, uint64_t nd, uint64_t units,
+                       cudaStream_t s);
+void host_copy(dc_plan_s* p, const dc_plan_s::Moves& m, uint64_t ufirst, uint64_t ulast, bool to_arena);
+void null_slots_upto(dc_plan_s* p, size_t* ns, uint64_t hi);
 // runtime.cpp
 dc_status device_error(dc_plan_s* p, cudaStream_t s);
 Pool& pool_of(dc_plan_s* p);
+OpKey key_of(const dc_op* op);
+dc_status wait_event(cudaEvent_t e);
+// x (and y) target blocks of the structs an op selects; structs whose x is empty are skipped
+struct Pick {
+  uint32_t sblk;
+  uint64_t elem;
+  uint32_t bx, by;
+};
+dc_status pick(const dc_plan_s* p, const dc_op* op, std::vector<Pick>* out);
 // The chain of (field, index) steps from the root to struct (block, elem).
 void path_to(const dc_plan_s* p, uint32_t block, uint64_t elem, std::vector<dc_step>* out);
 }  // namespace dc

@@ -16,6 +16,10 @@
 //                    arena in 16-byte units (the deep copy's transfer and the
 //                    copy back, one launch for every block instead of one DMA
 //                    per block).
+//   stream_kernel    the fused step: reads x and y of the selected structs from
+//                    host memory (mapped caller pages or the mapped pinned
+//                    arena), applies the leaf update, writes x and y into the
+//                    arena and x straight back to the host, in one pass.
 //   walk_kernel      one thread follows a chain and reports the address.
 #include <cuda_runtime.h>
 
@@ -258,6 +262,81 @@ __global__ void __launch_bounds__(LEAF_THREADS) move_kernel(MoveArgs a) {
   }
 }
 
+// ---- fused step: host -> update -> arena + host --------------------------------
+
+// Device-visible address of byte `off` of a block whose host copy is split in a
+// mapped interior [lo, hi) and the rest, kept in the mapped pinned arena.
+__device__ __forceinline__ uint64_t host_side(uint64_t h, uint64_t lo, uint64_t hi, uint64_t idev, uint64_t pin,
+                                              uint64_t off) {
+  const uint64_t a = h + off;
+  return (a >= lo && a < hi) ? idev + (a - lo) : pin + off;
+}
+
+template <typename T, int KIND>
+__global__ void __launch_bounds__(LEAF_THREADS) stream_kernel(StreamArgs a) {
+  using VT = typename V16<T>::type;
+  constexpr int EPU = V16<T>::N;
+  const T sc = (T)a.scale;
+  const StreamSeg* seg = a.seg;
+  auto ub = [&](uint32_t s) { return __ldg(&seg[s].ubeg); };
+  for (uint64_t t = blockIdx.x; t * LEAF_TILE < a.units; t += gridDim.x) {
+    const uint64_t u0 = t * LEAF_TILE;
+    const uint32_t lo = __ldg(&a.tile_seg[t]), hi = __ldg(&a.tile_seg[t + 1]);
+    VT xv[LEAF_UNROLL], yv[LEAF_UNROLL];
+    uint64_t xs[LEAF_UNROLL], xd[LEAF_UNROLL], yd[LEAF_UNROLL];
+    uint32_t cnt[LEAF_UNROLL];  // elements of this unit
+#pragma unroll
+    for (uint32_t k = 0; k < LEAF_UNROLL; k++) {  // issue every host read first
+      const uint64_t u = u0 + threadIdx.x + k * LEAF_THREADS;
+      cnt[k] = 0;
+      if (u >= a.units) continue;
+      const uint32_t s = lo == hi ? lo : search(lo, hi, u, ub);
+      const StreamSeg& g = seg[s];
+      const uint64_t e0 = (u - __ldg(&g.ubeg)) * EPU, off = e0 * sizeof(T);
+      const uint64_t left = __ldg(&g.n) - e0;
+      cnt[k] = left >= (uint64_t)EPU ? EPU : (uint32_t)left;
+      xs[k] = host_side(__ldg(&g.xh), __ldg(&g.xlo), __ldg(&g.xhi), __ldg(&g.xi), __ldg(&g.xp), off);
+      xd[k] = __ldg(&g.xd) + off;
+      uint64_t ys = 0;
+      if (KIND == DC_OP_AXPY_HALF) {
+        ys = host_side(__ldg(&g.yh), __ldg(&g.ylo), __ldg(&g.yhi), __ldg(&g.yi), __ldg(&g.yp), off);
+        yd[k] = __ldg(&g.yd) + off;
+      }
+      if (cnt[k] == EPU) {
+        xv[k] = *reinterpret_cast<const VT*>(xs[k]);
+        if (KIND == DC_OP_AXPY_HALF) yv[k] = *reinterpret_cast<const VT*>(ys);
+      } else {
+        T* xe = reinterpret_cast<T*>(&xv[k]);
+        T* ye = reinterpret_cast<T*>(&yv[k]);
+        for (uint32_t i = 0; i < cnt[k]; i++) {
+          xe[i] = reinterpret_cast<const T*>(xs[k])[i];
+          if (KIND == DC_OP_AXPY_HALF) ye[i] = reinterpret_cast<const T*>(ys)[i];
+        }
+      }
+    }
+#pragma unroll
+    for (uint32_t k = 0; k < LEAF_UNROLL; k++) {
+      if (!cnt[k]) continue;
+      T* x = reinterpret_cast<T*>(&xv[k]);
+      const T* y = reinterpret_cast<const T*>(&yv[k]);
+      if (cnt[k] == EPU) {
+        if (KIND == DC_OP_AXPY_HALF) *reinterpret_cast<VT*>(yd[k]) = yv[k];  // the deep copy of y
+#pragma unroll
+        for (int i = 0; i < EPU; i++) x[i] = apply<T, KIND>(x[i], KIND == DC_OP_AXPY_HALF ? y[i] : T(0), sc);
+        *reinterpret_cast<VT*>(xd[k]) = xv[k];  // the arena holds the updated x
+        *reinterpret_cast<VT*>(xs[k]) = xv[k];  // and so does the host
+      } else {
+        for (uint32_t i = 0; i < cnt[k]; i++) {
+          if (KIND == DC_OP_AXPY_HALF) reinterpret_cast<T*>(yd[k])[i] = y[i];
+          const T v = apply<T, KIND>(x[i], KIND == DC_OP_AXPY_HALF ? y[i] : T(0), sc);
+          reinterpret_cast<T*>(xd[k])[i] = v;
+          reinterpret_cast<T*>(xs[k])[i] = v;
+        }
+      }
+    }
+  }
+}
+
 // ---- per-element pointer chase ---------------------------------------------
 
 // A load the compiler must issue every time it appears (no hoisting or reuse).
@@ -372,6 +451,23 @@ cudaError_t launch_move(const MoveArgs& a, cudaStream_t s, int sm_count) {
   uint64_t tiles = (a.units + LEAF_TILE - 1) / LEAF_TILE;
   uint32_t grid = (uint32_t)std::min<uint64_t>(tiles, (uint64_t)sm_count * occ);
   move_kernel<<<grid, LEAF_THREADS, 0, s>>>(a);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stream(const StreamArgs& a, cudaStream_t s, int sm_count) {
+  if (a.units == 0 || a.nseg == 0) return cudaSuccess;
+  uint64_t tiles = (a.units + LEAF_TILE - 1) / LEAF_TILE;
+  auto go = [&](auto kernel) {
+    static int occ = 0;
+    if (!occ) occ = occupancy(kernel, LEAF_THREADS, 0);
+    uint32_t grid = (uint32_t)std::min<uint64_t>(tiles, (uint64_t)sm_count * occ);
+    kernel<<<grid, LEAF_THREADS, 0, s>>>(a);
+  };
+  if (a.f64)
+    a.kind == DC_OP_AXPY_HALF ? go(stream_kernel<double, DC_OP_AXPY_HALF>) : go(stream_kernel<double, DC_OP_SCALE>);
+  else
+    a.kind == DC_OP_AXPY_HALF ? go(stream_kernel<float, DC_OP_AXPY_HALF>) : go(stream_kernel<float, DC_OP_SCALE>);
   count_launch();
   return cudaGetLastError();
 }

@@ -53,11 +53,15 @@ DevLayout make_layout(const dc_plan_s* p) {
   uint64_t interiors = 0;
   for (const auto& b : p->blocks) interiors += interior_bytes(b) ? 1 : 0;
   L.tab_cap = nb + 2 * interiors;
-  for (uint64_t* t : {&L.mva, &L.mvat, &L.mvb, &L.mvbt, &L.bk, &L.bkt}) {
+  for (uint64_t* t : {&L.mva, &L.mvat, &L.mvb, &L.mvbt, &L.bk, &L.bkt, &L.sta, &L.stat, &L.stb, &L.stbt}) {
     *t = o;
-    bool tiles = (t == &L.mvat || t == &L.mvbt || t == &L.bkt);
+    bool tiles = (t == &L.mvat || t == &L.mvbt || t == &L.bkt || t == &L.stat || t == &L.stbt);
     o = align256(o + (tiles ? L.tseg_cap * 4 : L.tab_cap * sizeof(MoveDesc)));
   }
+  L.sts = o;  // fused-step segments and their tile table
+  o = align256(o + L.seg_cap * sizeof(StreamSeg));
+  L.stst = o;
+  o = align256(o + L.tseg_cap * 4);
   L.walk_cap = (uint64_t)p->max_depth + 2;
   L.walk = o;
   o = align256(o + L.walk_cap * sizeof(ChaseStep) + 16);
@@ -106,7 +110,9 @@ dc_status dc::device_error(dc_plan_s* p, cudaStream_t s) {
 
 namespace {
 
-OpKey key_of(const dc_op* op) {
+}  // namespace
+
+OpKey dc::key_of(const dc_op* op) {
   OpKey k;
   k.kind = op->kind;
   k.sel = op->sel;
@@ -117,14 +123,7 @@ OpKey key_of(const dc_op* op) {
   return k;
 }
 
-// x (and y) target blocks of the selected structs; structs whose x is empty are skipped.
-struct Pick {
-  uint32_t sblk;
-  uint64_t elem;
-  uint32_t bx, by;
-};
-
-dc_status pick(const dc_plan_s* p, const dc_op* op, std::vector<Pick>* out) {
+dc_status dc::pick(const dc_plan_s* p, const dc_op* op, std::vector<Pick>* out) {
   std::vector<std::pair<uint32_t, uint64_t>> sel;
   dc_status st = select_structs(p, op, &sel);
   if (st) return st;
@@ -150,6 +149,8 @@ dc_status pick(const dc_plan_s* p, const dc_op* op, std::vector<Pick>* out) {
   return DC_OK;
 }
 
+namespace {
+
 // chase steps from the root to struct (sblk, elem), appended to `steps`
 void chain_steps(const dc_plan_s* p, uint32_t sblk, uint64_t elem, std::vector<ChaseStep>* steps) {
   size_t start = steps->size();
@@ -165,10 +166,14 @@ void chain_steps(const dc_plan_s* p, uint32_t sblk, uint64_t elem, std::vector<C
   std::reverse(steps->begin() + start, steps->end());
 }
 
-dc_status wait_event(cudaEvent_t e) {
+}  // namespace
+
+dc_status dc::wait_event(cudaEvent_t e) {
   if (e) DC_CUDA(cudaEventSynchronize(e));
   return DC_OK;
 }
+
+namespace {
 
 dc_status path_steps(const dc_plan_s* p, const dc_step* path, uint32_t len, std::vector<ChaseStep>* out) {
   uint32_t blk, ty;
@@ -339,6 +344,7 @@ dc_status dc_bind_device(dc_plan_t p, void* dev, uint64_t bytes, dc_stream_t str
   DC_CUDA(cudaStreamSynchronize(s));
   p->back_key = ~0ull;
   p->bk_nd = 0;
+  p->step_key = OpKey();
   p->leaf_key = OpKey();
   p->chase_key = OpKey();
   p->written = nullptr;

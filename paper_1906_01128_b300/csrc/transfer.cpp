@@ -134,8 +134,6 @@ void release_transfers(dc_plan_s* p) {
   p->registered.clear();
 }
 
-namespace {
-
 // Upload a move table (descriptors + per-tile first descriptor) on `s`.  The
 // sources are pageable vectors: cudaMemcpyAsync returns once it has staged
 // them, so they may go away afterwards.
@@ -199,8 +197,6 @@ void null_slots_upto(dc_plan_s* p, size_t* ns, uint64_t hi) {
     (*ns)++;
   }
 }
-
-}  // namespace
 
 dc_status upload_h2d_tables(dc_plan_s* p, cudaStream_t s) {
   const uint64_t base = (uint64_t)(uintptr_t)p->dev;

@@ -330,3 +330,41 @@ def test_stream_ordering_on_a_side_stream():
     oracle.copy_back(s, cp.root, ref.root, oracle.Op())
     assert oracle.trees_equal(s, src.root, ref.root)[0]
     p.destroy()
+
+
+# ---- the fused round trip (deep copy + update + copy back in one call) ------------------
+
+def step_parity(make, op_kw, flags, repeat=1):
+    src, ref = make(), make()
+    s = src.schema
+    plan = dc.Plan(s, src.root, flags=flags)
+    plan.bind()
+    dop, oop = ops_pair(**op_kw)
+    for _ in range(repeat):
+        plan.roundtrip(dop)
+        cp = oracle.deep_copy(s, ref.root)  # the oracle's pass: copy, update, copy back
+        oracle.update(s, cp.root, oop)
+        oracle.copy_back(s, cp.root, ref.root, oop)
+        image_ok(plan, s, cp.root)  # the arena holds the updated copy
+        ok, msg = oracle.trees_equal(s, src.root, ref.root)
+        assert ok, msg
+    plan.destroy()
+    src.free()
+    ref.free()
+
+
+@pytest.mark.parametrize("flags", [dc.PLAN_MAP_HOST, 0])
+def test_step_dense_all_nodes(flags):
+    step_parity(lambda: tg.workload("dense"), {}, flags, repeat=2)
+
+
+def test_step_deep_chain_and_ragged():
+    step_parity(lambda: tg.workload("deep"), dict(sel=dc.SEL_CHAIN, path=tg.leaf_path(64)), dc.PLAN_MAP_HOST)
+    step_parity(lambda: tg.node_tree(3, 9, tg.uniform(0, 40000), seed=41), {}, dc.PLAN_MAP_HOST, repeat=2)
+    step_parity(lambda: tg.node_tree(5, 12, tg.uniform(1, 9), seed=13), {}, dc.PLAN_MAP_HOST)
+
+
+def test_step_scale_f64_and_null_slots():
+    step_parity(lambda: tg.linear_tree(6, 100000, "allinit", seed=3), dict(kind=dc.OP_SCALE, x=2, scale=1.5),
+                dc.PLAN_MAP_HOST)
+    step_parity(HandTree, {}, dc.PLAN_MAP_HOST, repeat=2)
