@@ -39,6 +39,9 @@ WORKLOADS = {
              "update through the 63-step chain to the leaf, seed 3"),
     "reloc_stress": ("pointer-heavy tree: 6 levels, fanout 16 (1,118,481 nodes), " + NODE + ", 10 fp32 per array "
                      "(the paper's n = 10 Dense case), seed 6"),
+    "batched": ("4,096 independent node trees of uneven shape: per tree levels U{1..5}, fanout U{1..8}; array "
+                "lengths lognormal(median 4,096, sigma 1.0, cap 2^20) fp32; trees redrawn until their payload is in "
+                "[16 KiB, 7 MiB] (~4.4 GiB in all), seed 4"),
 }
 
 
@@ -104,6 +107,8 @@ def rank_seed(workload: str, rank: int) -> int:
     """Each rank deep-copies its own independent tree of the workload: the
     workload's seed shifted by the rank (weak scaling, no shared data)."""
     import treegen as tg
+    if workload == "batched":
+        return 4 + rank
     return tg.WORKLOADS[workload][4] + rank
 
 
@@ -127,24 +132,26 @@ def run_reference(args, rank, world):
     import treegen as tg
     if rank != 0:
         return
-    t = tg.workload(args.workload)
-    s = t.schema
-    payload = t.payload_bytes
+    trees = tg.batched(512, seed=rank_seed("batched", 0)) if args.workload == "batched" else [tg.workload(args.workload)]
+    s = trees[0].schema
+    payload = sum(t.payload_bytes for t in trees)
     op = oracle_op(args.workload)
     times = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        cp = oracle.deep_copy(s, t.root)
-        oracle.update(s, cp.root, op)
-        oracle.copy_back(s, cp.root, t.root, op)
+        for t in trees:
+            cp = oracle.deep_copy(s, t.root)
+            oracle.update(s, cp.root, op)
+            oracle.copy_back(s, cp.root, t.root, op)
+            del cp
         dt = time.perf_counter() - t0
-        del cp
         if i >= args.warmup:
             times.append(dt)
     total = sum(times)
     v = payload * len(times) / total / 1e9
     sample = (f"{len(times)} full passes (deep copy into a fresh host arena, update every node, copy back) "
-              f"over the whole {payload / 1e6:.1f} MB workload, single thread")
+              f"over {'the first 512 trees' if args.workload == 'batched' else 'the whole workload'} "
+              f"({payload / 1e6:.1f} MB), single thread")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / len(times), 3),
@@ -200,6 +207,126 @@ def link_peaks(torch, nbytes=256 << 20, reps=5):
     return out
 
 
+def run_batched(args, rank, world):
+    """One forest plan over 4,096 trees (one fused relocation + update launch;
+    one round trip) against 4,096 per-structure plans (two launches each; one
+    round trip each), on the same GPU."""
+    import torch
+    import treegen as tg
+    import paper_1906_01128_b300 as dc
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ntrees = int(os.environ.get("DC_BATCH_TREES", "4096"))
+    trees = tg.batched(ntrees, seed=rank_seed("batched", rank))
+    s = trees[0].schema
+    payload = sum(t.payload_bytes for t in trees)
+    nelem = sum(t.nelems("Node", "position") for t in trees)
+    op = dc.Op()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    forest = dc.Plan(s, [t.root for t in trees], flags=dc.PLAN_MAP_HOST)
+    forest.bind()
+    info = forest.info
+    forest.deep_copy()
+    threads, ctas = forest.autotune(op)
+    forest.deep_copy()
+    forest.sync()
+    singles = [dc.Plan(s, t.root, flags=dc.PLAN_MAP_HOST) for t in trees]
+    for p in singles:
+        p.bind()
+        p.deep_copy()
+        p.update(op)
+    torch.cuda.synchronize()
+    clocks = Clocks()
+    clocks.start()
+
+    def timed(fn, reps):
+        ts = []
+        for _ in range(args.warmup):
+            flush.zero_()
+            fn()
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+        return statistics.median(ts), ts
+
+    launches0 = dc.kernel_launches()
+    t_forest, ts_forest = timed(lambda: forest.relocate_update(op), args.steps)
+    launches = dc.kernel_launches() - launches0
+
+    def per_structure():
+        for p in singles:
+            p.relocate()
+            p.update(op)
+    t_single, _ = timed(per_structure, max(3, args.steps // 4))
+
+    def wall(fn, reps):
+        ts = []
+        for i in range(args.warmup + reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                ts.append(time.perf_counter() - t0)
+        return statistics.median(ts)
+
+    e2e_forest = wall(lambda: forest.roundtrip(op), max(3, args.steps // 4))
+    e2e_single = wall(lambda: [p.roundtrip(op) for p in singles], 3)
+    clk = clocks.stop()
+    hbm, peak_kind = peaks()
+    reloc_bytes = info["nblocks"] * 24 + info["nstruct_blocks"] * 8
+    fused_bytes = 12 * nelem + reloc_bytes
+    t_mean = statistics.mean(ts_forest)
+    cpu = None
+    if not args.no_cpu:
+        import oracle
+        t_cpu, n = 0.0, 0
+        for t in trees[:512]:  # a bounded sample: the first 512 trees
+            t0 = time.perf_counter()
+            cp = oracle.deep_copy(s, t.root)
+            oracle.update(s, cp.root, oracle.Op())
+            oracle.copy_back(s, cp.root, t.root, oracle.Op())
+            t_cpu += time.perf_counter() - t0
+            n += t.payload_bytes
+        cpu = {"value": round(n / t_cpu / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"the first 512 of the {ntrees} trees ({n / 1e6:.1f} MB), deep copy + update + copy back, "
+                         f"one core"}
+    out = {
+        "metric": METRIC, "value": round(payload * world / t_mean / 1e9, 2), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_mean * 1e3, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS["batched"], "trees": ntrees, "nodes": info["nstructs"],
+                   "blocks": info["nblocks"], "payload_bytes": payload,
+                   "step": "dc_relocate_update on the forest (one persistent launch)",
+                   "l2": "flushed: 512 MiB write before every timed step (outside the events)"},
+        "roofline": {"bound": "hbm", "kernel": "fused_kernel<float, AXPY_HALF> (relocation + leaf update)",
+                     "achieved": round(fused_bytes / t_mean / 1e9, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(fused_bytes / t_mean / 1e9 / hbm, 4), "traffic": None,
+                     "peak_kind": peak_kind, "algorithmic_bytes_per_launch": fused_bytes,
+                     "avg_launch_us": round(t_mean * 1e6, 2)},
+        "batched": {"autotuned_split": {"threads_per_cta": threads, "ctas_per_sm": ctas or "max"},
+                    "device_step_ms": {"forest_one_launch": round(t_forest * 1e3, 4),
+                                       "per_structure_8192_launches": round(t_single * 1e3, 3)},
+                    "device_speedup": round(t_single / t_forest, 2),
+                    "e2e_ms": {"forest_roundtrip": round(e2e_forest * 1e3, 3),
+                               "per_structure_roundtrips": round(e2e_single * 1e3, 3)},
+                    "e2e_speedup": round(e2e_single / e2e_forest, 2)},
+        "e2e": {"value": round(payload * world / e2e_forest / 1e9, 3), "unit": "GB/s",
+                "h2d_bytes_per_step": info["data_bytes"], "d2h_bytes_per_step": 4 * nelem,
+                "api": "dc_roundtrip on the forest plan, DC_PLAN_MAP_HOST"},
+        "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    for p in singles:
+        p.destroy()
+    forest.destroy()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -216,6 +343,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batched":
+        return run_batched(args, rank, world)
 
     import torch
     import torch.distributed as dist

@@ -130,7 +130,8 @@ typedef struct {
   uint64_t nrelocs;        /* pointer slots rewritten by the relocation (nblocks - 1) */
   uint64_t nstructs;       /* struct instances in the tree */
   uint64_t nstruct_blocks; /* blocks that hold structs (root + child arrays) */
-  uint64_t root_offset;    /* offset of the root struct in the data region (0) */
+  uint64_t root_offset;    /* offset of the (first) root struct in the data region (0) */
+  uint64_t ntrees;         /* trees in the plan (1, or the count given to dc_plan_forest) */
 } dc_plan_info;
 
 /* Plan flags (dc_plan_set_flags, before dc_bind_device). */
@@ -157,6 +158,15 @@ typedef struct {
  * 16-byte boundary.  Errors: DC_EINVAL (NULL pointer with a non-zero count,
  * negative count, bad schema), DC_EALIAS / DC_ECYCLE (not a tree), DC_ENOMEM. */
 dc_status dc_plan(const dc_schema* schema, const void* host_root, dc_plan_t* out);
+/* dc_plan_forest — one plan (one arena, one relocation, one leaf stream) for
+ * `nroots` independent trees of the same schema, laid out tree after tree
+ * within each lane (the batched form of the deep copy).  SEL_ALL ops cover
+ * every tree; SEL_CHAIN paths and dc_resolve_chain / dc_verify_chain start at
+ * tree 0 (dc_resolve_chain_in takes a tree index).  The trees must not share
+ * blocks (DC_EALIAS). */
+dc_status dc_plan_forest(const dc_schema* schema, const void* const* roots, uint64_t nroots, dc_plan_t* out);
+/* Offset of tree `tree`'s root struct in the data region. */
+dc_status dc_plan_root(dc_plan_t plan, uint64_t tree, uint64_t* offset);
 dc_status dc_plan_set_flags(dc_plan_t plan, uint32_t flags);
 dc_status dc_plan_info_get(dc_plan_t plan, dc_plan_info* out);
 /* Block `i` in arena order: its host address, arena offset, byte size, lane,
@@ -206,12 +216,37 @@ dc_status dc_relocate(dc_plan_t plan, dc_stream_t stream);
  * and needs no device buffer. */
 dc_status dc_resolve_chain(dc_plan_t plan, const dc_step* path, uint32_t len, uint64_t* dev_addr);
 dc_status dc_resolve_offset(dc_plan_t plan, const dc_step* path, uint32_t len, uint64_t* offset);
+dc_status dc_resolve_chain_in(dc_plan_t plan, uint64_t tree, const dc_step* path, uint32_t len, uint64_t* dev_addr);
+dc_status dc_resolve_offset_in(dc_plan_t plan, uint64_t tree, const dc_step* path, uint32_t len, uint64_t* offset);
 
 /* dc_update_leaves — run the leaf kernel on the device copy through resolved
  * addresses: the selected structs' chains are resolved on the host and the
  * kernel streams over (x, y, n) segments with no pointer loads.  Errors:
  * DC_EINVAL (op fields / path / counts), DC_ESTATE, DC_ECUDA. */
 dc_status dc_update_leaves(dc_plan_t plan, const dc_op* op, dc_stream_t stream);
+
+/* dc_relocate_update — dc_relocate and dc_update_leaves(op) in one persistent
+ * kernel launch: work items are the relocation's tiles, then the leaf
+ * update's tiles.  The two are independent (the update goes through
+ * addresses resolved on the host), so for a forest (dc_plan_forest) one launch
+ * relocates and updates every tree.  Uses the split dc_autotune chose for this
+ * plan and op, else one cached for the same kind of op and length histogram in
+ * this process, else 256 threads per CTA and as many CTAs as fit.  Once the op's
+ * tables are on the device (after a first call) the call only launches a
+ * kernel, so it can be captured in a CUDA graph.  Errors: as
+ * dc_update_leaves. */
+dc_status dc_relocate_update(dc_plan_t plan, const dc_op* op, dc_stream_t stream);
+
+/* dc_autotune — time dc_relocate_update's launch on the bound arena under each
+ * work split (128, 256 or 512 threads per CTA, i.e. 8, 4 or 2 blocks or
+ * 16-byte units per thread per tile; 1, 2, 4 or 8 CTAs per SM, as far as they
+ * fit), keep the fastest for the plan and cache it for the process under a key
+ * made of the op's kind and element size, the plan's block count and the log2
+ * histogram of the selected arrays' lengths.  Blocking.  Each timing run applies
+ * the update, so the arena's x arrays change: tune before the deep copy of
+ * the data that matters, or deep copy again afterwards.  Outputs may be NULL. */
+dc_status dc_autotune(dc_plan_t plan, const dc_op* op, dc_stream_t stream, uint32_t* threads,
+                      uint32_t* ctas_per_sm);
 
 /* dc_update_chase — the same update, computed the way an unresolved chain
  * is: every element walks root -> ... -> struct -> x/y with device loads the

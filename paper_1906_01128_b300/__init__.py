@@ -71,7 +71,8 @@ class _Op(ctypes.Structure):
 
 class _Info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("data_bytes", "device_bytes", "payload_bytes", "nblocks",
-                                               "nrelocs", "nstructs", "nstruct_blocks", "root_offset")]
+                                               "nrelocs", "nstructs", "nstruct_blocks", "root_offset",
+                                               "ntrees")]
 
 
 # every entry point of include/dc.h, with its argument types
@@ -79,6 +80,8 @@ _P = ctypes.POINTER
 _vp, _u32, _u64, _i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
 SIGNATURES = {
     "dc_plan": [_P(_Schema), _vp, _P(_vp)],
+    "dc_plan_forest": [_P(_Schema), _P(_vp), _u64, _P(_vp)],
+    "dc_plan_root": [_vp, _u64, _P(_u64)],
     "dc_plan_set_flags": [_vp, _u32],
     "dc_plan_info_get": [_vp, _P(_Info)],
     "dc_plan_block": [_vp, _u64, _P(_u64), _P(_u64), _P(_u64), _P(_u32), _P(_u32), _P(_u32)],
@@ -90,6 +93,10 @@ SIGNATURES = {
     "dc_relocate_static": [_vp, _vp, _u64, _vp, _vp],
     "dc_resolve_chain": [_vp, _P(_Step), _u32, _P(_u64)],
     "dc_resolve_offset": [_vp, _P(_Step), _u32, _P(_u64)],
+    "dc_resolve_chain_in": [_vp, _u64, _P(_Step), _u32, _P(_u64)],
+    "dc_resolve_offset_in": [_vp, _u64, _P(_Step), _u32, _P(_u64)],
+    "dc_relocate_update": [_vp, _P(_Op), _vp],
+    "dc_autotune": [_vp, _P(_Op), _vp, _P(_u32), _P(_u32)],
     "dc_update_leaves": [_vp, _P(_Op), _vp],
     "dc_update_chase": [_vp, _P(_Op), _vp],
     "dc_verify_chain": [_vp, _P(_Step), _u32, _vp, _P(_u64)],
@@ -193,12 +200,18 @@ def _op(op):
 class Plan:
     """``dc_plan_t``: the walk and layout of one host tree, then its device copy."""
 
-    def __init__(self, schema, host_root: int, flags: int = 0, threads: int = 0):
+    def __init__(self, schema, host_root, flags: int = 0, threads: int = 0):
+        """``host_root``: the root's address, or a sequence of root addresses
+        for a forest (``dc_plan_forest``)."""
         self._schema_c, self._keep = schema_struct(schema)
         h = ctypes.c_void_p()
-        _check(lib.dc_plan(ctypes.byref(self._schema_c), host_root, ctypes.byref(h)))
+        if isinstance(host_root, int):
+            _check(lib.dc_plan(ctypes.byref(self._schema_c), host_root, ctypes.byref(h)))
+        else:
+            roots = (ctypes.c_void_p * len(host_root))(*host_root)
+            _check(lib.dc_plan_forest(ctypes.byref(self._schema_c), roots, len(host_root), ctypes.byref(h)))
         self._h = h.value
-        self.host_root = host_root
+        self.host_root = host_root if isinstance(host_root, int) else host_root[0]
         if flags:
             _check(lib.dc_plan_set_flags(self._h, flags))
         if threads:
@@ -244,6 +257,28 @@ class Plan:
         st, out = _steps(path), ctypes.c_uint64()
         _check(lib.dc_resolve_chain(self._h, st, len(path), ctypes.byref(out)))
         return out.value
+
+    def root_offset(self, tree: int) -> int:
+        out = ctypes.c_uint64()
+        _check(lib.dc_plan_root(self._h, tree, ctypes.byref(out)))
+        return out.value
+
+    def resolve_in(self, tree: int, path) -> int:
+        st, out = _steps(path), ctypes.c_uint64()
+        _check(lib.dc_resolve_chain_in(self._h, tree, st, len(path), ctypes.byref(out)))
+        return out.value
+
+    def relocate_update(self, op=None, stream=None):
+        """dc_relocate + dc_update_leaves in one persistent launch."""
+        o, keep = _op(op or Op())
+        _check(lib.dc_relocate_update(self._h, ctypes.byref(o), _stream(stream)))
+
+    def autotune(self, op=None, stream=None):
+        """Pick the fused launch's split; returns (threads per CTA, CTAs per SM)."""
+        o, keep = _op(op or Op())
+        t, c = ctypes.c_uint32(), ctypes.c_uint32()
+        _check(lib.dc_autotune(self._h, ctypes.byref(o), _stream(stream), ctypes.byref(t), ctypes.byref(c)))
+        return t.value, c.value
 
     def resolve_offset(self, path) -> int:
         st, out = _steps(path), ctypes.c_uint64()

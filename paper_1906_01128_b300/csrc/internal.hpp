@@ -153,6 +153,10 @@ cudaError_t launch_relocate(const RelocArgs& a, cudaStream_t s, int sm_count);
 cudaError_t launch_leaf(const LeafArgs& a, cudaStream_t s, int sm_count);
 cudaError_t launch_chase(const ChaseArgs& a, cudaStream_t s, int sm_count);
 cudaError_t launch_move(const MoveArgs& a, cudaStream_t s, int sm_count);
+// threads: 128, 256 or 512 per CTA; ctas_per_sm: 0 = as many as fit.  With
+// max_per_sm set, launches nothing and reports how many CTAs fit on an SM.
+cudaError_t launch_fused(const RelocArgs& r, const LeafArgs& l, uint32_t threads, uint32_t ctas_per_sm, int sm_count,
+                         cudaStream_t s, int* max_per_sm);
 cudaError_t launch_stream(const StreamArgs& a, cudaStream_t s, int sm_count);
 cudaError_t launch_walk(uint64_t root, const ChaseStep* steps, uint32_t nsteps, uint64_t final_add,
                         uint64_t* out, cudaStream_t s);
@@ -213,6 +217,7 @@ struct dc_plan_s {
   std::vector<uint64_t> struct_off;      // arena offset of each struct block
   std::vector<uint64_t> tile_base;       // per relocation tile: offset of its first block / 16
   std::vector<uint64_t> null_slots;      // arena offsets of slots with count 0 but a non-NULL host value
+  std::vector<uint32_t> roots;           // arena index of each tree's root struct block
   uint64_t nstructs = 0, nstruct_blocks = 0, payload = 0, data_bytes = 0, sum_depth = 0;
   uint32_t max_depth = 0;
   uint32_t flags = 0;
@@ -233,10 +238,14 @@ struct dc_plan_s {
   uint64_t leaf_nseg = 0, leaf_units = 0, chase_nseg = 0, chase_elems = 0;
   const std::vector<uint32_t>* written = nullptr;  // arrays the last update wrote (leaf_written or chase_written)
   std::vector<uint32_t> leaf_written, chase_written;  // ascending arena indices
+  std::vector<uint64_t> leaf_hist;  // log2 histogram of the selected arrays' lengths (the autotuner's key)
+  uint32_t tuned_threads = 0, tuned_ctas = 0;  // split chosen by dc_autotune (0 = default)
+  dc::OpKey tuned_key;
   uint64_t gen = 0;                // bumped whenever a written list is rebuilt
   uint64_t leaf_gen = 0, chase_gen = 0, written_gen = 0;
   bool op_run = false;
-  std::unique_ptr<dc::Pool> pool;
+  std::unique_ptr<dc::Pool> own_pool;  // only when dc_plan_set_threads asked for one
+  dc::Pool* pool = nullptr;
   // transfers (transfer.cpp), planned at the first bind
   struct Frag { uint64_t off, len; uint8_t* host; };  // staged bytes: arena offset, length, host address
   struct Unit { uint64_t first, last; };              // pieces [first, last), one host thread at a time
@@ -284,10 +293,10 @@ struct dc_uvm_s {
 };
 
 namespace dc {
-dc_status build_plan(const dc_schema* schema, const void* host_root, dc_plan_s* p);
+dc_status build_plan(const dc_schema* schema, const void* const* roots, uint64_t nroots, dc_plan_s* p);
 // Resolve a chain over the plan tables to (block, byte offset in block, type
 // of the struct reached or NONE when the last step was an ARRAY step, element).
-dc_status resolve(const dc_plan_s* p, const dc_step* path, uint32_t len, uint32_t* block,
+dc_status resolve(const dc_plan_s* p, uint64_t tree, const dc_step* path, uint32_t len, uint32_t* block,
                   uint64_t* within, uint32_t* type, uint64_t* elem);
 // The structs an op selects: (struct block, element) pairs.
 dc_status select_structs(const dc_plan_s* p, const dc_op* op,
@@ -320,6 +329,9 @@ struct Pick {
   uint32_t bx, by;
 };
 dc_status pick(const dc_plan_s* p, const dc_op* op, std::vector<Pick>* out);
+dc_status build_leaf_table(dc_plan_s* p, const dc_op* op, cudaStream_t s);
+LeafArgs leaf_args(const dc_plan_s* p, const dc_op* op);
+RelocArgs reloc_args(const dc_plan_s* p);
 // The chain of (field, index) steps from the root to struct (block, elem).
 void path_to(const dc_plan_s* p, uint32_t block, uint64_t elem, std::vector<dc_step>* out);
 }  // namespace dc

@@ -40,80 +40,83 @@ __device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, uint32_t lane) {
   return v;
 }
 
-// One tile of RELOC_TILE blocks per CTA iteration.  Warp w owns blocks
-// [base + w*32*ITEMS, base + (w+1)*32*ITEMS); its lanes read 32 consecutive
-// 16-byte records per instruction (coalesced).  The block sizes are scanned
-// with warp shuffles (slice by slice, carrying the running total), then across
-// the tile's warps, on top of the tile's base offset; every block's parent
-// slot is then rewritten.  Parents in an earlier tile take their offset from
-// the struct-offset table.
-__global__ void __launch_bounds__(RELOC_THREADS) relocate_kernel(RelocArgs a) {
-  constexpr uint32_t NW = RELOC_THREADS / 32;
-  constexpr uint32_t WSPAN = 32 * RELOC_ITEMS;  // blocks per warp
-  __shared__ uint64_t s_off[RELOC_TILE];
-  __shared__ uint64_t s_warp[NW];
+// One tile of RELOC_TILE blocks, done by a CTA of THREADS threads.  Warp w
+// owns blocks [base + w*32*ITEMS, base + (w+1)*32*ITEMS); its lanes read 32
+// consecutive 16-byte records per instruction (coalesced).  The block sizes
+// are scanned with warp shuffles (slice by slice, carrying the running total),
+// then across the tile's warps, on top of the tile's base offset; every
+// block's parent slot is then rewritten.  Parents in an earlier tile take
+// their offset from the struct-offset table.  Ends with a barrier.
+template <uint32_t THREADS>
+__device__ __forceinline__ void reloc_tile(const RelocArgs& a, uint32_t t, uint64_t* s_off, uint64_t* s_warp) {
+  constexpr uint32_t NW = THREADS / 32;
+  constexpr uint32_t ITEMS = RELOC_TILE / THREADS;
+  constexpr uint32_t WSPAN = 32 * ITEMS;  // blocks per warp
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t* err = &a.ctrl[CTRL_ERR];
-
-  for (uint32_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-    const uint64_t base = (uint64_t)t * RELOC_TILE;
-    const uint64_t wbase = base + warp * WSPAN;
-    BlockRec r[RELOC_ITEMS];
+  const uint64_t base = (uint64_t)t * RELOC_TILE;
+  const uint64_t wbase = base + warp * WSPAN;
+  BlockRec r[ITEMS];
 #pragma unroll
-    for (uint32_t k = 0; k < RELOC_ITEMS; k++) {
-      const uint64_t b = wbase + k * 32 + lane;
-      if (b < a.nblocks) {
-        const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.rec) + b);
-        r[k] = BlockRec{v.x, v.y, v.z, v.w};
-      } else {
-        r[k] = BlockRec{0, NONE, 0, 0};
-      }
+  for (uint32_t k = 0; k < ITEMS; k++) {
+    const uint64_t b = wbase + k * 32 + lane;
+    if (b < a.nblocks) {
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.rec) + b);
+      r[k] = BlockRec{v.x, v.y, v.z, v.w};
+    } else {
+      r[k] = BlockRec{0, NONE, 0, 0};
     }
-    // exclusive offsets inside the warp's span, slice by slice
-    uint64_t ex[RELOC_ITEMS];
-    uint64_t carry = 0;
-#pragma unroll
-    for (uint32_t k = 0; k < RELOC_ITEMS; k++) {
-      const uint64_t incl = warp_incl_scan(r[k].size16, lane);
-      ex[k] = carry + incl - r[k].size16;
-      carry += __shfl_sync(0xffffffffu, incl, 31);
-    }
-    if (lane == 0) s_warp[warp] = carry;
-    __syncthreads();
-    uint64_t wpre = 0;  // every warp adds up the totals of the warps before it
-#pragma unroll
-    for (uint32_t w = 0; w < NW; w++) wpre += w < warp ? s_warp[w] : 0;
-    const uint64_t o16 = __ldg(&a.tile_base[t]) + wpre;
-#pragma unroll
-    for (uint32_t k = 0; k < RELOC_ITEMS; k++) {
-      const uint64_t b = wbase + k * 32 + lane;
-      ex[k] = (o16 + ex[k]) * 16;  // byte offset of block b
-      s_off[b - base] = ex[k];
-      if (a.verify && b < a.nstruct_blocks && __ldg(&a.soff[b]) != ex[k]) atomicOr(err, ERR_VERIFY);
-    }
-    __syncthreads();
-    // rewrite the slot that points at each block (the root has none)
-#pragma unroll
-    for (uint32_t k = 0; k < RELOC_ITEMS; k++) {
-      const uint64_t b = wbase + k * 32 + lane;
-      const uint32_t p = r[k].parent;
-      if (b >= a.nblocks || p == NONE) continue;
-      if (p >= b || p >= a.nstruct_blocks) {
-        atomicOr(err, ERR_BOUNDS);
-        continue;
-      }
-      const uint64_t poff = p >= base ? s_off[p - base] : __ldg(&a.soff[p]);
-      const uint64_t slot = poff + r[k].slot_off;
-      if (slot + 8 > a.data_bytes || (slot & 7)) {
-        atomicOr(err, ERR_BOUNDS);
-        continue;
-      }
-      uint64_t* sp = reinterpret_cast<uint64_t*>(a.arena + slot);
-      if (a.verify && *sp != a.hostp[b]) atomicOr(err, ERR_VERIFY);
-      *sp = reinterpret_cast<uint64_t>(a.arena) + ex[k];
-    }
-    __syncthreads();  // s_off and s_warp are reused by the next tile
   }
+  // exclusive offsets inside the warp's span, slice by slice
+  uint64_t ex[ITEMS];
+  uint64_t carry = 0;
+#pragma unroll
+  for (uint32_t k = 0; k < ITEMS; k++) {
+    const uint64_t incl = warp_incl_scan(r[k].size16, lane);
+    ex[k] = carry + incl - r[k].size16;
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (lane == 0) s_warp[warp] = carry;
+  __syncthreads();
+  uint64_t wpre = 0;  // every warp adds up the totals of the warps before it
+#pragma unroll
+  for (uint32_t w = 0; w < NW; w++) wpre += w < warp ? s_warp[w] : 0;
+  const uint64_t o16 = __ldg(&a.tile_base[t]) + wpre;
+#pragma unroll
+  for (uint32_t k = 0; k < ITEMS; k++) {
+    const uint64_t b = wbase + k * 32 + lane;
+    ex[k] = (o16 + ex[k]) * 16;  // byte offset of block b
+    s_off[b - base] = ex[k];
+    if (a.verify && b < a.nstruct_blocks && __ldg(&a.soff[b]) != ex[k]) atomicOr(err, ERR_VERIFY);
+  }
+  __syncthreads();
+  // rewrite the slot that points at each block (roots have none)
+#pragma unroll
+  for (uint32_t k = 0; k < ITEMS; k++) {
+    const uint64_t b = wbase + k * 32 + lane;
+    const uint32_t p = r[k].parent;
+    if (b >= a.nblocks || p == NONE) continue;
+    if (p >= b || p >= a.nstruct_blocks) {
+      atomicOr(err, ERR_BOUNDS);
+      continue;
+    }
+    const uint64_t poff = p >= base ? s_off[p - base] : __ldg(&a.soff[p]);
+    const uint64_t slot = poff + r[k].slot_off;
+    if (slot + 8 > a.data_bytes || (slot & 7)) {
+      atomicOr(err, ERR_BOUNDS);
+      continue;
+    }
+    uint64_t* sp = reinterpret_cast<uint64_t*>(a.arena + slot);
+    if (a.verify && *sp != a.hostp[b]) atomicOr(err, ERR_VERIFY);
+    *sp = reinterpret_cast<uint64_t>(a.arena) + ex[k];
+  }
+  __syncthreads();  // s_off and s_warp are reused by the next tile
+}
+
+__global__ void __launch_bounds__(RELOC_THREADS) relocate_kernel(RelocArgs a) {
+  __shared__ uint64_t s_off[RELOC_TILE];
+  __shared__ uint64_t s_warp[RELOC_THREADS / 32];
+  for (uint32_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) reloc_tile<RELOC_THREADS>(a, t, s_off, s_warp);
 }
 
 // ---- leaf update over resolved segments -------------------------------------
@@ -159,57 +162,81 @@ __device__ __forceinline__ double2 ldcs(const double2* p) { return __ldcs(p); }
 __device__ __forceinline__ void stcs(float4* p, float4 v) { __stcs(p, v); }
 __device__ __forceinline__ void stcs(double2* p, double2 v) { __stcs(p, v); }
 
-template <typename T, int KIND>
-__global__ void __launch_bounds__(LEAF_THREADS) leaf_kernel(LeafArgs a) {
+// One tile of LEAF_TILE 16-byte units, done by a CTA of THREADS threads
+// (LEAF_TILE / THREADS units each).  No barriers.
+template <typename T, int KIND, uint32_t THREADS>
+__device__ __forceinline__ void leaf_tile(const LeafArgs& a, uint64_t t) {
   using VT = typename V16<T>::type;
   constexpr int EPU = V16<T>::N;
+  constexpr uint32_t UNROLL = LEAF_TILE / THREADS;
   const T sc = (T)a.scale;
   const Segment* seg = a.seg;
   auto ub = [&](uint32_t s) { return __ldg(&seg[s].ubeg); };
-  for (uint64_t t = blockIdx.x; t * LEAF_TILE < a.units; t += gridDim.x) {
-    const uint64_t u0 = t * LEAF_TILE;
-    // the tile's segments are [lo, hi]; most tiles lie inside one segment
-    const uint32_t lo = __ldg(&a.tile_seg[t]), hi = __ldg(&a.tile_seg[t + 1]);
-    VT xv[LEAF_UNROLL], yv[LEAF_UNROLL];
-    VT* xp[LEAF_UNROLL];
-    const VT* yp[LEAF_UNROLL];
-    uint32_t tail[LEAF_UNROLL];  // elements of this unit; EPU = a full vector
+  const uint64_t u0 = t * LEAF_TILE;
+  // the tile's segments are [lo, hi]; most tiles lie inside one segment
+  const uint32_t lo = __ldg(&a.tile_seg[t]), hi = __ldg(&a.tile_seg[t + 1]);
+  VT xv[UNROLL], yv[UNROLL];
+  VT* xp[UNROLL];
+  const VT* yp[UNROLL];
+  uint32_t tail[UNROLL];  // elements of this unit; EPU = a full vector
 #pragma unroll
-    for (uint32_t k = 0; k < LEAF_UNROLL; k++) {
-      const uint64_t u = u0 + threadIdx.x + k * LEAF_THREADS;
-      tail[k] = 0;
-      xp[k] = nullptr;
-      yp[k] = nullptr;
-      if (u >= a.units) continue;
-      const uint32_t s = lo == hi ? lo : search(lo, hi, u, ub);
-      const Segment g = seg[s];
-      const uint64_t e0 = (u - g.ubeg) * EPU;
-      xp[k] = reinterpret_cast<VT*>(g.x + e0 * sizeof(T));
-      yp[k] = reinterpret_cast<const VT*>(g.y + e0 * sizeof(T));
-      const uint64_t left = g.n - e0;
-      tail[k] = left >= (uint64_t)EPU ? EPU : (uint32_t)left;
+  for (uint32_t k = 0; k < UNROLL; k++) {
+    const uint64_t u = u0 + threadIdx.x + k * THREADS;
+    tail[k] = 0;
+    xp[k] = nullptr;
+    yp[k] = nullptr;
+    if (u >= a.units) continue;
+    const uint32_t s = lo == hi ? lo : search(lo, hi, u, ub);
+    const Segment g = seg[s];
+    const uint64_t e0 = (u - g.ubeg) * EPU;
+    xp[k] = reinterpret_cast<VT*>(g.x + e0 * sizeof(T));
+    yp[k] = reinterpret_cast<const VT*>(g.y + e0 * sizeof(T));
+    const uint64_t left = g.n - e0;
+    tail[k] = left >= (uint64_t)EPU ? EPU : (uint32_t)left;
+  }
+#pragma unroll
+  for (uint32_t k = 0; k < UNROLL; k++) {
+    if (tail[k] == EPU) {
+      xv[k] = ldcs(xp[k]);
+      if (KIND == DC_OP_AXPY_HALF) yv[k] = ldcs(yp[k]);
     }
+  }
 #pragma unroll
-    for (uint32_t k = 0; k < LEAF_UNROLL; k++) {
-      if (tail[k] == EPU) {
-        xv[k] = ldcs(xp[k]);
-        if (KIND == DC_OP_AXPY_HALF) yv[k] = ldcs(yp[k]);
-      }
+  for (uint32_t k = 0; k < UNROLL; k++) {
+    if (tail[k] == EPU) {
+      T* x = reinterpret_cast<T*>(&xv[k]);
+      const T* y = reinterpret_cast<const T*>(&yv[k]);
+#pragma unroll
+      for (int i = 0; i < EPU; i++) x[i] = apply<T, KIND>(x[i], KIND == DC_OP_AXPY_HALF ? y[i] : T(0), sc);
+      stcs(xp[k], xv[k]);
+    } else if (tail[k]) {
+      T* x = reinterpret_cast<T*>(xp[k]);
+      const T* y = reinterpret_cast<const T*>(yp[k]);
+      for (uint32_t i = 0; i < tail[k]; i++) x[i] = apply<T, KIND>(x[i], KIND == DC_OP_AXPY_HALF ? y[i] : T(0), sc);
     }
-#pragma unroll
-    for (uint32_t k = 0; k < LEAF_UNROLL; k++) {
-      if (tail[k] == EPU) {
-        T* x = reinterpret_cast<T*>(&xv[k]);
-        const T* y = reinterpret_cast<const T*>(&yv[k]);
-#pragma unroll
-        for (int i = 0; i < EPU; i++) x[i] = apply<T, KIND>(x[i], KIND == DC_OP_AXPY_HALF ? y[i] : T(0), sc);
-        stcs(xp[k], xv[k]);
-      } else if (tail[k]) {
-        T* x = reinterpret_cast<T*>(xp[k]);
-        const T* y = reinterpret_cast<const T*>(yp[k]);
-        for (uint32_t i = 0; i < tail[k]; i++) x[i] = apply<T, KIND>(x[i], KIND == DC_OP_AXPY_HALF ? y[i] : T(0), sc);
-      }
-    }
+  }
+}
+
+template <typename T, int KIND>
+__global__ void __launch_bounds__(LEAF_THREADS) leaf_kernel(LeafArgs a) {
+  for (uint64_t t = blockIdx.x; t * LEAF_TILE < a.units; t += gridDim.x) leaf_tile<T, KIND, LEAF_THREADS>(a, t);
+}
+
+// Relocation and leaf update in one persistent launch: work item w < the
+// relocation's tile count is a relocation tile, the rest are leaf tiles.  The
+// two are independent (the leaf kernel works through addresses resolved on
+// the host, the relocation writes only pointer slots), so one launch over a
+// forest replaces two per structure.
+template <typename T, int KIND, uint32_t THREADS>
+__global__ void __launch_bounds__(THREADS) fused_kernel(RelocArgs r, LeafArgs l, uint64_t leaf_tiles) {
+  __shared__ uint64_t s_off[RELOC_TILE];
+  __shared__ uint64_t s_warp[THREADS / 32];
+  const uint64_t total = (uint64_t)r.ntiles + leaf_tiles;
+  for (uint64_t w = blockIdx.x; w < total; w += gridDim.x) {
+    if (w < r.ntiles)
+      reloc_tile<THREADS>(r, (uint32_t)w, s_off, s_warp);
+    else
+      leaf_tile<T, KIND, THREADS>(l, w - r.ntiles);
   }
 }
 
@@ -443,6 +470,42 @@ cudaError_t launch_chase(const ChaseArgs& a, cudaStream_t s, int sm_count) {
     a.kind == DC_OP_AXPY_HALF ? go(chase_kernel<float, DC_OP_AXPY_HALF>) : go(chase_kernel<float, DC_OP_SCALE>);
   count_launch();
   return cudaGetLastError();
+}
+
+namespace {
+template <typename T, int KIND>
+cudaError_t fused_go(const RelocArgs& r, const LeafArgs& l, uint32_t threads, uint32_t ctas_per_sm, int sm_count,
+                     cudaStream_t s, int* max_per_sm) {
+  const uint64_t leaf_tiles = (l.units + LEAF_TILE - 1) / LEAF_TILE;
+  const uint64_t total = (uint64_t)r.ntiles + leaf_tiles;
+  auto go = [&](auto kernel, uint32_t nt) -> cudaError_t {
+    int occ = occupancy(kernel, (int)nt, 0);
+    if (max_per_sm) {
+      *max_per_sm = occ;
+      return cudaSuccess;
+    }
+    if (total == 0) return cudaSuccess;
+    uint32_t per = ctas_per_sm ? std::min<uint32_t>(ctas_per_sm, (uint32_t)occ) : (uint32_t)occ;
+    uint32_t grid = (uint32_t)std::min<uint64_t>(total, (uint64_t)sm_count * per);
+    kernel<<<grid, nt, 0, s>>>(r, l, leaf_tiles);
+    count_launch();
+    return cudaGetLastError();
+  };
+  switch (threads) {
+    case 128: return go(fused_kernel<T, KIND, 128>, 128);
+    case 512: return go(fused_kernel<T, KIND, 512>, 512);
+    default: return go(fused_kernel<T, KIND, 256>, 256);
+  }
+}
+}  // namespace
+
+cudaError_t launch_fused(const RelocArgs& r, const LeafArgs& l, uint32_t threads, uint32_t ctas_per_sm, int sm_count,
+                         cudaStream_t s, int* max_per_sm) {
+  if (l.f64)
+    return l.kind == DC_OP_AXPY_HALF ? fused_go<double, DC_OP_AXPY_HALF>(r, l, threads, ctas_per_sm, sm_count, s, max_per_sm)
+                                     : fused_go<double, DC_OP_SCALE>(r, l, threads, ctas_per_sm, sm_count, s, max_per_sm);
+  return l.kind == DC_OP_AXPY_HALF ? fused_go<float, DC_OP_AXPY_HALF>(r, l, threads, ctas_per_sm, sm_count, s, max_per_sm)
+                                   : fused_go<float, DC_OP_SCALE>(r, l, threads, ctas_per_sm, sm_count, s, max_per_sm);
 }
 
 cudaError_t launch_move(const MoveArgs& a, cudaStream_t s, int sm_count) {

@@ -269,12 +269,17 @@ struct Walker {
 
 }  // namespace
 
-dc_status build_plan(const dc_schema* schema, const void* host_root, dc_plan_s* p) {
-  if (!host_root) return fail(DC_EINVAL, "host_root is NULL");
+dc_status build_plan(const dc_schema* schema, const void* const* roots, uint64_t nroots, dc_plan_s* p) {
+  if (!roots || nroots == 0) return fail(DC_EINVAL, "no root");
   dc_status st = copy_schema(schema, &p->schema);
   if (st) return st;
   Walker w(p);
-  if ((st = w.run((const uint8_t*)host_root))) return st;
+  std::vector<uint32_t> root_ids;
+  for (uint64_t i = 0; i < nroots; i++) {  // trees one after another; they must not share blocks
+    if (!roots[i]) return fail(DC_EINVAL, "root %llu is NULL", (unsigned long long)i);
+    root_ids.push_back((uint32_t)w.emitted.size());
+    if ((st = w.run((const uint8_t*)roots[i]))) return st;
+  }
   std::vector<HostBlock>& E = w.emitted;
   const uint64_t nb = E.size();
 
@@ -313,6 +318,8 @@ dc_status build_plan(const dc_schema* schema, const void* host_root, dc_plan_s* 
   }
   for (auto& t : p->ptr_target)
     if (t != NONE) t = new_id[t];
+  p->roots.clear();
+  for (uint32_t r : root_ids) p->roots.push_back(new_id[r]);
   uint64_t off = 0;
   p->rec.resize(nb);
   p->hostp.resize(nb);
@@ -334,11 +341,12 @@ dc_status build_plan(const dc_schema* schema, const void* host_root, dc_plan_s* 
   return DC_OK;
 }
 
-dc_status resolve(const dc_plan_s* p, const dc_step* path, uint32_t len, uint32_t* block,
+dc_status resolve(const dc_plan_s* p, uint64_t tree, const dc_step* path, uint32_t len, uint32_t* block,
                   uint64_t* within, uint32_t* type, uint64_t* elem_out) {
   if (len && !path) return fail(DC_EINVAL, "path is NULL");
+  if (tree >= p->roots.size()) return fail(DC_EINVAL, "tree %llu out of range", (unsigned long long)tree);
   const SchemaCopy& S = p->schema;
-  uint32_t blk = 0;  // the root struct block is arena block 0
+  uint32_t blk = p->roots[tree];  // the tree's root struct block
   uint64_t elem = 0;
   uint32_t ti = S.root_type;
   for (uint32_t k = 0; k < len; k++) {
@@ -401,7 +409,7 @@ dc_status select_structs(const dc_plan_s* p, const dc_op* op,
   if (op->sel == DC_SEL_CHAIN) {
     uint32_t blk, ty;
     uint64_t within, elem;
-    dc_status st = resolve(p, op->path, op->path_len, &blk, &within, &ty, &elem);
+    dc_status st = resolve(p, 0, op->path, op->path_len, &blk, &within, &ty, &elem);
     if (st) return st;
     if (ty == NONE) return fail(DC_EINVAL, "op: the chain must end on a struct, not an array element");
     if (ty != op->type)

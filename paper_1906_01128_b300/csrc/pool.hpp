@@ -36,6 +36,7 @@ class Pool {
       for (uint64_t i = 0; i < n; i++) fn(i);
       return;
     }
+    std::lock_guard<std::mutex> one_job(job_);  // callers on several threads take turns
     {
       std::lock_guard<std::mutex> g(m_);
       fn_ = &fn;
@@ -77,6 +78,7 @@ class Pool {
   }
 
   std::vector<std::thread> workers_;
+  std::mutex job_;
   std::mutex m_;
   std::condition_variable cv_, done_cv_;
   const std::function<void(uint64_t)>* fn_ = nullptr;

@@ -87,7 +87,15 @@ unsigned default_threads() {
 }  // namespace
 
 Pool& dc::pool_of(dc_plan_s* p) {
-  if (!p->pool) p->pool.reset(new Pool(p->nthreads ? p->nthreads : default_threads()));
+  if (!p->pool) {
+    if (p->nthreads) {
+      p->own_pool.reset(new Pool(p->nthreads));
+      p->pool = p->own_pool.get();
+    } else {  // plans share one pool: thousands of plans must not mean thousands of threads
+      static Pool shared(default_threads());
+      p->pool = &shared;
+    }
+  }
   return *p->pool;
 }
 
@@ -151,8 +159,9 @@ dc_status dc::pick(const dc_plan_s* p, const dc_op* op, std::vector<Pick>* out) 
 
 namespace {
 
-// chase steps from the root to struct (sblk, elem), appended to `steps`
-void chain_steps(const dc_plan_s* p, uint32_t sblk, uint64_t elem, std::vector<ChaseStep>* steps) {
+// chase steps from its tree's root to struct (sblk, elem), appended to
+// `steps`; returns the root block
+uint32_t chain_steps(const dc_plan_s* p, uint32_t sblk, uint64_t elem, std::vector<ChaseStep>* steps) {
   size_t start = steps->size();
   const SchemaCopy& S = p->schema;
   while (p->blocks[sblk].parent != NONE) {
@@ -164,6 +173,7 @@ void chain_steps(const dc_plan_s* p, uint32_t sblk, uint64_t elem, std::vector<C
     sblk = B.parent;
   }
   std::reverse(steps->begin() + start, steps->end());
+  return sblk;
 }
 
 }  // namespace
@@ -178,7 +188,7 @@ namespace {
 dc_status path_steps(const dc_plan_s* p, const dc_step* path, uint32_t len, std::vector<ChaseStep>* out) {
   uint32_t blk, ty;
   uint64_t within, elem;
-  dc_status st = resolve(p, path, len, &blk, &within, &ty, &elem);  // validates the chain
+  dc_status st = resolve(p, 0, path, len, &blk, &within, &ty, &elem);  // validates the chain
   if (st) return st;
   const SchemaCopy& S = p->schema;
   uint32_t ti = S.root_type;
@@ -218,13 +228,21 @@ const char* dc_status_name(dc_status s) {
 uint64_t dc_kernel_launches(void) { return g_launches.load(); }
 
 dc_status dc_plan(const dc_schema* schema, const void* host_root, dc_plan_t* out) {
+  if (!host_root) {
+    if (out) *out = nullptr;
+    return fail(DC_EINVAL, "host_root is NULL");
+  }
+  return dc_plan_forest(schema, &host_root, 1, out);
+}
+
+dc_status dc_plan_forest(const dc_schema* schema, const void* const* roots, uint64_t nroots, dc_plan_t* out) {
   if (!out) return fail(DC_EINVAL, "out is NULL");
   *out = nullptr;
   dc_plan_s* p = new (std::nothrow) dc_plan_s;
   if (!p) return fail(DC_ENOMEM, "out of host memory");
   dc_status st;
   try {
-    st = build_plan(schema, host_root, p);
+    st = build_plan(schema, roots, nroots, p);
   } catch (const std::bad_alloc&) {
     st = fail(DC_ENOMEM, "out of host memory while planning");
   }
@@ -246,7 +264,8 @@ dc_status dc_plan_set_flags(dc_plan_t p, uint32_t flags) {
 dc_status dc_plan_set_threads(dc_plan_t p, uint32_t n) {
   if (!p) return fail(DC_EINVAL, "plan is NULL");
   p->nthreads = n;
-  p->pool.reset();
+  p->pool = nullptr;
+  p->own_pool.reset();
   return DC_OK;
 }
 
@@ -260,6 +279,14 @@ dc_status dc_plan_info_get(dc_plan_t p, dc_plan_info* out) {
   out->nstructs = p->nstructs;
   out->nstruct_blocks = p->nstruct_blocks;
   out->root_offset = 0;
+  out->ntrees = p->roots.size();
+  return DC_OK;
+}
+
+dc_status dc_plan_root(dc_plan_t p, uint64_t tree, uint64_t* offset) {
+  if (!p || !offset) return fail(DC_EINVAL, "NULL argument");
+  if (tree >= p->roots.size()) return fail(DC_EINVAL, "tree %llu out of range", (unsigned long long)tree);
+  *offset = p->blocks[p->roots[tree]].off;
   return DC_OK;
 }
 
@@ -364,18 +391,7 @@ dc_status dc_relocate(dc_plan_t p, dc_stream_t stream) {
   if (!p->dev) return fail(DC_ESTATE, "no device buffer bound");
   cudaStream_t s = stream;
   // Fig 2 step d: rebuild every pointer on the device
-  RelocArgs a;
-  a.arena = p->dev;
-  a.data_bytes = p->data_bytes;
-  a.rec = reinterpret_cast<const BlockRec*>(p->dev + p->L.rec);
-  a.hostp = reinterpret_cast<const uint64_t*>(p->dev + p->L.hostp);
-  a.soff = reinterpret_cast<const uint64_t*>(p->dev + p->L.soff);
-  a.tile_base = reinterpret_cast<const uint64_t*>(p->dev + p->L.status);
-  a.ctrl = reinterpret_cast<uint32_t*>(p->dev + p->L.ctrl);
-  a.nblocks = (uint32_t)p->blocks.size();
-  a.nstruct_blocks = (uint32_t)p->nstruct_blocks;
-  a.ntiles = (uint32_t)p->L.ntiles;
-  a.verify = (p->flags & DC_PLAN_VERIFY) ? 1u : 0u;
+  const RelocArgs a = reloc_args(p);
   DC_CUDA(launch_relocate(a, s, p->sm_count));
   return DC_OK;
 }
@@ -394,84 +410,95 @@ dc_status dc_deep_copy(dc_plan_t p, dc_stream_t stream) {
 }
 
 dc_status dc_resolve_offset(dc_plan_t p, const dc_step* path, uint32_t len, uint64_t* offset) {
+  return dc_resolve_offset_in(p, 0, path, len, offset);
+}
+
+dc_status dc_resolve_offset_in(dc_plan_t p, uint64_t tree, const dc_step* path, uint32_t len, uint64_t* offset) {
   if (!p || !offset) return fail(DC_EINVAL, "NULL argument");
   uint32_t blk, ty;
   uint64_t within;
-  dc_status st = resolve(p, path, len, &blk, &within, &ty, nullptr);
+  dc_status st = resolve(p, tree, path, len, &blk, &within, &ty, nullptr);
   if (st) return st;
   *offset = p->blocks[blk].off + within;
   return DC_OK;
 }
 
 dc_status dc_resolve_chain(dc_plan_t p, const dc_step* path, uint32_t len, uint64_t* dev_addr) {
+  return dc_resolve_chain_in(p, 0, path, len, dev_addr);
+}
+
+dc_status dc_resolve_chain_in(dc_plan_t p, uint64_t tree, const dc_step* path, uint32_t len, uint64_t* dev_addr) {
   if (!p || !dev_addr) return fail(DC_EINVAL, "NULL argument");
   if (!p->dev) return fail(DC_ESTATE, "no device buffer bound");
   uint64_t off;
-  dc_status st = dc_resolve_offset(p, path, len, &off);
+  dc_status st = dc_resolve_offset_in(p, tree, path, len, &off);
   if (st) return st;
   *dev_addr = (uint64_t)(uintptr_t)p->dev + off;
   return DC_OK;
 }
 
-dc_status dc_update_leaves(dc_plan_t p, const dc_op* op, dc_stream_t stream) {
-  if (!p) return fail(DC_EINVAL, "plan is NULL");
-  dc_status st = check_op(p, op);
-  if (st) return st;
-  if (!p->dev) return fail(DC_ESTATE, "no device buffer bound");
-  cudaStream_t s = stream;
+}  // extern "C"
+
+dc_status dc::build_leaf_table(dc_plan_s* p, const dc_op* op, cudaStream_t s) {
   const dc_field& X = p->schema.fields[op->type][op->x_field];
   OpKey key = key_of(op);
-  if (!(key == p->leaf_key)) {
-    std::vector<Pick> picks;
-    if ((st = pick(p, op, &picks))) return st;
-    if ((st = wait_event(p->tab_done))) return st;
-    Segment* seg = reinterpret_cast<Segment*>(p->pin_tab + tab_seg(p->L));
-    const uint64_t base = (uint64_t)(uintptr_t)p->dev;
-    const uint64_t esz = X.elem_size;
-    const bool axpy = op->kind == DC_OP_AXPY_HALF;
-    uint64_t units = 0, nseg = 0;
-    p->leaf_written.clear();
-    p->leaf_gen = ++p->gen;
-    for (size_t i = 0; i < picks.size(); i++) {
-      const HostBlock& bx = p->blocks[picks[i].bx];
-      const uint64_t x = base + bx.off, y = picks[i].by == NONE ? 0 : base + p->blocks[picks[i].by].off;
-      p->leaf_written.push_back(picks[i].bx);
-      if (nseg) {  // x (and y) continue the previous segment after at most its padding: one stream
-        Segment& g = seg[nseg - 1];
-        const uint64_t end = g.x + g.n * esz;
-        if (x >= end && x - end < 16 && (x - g.x) % esz == 0 && (!axpy || y - g.y == x - g.x)) {
-          g.n = (x - g.x) / esz + bx.count;
-          continue;
-        }
+  if (key == p->leaf_key) return DC_OK;
+  std::vector<Pick> picks;
+  dc_status st;
+  if ((st = pick(p, op, &picks))) return st;
+  if ((st = wait_event(p->tab_done))) return st;
+  Segment* seg = reinterpret_cast<Segment*>(p->pin_tab + tab_seg(p->L));
+  const uint64_t base = (uint64_t)(uintptr_t)p->dev;
+  const uint64_t esz = X.elem_size;
+  const bool axpy = op->kind == DC_OP_AXPY_HALF;
+  uint64_t units = 0, nseg = 0;
+  p->leaf_written.clear();
+  p->leaf_gen = ++p->gen;
+  p->leaf_hist.assign(40, 0);
+  for (size_t i = 0; i < picks.size(); i++) {
+    const HostBlock& bx = p->blocks[picks[i].bx];
+    const uint64_t x = base + bx.off, y = picks[i].by == NONE ? 0 : base + p->blocks[picks[i].by].off;
+    p->leaf_written.push_back(picks[i].bx);
+    uint32_t lg = 0;
+    while (lg < 39 && (1ull << lg) < bx.count) lg++;
+    p->leaf_hist[lg]++;
+    if (nseg) {  // x (and y) continue the previous segment after at most its padding: one stream
+      Segment& g = seg[nseg - 1];
+      const uint64_t end = g.x + g.n * esz;
+      if (x >= end && x - end < 16 && (x - g.x) % esz == 0 && (!axpy || y - g.y == x - g.x)) {
+        g.n = (x - g.x) / esz + bx.count;
+        continue;
       }
-      seg[nseg++] = Segment{x, y, bx.count, 0};
     }
-    for (uint64_t i = 0; i < nseg; i++) {
-      seg[i].ubeg = units;
-      units += (seg[i].n * esz + 15) / 16;
-    }
-    // tile -> segment holding the tile's first unit (two-pointer walk)
-    uint32_t* tseg = reinterpret_cast<uint32_t*>(p->pin_tab + tab_tseg(p->L));
-    const uint64_t ntiles = (units + LEAF_TILE - 1) / LEAF_TILE;
-    if (ntiles + 1 > p->L.tseg_cap) return fail(DC_EINVAL, "tile table larger than planned");
-    for (uint64_t t = 0, sg = 0; t < ntiles; t++) {
-      const uint64_t u = t * LEAF_TILE;
-      while (sg + 1 < nseg && seg[sg + 1].ubeg <= u) sg++;
-      tseg[t] = (uint32_t)sg;
-    }
-    tseg[ntiles] = nseg ? (uint32_t)(nseg - 1) : 0;
-    if (nseg) {
-      DC_CUDA(cudaMemcpyAsync(p->dev + p->L.seg, seg, nseg * sizeof(Segment), cudaMemcpyHostToDevice, s));
-      DC_CUDA(cudaMemcpyAsync(p->dev + p->L.tseg, tseg, (ntiles + 1) * 4, cudaMemcpyHostToDevice, s));
-    }
-    DC_CUDA(cudaEventRecord(p->tab_done, s));
-    p->leaf_nseg = nseg;
-    p->leaf_units = units;
-    p->leaf_key = key;
+    seg[nseg++] = Segment{x, y, bx.count, 0};
   }
-  p->written = &p->leaf_written;
-  p->written_gen = p->leaf_gen;
-  p->op_run = true;
+  for (uint64_t i = 0; i < nseg; i++) {
+    seg[i].ubeg = units;
+    units += (seg[i].n * esz + 15) / 16;
+  }
+  // tile -> segment holding the tile's first unit (two-pointer walk)
+  uint32_t* tseg = reinterpret_cast<uint32_t*>(p->pin_tab + tab_tseg(p->L));
+  const uint64_t ntiles = (units + LEAF_TILE - 1) / LEAF_TILE;
+  if (ntiles + 1 > p->L.tseg_cap) return fail(DC_EINVAL, "tile table larger than planned");
+  for (uint64_t t = 0, sg = 0; t < ntiles; t++) {
+    const uint64_t u = t * LEAF_TILE;
+    while (sg + 1 < nseg && seg[sg + 1].ubeg <= u) sg++;
+    tseg[t] = (uint32_t)sg;
+  }
+  tseg[ntiles] = nseg ? (uint32_t)(nseg - 1) : 0;
+  if (nseg) {
+    DC_CUDA(cudaMemcpyAsync(p->dev + p->L.seg, seg, nseg * sizeof(Segment), cudaMemcpyHostToDevice, s));
+    DC_CUDA(cudaMemcpyAsync(p->dev + p->L.tseg, tseg, (ntiles + 1) * 4, cudaMemcpyHostToDevice, s));
+  }
+  DC_CUDA(cudaEventRecord(p->tab_done, s));
+  p->leaf_nseg = nseg;
+  p->leaf_units = units;
+  p->leaf_key = key;
+  return DC_OK;
+}
+
+LeafArgs dc::leaf_args(const dc_plan_s* p, const dc_op* op) {
+  const dc_field& X = p->schema.fields[op->type][op->x_field];
   LeafArgs a;
   a.seg = reinterpret_cast<const Segment*>(p->dev + p->L.seg);
   a.tile_seg = reinterpret_cast<const uint32_t*>(p->dev + p->L.tseg);
@@ -480,7 +507,38 @@ dc_status dc_update_leaves(dc_plan_t p, const dc_op* op, dc_stream_t stream) {
   a.kind = op->kind;
   a.f64 = X.elem_kind == DC_E_F64;
   a.scale = op->scale;
-  DC_CUDA(launch_leaf(a, s, p->sm_count));
+  return a;
+}
+
+RelocArgs dc::reloc_args(const dc_plan_s* p) {
+  RelocArgs a;
+  a.arena = p->dev;
+  a.data_bytes = p->data_bytes;
+  a.rec = reinterpret_cast<const BlockRec*>(p->dev + p->L.rec);
+  a.hostp = reinterpret_cast<const uint64_t*>(p->dev + p->L.hostp);
+  a.soff = reinterpret_cast<const uint64_t*>(p->dev + p->L.soff);
+  a.tile_base = reinterpret_cast<const uint64_t*>(p->dev + p->L.status);
+  a.ctrl = reinterpret_cast<uint32_t*>(p->dev + p->L.ctrl);
+  a.nblocks = (uint32_t)p->blocks.size();
+  a.nstruct_blocks = (uint32_t)p->nstruct_blocks;
+  a.ntiles = (uint32_t)p->L.ntiles;
+  a.verify = (p->flags & DC_PLAN_VERIFY) ? 1u : 0u;
+  return a;
+}
+
+extern "C" {
+
+dc_status dc_update_leaves(dc_plan_t p, const dc_op* op, dc_stream_t stream) {
+  if (!p) return fail(DC_EINVAL, "plan is NULL");
+  dc_status st = check_op(p, op);
+  if (st) return st;
+  if (!p->dev) return fail(DC_ESTATE, "no device buffer bound");
+  cudaStream_t s = stream;
+  if ((st = build_leaf_table(p, op, s))) return st;
+  p->written = &p->leaf_written;
+  p->written_gen = p->leaf_gen;
+  p->op_run = true;
+  DC_CUDA(launch_leaf(leaf_args(p, op), s, p->sm_count));
   return DC_OK;
 }
 
@@ -505,8 +563,8 @@ dc_status dc_update_chase(dc_plan_t p, const dc_op* op, dc_stream_t stream) {
     p->chase_gen = ++p->gen;
     for (size_t i = 0; i < picks.size(); i++) {
       uint32_t first = (uint32_t)steps.size();
-      chain_steps(p, picks[i].sblk, picks[i].elem, &steps);
-      seg[i].root = (uint64_t)(uintptr_t)p->dev;
+      const uint32_t root = chain_steps(p, picks[i].sblk, picks[i].elem, &steps);
+      seg[i].root = (uint64_t)(uintptr_t)p->dev + p->blocks[root].off;
       seg[i].step_first = first;
       seg[i].nsteps = (uint32_t)(steps.size() - first);
       seg[i].n = p->blocks[picks[i].bx].count;
@@ -677,8 +735,8 @@ dc_status dc_uvm_update(dc_uvm_t u, const dc_op* op, dc_stream_t stream) {
     u->written.clear();
     for (size_t i = 0; i < picks.size(); i++) {
       uint32_t first = (uint32_t)steps.size();
-      chain_steps(p, picks[i].sblk, picks[i].elem, &steps);
-      seg[i] = ChaseSeg{u->root, first, (uint32_t)(steps.size() - first), p->blocks[picks[i].bx].count, elems};
+      const uint32_t root = chain_steps(p, picks[i].sblk, picks[i].elem, &steps);
+      seg[i] = ChaseSeg{(uint64_t)(uintptr_t)u->managed[root], first, (uint32_t)(steps.size() - first), p->blocks[picks[i].bx].count, elems};
       elems += seg[i].n;
       u->written.push_back(picks[i].bx);
     }

@@ -1,0 +1,108 @@
+// tune.cpp — the relocation and the leaf update in one persistent launch
+// (dc_relocate_update), and the autotuner that picks its work split
+// (dc_autotune): CTA size (128/256/512 threads, i.e. 8/4/2 blocks or 16-byte
+// units per thread and tile) and CTAs per SM, timed on the bound arena and
+// cached per process by the op and the length histogram of its arrays.
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+
+#include "internal.hpp"
+
+using namespace dc;
+
+namespace {
+
+std::mutex g_mu;
+std::map<std::string, std::pair<uint32_t, uint32_t>> g_cache;  // key -> (threads, ctas per SM)
+
+std::string tune_key(const dc_plan_s* p, const dc_op* op) {
+  std::string k = std::to_string(op->kind) + "/" +
+                  std::to_string(p->schema.fields[op->type][op->x_field].elem_size) + "/" +
+                  std::to_string(64 - __builtin_clzll(p->blocks.size() | 1)) + ":";
+  for (size_t i = 0; i < p->leaf_hist.size(); i++)
+    if (p->leaf_hist[i]) k += std::to_string(i) + "=" + std::to_string(64 - __builtin_clzll(p->leaf_hist[i])) + ",";
+  return k;
+}
+
+dc_status prepare(dc_plan_s* p, const dc_op* op, cudaStream_t s) {
+  if (!p) return fail(DC_EINVAL, "plan is NULL");
+  dc_status st = check_op(p, op);
+  if (st) return st;
+  if (!p->dev) return fail(DC_ESTATE, "no device buffer bound");
+  return build_leaf_table(p, op, s);
+}
+
+}  // namespace
+
+extern "C" dc_status dc_relocate_update(dc_plan_t p, const dc_op* op, dc_stream_t stream) {
+  cudaStream_t s = stream;
+  dc_status st = prepare(p, op, s);
+  if (st) return st;
+  uint32_t threads = 256, ctas = 0;
+  if (p->tuned_threads && p->tuned_key == key_of(op)) {
+    threads = p->tuned_threads;
+    ctas = p->tuned_ctas;
+  } else {
+    std::lock_guard<std::mutex> g(g_mu);
+    auto it = g_cache.find(tune_key(p, op));
+    if (it != g_cache.end()) {
+      threads = it->second.first;
+      ctas = it->second.second;
+    }
+  }
+  p->written = &p->leaf_written;
+  p->written_gen = p->leaf_gen;
+  p->op_run = true;
+  DC_CUDA(launch_fused(reloc_args(p), leaf_args(p, op), threads, ctas, p->sm_count, s, nullptr));
+  return DC_OK;
+}
+
+extern "C" dc_status dc_autotune(dc_plan_t p, const dc_op* op, dc_stream_t stream, uint32_t* threads_out,
+                                 uint32_t* ctas_out) {
+  cudaStream_t s = stream;
+  dc_status st = prepare(p, op, s);
+  if (st) return st;
+  const RelocArgs r = reloc_args(p);
+  const LeafArgs l = leaf_args(p, op);
+  cudaEvent_t e0, e1;
+  DC_CUDA(cudaEventCreate(&e0));
+  DC_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  uint32_t bt = 256, bc = 0;
+  for (uint32_t threads : {128u, 256u, 512u}) {
+    int fit = 0;
+    DC_CUDA(launch_fused(r, l, threads, 0, p->sm_count, s, &fit));
+    for (uint32_t ctas : {1u, 2u, 4u, 8u}) {
+      if (ctas > (uint32_t)fit) break;
+      float t[3];
+      DC_CUDA(launch_fused(r, l, threads, ctas, p->sm_count, s, nullptr));  // warm
+      for (float& ms : t) {
+        DC_CUDA(cudaEventRecord(e0, s));
+        DC_CUDA(launch_fused(r, l, threads, ctas, p->sm_count, s, nullptr));
+        DC_CUDA(cudaEventRecord(e1, s));
+        DC_CUDA(cudaEventSynchronize(e1));
+        DC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      }
+      std::sort(t, t + 3);
+      if (t[1] < best) {
+        best = t[1];
+        bt = threads;
+        bc = ctas;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p->tuned_threads = bt;
+  p->tuned_ctas = bc;
+  p->tuned_key = key_of(op);
+  {
+    std::lock_guard<std::mutex> g(g_mu);
+    g_cache[tune_key(p, op)] = {bt, bc};
+  }
+  if (threads_out) *threads_out = bt;
+  if (ctas_out) *ctas_out = bc;
+  return device_error(p, s);
+}

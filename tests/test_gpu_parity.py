@@ -368,3 +368,93 @@ def test_step_scale_f64_and_null_slots():
     step_parity(lambda: tg.linear_tree(6, 100000, "allinit", seed=3), dict(kind=dc.OP_SCALE, x=2, scale=1.5),
                 dc.PLAN_MAP_HOST)
     step_parity(HandTree, {}, dc.PLAN_MAP_HOST, repeat=2)
+
+
+# ---- forests: one plan for many trees; fused relocation + update -------------------
+
+def forest_parity(ntrees, t_max, mode, flags=0, seed=4):
+    src = tg.batched(ntrees, seed=seed, t_max=t_max)
+    ref = tg.batched(ntrees, seed=seed, t_max=t_max)
+    s = src[0].schema
+    plan = dc.Plan(s, [t.root for t in src], flags=flags)
+    info = plan.info
+    assert info["ntrees"] == ntrees
+    plan.bind()
+    dop, oop = ops_pair()
+    if mode == "roundtrip":
+        plan.roundtrip(dop)
+    else:
+        plan.deep_copy()
+        plan.sync()
+        img, base = plan.image(), plan.device_base
+        for i, t in enumerate(src):  # every tree of the arena is its source's replica
+            ok, msg, _ = oracle.check_image(s, t.root, img, base, plan.root_offset(i))
+            assert ok, (i, msg)
+        if mode == "fused":
+            plan.relocate_update(dop)
+        elif mode == "tuned":
+            plan.autotune(dop)
+            plan.deep_copy()  # the tuning runs applied the update: start again
+            plan.relocate_update(dop)
+        elif mode == "graph":
+            plan.relocate_update(dop)  # puts the op's tables on the device
+            plan.sync()
+            plan.deep_copy()
+            g = torch.cuda.CUDAGraph()
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                with torch.cuda.graph(g, stream=side):
+                    plan.relocate_update(dop, stream=side)
+            torch.cuda.current_stream().wait_stream(side)
+            plan.deep_copy()  # capture does not run the kernel; start from the copy
+            plan.sync()
+            g.replay()
+        else:
+            plan.update(dop)
+        plan.copy_back()
+    for t, r in zip(src, ref):
+        cp = oracle.deep_copy(s, r.root)
+        oracle.update(s, cp.root, oop)
+        oracle.copy_back(s, cp.root, r.root, oop)
+        ok, msg = oracle.trees_equal(s, t.root, r.root)
+        assert ok, msg
+    plan.destroy()
+
+
+@pytest.mark.parametrize("mode", ["plain", "fused", "tuned", "graph", "roundtrip"])
+def test_forest_of_uneven_trees(mode):
+    forest_parity(300, 256 << 10, mode, flags=dc.PLAN_MAP_HOST if mode == "roundtrip" else 0)
+
+
+def test_forest_resolution_per_tree():
+    trees = tg.batched(20, seed=9, t_max=64 << 10)
+    s = trees[0].schema
+    p = dc.Plan(s, [t.root for t in trees])
+    p.bind()
+    p.deep_copy()
+    p.sync()
+    img, base = p.image(), p.device_base
+    for i, t in enumerate(trees):
+        ok, msg, _ = oracle.check_image(s, t.root, img, base, p.root_offset(i))
+        assert ok, msg
+        assert p.resolve_in(i, []) == base + p.root_offset(i)
+        assert p.resolve_in(i, [(2, 0)]) == oracle.image_resolve(s, img, base, [(2, 0)], p.root_offset(i))
+    p.destroy()
+
+
+def test_fused_single_tree_workloads():
+    full_parity(lambda: tg.workload("dense"), {}, mode="leaf")
+    for make in (lambda: tg.workload("dense"), lambda: tg.node_tree(5, 12, tg.uniform(1, 9), seed=13)):
+        src, ref = make(), make()
+        s = src.schema
+        plan = dc.Plan(s, src.root)
+        plan.bind()
+        plan.deep_copy()
+        dop, oop = ops_pair()
+        plan.relocate_update(dop)
+        plan.sync()
+        cp = oracle.deep_copy(s, ref.root)
+        oracle.update(s, cp.root, oop)
+        image_ok(plan, s, cp.root)
+        plan.destroy()

@@ -431,3 +431,25 @@ def random_schema(rng) -> tuple:
                               uniform(0, rng.choice([0, 7, 33, 5000]))))
     levels = rng.randint(1, 6)
     return Schema(types, rng.randrange(ntypes)), levels, rules
+
+
+# Batched workload ------------------------------------------------------------------
+
+def batched(ntrees: int = 4096, seed: int = 4, t_min: int = 16 << 10, t_max: int = 7 << 20,
+            median: int = 4096, sigma: float = 1.0, cap: int = 1 << 20):
+    """``ntrees`` independent node trees of uneven shape: per tree, levels
+    uniform in 1-5 and fanout uniform in 1-8; array lengths lognormal (median
+    ``median``, sigma ``sigma``, capped at ``cap``); a tree whose payload falls
+    outside [t_min, t_max] bytes is redrawn with the next seed."""
+    import random as _random
+    rng = _random.Random(seed)
+    trees = []
+    for i in range(ntrees):
+        while True:
+            levels, fanout, s = rng.randint(1, 5), rng.randint(1, 8), rng.getrandbits(63)
+            n = lognormal(median, sigma, cap)
+            rules = [Rule(0, 0, n, n), Rule(0, 1, const(fanout), const(0))]
+            if t_min <= dry_bytes(node_schema(), levels, rules, s) <= t_max:
+                break
+        trees.append(Tree(node_schema(), levels, rules, s, name=f"batched-{i}", nthreads=1))
+    return trees
