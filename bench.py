@@ -39,6 +39,9 @@ WORKLOADS = {
              "update through the 63-step chain to the leaf, seed 3"),
     "reloc_stress": ("pointer-heavy tree: 6 levels, fanout 16 (1,118,481 nodes), " + NODE + ", 10 fp32 per array "
                      "(the paper's n = 10 Dense case), seed 6"),
+    "served": ("a Poisson stream (mean 2,000 requests/s) of deep-copy-and-update requests on node trees drawn as in "
+               "the batched workload with payloads in [16 KiB, 64 MiB]; 30% of requests re-touch a tree served "
+               "before (uniform over them); 40 GB HBM budget; seed 5"),
     "batched": ("4,096 independent node trees of uneven shape: per tree levels U{1..5}, fanout U{1..8}; array "
                 "lengths lognormal(median 4,096, sigma 1.0, cap 2^20) fp32; trees redrawn until their payload is in "
                 "[16 KiB, 7 MiB] (~4.4 GiB in all), seed 4"),
@@ -109,6 +112,8 @@ def rank_seed(workload: str, rank: int) -> int:
     import treegen as tg
     if workload == "batched":
         return 4 + rank
+    if workload == "served":
+        return 5 + rank
     return tg.WORKLOADS[workload][4] + rank
 
 
@@ -327,6 +332,65 @@ def run_batched(args, rank, world):
     forest.destroy()
 
 
+def run_served(args, rank, world):
+    """The request server (8 slots, continuous batching, resident trees)
+    against the same stream handled sequentially with nothing resident."""
+    import random
+    import torch
+    import treegen as tg
+    import paper_1906_01128_b300 as dc
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    duration = float(os.environ.get("DC_SERVED_SECONDS", "2"))
+    rate = 2000.0
+    rng = random.Random(5 + rank)
+    reqs, seen, t = [], [], 0.0
+    while True:
+        t += rng.expovariate(rate)
+        if t >= duration:
+            break
+        if seen and rng.random() < 0.3:
+            reqs.append((rng.choice(seen), t, 1))
+        else:
+            seen.append(len(seen))
+            reqs.append((seen[-1], t, 0))
+    trees = tg.batched(len(seen), seed=5 + rank, t_min=16 << 10, t_max=64 << 20)
+    s = trees[0].schema
+    payload = sum(trees[k].payload_bytes for k, _, _ in reqs)
+    pool = torch.empty(40 << 30, dtype=torch.uint8, device="cuda")
+    pinned = int(os.environ.get("DC_SERVED_PINNED_GB", "24")) << 30
+    results = {}
+    clocks = Clocks()
+    clocks.start()
+    for mode, slots, flags in (("served", 8, 0), ("sequential", 1, dc.SERVER_SEQUENTIAL)):
+        srv = dc.Server(s, pool, pinned_bytes=pinned, slots=slots, flags=flags)
+        lat = srv.run([(k, trees[k].root, a, r) for k, a, r in reqs])
+        st = srv.stats
+        srv.destroy()
+        lat.sort()
+        results[mode] = {"p50_ms": round(lat[len(lat) // 2], 3), "p99_ms": round(lat[int(len(lat) * 0.99)], 3),
+                         "max_ms": round(lat[-1], 3), "wall_s": round(st["wall_s"], 3),
+                         "gbs": round(payload / st["wall_s"] / 1e9, 3), "resident_hits": st["resident_hits"],
+                         "evictions": st["evictions"], "deep_copied_bytes": st["h2d_bytes"],
+                         "copied_back_bytes": st["d2h_bytes"], "peak_resident_bytes": st["peak_resident_bytes"]}
+    clk = clocks.stop()
+    sv, sq = results["served"], results["sequential"]
+    out = {
+        "metric": METRIC, "value": sv["gbs"], "unit": "GB/s", "n_gpus": world, "steps": len(reqs), "warmup": 0,
+        "ms_per_step": round(1e3 * sv["wall_s"] / len(reqs), 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS["served"], "requests": len(reqs), "distinct_trees": len(seen),
+                   "duration_s": duration, "payload_bytes": payload, "slots": 8, "budget_bytes": 40 << 30},
+        "served": results,
+        "speedup": {"throughput": round(sv["gbs"] / sq["gbs"], 2), "p50": round(sq["p50_ms"] / sv["p50_ms"], 2),
+                    "p99": round(sq["p99_ms"] / sv["p99_ms"], 2)},
+        "e2e": {"value": sv["gbs"], "unit": "GB/s", "h2d_bytes_per_step": sv["deep_copied_bytes"] // len(reqs),
+                "d2h_bytes_per_step": sv["copied_back_bytes"] // len(reqs), "api": "dc_server_run"},
+        "roofline": None, "cpu_baseline": None, "clocks": clk, "gpu_launches": None,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -345,6 +409,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "batched":
         return run_batched(args, rank, world)
+    if args.workload == "served":
+        return run_served(args, rank, world)
 
     import torch
     import torch.distributed as dist

@@ -337,6 +337,48 @@ dc_status dc_uvm_destroy(dc_uvm_t uvm);
 dc_status dc_relocate_static(dc_plan_t plan, void* dev_data, uint64_t data_bytes, uint32_t* dev_status,
                              dc_stream_t stream);
 
+/* ---- served requests (a request loop with continuous batching) ----------------
+ * A server deep-copies and updates trees on request.  It owns `dev_pool`
+ * (a caller-owned device buffer, the HBM budget) and a mapped pinned host
+ * pool of `pinned_bytes`, both sub-allocated first-fit, and `nslots` worker
+ * slots, each a host thread with its own CUDA stream.  Requests are admitted
+ * as they arrive and as slots and memory free up, so the work of requests on
+ * different slots overlaps on the device; requests on one key keep their
+ * order.  A served tree stays resident (plan, arena, pinned staging) until
+ * its memory is needed; then the least recently used idle tree is evicted.
+ * A request's result is the same as dc_roundtrip's on a fresh plan: the host
+ * tree's x arrays hold the update.  A request with `retouch` set on a resident
+ * key skips the deep copy (its device copy already equals the host tree,
+ * which the caller asserts it has not changed since).  With
+ * DC_SERVER_SEQUENTIAL the requests are handled one at a time in arrival
+ * order and nothing stays resident (the plain per-structure path).
+ * All requests of a server share one schema; trees must not change shape
+ * while resident. */
+typedef struct dc_server_s* dc_server_t;
+typedef struct {
+  uint64_t key;          /* identifies the tree (equal keys = the same tree) */
+  const void* host_root; /* its root */
+  double arrival_s;      /* arrival time, seconds after dc_server_run starts */
+  int32_t retouch;       /* 1: the host tree is unchanged since this key's last request */
+} dc_request;
+typedef struct {
+  uint64_t served, failed, resident_hits, evictions;
+  uint64_t h2d_bytes, d2h_bytes;       /* payload deep-copied / copied back */
+  uint64_t peak_resident_bytes, resident_bytes;
+  double wall_s;                       /* time spent in dc_server_run */
+} dc_server_stats;
+#define DC_SERVER_SEQUENTIAL 1u
+dc_status dc_server_create(const dc_schema* schema, void* dev_pool, uint64_t dev_bytes, uint64_t pinned_bytes,
+                           uint32_t nslots, uint32_t flags, dc_server_t* out);
+/* Run a request stream: each request is injected at its arrival time and
+ * served with `op`; returns when all are done.  latency_ms[i] (may be NULL)
+ * receives the time from request i's arrival to its results being in host
+ * memory, or -1 if it failed (the first failure's status is returned). */
+dc_status dc_server_run(dc_server_t server, const dc_request* requests, uint64_t n, const dc_op* op,
+                        double* latency_ms);
+dc_status dc_server_stats_get(dc_server_t server, dc_server_stats* out);
+dc_status dc_server_destroy(dc_server_t server);
+
 /* ---- misc ------------------------------------------------------------------ */
 const char* dc_last_error(void);
 const char* dc_status_name(dc_status s);

@@ -75,6 +75,17 @@ class _Info(ctypes.Structure):
                                                "ntrees")]
 
 
+class _Request(ctypes.Structure):
+    _fields_ = [("key", ctypes.c_uint64), ("host_root", ctypes.c_void_p), ("arrival_s", ctypes.c_double),
+                ("retouch", ctypes.c_int32)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("served", "failed", "resident_hits", "evictions", "h2d_bytes",
+                                               "d2h_bytes", "peak_resident_bytes", "resident_bytes")] + \
+               [("wall_s", ctypes.c_double)]
+
+
 # every entry point of include/dc.h, with its argument types
 _P = ctypes.POINTER
 _vp, _u32, _u64, _i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
@@ -111,6 +122,10 @@ SIGNATURES = {
     "dc_uvm_copy_back": [_vp, _vp, _u32],
     "dc_uvm_sync": [_vp, _vp],
     "dc_uvm_destroy": [_vp],
+    "dc_server_create": [_P(_Schema), _vp, _u64, _u64, _u32, _u32, _P(_vp)],
+    "dc_server_run": [_vp, _P(_Request), _u64, _P(_Op), _P(ctypes.c_double)],
+    "dc_server_stats_get": [_vp, _P(_ServerStats)],
+    "dc_server_destroy": [_vp],
 }
 
 
@@ -365,6 +380,51 @@ class Uvm:
     def destroy(self):
         if getattr(self, "_h", None):
             lib.dc_uvm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+SERVER_SEQUENTIAL = 1
+
+
+class Server:
+    """``dc_server_t``: a request loop over a device pool (a torch CUDA uint8
+    tensor, the HBM budget) with ``slots`` concurrent workers."""
+
+    def __init__(self, schema, pool: torch.Tensor, pinned_bytes: int, slots: int = 4, flags: int = 0):
+        self._schema_c, self._keep = schema_struct(schema)
+        h = ctypes.c_void_p()
+        _check(lib.dc_server_create(ctypes.byref(self._schema_c), pool.data_ptr(), pool.numel(), pinned_bytes,
+                                    slots, flags, ctypes.byref(h)))
+        self._h = h.value
+        self.pool = pool
+
+    def run(self, requests, op=None):
+        """requests: (key, host_root, arrival_s, retouch) tuples.  Returns the
+        per-request latencies in ms (-1 for a failed request)."""
+        n = len(requests)
+        arr = (_Request * max(1, n))()
+        for i, (k, r, a, t) in enumerate(requests):
+            arr[i] = _Request(k, r, a, int(t))
+        lat = (ctypes.c_double * max(1, n))()
+        o, keep = _op(op or Op())
+        _check(lib.dc_server_run(self._h, arr, n, ctypes.byref(o), lat))
+        return list(lat)[:n]
+
+    @property
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check(lib.dc_server_stats_get(self._h, ctypes.byref(st)))
+        return {n: getattr(st, n) for n, _ in _ServerStats._fields_}
+
+    def destroy(self):
+        if getattr(self, "_h", None):
+            lib.dc_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

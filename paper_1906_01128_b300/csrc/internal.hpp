@@ -229,6 +229,7 @@ struct dc_plan_s {
   dc::DevLayout L;
   uint8_t* pinned = nullptr;      // data-region staging arena (cudaHostAlloc)
   uint8_t* pin_tab = nullptr;     // segment / chase table staging (cudaHostAlloc)
+  bool borrowed_pinned = false;   // pinned memory lent by a server (not freed by the plan)
   uint64_t pin_tab_bytes = 0;
   cudaEvent_t h2d_done = nullptr; // last deep copy's transfers
   cudaEvent_t tab_done = nullptr; // last table upload
@@ -332,6 +333,10 @@ dc_status pick(const dc_plan_s* p, const dc_op* op, std::vector<Pick>* out);
 dc_status build_leaf_table(dc_plan_s* p, const dc_op* op, cudaStream_t s);
 LeafArgs leaf_args(const dc_plan_s* p, const dc_op* op);
 RelocArgs reloc_args(const dc_plan_s* p);
+// Pinned bytes a plan needs (arena + table staging), and binding with pinned
+// memory lent by the caller (the request server's pool; mapped).
+uint64_t pinned_need(const dc_plan_s* p);
+dc_status bind_borrowed(dc_plan_s* p, void* dev, uint64_t bytes, uint8_t* pinned, uint8_t* pinned_dev, cudaStream_t s);
 // The chain of (field, index) steps from the root to struct (block, elem).
 void path_to(const dc_plan_s* p, uint32_t block, uint64_t elem, std::vector<dc_step>* out);
 }  // namespace dc

@@ -308,8 +308,8 @@ dc_status dc_plan_destroy(dc_plan_t p) {
   if (!p) return DC_OK;
   if (p->h2d_done) cudaEventSynchronize(p->h2d_done);
   if (p->tab_done) cudaEventSynchronize(p->tab_done);
-  if (p->pinned) cudaFreeHost(p->pinned);
-  if (p->pin_tab) cudaFreeHost(p->pin_tab);
+  if (p->pinned && !p->borrowed_pinned) cudaFreeHost(p->pinned);
+  if (p->pin_tab && !p->borrowed_pinned) cudaFreeHost(p->pin_tab);
   release_transfers(p);
   if (p->h2d_done) cudaEventDestroy(p->h2d_done);
   if (p->tab_done) cudaEventDestroy(p->tab_done);
@@ -345,7 +345,7 @@ dc_status dc_bind_device(dc_plan_t p, void* dev, uint64_t bytes, dc_stream_t str
   }
   if (!p->transfers_ready) plan_transfers(p);
   if (!p->pin_tab || p->pin_tab_bytes < tab_total(p->L)) {
-    if (p->pin_tab) cudaFreeHost(p->pin_tab);
+    if (p->pin_tab && !p->borrowed_pinned) cudaFreeHost(p->pin_tab);
     p->pin_tab_bytes = tab_total(p->L);
     cudaError_t e = cudaHostAlloc((void**)&p->pin_tab, p->pin_tab_bytes, cudaHostAllocDefault);
     if (e != cudaSuccess) {
@@ -378,6 +378,23 @@ dc_status dc_bind_device(dc_plan_t p, void* dev, uint64_t bytes, dc_stream_t str
   p->op_run = false;
   return DC_OK;
 }
+
+}  // extern "C"
+
+uint64_t dc::pinned_need(const dc_plan_s* p) { return round_up(p->data_bytes, 256) + tab_total(p->L); }
+
+dc_status dc::bind_borrowed(dc_plan_s* p, void* dev, uint64_t bytes, uint8_t* pinned, uint8_t* pinned_dev,
+                            cudaStream_t s) {
+  if (p->pinned && !p->borrowed_pinned) return fail(DC_ESTATE, "plan already owns a pinned arena");
+  p->borrowed_pinned = true;
+  p->pinned = pinned;
+  p->pinned_dev = pinned_dev;
+  p->pin_tab = pinned + round_up(p->data_bytes, 256);
+  p->pin_tab_bytes = tab_total(p->L);
+  return dc_bind_device(p, dev, bytes, s);
+}
+
+extern "C" {
 
 dc_status dc_device_base(dc_plan_t p, uint64_t* base) {
   if (!p || !base) return fail(DC_EINVAL, "NULL argument");
