@@ -281,6 +281,15 @@ dc_status dc_copy_back(dc_plan_t plan, uint32_t flags, dc_stream_t stream);
  * three calls. */
 dc_status dc_roundtrip(dc_plan_t plan, const dc_op* op, dc_stream_t stream);
 
+/* dc_roundtrip_selected — the paper's pointerchain transfer scheme (Sec. 3;
+ * Sec. 4.1.1 item 3): only the arrays the op reads and writes move, each to its
+ * effective device address; the update runs and x comes back.  Structs and
+ * other arrays are neither copied nor relocated (their device copies are
+ * whatever an earlier deep copy left), so it suits kernels that work through
+ * resolved addresses only.  The host result equals dc_roundtrip's.
+ * Blocking.  Errors: as dc_roundtrip. */
+dc_status dc_roundtrip_selected(dc_plan_t plan, const dc_op* op, dc_stream_t stream);
+
 /* dc_sync — wait for the plan's work on `stream` and report (then clear) the
  * device error word: DC_EDEVICE_BOUNDS, DC_ETIMEOUT or DC_EVERIFY. */
 dc_status dc_sync(dc_plan_t plan, dc_stream_t stream);
@@ -336,6 +345,24 @@ dc_status dc_uvm_destroy(dc_uvm_t uvm);
 #define DC_STATIC_SCRATCH_BYTES 1573888u /* 1 MiB block records + 512 KiB offsets + look-back/control words */
 dc_status dc_relocate_static(dc_plan_t plan, void* dev_data, uint64_t data_bytes, uint32_t* dev_status,
                              dc_stream_t stream);
+
+/* ---- host arenas (Algorithm 1's allocation requests served from one buffer) ----
+ * A host arena is pinned, mapped host memory of the library's own; blocks
+ * handed out by dc_host_arena_alloc (16-byte aligned at least) are blocks a
+ * tree can be built from.  A plan recognises blocks inside an arena and
+ * moves them between the arena and the device without any marshal or
+ * scatter: the deep copy reads them and the copy back writes them in place,
+ * one kernel launch each way, whatever their sizes (no DC_PLAN_MAP_HOST
+ * needed; nothing outside the arena is touched).  dc_roundtrip then also
+ * takes its fused path.  dc_host_arena_alloc returns NULL when the arena is
+ * full; dc_host_arena_reset forgets every allocation (no plan may still use
+ * them); an arena must outlive the plans that use it. */
+typedef struct dc_host_arena_s* dc_host_arena_t;
+dc_status dc_host_arena_create(uint64_t bytes, dc_host_arena_t* out);
+void* dc_host_arena_alloc(dc_host_arena_t arena, uint64_t bytes, uint64_t align);
+dc_status dc_host_arena_used(dc_host_arena_t arena, uint64_t* used);
+dc_status dc_host_arena_reset(dc_host_arena_t arena);
+dc_status dc_host_arena_destroy(dc_host_arena_t arena);
 
 /* ---- served requests (a request loop with continuous batching) ----------------
  * A server deep-copies and updates trees on request.  It owns `dev_pool`

@@ -113,6 +113,7 @@ SIGNATURES = {
     "dc_verify_chain": [_vp, _P(_Step), _u32, _vp, _P(_u64)],
     "dc_copy_back": [_vp, _u32, _vp],
     "dc_roundtrip": [_vp, _P(_Op), _vp],
+    "dc_roundtrip_selected": [_vp, _P(_Op), _vp],
     "dc_sync": [_vp, _vp],
     "dc_device_base": [_vp, _P(_u64)],
     "dc_uvm_build": [_P(_Schema), _vp, _P(_vp)],
@@ -126,6 +127,10 @@ SIGNATURES = {
     "dc_server_run": [_vp, _P(_Request), _u64, _P(_Op), _P(ctypes.c_double)],
     "dc_server_stats_get": [_vp, _P(_ServerStats)],
     "dc_server_destroy": [_vp],
+    "dc_host_arena_create": [_u64, _P(_vp)],
+    "dc_host_arena_used": [_vp, _P(_u64)],
+    "dc_host_arena_reset": [_vp],
+    "dc_host_arena_destroy": [_vp],
 }
 
 
@@ -144,6 +149,8 @@ def _load():
     L.dc_status_name.argtypes = [ctypes.c_int]
     L.dc_kernel_launches.restype = ctypes.c_uint64
     L.dc_kernel_launches.argtypes = []
+    L.dc_host_arena_alloc.restype = ctypes.c_void_p
+    L.dc_host_arena_alloc.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64]
     return L
 
 
@@ -318,6 +325,11 @@ class Plan:
         o, keep = _op(op or Op())
         _check(lib.dc_roundtrip(self._h, ctypes.byref(o), _stream(stream)))
 
+    def roundtrip_selected(self, op=None, stream=None):
+        """Move only the op's arrays (pointerchain), update, copy x back."""
+        o, keep = _op(op or Op())
+        _check(lib.dc_roundtrip_selected(self._h, ctypes.byref(o), _stream(stream)))
+
     def copy_back(self, all_arrays: bool = False, stream=None):
         _check(lib.dc_copy_back(self._h, COPY_ALL_ARRAYS if all_arrays else 0, _stream(stream)))
 
@@ -425,6 +437,45 @@ class Server:
     def destroy(self):
         if getattr(self, "_h", None):
             lib.dc_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class HostArena:
+    """``dc_host_arena_t``: pinned, mapped host memory of the library's own to
+    build trees in (Algorithm 1's allocation requests served from one
+    buffer); plans move its blocks without a marshal.  ``allocator`` is the
+    (function address, context) pair for C code that builds trees."""
+
+    def __init__(self, nbytes: int):
+        h = ctypes.c_void_p()
+        _check(lib.dc_host_arena_create(nbytes, ctypes.byref(h)))
+        self._h = h.value
+
+    @property
+    def allocator(self):
+        return ctypes.cast(lib.dc_host_arena_alloc, ctypes.c_void_p).value, self._h
+
+    def alloc(self, nbytes: int, align: int = 16) -> int:
+        return lib.dc_host_arena_alloc(self._h, nbytes, align) or 0
+
+    @property
+    def used(self) -> int:
+        out = ctypes.c_uint64()
+        _check(lib.dc_host_arena_used(self._h, ctypes.byref(out)))
+        return out.value
+
+    def reset(self):
+        _check(lib.dc_host_arena_reset(self._h))
+
+    def destroy(self):
+        if getattr(self, "_h", None):
+            lib.dc_host_arena_destroy(self._h)
             self._h = None
 
     def __del__(self):

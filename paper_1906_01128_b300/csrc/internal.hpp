@@ -265,6 +265,7 @@ struct dc_plan_s {
   uint8_t* pinned_dev = nullptr;      // device view of the (mapped) pinned arena
   std::vector<uint64_t> ilo, ihi, idev;  // per block: mapped interior host range, its device address
   std::vector<std::pair<void*, uint64_t>> registered;  // caller pages this plan page-locked
+  bool has_arena_blocks = false;       // some blocks live in a host arena (moved directly)
   Moves h2d;
   uint64_t h2d_int_nd = 0, h2d_int_units = 0, h2d_frag_nd = 0, h2d_frag_units = 0;
   uint64_t back_key = ~0ull;          // generation of the block list `back` was built for (0 = all arrays)
@@ -303,6 +304,8 @@ dc_status resolve(const dc_plan_s* p, uint64_t tree, const dc_step* path, uint32
 dc_status select_structs(const dc_plan_s* p, const dc_op* op,
                          std::vector<std::pair<uint32_t, uint64_t>>* out);
 dc_status check_op(const dc_plan_s* p, const dc_op* op);
+// arena.cpp: is [host, host + bytes) inside a host arena?  Its device view.
+bool in_host_arena(const void* host, uint64_t bytes, uint64_t* dev);
 // transfer.cpp
 uint64_t interior_bytes(const HostBlock& b);
 void plan_moves(const dc_plan_s* p, const std::vector<uint32_t>& list, dc_plan_s::Moves* m);

@@ -17,20 +17,21 @@ using namespace dc;
 
 namespace {
 
-dc_status build_step(dc_plan_s* p, const dc_op* op, cudaStream_t s) {
+// The op's blocks and the rest, their moves, and (when the fused kernel can
+// run: `direct` and 16-byte aligned host arrays) its device tables.
+dc_status build_step(dc_plan_s* p, const dc_op* op, bool direct, cudaStream_t s) {
   std::vector<Pick> picks;
   dc_status st = pick(p, op, &picks);
   if (st) return st;
   const uint64_t nb = p->blocks.size();
   const bool axpy = op->kind == DC_OP_AXPY_HALF;
-  p->step_fused = true;
+  p->step_fused = direct;
   std::vector<uint8_t> mark(nb, 0);
   for (const auto& k : picks) {
     mark[k.bx] = 1;
     if (axpy && k.by != NONE) mark[k.by] = 1;
     if ((uintptr_t)p->blocks[k.bx].host % 16 || (axpy && (uintptr_t)p->blocks[k.by].host % 16)) p->step_fused = false;
   }
-  if (!p->step_fused) return DC_OK;
   std::vector<uint32_t> rest, xy, x;
   for (uint32_t b = 0; b < nb; b++) (mark[b] ? xy : rest).push_back(b);
   for (const auto& k : picks) x.push_back(k.bx);
@@ -38,6 +39,9 @@ dc_status build_step(dc_plan_s* p, const dc_op* op, cudaStream_t s) {
   plan_moves(p, rest, &p->step_rest);
   plan_moves(p, xy, &p->step_xy);      // the parts of x and y outside mapped interiors
   plan_moves(p, x, &p->step_xback);    // the parts of x the host scatters afterwards
+  p->step_written = x;
+  p->step_gen = ++p->gen;
+  if (!p->step_fused) return DC_OK;
   const uint64_t base = (uint64_t)(uintptr_t)p->dev, pin = (uint64_t)(uintptr_t)p->pinned_dev;
   std::vector<MoveDesc> d;
   for (uint32_t b : p->step_rest.interiors)
@@ -88,8 +92,33 @@ dc_status build_step(dc_plan_s* p, const dc_op* op, cudaStream_t s) {
     DC_CUDA(cudaMemcpyAsync(p->dev + p->L.sts, seg.data(), seg.size() * sizeof(StreamSeg), cudaMemcpyHostToDevice, s));
     DC_CUDA(cudaMemcpyAsync(p->dev + p->L.stst, tiles.data(), tiles.size() * 4, cudaMemcpyHostToDevice, s));
   }
-  p->step_written = x;
-  p->step_gen = ++p->gen;
+  return DC_OK;
+}
+
+dc_status prepare_step(dc_plan_s* p, const dc_op* op, cudaStream_t s) {
+  const bool direct = (p->flags & DC_PLAN_MAP_HOST) || p->has_arena_blocks;
+  OpKey key = key_of(op);
+  if (key == p->step_key) return DC_OK;
+  dc_status st = wait_event(p->h2d_done);
+  if (st) return st;
+  if ((st = build_step(p, op, direct, s))) return st;
+  p->step_key = key;
+  return DC_OK;
+}
+
+dc_status launch_step_kernel(dc_plan_s* p, const dc_op* op, cudaStream_t s) {
+  StreamArgs a;
+  a.seg = reinterpret_cast<const StreamSeg*>(p->dev + p->L.sts);
+  a.tile_seg = reinterpret_cast<const uint32_t*>(p->dev + p->L.stst);
+  a.nseg = (uint32_t)p->st_nseg;
+  a.units = p->st_units;
+  a.kind = op->kind;
+  a.f64 = p->schema.fields[op->type][op->x_field].elem_kind == DC_E_F64;
+  a.scale = op->scale;
+  DC_CUDA(launch_stream(a, s, p->sm_count));
+  p->written = &p->step_written;
+  p->written_gen = p->step_gen;
+  p->op_run = true;
   return DC_OK;
 }
 
@@ -102,15 +131,8 @@ extern "C" dc_status dc_roundtrip(dc_plan_t p, const dc_op* op, dc_stream_t stre
   if (!p->dev) return fail(DC_ESTATE, "no device buffer bound");
   cudaStream_t s = stream;
   pool_of(p);
-  if (p->flags & DC_PLAN_MAP_HOST) {
-    OpKey key = key_of(op);
-    if (!(key == p->step_key)) {
-      if ((st = wait_event(p->h2d_done))) return st;
-      if ((st = build_step(p, op, s))) return st;
-      p->step_key = key;
-    }
-  }
-  if (!(p->flags & DC_PLAN_MAP_HOST) || !p->step_fused) {
+  if ((st = prepare_step(p, op, s))) return st;
+  if (!p->step_fused) {
     if ((st = dc_deep_copy(p, stream))) return st;
     if ((st = dc_update_leaves(p, op, stream))) return st;
     return dc_copy_back(p, 0, stream);
@@ -126,20 +148,34 @@ extern "C" dc_status dc_roundtrip(dc_plan_t p, const dc_op* op, dc_stream_t stre
   DC_CUDA(cudaEventRecord(p->h2d_done, s));
   if ((st = dc_relocate(p, stream))) return st;
   // the selected arrays: host -> update -> arena and host, in one pass
-  StreamArgs a;
-  a.seg = reinterpret_cast<const StreamSeg*>(p->dev + p->L.sts);
-  a.tile_seg = reinterpret_cast<const uint32_t*>(p->dev + p->L.stst);
-  a.nseg = (uint32_t)p->st_nseg;
-  a.units = p->st_units;
-  a.kind = op->kind;
-  a.f64 = p->schema.fields[op->type][op->x_field].elem_kind == DC_E_F64;
-  a.scale = op->scale;
-  DC_CUDA(launch_stream(a, s, p->sm_count));
-  p->written = &p->step_written;
-  p->written_gen = p->step_gen;
-  p->op_run = true;
+  if ((st = launch_step_kernel(p, op, s))) return st;
   if ((st = device_error(p, s))) return st;  // synchronizes the stream
   // x bytes that went through the pinned arena (outside mapped interiors)
   host_copy(p, p->step_xback, 0, p->step_xback.units.size(), false);
   return DC_OK;
+}
+
+extern "C" dc_status dc_roundtrip_selected(dc_plan_t p, const dc_op* op, dc_stream_t stream) {
+  if (!p) return fail(DC_EINVAL, "plan is NULL");
+  dc_status st = check_op(p, op);
+  if (st) return st;
+  if (!p->dev) return fail(DC_ESTATE, "no device buffer bound");
+  cudaStream_t s = stream;
+  pool_of(p);
+  if ((st = prepare_step(p, op, s))) return st;
+  if ((st = wait_event(p->h2d_done))) return st;
+  // only the op's arrays move, by their effective addresses (Sec. 3)
+  host_copy(p, p->step_xy, 0, p->step_xy.units.size(), true);
+  if (p->step_fused) {
+    if ((st = launch_step_kernel(p, op, s))) return st;
+    DC_CUDA(cudaEventRecord(p->h2d_done, s));
+    if ((st = device_error(p, s))) return st;
+    host_copy(p, p->step_xback, 0, p->step_xback.units.size(), false);
+    return DC_OK;
+  }
+  for (const auto& r : p->step_xy.runs)
+    DC_CUDA(cudaMemcpyAsync(p->dev + r.lo, p->pinned + r.lo, r.hi - r.lo, cudaMemcpyHostToDevice, s));
+  DC_CUDA(cudaEventRecord(p->h2d_done, s));
+  if ((st = dc_update_leaves(p, op, stream))) return st;
+  return dc_copy_back(p, 0, stream);
 }

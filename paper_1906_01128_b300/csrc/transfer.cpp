@@ -37,6 +37,7 @@ uint64_t page_down(uint64_t x) { return x / PAGE * PAGE; }
 }  // namespace
 
 uint64_t interior_bytes(const HostBlock& b) {
+  if (in_host_arena(b.host, b.bytes, nullptr)) return b.bytes;  // the whole block
   if (b.lane == 0) return 0;  // struct blocks always go through the pinned arena
   const uint64_t h = (uint64_t)(uintptr_t)b.host;
   const uint64_t lo = page_up(h), hi = page_down(h + b.bytes);
@@ -103,10 +104,28 @@ void plan_transfers(dc_plan_s* p) {
   p->ilo.assign(nb, 0);
   p->ihi.assign(nb, 0);
   p->idev.assign(nb, 0);
+  {  // blocks in a host arena: the GPU reads and writes them in place (struct
+     // blocks with NULL-slot fix-ups excepted: those go through the pinned arena)
+    std::vector<uint8_t> fixup(nb, 0);
+    for (uint64_t off : p->null_slots) {
+      auto it = std::upper_bound(p->blocks.begin(), p->blocks.begin() + p->nstruct_blocks, off,
+                                 [](uint64_t o, const HostBlock& hb) { return o < hb.off; });
+      fixup[(it - p->blocks.begin()) - 1] = 1;
+    }
+    for (uint32_t b = 0; b < nb; b++) {
+      uint64_t dev;
+      const HostBlock& B = p->blocks[b];
+      if (fixup[b] || !in_host_arena(B.host, B.bytes, &dev)) continue;
+      p->ilo[b] = (uint64_t)(uintptr_t)B.host;
+      p->ihi[b] = p->ilo[b] + B.bytes;
+      p->idev[b] = dev;
+      p->has_arena_blocks = true;
+    }
+  }
   if (p->flags & DC_PLAN_MAP_HOST) {
     for (uint32_t b = 0; b < nb; b++) {
       const HostBlock& B = p->blocks[b];
-      if (!interior_bytes(B)) continue;
+      if (p->ihi[b] > p->ilo[b] || !interior_bytes(B)) continue;
       const uint64_t lo = page_up((uint64_t)(uintptr_t)B.host), hi = page_down((uint64_t)(uintptr_t)B.host + B.bytes);
       void* dptr = nullptr;
       if (cudaHostRegister((void*)lo, hi - lo, cudaHostRegisterMapped) != cudaSuccess) {

@@ -21,7 +21,7 @@ HEADER = os.path.join(ROOT, "include", "dc.h")
 
 def declared_functions():
     text = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:dc_status|const char\*|uint64_t)\s+(dc_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:dc_status|const char\*|uint64_t|void\*)\s+(dc_\w+)\s*\(", text, re.M)))
 
 
 def test_library_exports_every_declared_symbol():
@@ -33,7 +33,8 @@ def test_library_exports_every_declared_symbol():
     assert not missing, missing
     for n in names:  # and ctypes can bind each one
         assert getattr(dc.lib, n) is not None
-    assert set(dc.SIGNATURES) | {"dc_last_error", "dc_status_name", "dc_kernel_launches"} == set(names)
+    assert set(dc.SIGNATURES) | {"dc_last_error", "dc_status_name", "dc_kernel_launches",
+                                 "dc_host_arena_alloc"} == set(names)
 
 
 def host_image(plan, base):

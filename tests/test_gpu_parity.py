@@ -458,3 +458,71 @@ def test_fused_single_tree_workloads():
         oracle.update(s, cp.root, oop)
         image_ok(plan, s, cp.root)
         plan.destroy()
+
+
+# ---- host arenas (allocation requests served from one pinned buffer) -----------------
+
+def arena_case(make_tree, op_kw, mode, arena_bytes):
+    arena = dc.HostArena(arena_bytes)
+    src = make_tree(arena.allocator)  # every block of the source tree comes from the arena
+    ref = make_tree(None)
+    assert arena.used >= src.payload_bytes
+    s = src.schema
+    plan = dc.Plan(s, src.root)
+    plan.bind()
+    dop, oop = ops_pair(**op_kw)
+    if mode == "calls":
+        plan.deep_copy()
+        plan.sync()
+        image_ok(plan, s, src.root)
+        plan.update(dop)
+        plan.copy_back()
+    elif mode == "roundtrip":
+        plan.roundtrip(dop)
+    else:
+        plan.roundtrip_selected(dop)
+    cp = oracle.deep_copy(s, ref.root)
+    oracle.update(s, cp.root, oop)
+    oracle.copy_back(s, cp.root, ref.root, oop)
+    ok, msg = oracle.trees_equal(s, src.root, ref.root)
+    assert ok, msg
+    plan.destroy()
+    src.free()
+    arena.destroy()
+
+
+@pytest.mark.parametrize("mode", ["calls", "roundtrip", "selected"])
+def test_trees_built_in_a_host_arena(mode):
+    arena_case(lambda a: tg.workload("dense", alloc=a), {}, mode, 400 << 20)
+    arena_case(lambda a: tg.node_tree(5, 12, tg.uniform(1, 9), seed=13, alloc=a), {}, mode, 64 << 20)
+    arena_case(lambda a: tg.node_tree(64, 1, 1024, 1 << 20, seed=3, alloc=a),
+               dict(sel=dc.SEL_CHAIN, path=tg.leaf_path(64)), mode, 64 << 20)
+
+
+# ---- the pointerchain transfer scheme: only the op's arrays move ----------------------
+
+@pytest.mark.parametrize("flags", [0, dc.PLAN_MAP_HOST])
+def test_roundtrip_selected_matches_the_oracle(flags):
+    cases = [
+        (lambda: tg.workload("deep"), dict(sel=dc.SEL_CHAIN, path=tg.leaf_path(64))),
+        (lambda: tg.workload("dense"), {}),
+        (lambda: tg.workload("dense"), dict(sel=dc.SEL_CHAIN, path=[(NODE_LEAF, 15), (NODE_LEAF, 15)])),
+        (lambda: tg.linear_tree(10, 10 ** 6, "allinit", seed=8),
+         dict(kind=dc.OP_SCALE, sel=dc.SEL_CHAIN, x=2, scale=1.5, path=[(3, 0)] * 9)),
+    ]
+    for make, kw in cases:
+        src, ref = make(), make()
+        s = src.schema
+        plan = dc.Plan(s, src.root, flags=flags)
+        plan.bind()
+        dop, oop = ops_pair(**kw)
+        for _ in range(2):
+            plan.roundtrip_selected(dop)
+            cp = oracle.deep_copy(s, ref.root)
+            oracle.update(s, cp.root, oop)
+            oracle.copy_back(s, cp.root, ref.root, oop)
+            ok, msg = oracle.trees_equal(s, src.root, ref.root)
+            assert ok, msg
+        plan.destroy()
+        src.free()
+        ref.free()

@@ -89,6 +89,9 @@ def lib():
         L = ctypes.CDLL(build_lib())
         L.tg_build.restype = ctypes.c_void_p
         L.tg_build.argtypes = [ctypes.POINTER(_Schema), ctypes.POINTER(_Shape), ctypes.c_uint64]
+        L.tg_build_ex.restype = ctypes.c_void_p
+        L.tg_build_ex.argtypes = [ctypes.POINTER(_Schema), ctypes.POINTER(_Shape), ctypes.c_uint64,
+                                  ctypes.c_void_p, ctypes.c_void_p]
         L.tg_dry_bytes.restype = ctypes.c_int
         L.tg_dry_bytes.argtypes = [ctypes.POINTER(_Schema), ctypes.POINTER(_Shape), ctypes.c_uint64,
                                    ctypes.POINTER(ctypes.c_uint64)]
@@ -281,13 +284,19 @@ class Tree:
     The memory is freed by ``free()`` (or when the object is collected)."""
 
     def __init__(self, schema: Schema, levels: int, rules: Sequence[Rule], seed: int,
-                 name: str = "", nthreads: int = 0):
+                 name: str = "", nthreads: int = 0, alloc=None):
+        """``alloc``: optional (function address, context) of a C allocator
+        ``void* fn(void* ctx, uint64_t bytes, uint64_t align)`` that provides
+        every block (e.g. an arena); such blocks are not freed by ``free()``."""
         L = lib()
         self.schema, self.levels, self.rules, self.seed, self.name = schema, levels, list(rules), seed, name
         cs, self._keep = to_ctypes(schema, _Field, _Type, _Schema, _tg_field_args)
         sh, rk = _shape(levels, rules, nthreads)
         self._keep.append(rk)
-        h = L.tg_build(ctypes.byref(cs), ctypes.byref(sh), seed)
+        if alloc is None:
+            h = L.tg_build(ctypes.byref(cs), ctypes.byref(sh), seed)
+        else:
+            h = L.tg_build_ex(ctypes.byref(cs), ctypes.byref(sh), seed, alloc[0], alloc[1])
         if not h:
             raise RuntimeError("treegen: " + L.tg_error().decode())
         self._h = h
@@ -324,7 +333,7 @@ def dry_bytes(schema: Schema, levels: int, rules: Sequence[Rule], seed: int) -> 
 
 
 def node_tree(levels: int, fanout, n_interior, n_leaf=None, seed: int = 0, name: str = "",
-              nthreads: int = 0) -> Tree:
+              nthreads: int = 0, alloc=None) -> Tree:
     """A node-struct tree: ``fanout`` and the lengths are (dist, a, b, c) tuples
     or plain integers (constants)."""
     s = node_schema()
@@ -332,7 +341,7 @@ def node_tree(levels: int, fanout, n_interior, n_leaf=None, seed: int = 0, name:
     ni = n_interior if isinstance(n_interior, tuple) else const(n_interior)
     nl = ni if n_leaf is None else (n_leaf if isinstance(n_leaf, tuple) else const(n_leaf))
     rules = [Rule(0, 0, ni, nl), Rule(0, 1, f, const(0))]
-    return Tree(s, levels, rules, seed, name=name, nthreads=nthreads)
+    return Tree(s, levels, rules, seed, name=name, nthreads=nthreads, alloc=alloc)
 
 
 def linear_tree(k: int, n: int, layout: str = "allinit", seed: int = 0) -> Tree:
@@ -374,10 +383,10 @@ WORKLOADS = {
 }
 
 
-def workload(name: str, seed: Optional[int] = None, nthreads: int = 0) -> Tree:
+def workload(name: str, seed: Optional[int] = None, nthreads: int = 0, alloc=None) -> Tree:
     levels, fanout, ni, nl, s = WORKLOADS[name]
     return node_tree(levels, fanout, ni, nl, seed=s if seed is None else seed, name=name,
-                     nthreads=nthreads)
+                     nthreads=nthreads, alloc=alloc)
 
 
 def leaf_path(levels: int, index: int = 0, child_field: int = 4):

@@ -124,6 +124,8 @@ typedef struct {
   rng_t rng;
   tg_tree* t;
   int dry;
+  tg_alloc_fn alloc;
+  void* actx;
   uint64_t payload, nstructs, nblocks;
   uint8_t is_count[64][TG_MAX_FIELDS];
 } ctx_t;
@@ -185,6 +187,7 @@ static const tg_rule* find_rule(const tg_shape* sh, uint32_t type, uint32_t fiel
 }
 
 static void* tg_alloc(ctx_t* c, uint64_t bytes) {
+  if (c->alloc) return c->alloc(c->actx, bytes ? bytes : 1, 16);
   void* p = malloc(bytes ? bytes : 1);
   if (!p) return NULL;
   if (push_alloc(c->t, p)) {
@@ -417,6 +420,10 @@ static int fill_all(tg_tree* t, uint32_t nthreads) {
 /* ---- public API --------------------------------------------------------- */
 
 tg_tree* tg_build(const tg_schema* s, const tg_shape* sh, uint64_t seed) {
+  return tg_build_ex(s, sh, seed, NULL, NULL);
+}
+
+tg_tree* tg_build_ex(const tg_schema* s, const tg_shape* sh, uint64_t seed, tg_alloc_fn alloc, void* actx) {
   if (check_schema(s, sh)) return NULL;
   tg_tree* t = calloc(1, sizeof *t);
   if (!t) return NULL;
@@ -431,6 +438,8 @@ tg_tree* tg_build(const tg_schema* s, const tg_shape* sh, uint64_t seed) {
   }
   init_ctx(c, s, sh, seed);
   c->t = t;
+  c->alloc = alloc;
+  c->actx = actx;
   const tg_type* R = &s->types[s->root_type];
   t->root = tg_alloc(c, R->size);
   if (!t->root) {

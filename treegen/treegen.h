@@ -81,6 +81,10 @@ typedef struct tg_tree_s tg_tree;
 /* Build one tree. Count fields without a rule are 0; other scalars and all
  * struct bytes not covered by a field take random values. NULL on error. */
 tg_tree* tg_build(const tg_schema* s, const tg_shape* shape, uint64_t seed);
+/* The same, with every block taken from `alloc(ctx, bytes, 16)` instead of
+ * malloc (e.g. an arena); tg_free then frees none of the blocks. */
+typedef void* (*tg_alloc_fn)(void* ctx, uint64_t bytes, uint64_t align);
+tg_tree* tg_build_ex(const tg_schema* s, const tg_shape* shape, uint64_t seed, tg_alloc_fn alloc, void* ctx);
 /* Same draws as tg_build, nothing allocated: the tree's payload bytes. */
 int tg_dry_bytes(const tg_schema* s, const tg_shape* shape, uint64_t seed, uint64_t* bytes);
 void* tg_root(const tg_tree* t);
