@@ -42,6 +42,11 @@ WORKLOADS = {
     "served": ("a Poisson stream (mean 2,000 requests/s) of deep-copy-and-update requests on node trees drawn as in "
                "the batched workload with payloads in [16 KiB, 64 MiB]; 30% of requests re-touch a tree served "
                "before (uniform over them); 40 GB HBM budget; seed 5"),
+    "paper": ("the paper's own scenarios: the Linear chain {int nA; int nLnext; double* A; L* Lnext} with k = 2..10 "
+              "levels of n doubles (allinit-LLused: Listing 2's scaling kernel on the last level) and the Dense tree "
+              "with q = 4/8/16 structs per intermediate array, D = 3, n = 10..1000 (the Lnext[q-1] chain of Listing 2 "
+              "scaled), comparing marshalling (full deep copy), pointerchain (only the effective-address array) and "
+              "UVM (managed memory, first touch)"),
     "batched": ("4,096 independent node trees of uneven shape: per tree levels U{1..5}, fanout U{1..8}; array "
                 "lengths lognormal(median 4,096, sigma 1.0, cap 2^20) fp32; trees redrawn until their payload is in "
                 "[16 KiB, 7 MiB] (~4.4 GiB in all), seed 4"),
@@ -335,25 +340,13 @@ def run_batched(args, rank, world):
 def run_served(args, rank, world):
     """The request server (8 slots, continuous batching, resident trees)
     against the same stream handled sequentially with nothing resident."""
-    import random
     import torch
     import treegen as tg
     import paper_1906_01128_b300 as dc
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     duration = float(os.environ.get("DC_SERVED_SECONDS", "2"))
-    rate = 2000.0
-    rng = random.Random(5 + rank)
-    reqs, seen, t = [], [], 0.0
-    while True:
-        t += rng.expovariate(rate)
-        if t >= duration:
-            break
-        if seen and rng.random() < 0.3:
-            reqs.append((rng.choice(seen), t, 1))
-        else:
-            seen.append(len(seen))
-            reqs.append((seen[-1], t, 0))
-    trees = tg.batched(len(seen), seed=5 + rank, t_min=16 << 10, t_max=64 << 20)
+    reqs, nkeys = tg.poisson_requests(duration, 2000.0, 0.3, seed=5 + rank)
+    trees = tg.batched(nkeys, seed=5 + rank, t_min=16 << 10, t_max=64 << 20)
     s = trees[0].schema
     payload = sum(trees[k].payload_bytes for k, _, _ in reqs)
     pool = torch.empty(40 << 30, dtype=torch.uint8, device="cuda")
@@ -378,7 +371,7 @@ def run_served(args, rank, world):
         "metric": METRIC, "value": sv["gbs"], "unit": "GB/s", "n_gpus": world, "steps": len(reqs), "warmup": 0,
         "ms_per_step": round(1e3 * sv["wall_s"] / len(reqs), 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOADS["served"], "requests": len(reqs), "distinct_trees": len(seen),
+        "config": {"workload": WORKLOADS["served"], "requests": len(reqs), "distinct_trees": nkeys,
                    "duration_s": duration, "payload_bytes": payload, "slots": 8, "budget_bytes": 40 << 30},
         "served": results,
         "speedup": {"throughput": round(sv["gbs"] / sq["gbs"], 2), "p50": round(sq["p50_ms"] / sv["p50_ms"], 2),
@@ -386,6 +379,141 @@ def run_served(args, rank, world):
         "e2e": {"value": sv["gbs"], "unit": "GB/s", "h2d_bytes_per_step": sv["deep_copied_bytes"] // len(reqs),
                 "d2h_bytes_per_step": sv["copied_back_bytes"] // len(reqs), "api": "dc_server_run"},
         "roofline": None, "cpu_baseline": None, "clocks": clk, "gpu_launches": None,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def run_paper(args, rank, world):
+    """The paper's transfer-scheme comparison (Sec. 4-6) measured on this GPU:
+    wall time of transfer + kernel + transfer back for marshalling (a full deep
+    copy), pointerchain (only the effective-address array moves) and UVM, the
+    same two schemes on a tree built in a host arena (no marshal at all), and
+    the resolved vs pointer-chasing kernel time per chain length (the
+    dereference cost behind Tables 3-4)."""
+    import torch
+    import treegen as tg
+    import paper_1906_01128_b300 as dc
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    n_lin = int(os.environ.get("DC_PAPER_N", str(10 ** 7)))
+    reps = max(3, args.steps // 4)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def wall(fn):
+        ts = []
+        for i in range(2 + reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            if i >= 2:
+                ts.append(time.perf_counter() - t0)
+        return statistics.median(ts) * 1e3
+
+    def kernel_us(fn):
+        ts = []
+        for i in range(2 + reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            if i >= 2:
+                ts.append(e0.elapsed_time(e1) * 1e3)
+        return statistics.median(ts)
+
+    def uvm_ms(s, t, op):
+        u = dc.Uvm(s, t.root)
+        ts = []
+        for i in range(2 + reps):
+            u.prefetch(False)  # pages back on the host, as after the host initialised them
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            u.update(op)
+            u.sync()
+            u.copy_back()  # the host reads the result
+            if i >= 2:
+                ts.append(time.perf_counter() - t0)
+        u.destroy()
+        return statistics.median(ts) * 1e3
+
+    def arena_ms(make, bytes_, op):
+        arena = dc.HostArena(bytes_ + (64 << 20))
+        t = make(arena.allocator)
+        p = dc.Plan(t.schema, t.root)
+        p.bind()
+        full = wall(lambda: p.roundtrip(op))
+        sel = wall(lambda: p.roundtrip_selected(op))
+        p.destroy()
+        t.free()
+        arena.destroy()
+        return full, sel
+
+    ks = (2, 4, 6, 8, 10)
+    # one leaf and one chase launch per k first: the launch sequence an ncu capture of the
+    # dereference cost reads (-k 'leaf_kernel|chase_kernel' -c 10)
+    chains = []
+    for k in ks:
+        t = tg.linear_tree(k, n_lin, "allinit", seed=k)
+        p = dc.Plan(t.schema, t.root, flags=dc.PLAN_MAP_HOST)
+        p.bind()
+        op = dc.Op(kind=dc.OP_SCALE, sel=dc.SEL_CHAIN, x_field=2, scale=1.5, path=[(3, 0)] * (k - 1))
+        p.deep_copy()
+        p.update(op)
+        p.update_chase(op)
+        p.sync()
+        chains.append((k, t, p, op))
+    linear = []
+    for k, t, p, op in chains:
+        s = t.schema
+        row = {"k": k, "n": n_lin, "bytes": t.payload_bytes,
+               "marshalling_ms": round(wall(lambda: (p.deep_copy(), p.update(op), p.copy_back())), 3),
+               "pointerchain_ms": round(wall(lambda: p.roundtrip_selected(op)), 3),
+               "uvm_ms": round(uvm_ms(s, t, op), 3)}
+        p.deep_copy()
+        row["resolved_kernel_us"] = round(kernel_us(lambda: p.update(op)), 2)
+        row["chase_kernel_us"] = round(kernel_us(lambda: p.update_chase(op)), 2)
+        bytes_ = t.payload_bytes
+        p.destroy()
+        t.free()
+        full, sel = arena_ms(lambda a: tg.linear_tree(k, n_lin, "allinit", seed=k, alloc=a), bytes_, op)
+        row["arena_marshalling_ms"], row["arena_pointerchain_ms"] = round(full, 3), round(sel, 3)
+        for key in ("marshalling", "pointerchain", "arena_marshalling", "arena_pointerchain"):
+            row[key + "_vs_uvm"] = round(row[key + "_ms"] / row["uvm_ms"], 3)
+        linear.append(row)
+    dense = []
+    for q in (4, 8, 16):
+        for n in (10, 100, 1000):
+            t = tg.dense_tree(q, n, 3, seed=q * n)
+            s = t.schema
+            op = dc.Op(kind=dc.OP_SCALE, sel=dc.SEL_CHAIN, type=3, x_field=1, scale=1.5, path=[(3, q - 1)] * 3)
+            p = dc.Plan(s, t.root)
+            p.bind()
+            row = {"q": q, "n": n, "bytes": t.payload_bytes, "structs": t.nstructs,
+                   "marshalling_ms": round(wall(lambda: (p.deep_copy(), p.update(op), p.copy_back())), 4),
+                   "pointerchain_ms": round(wall(lambda: p.roundtrip_selected(op)), 4),
+                   "uvm_ms": round(uvm_ms(s, t, op), 4)}
+            bytes_ = t.payload_bytes
+            p.destroy()
+            t.free()
+            full, sel = arena_ms(lambda a: tg.dense_tree(q, n, 3, seed=q * n, alloc=a), bytes_, op)
+            row["arena_marshalling_ms"], row["arena_pointerchain_ms"] = round(full, 4), round(sel, 4)
+            for key in ("pointerchain", "uvm", "arena_marshalling", "arena_pointerchain"):
+                row[key + "_speedup_over_marshalling"] = round(row["marshalling_ms"] / row[key + "_ms"], 2)
+            dense.append(row)
+    pc = [r["pointerchain_speedup_over_marshalling"] for r in dense if r["n"] in (10, 100)]
+    out = {
+        "metric": METRIC, "value": round(statistics.geometric_mean(pc), 2),
+        "unit": "x (Dense, n = 10 and 100: marshalling time / pointerchain time, geometric mean)",
+        "n_gpus": world, "steps": reps, "warmup": 2, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS["paper"],
+                   "l2": "flushed: 512 MiB write before every timed call (outside the timers)",
+                   "linear_plan": "DC_PLAN_MAP_HOST", "dense_plan": "staged"},
+        "linear_allinit_llused": linear, "dense_llused": dense,
+        "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None,
     }
     if rank == 0:
         print(json.dumps(out))
@@ -411,6 +539,8 @@ def main():
         return run_batched(args, rank, world)
     if args.workload == "served":
         return run_served(args, rank, world)
+    if args.workload == "paper":
+        return run_paper(args, rank, world)
 
     import torch
     import torch.distributed as dist

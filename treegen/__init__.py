@@ -344,17 +344,17 @@ def node_tree(levels: int, fanout, n_interior, n_leaf=None, seed: int = 0, name:
     return Tree(s, levels, rules, seed, name=name, nthreads=nthreads, alloc=alloc)
 
 
-def linear_tree(k: int, n: int, layout: str = "allinit", seed: int = 0) -> Tree:
+def linear_tree(k: int, n: int, layout: str = "allinit", seed: int = 0, alloc=None) -> Tree:
     """The Linear scenario with k levels and n doubles per A array.  ``allinit``
     allocates every level's A (allinit-allused / allinit-LLused); ``llinit``
     only the last level's (LLinit-LLused: the others are NULL, nA = 0)."""
     s = linear_schema()
     interior = const(n) if layout == "allinit" else const(0)
     rules = [Rule(0, 0, interior, const(n)), Rule(0, 1, const(1), const(0))]
-    return Tree(s, k, rules, seed, name=f"linear-{layout}-k{k}-n{n}")
+    return Tree(s, k, rules, seed, name=f"linear-{layout}-k{k}-n{n}", alloc=alloc)
 
 
-def dense_tree(q: int, n: int, D: int, seed: int = 0) -> Tree:
+def dense_tree(q: int, n: int, D: int, seed: int = 0, alloc=None) -> Tree:
     """The Dense scenario: D+1 struct levels, q structs per intermediate array,
     n doubles per A array."""
     s = dense_schema(D)
@@ -363,7 +363,7 @@ def dense_tree(q: int, n: int, D: int, seed: int = 0) -> Tree:
         rules.append(Rule(i, 0, const(n), const(n)))
         rules.append(Rule(i, 1, const(q), const(q)))
     rules.append(Rule(D, 0, const(n), const(n)))
-    return Tree(s, D + 1, rules, seed, name=f"dense-q{q}-n{n}-D{D}")
+    return Tree(s, D + 1, rules, seed, name=f"dense-q{q}-n{n}-D{D}", alloc=alloc)
 
 
 def listing1_tree(n_atoms: int, seed: int = 0) -> Tree:
@@ -443,6 +443,26 @@ def random_schema(rng) -> tuple:
 
 
 # Batched workload ------------------------------------------------------------------
+
+def poisson_requests(duration: float, rate: float = 2000.0, retouch: float = 0.3, seed: int = 5):
+    """A request stream: arrivals of a Poisson process of ``rate`` per second
+    over ``duration`` seconds; each request re-touches a key served before
+    (uniform over them) with probability ``retouch``, else names a new key.
+    Returns ([(key, arrival_s, retouch 0/1)], number of keys)."""
+    import random as _random
+    rng = _random.Random(seed)
+    reqs, nkeys, t = [], 0, 0.0
+    while True:
+        t += rng.expovariate(rate)
+        if t >= duration:
+            break
+        if nkeys and rng.random() < retouch:
+            reqs.append((rng.randrange(nkeys), t, 1))
+        else:
+            reqs.append((nkeys, t, 0))
+            nkeys += 1
+    return reqs, nkeys
+
 
 def batched(ntrees: int = 4096, seed: int = 4, t_min: int = 16 << 10, t_max: int = 7 << 20,
             median: int = 4096, sigma: float = 1.0, cap: int = 1 << 20):
