@@ -2,16 +2,18 @@
 16, 273 nodes, lognormal fp32 arrays, ~338 MB), printing one JSON line.
 
   value  device-resident step: the arena is already in HBM; one step relocates
-         every pointer (dc_relocate) and runs the leaf update through resolved
-         chains (dc_update_leaves).  GB/s = payload bytes / step time, CUDA
-         events on the launching stream, L2 flushed (512 MiB write) before each
-         step.
+         every pointer and runs the leaf update through resolved chains, in one
+         persistent launch (dc_relocate_update).  GB/s = payload bytes / step
+         time, CUDA events on the launching stream.  Between steps, L2 is
+         flushed (512 MiB write) unless one step streams more than twice the L2
+         (then no input of a step is still in L2 when the next step reads it).
   e2e    the same metric through the C ABI with host buffers: dc_deep_copy
          (transfer + relocation), dc_update_leaves, dc_copy_back (back into the
          host arrays), host clock around synchronized steps; reported for a plan
          with DC_PLAN_MAP_HOST (e2e) and for the default staged plan (e2e_staged).
-  roofline  the leaf kernel: algorithmic bytes (12 B per element: read x and y,
-         write x) / its CUDA-event time, against the measured HBM copy peak.
+  roofline  the step's kernel: algorithmic bytes (12 B per leaf element: read x
+         and y, write x; 20 B per pointer slot + 16 B per block for the
+         relocation) / its CUDA-event time, against the measured HBM copy peak.
 
 ``--impl reference`` times the CPU oracle (plain recursive deep copy + update +
 copy back, one core) on the same workload instead.
@@ -51,6 +53,22 @@ WORKLOADS = {
                 "lengths lognormal(median 4,096, sigma 1.0, cap 2^20) fp32; trees redrawn until their payload is in "
                 "[16 KiB, 7 MiB] (~4.4 GiB in all), seed 4"),
 }
+
+
+# DRAM bytes (read + write) per launch of the step's kernel from one ncu capture, by (workload, split);
+# the summary beside each gives the command.  An entry stands only while the kernel is unchanged.
+NCU_TRAFFIC = {
+    ("dense", 512, 2): (460_697_728, "profiles/fused_kernel_dense.md"),
+}
+
+
+def l2_policy(torch, step_bytes):
+    """Whether to flush L2 between timed steps, and the line that says so."""
+    l2 = torch.cuda.get_device_properties(torch.cuda.current_device()).L2_cache_size
+    if step_bytes > 2 * l2:
+        return False, (f"not flushed: inputs larger than L2 (one step streams {step_bytes / 1e6:.1f} MB in the same "
+                       f"order every step; L2 {l2 / 1e6:.1f} MB)")
+    return True, "flushed: 512 MiB write before every timed step (outside the events)"
 
 
 def peaks():
@@ -239,6 +257,7 @@ def run_batched(args, rank, world):
     threads, ctas = forest.autotune(op)
     forest.deep_copy()
     forest.sync()
+    do_flush, l2_line = l2_policy(torch, 12 * nelem + info["nrelocs"] * 20 + info["nblocks"] * 16)
     singles = [dc.Plan(s, t.root, flags=dc.PLAN_MAP_HOST) for t in trees]
     for p in singles:
         p.bind()
@@ -251,10 +270,12 @@ def run_batched(args, rank, world):
     def timed(fn, reps):
         ts = []
         for _ in range(args.warmup):
-            flush.zero_()
+            if do_flush:
+                flush.zero_()
             fn()
         for _ in range(reps):
-            flush.zero_()
+            if do_flush:
+                flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             fn()
@@ -288,7 +309,7 @@ def run_batched(args, rank, world):
     e2e_single = wall(lambda: [p.roundtrip(op) for p in singles], 3)
     clk = clocks.stop()
     hbm, peak_kind = peaks()
-    reloc_bytes = info["nblocks"] * 24 + info["nstruct_blocks"] * 8
+    reloc_bytes = info["nrelocs"] * 20 + info["nblocks"] * 16  # 12 B entry + 8 B slot; 8 B size + 8 B offset
     fused_bytes = 12 * nelem + reloc_bytes
     t_mean = statistics.mean(ts_forest)
     cpu = None
@@ -312,7 +333,7 @@ def run_batched(args, rank, world):
         "config": {"workload": WORKLOADS["batched"], "trees": ntrees, "nodes": info["nstructs"],
                    "blocks": info["nblocks"], "payload_bytes": payload,
                    "step": "dc_relocate_update on the forest (one persistent launch)",
-                   "l2": "flushed: 512 MiB write before every timed step (outside the events)"},
+                   "l2": l2_line},
         "roofline": {"bound": "hbm", "kernel": "fused_kernel<float, AXPY_HALF> (relocation + leaf update)",
                      "achieved": round(fused_bytes / t_mean / 1e9, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(fused_bytes / t_mean / 1e9 / hbm, 4), "traffic": None,
@@ -581,49 +602,75 @@ def main():
 
     plan.deep_copy()
     plan.sync()
+    tuned = plan.autotune(op)  # the tuning runs apply the update: start again from the host tree
+    plan.deep_copy()
+    plan.sync()
+    leaf_bytes = 12 * nelem
+    # relocation: 12-byte entry read + 8-byte slot written per pointer, 8-byte size read + 8-byte offset
+    # written per block; this library's records move 16 B per block + 8 B per slot + 8 B per struct block
+    reloc_bytes = info["nrelocs"] * 20 + info["nblocks"] * 16
+    reloc_moved = info["nblocks"] * (16 + 8) + info["nstruct_blocks"] * 8
+    fused_bytes = leaf_bytes + reloc_bytes
+    do_flush, l2_line = l2_policy(torch, fused_bytes)
+
+    def timed_loop(parts, label):
+        """CUDA events between the parts of each step (L2 policy above).  The timed steps sit
+        in an NVTX range named ``label`` (an ncu capture can select them by it)."""
+        for _ in range(args.warmup):
+            if do_flush:
+                flush.zero_()
+            for f in parts:
+                f()
+        barrier()
+        torch.cuda.nvtx.range_push(label)
+        ev = []
+        for _ in range(args.steps):
+            if do_flush:
+                flush.zero_()  # outside the events
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(len(parts) + 1)]
+            e[0].record()
+            for i, f in enumerate(parts):
+                f()
+                e[i + 1].record()
+            ev.append(e)
+        torch.cuda.nvtx.range_pop()
+        barrier()
+        return [[e[i].elapsed_time(e[i + 1]) * 1e-3 for e in ev] for i in range(len(parts))]
 
     clocks = Clocks()
     clocks.start()
-    # ---- device-resident step: relocation + leaf update --------------------
-    for _ in range(args.warmup):
-        flush.zero_()
-        plan.relocate()
-        plan.update(op)
-    barrier()
+    # ---- device-resident step: relocation + leaf update in one launch -------
     launches0 = dc.kernel_launches()
-    ev = []
-    for _ in range(args.steps):
-        flush.zero_()  # L2 flush, outside the events; gives the host time to queue the step
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        e[0].record()
-        plan.relocate()
-        e[1].record()
-        plan.update(op)
-        e[2].record()
-        ev.append(e)
-    barrier()
-    launches = dc.kernel_launches() - launches0
+    (t_fused,) = timed_loop([lambda: plan.relocate_update(op)], "dc_step")
+    launches = dc.kernel_launches() - launches0 - args.warmup
     plan.sync()
-    t_reloc = [a.elapsed_time(b) * 1e-3 for a, b, c in ev]
-    t_leaf = [b.elapsed_time(c) * 1e-3 for a, b, c in ev]
-    value, t_step = aggregate(payload, args.steps, sum(x + y for x, y in zip(t_reloc, t_leaf)), world,
-                              dist if world > 1 else None)
-    step_median = max_over_ranks(statistics.median([x + y for x, y in zip(t_reloc, t_leaf)]))
+    value, t_step = aggregate(payload, args.steps, sum(t_fused), world, dist if world > 1 else None)
+    step_median = max_over_ranks(statistics.median(t_fused))
+    # the same step as two launches: each kernel on its own
+    t_reloc, t_leaf = timed_loop([plan.relocate, lambda: plan.update(op)], "dc_two_launch_step")
+    plan.sync()
 
     hbm, peak_kind = peaks()
-    leaf_bytes = 12 * nelem
     leaf_avg = statistics.mean(t_leaf)
     reloc_avg = statistics.mean(t_reloc)
     leaf_med = statistics.median(t_leaf)
     reloc_med = statistics.median(t_reloc)
-    reloc_bytes = info["nblocks"] * (16 + 8) + info["nstruct_blocks"] * 8
-    roofline = {"bound": "hbm", "kernel": "leaf_kernel<float, AXPY_HALF>",
-                "achieved": round(leaf_bytes / leaf_avg / 1e9, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(leaf_bytes / leaf_avg / 1e9 / hbm, 4), "traffic": None,
-                "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
-                "algorithmic_bytes_per_launch": leaf_bytes, "avg_launch_us": round(leaf_avg * 1e6, 2),
-                "median_launch_us": round(leaf_med * 1e6, 2),
-                "frac_at_median": round(leaf_bytes / leaf_med / 1e9 / hbm, 4)}
+    fused_avg = statistics.mean(t_fused)
+    fused_med = statistics.median(t_fused)
+    pk = peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind
+    roofline = {"bound": "hbm", "kernel": "fused_kernel<float, AXPY_HALF> (relocation tiles, then leaf tiles)",
+                "achieved": round(fused_bytes / fused_avg / 1e9, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(fused_bytes / fused_avg / 1e9 / hbm, 4),
+                "traffic": NCU_TRAFFIC.get((args.workload,) + tuple(tuned), (None,))[0], "peak_kind": pk,
+                "algorithmic_bytes_per_launch": fused_bytes, "avg_launch_us": round(fused_avg * 1e6, 2),
+                "median_launch_us": round(fused_med * 1e6, 2),
+                "frac_at_median": round(fused_bytes / fused_med / 1e9 / hbm, 4),
+                "split": {"threads_per_cta": tuned[0], "ctas_per_sm": tuned[1]},
+                "traffic_source": NCU_TRAFFIC.get((args.workload,) + tuple(tuned), (None, None))[1]}
+    leaf = {"kernel": "leaf_kernel<float, AXPY_HALF>", "algorithmic_bytes": leaf_bytes,
+            "avg_launch_us": round(leaf_avg * 1e6, 2), "median_launch_us": round(leaf_med * 1e6, 2),
+            "achieved_gbs": round(leaf_bytes / leaf_avg / 1e9, 1), "frac": round(leaf_bytes / leaf_avg / 1e9 / hbm, 4),
+            "frac_at_median": round(leaf_bytes / leaf_med / 1e9 / hbm, 4)}
 
     # ---- end to end through the C ABI with host buffers ----------------------
     def measure_e2e(pl):
@@ -701,7 +748,8 @@ def main():
         compare = {}
         t = []
         for i in range(5):
-            flush.zero_()
+            if do_flush:
+                flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             plan.update_chase(op)
@@ -743,13 +791,17 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "nodes": info["nstructs"], "blocks": info["nblocks"],
                        "payload_bytes": payload, "arena_bytes": info["data_bytes"], "elements": nelem,
-                       "step": "dc_relocate + dc_update_leaves on the resident arena",
-                       "l2": "flushed: 512 MiB write before every timed step (outside the events)",
+                       "step": "dc_relocate_update (relocation + leaf update, one persistent launch, split by "
+                               "dc_autotune) on the resident arena",
+                       "l2": l2_line,
                        "parallelism": f"{world} independent tree(s), one per GPU"},
             "roofline": roofline,
-            "relocation": {"avg_launch_us": round(reloc_avg * 1e6, 2), "median_launch_us": round(reloc_med * 1e6, 2),
+            "leaf": leaf,
+            "relocation": {"kernel": "relocate_kernel", "avg_launch_us": round(reloc_avg * 1e6, 2),
+                           "median_launch_us": round(reloc_med * 1e6, 2),
                            "algorithmic_bytes": reloc_bytes, "achieved_gbs": round(reloc_bytes / reloc_avg / 1e9, 1),
-                           "frac": round(reloc_bytes / reloc_avg / 1e9 / hbm, 4)},
+                           "frac": round(reloc_bytes / reloc_avg / 1e9 / hbm, 4), "record_bytes_moved": reloc_moved},
+            "two_launch_step_us": round((reloc_avg + leaf_avg) * 1e6, 2),
             "step_median_ms": round(step_median * 1e3, 4),
             "e2e": e2e, "e2e_three_calls_map_host": e2e_mapped, "e2e_staged": e2e_staged, "link": link, "compare": compare, "cpu_baseline": cpu,
             "clocks": clk,
