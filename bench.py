@@ -57,9 +57,7 @@ WORKLOADS = {
 
 # DRAM bytes (read + write) per launch of the step's kernel from one ncu capture, by (workload, split);
 # the summary beside each gives the command.  An entry stands only while the kernel is unchanged.
-NCU_TRAFFIC = {
-    ("dense", 512, 2): (460_697_728, "profiles/fused_kernel_dense.md"),
-}
+NCU_TRAFFIC = {}
 
 
 def l2_policy(torch, step_bytes):

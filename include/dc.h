@@ -330,8 +330,10 @@ dc_status dc_uvm_destroy(dc_uvm_t uvm);
  * at least data_bytes long; pointers become dev_data + block offset) with all
  * of its scratch in one fixed device array of DC_STATIC_SCRATCH_BYTES bytes
  * inside the library, which every GPU that loads the library keeps until the
- * process exits.  Limits: plans of at most DC_STATIC_MAX_BLOCKS blocks
- * (DC_EBUDGET otherwise); no DC_PLAN_VERIFY check.  It calls no cudaMalloc,
+ * process exits.  Limits: plans of at most DC_STATIC_MAX_BLOCKS blocks whose
+ * pointer slots lie in at most DC_STATIC_MAX_TILES of the 8 KiB ranges the
+ * struct blocks are relocated in (DC_EBUDGET otherwise); no DC_PLAN_VERIFY
+ * check.  It calls no cudaMalloc,
  * cudaHostAlloc, cudaFree or other allocating routine.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
@@ -340,9 +342,10 @@ dc_status dc_uvm_destroy(dc_uvm_t uvm);
  * zero), so calls whose work overlaps on the GPU race: order them on one
  * stream.  If `dev_status` is not NULL, the device word it points to receives
  * the kernel's error bits once the work completes (0 = success, 1 = an offset
- * outside the buffers, 2 = a device-side wait gave up). */
+ * outside the buffers). */
 #define DC_STATIC_MAX_BLOCKS 65536u
-#define DC_STATIC_SCRATCH_BYTES 1573888u /* 1 MiB block records + 512 KiB offsets + look-back/control words */
+#define DC_STATIC_MAX_TILES 16384u /* 8 KiB ranges of struct bytes that hold a pointer slot */
+#define DC_STATIC_SCRATCH_BYTES 1835776u /* 512 KiB records + 1 MiB lane groups + 256 KiB tile table + control words */
 dc_status dc_relocate_static(dc_plan_t plan, void* dev_data, uint64_t data_bytes, uint32_t* dev_status,
                              dc_stream_t stream);
 

@@ -32,15 +32,39 @@ const char* last_error();
 
 // ---- device-side records -----------------------------------------------------
 
-// One block of the arena, in arena order; 16 bytes so the relocation kernel
-// reads it with one vector load.
-struct BlockRec {
-  uint32_t size16;   // block bytes rounded up to 16, in units of 16 bytes
-  uint32_t parent;   // arena index of the struct block holding the pointer slot; NONE = root
-  uint32_t slot_off; // byte offset of that pointer slot inside the parent block
-  uint32_t lane;     // 0 = struct lane, else 1 + ARRAY-field lane index
+// The relocation's tables.  Every lane of the arena holds its blocks in the
+// order of the slots that point at them (lane 0: the roots, then child arrays
+// breadth first), so the blocks whose slots lie in one RELOC_SPAN-byte range
+// of the struct lane are, in every lane, a run of consecutive blocks.  A
+// relocation tile is such a range; its records are grouped by lane, each
+// group holding consecutive target blocks.
+//
+// One pointer slot: the target block's padded size in 16-byte units and the
+// slot's arena byte offset / 8 (slots are 8-byte aligned).
+struct RelocRec {
+  uint32_t size16;
+  uint32_t slot8;
 };
-static_assert(sizeof(BlockRec) == 16, "BlockRec is one 16-byte vector");
+static_assert(sizeof(RelocRec) == 8, "RelocRec is 8 bytes");
+// One (tile, lane) group: the arena offset / 16 of its first target block and
+// the index of its first record.  The table ends with a group whose
+// rec_begin is the record count.
+struct RelocSeg {
+  uint64_t base16;
+  uint32_t rec_begin, pad;
+};
+static_assert(sizeof(RelocSeg) == 16, "RelocSeg is 16 bytes");
+// One relocation tile with at least one slot: the tile (its struct bytes are
+// [t, t+1) * RELOC_SPAN), its first record and lane group, and the counts
+// (records in the low 16 bits, lane groups in the high 16 bits).  Only such
+// tiles are listed.
+struct RelocTile {
+  uint32_t t, r0, g0, counts;
+};
+static_assert(sizeof(RelocTile) == 16, "RelocTile is one 16-byte vector");
+constexpr uint32_t RELOC_SPAN = 8192;             // struct-lane bytes per relocation tile
+constexpr uint32_t RELOC_MAXREC = RELOC_SPAN / 8;  // at most one slot per 8 bytes
+constexpr uint32_t RELOC_MAXGROUPS = 64;           // lanes per plan (struct lane + array fields)
 
 // A resolved leaf segment for the streaming kernel: effective addresses of
 // x and y, the element count, and the exclusive prefix of 16-byte units
@@ -68,24 +92,26 @@ struct ChaseStep {
 static_assert(sizeof(ChaseStep) == 16, "ChaseStep is 16 bytes");
 
 // Control words in device scratch.
-enum CtrlWord : uint32_t { CTRL_ERR = 2, CTRL_WORDS = 16 };
+// CTRL_NEXT / CTRL_DONE: the fused launch's leaf-tile counter and finished-CTA
+// count; both are zero between launches (the last CTA of a launch resets them).
+enum CtrlWord : uint32_t { CTRL_ERR = 2, CTRL_NEXT = 4 /* words 4-5: 64-bit */, CTRL_DONE = 6, CTRL_WORDS = 16 };
 enum DeviceErr : uint32_t { ERR_BOUNDS = 1u, ERR_TIMEOUT = 2u, ERR_VERIFY = 4u };
 
 constexpr uint32_t RELOC_THREADS = 256;
-constexpr uint32_t RELOC_ITEMS = 4;  // blocks per thread
-constexpr uint32_t RELOC_TILE = RELOC_THREADS * RELOC_ITEMS;
 
 // ---- kernels (kernels.cu) ------------------------------------------------------
 
 struct RelocArgs {
   uint8_t* arena;
   uint64_t data_bytes;
-  const BlockRec* rec;
-  const uint64_t* hostp;       // host address of each block (checked with DC_PLAN_VERIFY)
-  const uint64_t* soff;        // byte offset of each struct block (the parents)
-  const uint64_t* tile_base;   // per tile of RELOC_TILE blocks: offset of its first block, 16-byte units
+  uint64_t struct_bytes;       // the struct lane is [0, struct_bytes) of the arena
+  const RelocRec* rec;         // nrec records, tile by tile
+  const RelocSeg* seg;         // nseg groups + the closing one
+  const RelocTile* tiles;      // ntiles entries: the tiles that hold a slot
+  const uint64_t* rec_host;    // DC_PLAN_VERIFY: host address of each record's target
+  const uint64_t* rec_off;     // DC_PLAN_VERIFY: arena offset of each record's target
   uint32_t* ctrl;
-  uint32_t nblocks, nstruct_blocks, ntiles, verify;
+  uint32_t nrec, nseg, ntiles, verify;
 };
 
 constexpr uint32_t LEAF_THREADS = 256;
@@ -192,7 +218,7 @@ dc_status copy_schema(const dc_schema* s, SchemaCopy* out);
 
 // Layout of the caller's device buffer (byte offsets).
 struct DevLayout {
-  uint64_t data = 0, rec = 0, hostp = 0, soff = 0, status = 0, ctrl = 0;
+  uint64_t data = 0, rec = 0, hostp = 0, soff = 0, status = 0, rtile = 0, ctrl = 0;
   uint64_t seg = 0, tseg = 0, cseg = 0, steps = 0, walk = 0, total = 0;
   uint64_t mva = 0, mvat = 0, mvb = 0, mvbt = 0, bk = 0, bkt = 0;  // move tables + their tile tables
   uint64_t sta = 0, stat = 0, stb = 0, stbt = 0, sts = 0, stst = 0;  // fused-step tables
@@ -212,10 +238,12 @@ struct dc_plan_s {
   dc::SchemaCopy schema;
   std::vector<dc::HostBlock> blocks;     // arena order
   std::vector<uint32_t> ptr_target;      // per struct element, per pointer field: block or NONE
-  std::vector<dc::BlockRec> rec;
-  std::vector<uint64_t> hostp;
-  std::vector<uint64_t> struct_off;      // arena offset of each struct block
-  std::vector<uint64_t> tile_base;       // per relocation tile: offset of its first block / 16
+  std::vector<dc::RelocRec> rrec;        // relocation records, tile by tile
+  std::vector<dc::RelocSeg> rseg;        // (tile, lane) groups + the closing one
+  std::vector<dc::RelocTile> rtiles;     // per relocation tile: its records and lane groups
+  std::vector<uint64_t> rec_host;        // per record: the target's host address (DC_PLAN_VERIFY)
+  std::vector<uint64_t> rec_off;         // per record: the target's arena offset (DC_PLAN_VERIFY)
+  uint64_t struct_bytes = 0;             // bytes of the struct lane (lane 0)
   std::vector<uint64_t> null_slots;      // arena offsets of slots with count 0 but a non-NULL host value
   std::vector<uint32_t> roots;           // arena index of each tree's root struct block
   uint64_t nstructs = 0, nstruct_blocks = 0, payload = 0, data_bytes = 0, sum_depth = 0;

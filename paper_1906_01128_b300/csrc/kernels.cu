@@ -1,11 +1,14 @@
 // kernels.cu — device side of the deep-copy hot path (sm_103a).
 //
-//   relocate_kernel  Fig 2 step d / Algorithm 1's attach loop: one pass that
-//                    computes every block's arena offset (an exclusive scan of
-//                    the 16-byte block sizes with warp shuffles, on top of the
-//                    tile's base offset) and rewrites the pointer slot that
-//                    refers to each block with the block's device address.
-//                    Block records are read as 16-byte vectors.
+//   relocate_kernel  Fig 2 step d / Algorithm 1's attach loop: one pass over
+//                    the struct lane in RELOC_SPAN-byte tiles.  A tile stages
+//                    its struct bytes in shared memory, computes the arena
+//                    offset of every block its slots point at (an exclusive
+//                    scan of the 16-byte block sizes with warp shuffles, on top
+//                    of each lane group's base offset), writes each block's
+//                    device address into its slot, and stores the tile back:
+//                    whole coalesced sectors instead of one 8-byte store per
+//                    pointer.
 //   leaf_kernel      the leaf update through resolved effective addresses
 //                    (Sec. 3): x += 0.5*y or x *= scale over (x, y, n)
 //                    segments, 16-byte vector loads/stores, no pointer loads.
@@ -31,92 +34,243 @@ namespace dc {
 
 namespace {
 
-__device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, uint32_t lane) {
+__device__ __forceinline__ uint32_t warp_incl_scan32(uint32_t v, uint32_t lane) {
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    uint64_t o = __shfl_up_sync(0xffffffffu, v, d);
+    const uint32_t o = __shfl_up_sync(0xffffffffu, v, d);
     if (lane >= (uint32_t)d) v += o;
   }
   return v;
 }
 
-// One tile of RELOC_TILE blocks, done by a CTA of THREADS threads.  Warp w
-// owns blocks [base + w*32*ITEMS, base + (w+1)*32*ITEMS); its lanes read 32
-// consecutive 16-byte records per instruction (coalesced).  The block sizes
-// are scanned with warp shuffles (slice by slice, carrying the running total),
-// then across the tile's warps, on top of the tile's base offset; every
-// block's parent slot is then rewritten.  Parents in an earlier tile take
-// their offset from the struct-offset table.  Ends with a barrier.
-template <uint32_t THREADS>
-__device__ __forceinline__ void reloc_tile(const RelocArgs& a, uint32_t t, uint64_t* s_off, uint64_t* s_warp) {
-  constexpr uint32_t NW = THREADS / 32;
-  constexpr uint32_t ITEMS = RELOC_TILE / THREADS;
-  constexpr uint32_t WSPAN = 32 * ITEMS;  // blocks per warp
-  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  uint32_t* err = &a.ctrl[CTRL_ERR];
-  const uint64_t base = (uint64_t)t * RELOC_TILE;
-  const uint64_t wbase = base + warp * WSPAN;
-  BlockRec r[ITEMS];
-#pragma unroll
-  for (uint32_t k = 0; k < ITEMS; k++) {
-    const uint64_t b = wbase + k * 32 + lane;
-    if (b < a.nblocks) {
-      const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.rec) + b);
-      r[k] = BlockRec{v.x, v.y, v.z, v.w};
-    } else {
-      r[k] = BlockRec{0, NONE, 0, 0};
-    }
+// ---- 1-D bulk copies (TMA) and mbarriers ------------------------------------
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// global -> shared, completing `bytes` of the barrier's transaction count
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+constexpr uint32_t WAIT_LIMIT = 1u << 22;  // try_wait rounds before a wait gives up (well over a second)
+
+// ---- relocation ----------------------------------------------------------------
+
+constexpr uint32_t RSTAGES = 2;
+
+// One pipeline stage: a tile's struct bytes, its records (from an even
+// index, so the copy starts on 16 bytes) and its lane groups.
+struct __align__(16) RelocStage {
+  uint4 img[RELOC_SPAN / 16];
+  uint2 rec[RELOC_MAXREC + 2];
+  RelocSeg grp[RELOC_MAXGROUPS + 1];
+};
+struct __align__(16) RelocSmem {
+  RelocStage st[RSTAGES];
+  uint64_t bar[RSTAGES];
+  uint4 hdr[RSTAGES];  // the staged tile: (t, r0, r1, ng); t = NONE ends the CTA's tiles
+  uint4 gb[RELOC_MAXGROUPS];  // per lane group: base offset / 16 (x, y) and minus its first record's size prefix (z)
+  uint32_t warp_sum[32];
+};
+
+// The producer (thread 0) fills stage s with listed tile i of the CTA (or
+// marks the CTA's tiles done, i = NONE), after checking the tile's header
+// against the tables; a header that fails is recorded and its stage skipped.
+__device__ __forceinline__ void issue_tile(const RelocArgs& a, RelocSmem& sm, uint32_t s, uint32_t i, uint4 h) {
+  RelocStage& S = sm.st[s];
+  if (i == NONE) {
+    sm.hdr[s] = make_uint4(NONE, 0, 0, 0);
+    mbar_arrive_tx(&sm.bar[s], 0);
+    return;
   }
-  // exclusive offsets inside the warp's span, slice by slice
-  uint64_t ex[ITEMS];
-  uint64_t carry = 0;
-#pragma unroll
-  for (uint32_t k = 0; k < ITEMS; k++) {
-    const uint64_t incl = warp_incl_scan(r[k].size16, lane);
-    ex[k] = carry + incl - r[k].size16;
-    carry += __shfl_sync(0xffffffffu, incl, 31);
+  const uint32_t t = h.x, r0 = h.y, g0 = h.z, nr = h.w & 0xFFFFu, ng = h.w >> 16;
+  const uint64_t lo = (uint64_t)t * RELOC_SPAN, hi = min(a.struct_bytes, lo + RELOC_SPAN);
+  if (nr == 0 || nr > RELOC_MAXREC || (uint64_t)r0 + nr > a.nrec || ng == 0 || ng > RELOC_MAXGROUPS ||
+      (uint64_t)g0 + ng > a.nseg || lo >= hi || (hi - lo) % 16 || hi > a.data_bytes) {
+    atomicOr(&a.ctrl[CTRL_ERR], ERR_BOUNDS);
+    sm.hdr[s] = make_uint4(t, r0, r0, 0);  // nothing to do in this stage
+    mbar_arrive_tx(&sm.bar[s], 0);
+    return;
   }
-  if (lane == 0) s_warp[warp] = carry;
-  __syncthreads();
-  uint64_t wpre = 0;  // every warp adds up the totals of the warps before it
-#pragma unroll
-  for (uint32_t w = 0; w < NW; w++) wpre += w < warp ? s_warp[w] : 0;
-  const uint64_t o16 = __ldg(&a.tile_base[t]) + wpre;
-#pragma unroll
-  for (uint32_t k = 0; k < ITEMS; k++) {
-    const uint64_t b = wbase + k * 32 + lane;
-    ex[k] = (o16 + ex[k]) * 16;  // byte offset of block b
-    s_off[b - base] = ex[k];
-    if (a.verify && b < a.nstruct_blocks && __ldg(&a.soff[b]) != ex[k]) atomicOr(err, ERR_VERIFY);
-  }
-  __syncthreads();
-  // rewrite the slot that points at each block (roots have none)
-#pragma unroll
-  for (uint32_t k = 0; k < ITEMS; k++) {
-    const uint64_t b = wbase + k * 32 + lane;
-    const uint32_t p = r[k].parent;
-    if (b >= a.nblocks || p == NONE) continue;
-    if (p >= b || p >= a.nstruct_blocks) {
-      atomicOr(err, ERR_BOUNDS);
-      continue;
-    }
-    const uint64_t poff = p >= base ? s_off[p - base] : __ldg(&a.soff[p]);
-    const uint64_t slot = poff + r[k].slot_off;
-    if (slot + 8 > a.data_bytes || (slot & 7)) {
-      atomicOr(err, ERR_BOUNDS);
-      continue;
-    }
-    uint64_t* sp = reinterpret_cast<uint64_t*>(a.arena + slot);
-    if (a.verify && *sp != a.hostp[b]) atomicOr(err, ERR_VERIFY);
-    *sp = reinterpret_cast<uint64_t>(a.arena) + ex[k];
-  }
-  __syncthreads();  // s_off and s_warp are reused by the next tile
+  const uint32_t ra = r0 & ~1u, rb = (r0 + nr + 1) & ~1u;  // even bounds: 16-byte aligned (the table has 2 spare)
+  const uint32_t b_img = (uint32_t)(hi - lo), b_rec = (rb - ra) * 8, b_grp = (ng + 1) * 16;
+  sm.hdr[s] = make_uint4(t, r0, r0 + nr, ng);
+  mbar_arrive_tx(&sm.bar[s], b_img + b_rec + b_grp);
+  bulk_load(S.img, a.arena + lo, b_img, &sm.bar[s]);
+  bulk_load(S.rec, a.rec + ra, b_rec, &sm.bar[s]);
+  bulk_load(S.grp, a.seg + g0, b_grp, &sm.bar[s]);
 }
 
+// Every listed relocation tile i = blockIdx.x + k * gridDim.x, through a
+// two-stage pipeline: while the CTA rewrites the slots of one staged tile,
+// the bulk copies of the next are in flight, and the producer has the header
+// after that in a register.  The sizes are scanned with warp shuffles, slice
+// by slice, then across the warps.  Sizes and prefixes are 32-bit: the plan splits lane groups so that the blocks of one
+// group total less than 2^32 units, and a block's offset is its group's base
+// plus a difference of two prefixes, exact modulo 2^32.  The staged tile is
+// written back by one bulk store.  The loop's exits are uniform across the
+// CTA; every wait has an iteration limit.
+template <uint32_t THREADS, bool VERIFY>
+__device__ __forceinline__ void reloc_tiles(const RelocArgs& a, RelocSmem& sm) {
+  constexpr uint32_t NW = THREADS / 32;
+  constexpr uint32_t ITEMS = RELOC_MAXREC / THREADS;
+  static_assert(ITEMS * THREADS == RELOC_MAXREC, "tile shape");
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t* err = &a.ctrl[CTRL_ERR];
+  if (blockIdx.x >= a.ntiles) return;
+  const uint4* hdrs = reinterpret_cast<const uint4*>(a.tiles);
+  uint32_t in = NONE;  // the producer's next listed tile and its header
+  uint4 hn = make_uint4(0, 0, 0, 0);
+  if (tid == 0) {
+    for (uint32_t s = 0; s < RSTAGES; s++) mbar_init(&sm.bar[s]);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t i = blockIdx.x;
+    for (uint32_t s = 0; s < RSTAGES; s++, i += gridDim.x) {
+      const bool have = i < a.ntiles;
+      issue_tile(a, sm, s, have ? i : NONE, have ? __ldg(hdrs + i) : hn);
+    }
+    in = i < a.ntiles ? i : NONE;
+    if (in != NONE) hn = __ldg(hdrs + in);
+  }
+  const uint64_t base = reinterpret_cast<uint64_t>(a.arena);
+  for (uint32_t k = 0;; k++) {
+    const uint32_t s = k % RSTAGES, parity = (k / RSTAGES) & 1;
+    uint32_t spins = 0;
+    bool late = false;
+    while (!mbar_try_wait(&sm.bar[s], parity))
+      if (++spins >= WAIT_LIMIT) {
+        late = true;
+        break;
+      }
+    if (__syncthreads_or(late)) {
+      if (tid == 0) {  // give the copies in flight another bounded wait before leaving
+        atomicOr(err, ERR_TIMEOUT);
+        for (uint32_t q = 0; q < RSTAGES; q++) {
+          const uint32_t kq = k + q;
+          for (uint32_t n = 0; n < WAIT_LIMIT && !mbar_try_wait(&sm.bar[kq % RSTAGES], (kq / RSTAGES) & 1); n++) {
+          }
+        }
+      }
+      break;
+    }
+    const uint4 h = sm.hdr[s];
+    if (h.x == NONE) break;  // uniform: every thread reads the same header
+    RelocStage& S = sm.st[s];
+    const uint32_t t = h.x, r0 = h.y, nr = h.z - h.y, ng = h.w, sh = r0 & 1u;
+    const uint64_t lo = (uint64_t)t * RELOC_SPAN, hi = min(a.struct_bytes, lo + RELOC_SPAN);
+    if (nr) {  // uniform
+      // records warp-striped: warp w owns [w*32*ITEMS, (w+1)*32*ITEMS), its lane L the records k*32 + L
+      // (conflict-free shared loads; slot writes of consecutive records land 8 bytes x stride apart)
+      const uint32_t wb = warp * 32 * ITEMS;
+      uint2 r[ITEMS];
+#pragma unroll
+      for (uint32_t i = 0; i < ITEMS; i++) {
+        const uint32_t j = wb + i * 32 + lane;
+        r[i] = j < nr ? S.rec[sh + j] : make_uint2(0, 0);
+      }
+      // exclusive prefix of the sizes inside the warp's span, slice by slice, then across warps
+      uint32_t ex[ITEMS];
+      uint32_t carry = 0;
+#pragma unroll
+      for (uint32_t i = 0; i < ITEMS; i++) {
+        const uint32_t incl = warp_incl_scan32(r[i].x, lane);
+        ex[i] = carry + incl - r[i].x;
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+      }
+      if (lane == 0) sm.warp_sum[warp] = carry;
+      __syncthreads();
+      uint32_t wt = lane < NW ? sm.warp_sum[lane] : 0u;
+      wt = warp_incl_scan32(wt, lane);
+      const uint32_t wpre = warp ? __shfl_sync(0xffffffffu, wt, (warp - 1) & 31) : 0u;
+      // each record's lane group (ascending with the record index) and every group's start prefix
+      uint32_t grp[ITEMS];
+      uint32_t g = 0;
+#pragma unroll
+      for (uint32_t i = 0; i < ITEMS; i++) {
+        ex[i] += wpre;
+        const uint32_t j = wb + i * 32 + lane;
+        while (g + 1 < ng && S.grp[g + 1].rec_begin - r0 <= j) g++;
+        grp[i] = g;
+        if (j < nr && S.grp[g].rec_begin - r0 == j) {
+          const uint64_t b16 = S.grp[g].base16;
+          sm.gb[g] = make_uint4((uint32_t)b16, (uint32_t)(b16 >> 32), 0u - ex[i], 0u);
+        }
+      }
+      __syncthreads();  // every group's base and start prefix are in shared memory
+      uint64_t* img64 = reinterpret_cast<uint64_t*>(S.img);
+      const uint32_t lo8 = (uint32_t)(lo / 8), n8 = (uint32_t)((hi - lo) / 8);
+#pragma unroll
+      for (uint32_t i = 0; i < ITEMS; i++) {
+        const uint32_t j = wb + i * 32 + lane;
+        if (j >= nr) continue;
+        // base + (prefix - prefix at the group start), the difference taken modulo 2^32
+        const uint4 G = sm.gb[grp[i]];
+        const uint64_t off = ((((uint64_t)G.y << 32) | G.x) + (uint32_t)(ex[i] + G.z)) * 16;
+        const uint32_t rel = r[i].y - lo8;  // the slot, in 8-byte words from the tile start
+        if (rel >= n8) {
+          atomicOr(err, ERR_BOUNDS);
+          continue;
+        }
+        uint64_t* sp = img64 + rel;
+        if (VERIFY) {
+          const uint32_t ri = r0 + j;
+          if (*sp != __ldg(&a.rec_host[ri]) || off != __ldg(&a.rec_off[ri])) atomicOr(err, ERR_VERIFY);
+        }
+        *sp = base + off;
+      }
+      fence_async_smem();  // the slot writes are seen by the bulk store
+    }
+    __syncthreads();  // nobody reads stage s any more
+    if (tid == 0) {
+      if (nr) {
+        bulk_store(a.arena + lo, S.img, (uint32_t)(hi - lo));
+        bulk_wait_read();  // the store has read stage s: refill it
+      }
+      issue_tile(a, sm, s, in, hn);
+      if (in != NONE) {
+        in += gridDim.x;
+        in = in < a.ntiles ? in : NONE;
+        if (in != NONE) hn = __ldg(hdrs + in);  // used at the next refill
+      }
+    }
+  }
+  if (tid == 0) bulk_wait_all();
+  __syncthreads();  // shared memory may be reused
+}
+
+template <bool VERIFY>
 __global__ void __launch_bounds__(RELOC_THREADS) relocate_kernel(RelocArgs a) {
-  __shared__ uint64_t s_off[RELOC_TILE];
-  __shared__ uint64_t s_warp[RELOC_THREADS / 32];
-  for (uint32_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) reloc_tile<RELOC_THREADS>(a, t, s_off, s_warp);
+  __shared__ RelocSmem sm;
+  reloc_tiles<RELOC_THREADS, VERIFY>(a, sm);
 }
 
 // ---- leaf update over resolved segments -------------------------------------
@@ -228,15 +382,31 @@ __global__ void __launch_bounds__(LEAF_THREADS) leaf_kernel(LeafArgs a) {
 // the host, the relocation writes only pointer slots), so one launch over a
 // forest replaces two per structure.
 template <typename T, int KIND, uint32_t THREADS>
+// CTAs take leaf tiles from a counter, so the ones that relocated take fewer.
+// The last CTA to finish resets the counter for the next launch (launches on
+// one stream never overlap).
 __global__ void __launch_bounds__(THREADS) fused_kernel(RelocArgs r, LeafArgs l, uint64_t leaf_tiles) {
-  __shared__ uint64_t s_off[RELOC_TILE];
-  __shared__ uint64_t s_warp[THREADS / 32];
-  const uint64_t total = (uint64_t)r.ntiles + leaf_tiles;
-  for (uint64_t w = blockIdx.x; w < total; w += gridDim.x) {
-    if (w < r.ntiles)
-      reloc_tile<THREADS>(r, (uint32_t)w, s_off, s_warp);
-    else
-      leaf_tile<T, KIND, THREADS>(l, w - r.ntiles);
+  __shared__ RelocSmem sm;
+  __shared__ unsigned long long s_w;
+  if (r.verify)
+    reloc_tiles<THREADS, true>(r, sm);
+  else
+    reloc_tiles<THREADS, false>(r, sm);
+  unsigned long long* next = reinterpret_cast<unsigned long long*>(&r.ctrl[CTRL_NEXT]);
+  for (;;) {
+    if (threadIdx.x == 0) s_w = atomicAdd(next, 1ull);
+    __syncthreads();
+    const uint64_t w = s_w;
+    __syncthreads();
+    if (w >= leaf_tiles) break;
+    leaf_tile<T, KIND, THREADS>(l, w);
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&r.ctrl[CTRL_DONE], 1u) == gridDim.x - 1) {
+      atomicExch(next, 0ull);
+      atomicExch(&r.ctrl[CTRL_DONE], 0u);
+    }
   }
 }
 
@@ -430,10 +600,13 @@ int occupancy(K kernel, int threads, size_t smem) {
 }  // namespace
 
 cudaError_t launch_relocate(const RelocArgs& a, cudaStream_t s, int sm_count) {
-  (void)sm_count;
-  uint32_t grid = a.ntiles;  // one tile per CTA; the block scheduler overlaps their phases
-  if (grid == 0) grid = 1;
-  relocate_kernel<<<grid, RELOC_THREADS, 0, s>>>(a);
+  if (a.ntiles == 0) return cudaSuccess;
+  static int occ = occupancy(relocate_kernel<false>, RELOC_THREADS, 0);
+  const uint32_t grid = (uint32_t)std::min<uint64_t>(a.ntiles, (uint64_t)sm_count * occ);  // persistent CTAs
+  if (a.verify)
+    relocate_kernel<true><<<grid, RELOC_THREADS, 0, s>>>(a);
+  else
+    relocate_kernel<false><<<grid, RELOC_THREADS, 0, s>>>(a);
   count_launch();
   return cudaGetLastError();
 }

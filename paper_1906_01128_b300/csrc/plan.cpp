@@ -300,16 +300,37 @@ dc_status build_plan(const dc_schema* schema, const void* const* roots, uint64_t
     }
   }
 
-  // lanes: stable counting sort of the emission order
+  // Lanes in slot order: lane 0 holds the roots, then the child arrays breadth
+  // first (each struct block's children by slot offset); every array lane holds
+  // its blocks in the order of their parents, then of their slot offsets.  So
+  // within every lane the slots that point at consecutive blocks ascend.
   const uint32_t nl = p->schema.nlanes;
-  std::vector<uint64_t> lane_start(nl + 1, 0);
-  for (auto& b : E) lane_start[b.lane + 1]++;
-  for (uint32_t l = 0; l < nl; l++) lane_start[l + 1] += lane_start[l];
-  std::vector<uint32_t> new_id(nb);
+  if (nl > RELOC_MAXGROUPS)
+    return fail(DC_EINVAL, "the schema has %u ARRAY fields; at most %u are supported", nl - 1, RELOC_MAXGROUPS - 1);
+  std::vector<uint32_t> kbeg(nb + 1, 0), kid(nb);
+  for (uint64_t i = 0; i < nb; i++)
+    if (E[i].parent != NONE) kbeg[E[i].parent + 1]++;
+  for (uint64_t i = 0; i < nb; i++) kbeg[i + 1] += kbeg[i];
   {
-    std::vector<uint64_t> cur(lane_start.begin(), lane_start.end() - 1);
-    for (uint64_t i = 0; i < nb; i++) new_id[i] = (uint32_t)cur[E[i].lane]++;
+    std::vector<uint32_t> fill(kbeg.begin(), kbeg.end() - 1);
+    for (uint64_t i = 0; i < nb; i++)
+      if (E[i].parent != NONE) kid[fill[E[i].parent]++] = (uint32_t)i;
   }
+  for (uint64_t i = 0; i < nb; i++)
+    std::sort(kid.begin() + kbeg[i], kid.begin() + kbeg[i + 1],
+              [&](uint32_t a, uint32_t b) { return E[a].slot_off < E[b].slot_off; });
+  std::vector<std::vector<uint32_t>> lanes(nl);
+  for (uint32_t r : root_ids) lanes[0].push_back(r);
+  for (size_t q = 0; q < lanes[0].size(); q++)
+    for (uint32_t k = kbeg[lanes[0][q]]; k < kbeg[lanes[0][q] + 1]; k++) lanes[E[kid[k]].lane].push_back(kid[k]);
+  std::vector<uint64_t> lane_start(nl + 1, 0);
+  for (uint32_t l = 0; l < nl; l++) lane_start[l + 1] = lane_start[l] + lanes[l].size();
+  if (lane_start[nl] != nb) return fail(DC_EINVAL, "internal: %llu of %llu blocks reached in the lane order",
+                                        (unsigned long long)lane_start[nl], (unsigned long long)nb);
+  std::vector<uint32_t> new_id(nb);
+  for (uint32_t l = 0; l < nl; l++)
+    for (size_t j = 0; j < lanes[l].size(); j++) new_id[lanes[l][j]] = (uint32_t)(lane_start[l] + j);
+  lanes.clear();
   p->blocks.resize(nb);
   for (uint64_t i = 0; i < nb; i++) {
     HostBlock b = E[i];
@@ -321,20 +342,66 @@ dc_status build_plan(const dc_schema* schema, const void* const* roots, uint64_t
   p->roots.clear();
   for (uint32_t r : root_ids) p->roots.push_back(new_id[r]);
   uint64_t off = 0;
-  p->rec.resize(nb);
-  p->hostp.resize(nb);
   for (uint64_t i = 0; i < nb; i++) {
     HostBlock& b = p->blocks[i];
     b.off = off;
     off += round_up(b.bytes, 16);
-    p->rec[i] = BlockRec{(uint32_t)(round_up(b.bytes, 16) / 16), b.parent, b.slot_off, b.lane};
-    p->hostp[i] = (uint64_t)(uintptr_t)b.host;
   }
   p->data_bytes = off;
-  p->struct_off.resize(p->nstruct_blocks);
-  for (uint64_t i = 0; i < p->nstruct_blocks; i++) p->struct_off[i] = p->blocks[i].off;
-  p->tile_base.clear();
-  for (uint64_t i = 0; i < nb; i += RELOC_TILE) p->tile_base.push_back(p->blocks[i].off / 16);
+  p->struct_bytes = p->nstruct_blocks ? p->blocks[p->nstruct_blocks - 1].off +
+                                            round_up(p->blocks[p->nstruct_blocks - 1].bytes, 16)
+                                      : 0;
+  if (p->struct_bytes / 8 > 0xFFFFFFFFull) return fail(DC_EINVAL, "struct lane larger than 32 GiB");
+
+  // Relocation tables: tile t covers the struct-lane bytes [t, t+1) * RELOC_SPAN;
+  // its records are, lane by lane, the consecutive blocks whose slots lie there.
+  const uint64_t ntiles = (p->struct_bytes + RELOC_SPAN - 1) / RELOC_SPAN;
+  const uint64_t nr = p->roots.size();
+  std::vector<uint64_t> cur(lane_start.begin(), lane_start.end() - 1), last(nl, 0);
+  cur[0] += nr;  // the roots are pointed at by no slot
+  auto slot = [&](uint64_t b) { return p->blocks[p->blocks[b].parent].off + p->blocks[b].slot_off; };
+  p->rrec.clear();
+  p->rseg.clear();
+  p->rtiles.clear();
+  p->rec_host.clear();
+  p->rec_off.clear();
+  p->rrec.reserve(nb - nr);
+  p->rec_host.reserve(nb - nr);
+  p->rec_off.reserve(nb - nr);
+  for (uint64_t t = 0; t < ntiles; t++) {
+    const uint32_t tr0 = (uint32_t)p->rrec.size(), tg0 = (uint32_t)p->rseg.size();
+    const uint64_t hi = (t + 1) * RELOC_SPAN;
+    for (uint32_t l = 0; l < nl; l++) {
+      // a group's records must see size prefixes below 2^32 units (the kernel's
+      // prefixes are 32-bit): a longer run starts a new group
+      uint64_t run = ~0ull;
+      for (; cur[l] < lane_start[l + 1] && slot(cur[l]) < hi; cur[l]++) {
+        const HostBlock& b = p->blocks[cur[l]];
+        const uint64_t sl = slot(cur[l]);
+        if (b.parent == NONE || sl < last[l] || sl % 8)
+          return fail(DC_EINVAL, "internal: lane %u is not in slot order at block %llu", l,
+                      (unsigned long long)cur[l]);
+        last[l] = sl + 8;
+        const uint64_t size16 = round_up(b.bytes, 16) / 16;
+        if (run > 0xFFFFFFFFull) {
+          p->rseg.push_back(RelocSeg{b.off / 16, (uint32_t)p->rrec.size(), 0});
+          run = 0;
+        }
+        run += size16;
+        p->rrec.push_back(RelocRec{(uint32_t)size16, (uint32_t)(sl / 8)});
+        p->rec_host.push_back((uint64_t)(uintptr_t)b.host);
+        p->rec_off.push_back(b.off);
+      }
+    }
+    if (p->rseg.size() - tg0 > RELOC_MAXGROUPS)
+      return fail(DC_EINVAL, "relocation tile %llu needs more than %u lane groups", (unsigned long long)t,
+                  RELOC_MAXGROUPS);
+    const uint32_t nrt = (uint32_t)p->rrec.size() - tr0, ngt = (uint32_t)p->rseg.size() - tg0;
+    if (nrt) p->rtiles.push_back(RelocTile{(uint32_t)t, tr0, tg0, nrt | ngt << 16});
+  }
+  p->rseg.push_back(RelocSeg{0, (uint32_t)p->rrec.size(), 0});
+  for (uint32_t l = 0; l < nl; l++)
+    if (cur[l] != lane_start[l + 1]) return fail(DC_EINVAL, "internal: lane %u has slots outside the struct lane", l);
   p->null_slots.clear();
   for (auto& ns : w.null_slots) p->null_slots.push_back(p->blocks[new_id[ns.first]].off + ns.second);
   std::sort(p->null_slots.begin(), p->null_slots.end());

@@ -26,15 +26,18 @@ DevLayout make_layout(const dc_plan_s* p) {
   DevLayout L;
   const uint64_t nb = p->blocks.size();
   uint64_t o = align256(p->data_bytes);
-  L.rec = o;
-  o = align256(o + nb * sizeof(BlockRec));
-  L.hostp = o;
-  o = align256(o + nb * 8);
-  L.soff = o;
-  o = align256(o + std::max<uint64_t>(1, p->nstruct_blocks) * 8);
-  L.ntiles = (nb + RELOC_TILE - 1) / RELOC_TILE;
-  L.status = o;  // tile base offsets
-  o = align256(o + L.ntiles * 8);
+  const uint64_t nrec = std::max<uint64_t>(1, p->rrec.size());
+  L.rec = o;  // relocation records, and two spare ones (copies of a tile's records start and end on 16 bytes)
+  o = align256(o + (nrec + 2) * sizeof(RelocRec));
+  L.hostp = o;  // per record: the target's host address
+  o = align256(o + nrec * 8);
+  L.soff = o;  // per record: the target's arena offset
+  o = align256(o + nrec * 8);
+  L.ntiles = p->rtiles.size();
+  L.status = o;  // (tile, lane) groups
+  o = align256(o + p->rseg.size() * sizeof(RelocSeg));
+  L.rtile = o;  // per tile: its records and groups
+  o = align256(o + std::max<uint64_t>(1, p->rtiles.size()) * sizeof(RelocTile));
   L.ctrl = o;
   o = align256(o + CTRL_WORDS * 4);
   L.seg_cap = std::max<uint64_t>(1, p->nstructs);
@@ -357,13 +360,18 @@ dc_status dc_bind_device(dc_plan_t p, void* dev, uint64_t bytes, dc_stream_t str
   if (!p->tab_done) DC_CUDA(cudaEventCreateWithFlags(&p->tab_done, cudaEventDisableTiming));
   p->dev = (uint8_t*)dev;
   p->dev_bytes = bytes;
-  const uint64_t nb = p->blocks.size();
-  DC_CUDA(cudaMemcpyAsync(p->dev + p->L.rec, p->rec.data(), nb * sizeof(BlockRec), cudaMemcpyHostToDevice, s));
-  DC_CUDA(cudaMemcpyAsync(p->dev + p->L.hostp, p->hostp.data(), nb * 8, cudaMemcpyHostToDevice, s));
+  const uint64_t nrec = p->rrec.size();
+  if (nrec) {
+    DC_CUDA(cudaMemcpyAsync(p->dev + p->L.rec, p->rrec.data(), nrec * sizeof(RelocRec), cudaMemcpyHostToDevice, s));
+    DC_CUDA(cudaMemcpyAsync(p->dev + p->L.hostp, p->rec_host.data(), nrec * 8, cudaMemcpyHostToDevice, s));
+    DC_CUDA(cudaMemcpyAsync(p->dev + p->L.soff, p->rec_off.data(), nrec * 8, cudaMemcpyHostToDevice, s));
+  }
   DC_CUDA(cudaMemsetAsync(p->dev + p->L.ctrl, 0, CTRL_WORDS * 4, s));
-  DC_CUDA(cudaMemcpyAsync(p->dev + p->L.soff, p->struct_off.data(), p->struct_off.size() * 8, cudaMemcpyHostToDevice, s));
-  DC_CUDA(cudaMemcpyAsync(p->dev + p->L.status, p->tile_base.data(), p->tile_base.size() * 8, cudaMemcpyHostToDevice,
-                          s));
+  DC_CUDA(cudaMemcpyAsync(p->dev + p->L.status, p->rseg.data(), p->rseg.size() * sizeof(RelocSeg),
+                          cudaMemcpyHostToDevice, s));
+  if (!p->rtiles.empty())
+    DC_CUDA(cudaMemcpyAsync(p->dev + p->L.rtile, p->rtiles.data(), p->rtiles.size() * sizeof(RelocTile),
+                            cudaMemcpyHostToDevice, s));
   {
     dc_status st = upload_h2d_tables(p, s);
     if (st) return st;
@@ -531,13 +539,15 @@ RelocArgs dc::reloc_args(const dc_plan_s* p) {
   RelocArgs a;
   a.arena = p->dev;
   a.data_bytes = p->data_bytes;
-  a.rec = reinterpret_cast<const BlockRec*>(p->dev + p->L.rec);
-  a.hostp = reinterpret_cast<const uint64_t*>(p->dev + p->L.hostp);
-  a.soff = reinterpret_cast<const uint64_t*>(p->dev + p->L.soff);
-  a.tile_base = reinterpret_cast<const uint64_t*>(p->dev + p->L.status);
+  a.struct_bytes = p->struct_bytes;
+  a.rec = reinterpret_cast<const RelocRec*>(p->dev + p->L.rec);
+  a.seg = reinterpret_cast<const RelocSeg*>(p->dev + p->L.status);
+  a.tiles = reinterpret_cast<const RelocTile*>(p->dev + p->L.rtile);
+  a.rec_host = reinterpret_cast<const uint64_t*>(p->dev + p->L.hostp);
+  a.rec_off = reinterpret_cast<const uint64_t*>(p->dev + p->L.soff);
   a.ctrl = reinterpret_cast<uint32_t*>(p->dev + p->L.ctrl);
-  a.nblocks = (uint32_t)p->blocks.size();
-  a.nstruct_blocks = (uint32_t)p->nstruct_blocks;
+  a.nrec = (uint32_t)p->rrec.size();
+  a.nseg = (uint32_t)(p->rseg.size() - 1);
   a.ntiles = (uint32_t)p->L.ntiles;
   a.verify = (p->flags & DC_PLAN_VERIFY) ? 1u : 0u;
   return a;

@@ -1,7 +1,7 @@
 // static_scratch.cu — dc_relocate_static: the relocation kernel run with its
-// scratch (block records, struct-block offsets, tile offsets, control words)
-// taken from one fixed array in device memory instead of from a buffer the
-// caller sized and allocated.  Nothing here allocates: no cudaMalloc,
+// scratch (relocation records, lane groups, tile table, control words) taken
+// from one fixed array in device memory instead of from a buffer the caller
+// sized and allocated.  Nothing here allocates: no cudaMalloc,
 // cudaHostAlloc or cudaFree, and no allocating library call.
 #include <cuda_runtime.h>
 
@@ -13,16 +13,15 @@ using namespace dc;
 
 namespace {
 
-constexpr uint64_t MAX_BLOCKS = DC_STATIC_MAX_BLOCKS;
-constexpr uint64_t MAX_TILES = 64;  // tile words reserved; enough for any tile of >= 1024 blocks
-static_assert(MAX_BLOCKS <= MAX_TILES * RELOC_TILE, "tile words cover every tile");
+constexpr uint64_t MAX_BLOCKS = DC_STATIC_MAX_BLOCKS;  // records: at most one per block
+constexpr uint64_t MAX_SEGS = DC_STATIC_MAX_BLOCKS;    // a lane group holds at least one record
+constexpr uint64_t MAX_TILES = DC_STATIC_MAX_TILES;    // relocation tiles that hold a pointer slot
 constexpr uint64_t al256(uint64_t x) { return (x + 255) / 256 * 256; }
 // byte layout of the array
-constexpr uint64_t OFF_REC = 0;                                   // 16 B per block
-constexpr uint64_t OFF_SOFF = al256(OFF_REC + 16 * MAX_BLOCKS);   // 8 B per struct block
-constexpr uint64_t OFF_STATUS = al256(OFF_SOFF + 8 * MAX_BLOCKS); // 8 B per tile: tile base offsets
-constexpr uint64_t OFF_READY = al256(OFF_STATUS + 8 * MAX_TILES); // 4 B per tile (unused)
-constexpr uint64_t OFF_CTRL = al256(OFF_READY + 4 * MAX_TILES);   // control words
+constexpr uint64_t OFF_REC = 0;                                              // 8 B per record
+constexpr uint64_t OFF_SEG = al256(OFF_REC + sizeof(RelocRec) * (MAX_BLOCKS + 2));  // 16 B per group + 1
+constexpr uint64_t OFF_TILE = al256(OFF_SEG + sizeof(RelocSeg) * (MAX_SEGS + 1));  // 16 B per tile
+constexpr uint64_t OFF_CTRL = al256(OFF_TILE + sizeof(RelocTile) * MAX_TILES);      // control words
 constexpr uint64_t SCRATCH_BYTES = al256(OFF_CTRL + 4 * CTRL_WORDS);
 static_assert(SCRATCH_BYTES == DC_STATIC_SCRATCH_BYTES, "dc.h states the array's size");
 
@@ -66,6 +65,12 @@ extern "C" dc_status dc_relocate_static(dc_plan_t p, void* dev_data, uint64_t da
   if (nb > MAX_BLOCKS)
     return fail(DC_EBUDGET, "the plan has %llu blocks; dc_relocate_static handles at most %llu (use dc_relocate)",
                 (unsigned long long)nb, (unsigned long long)MAX_BLOCKS);
+  const uint64_t ntiles = p->rtiles.size(), nseg = p->rseg.size() - 1, nrec = p->rrec.size();
+  if (ntiles > MAX_TILES)
+    return fail(DC_EBUDGET, "the plan has pointer slots in %llu relocation tiles of %u bytes; dc_relocate_static "
+                "handles at most %llu (use dc_relocate)", (unsigned long long)ntiles, RELOC_SPAN,
+                (unsigned long long)MAX_TILES);
+  if (nseg > MAX_SEGS || nrec > MAX_BLOCKS) return fail(DC_EINVAL, "internal: relocation tables exceed the array");
   int dev = 0;
   DC_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= MAX_DEVICES) return fail(DC_EINVAL, "device ordinal %d out of range", dev);
@@ -77,20 +82,23 @@ extern "C" dc_status dc_relocate_static(dc_plan_t p, void* dev_data, uint64_t da
   // the array keeps the previous call's contents: the error word must start
   // at zero, and this plan's tables replace the last call's
   DC_CUDA(cudaMemsetAsync(s + OFF_CTRL, 0, SCRATCH_BYTES - OFF_CTRL, cs));
-  DC_CUDA(cudaMemcpyAsync(s + OFF_REC, p->rec.data(), nb * sizeof(BlockRec), cudaMemcpyHostToDevice, cs));
-  DC_CUDA(cudaMemcpyAsync(s + OFF_SOFF, p->struct_off.data(), p->struct_off.size() * 8, cudaMemcpyHostToDevice, cs));
-  DC_CUDA(cudaMemcpyAsync(s + OFF_STATUS, p->tile_base.data(), p->tile_base.size() * 8, cudaMemcpyHostToDevice, cs));
+  if (nrec) DC_CUDA(cudaMemcpyAsync(s + OFF_REC, p->rrec.data(), nrec * sizeof(RelocRec), cudaMemcpyHostToDevice, cs));
+  DC_CUDA(cudaMemcpyAsync(s + OFF_SEG, p->rseg.data(), p->rseg.size() * sizeof(RelocSeg), cudaMemcpyHostToDevice, cs));
+  if (ntiles)
+    DC_CUDA(cudaMemcpyAsync(s + OFF_TILE, p->rtiles.data(), ntiles * sizeof(RelocTile), cudaMemcpyHostToDevice, cs));
   RelocArgs a;
   a.arena = static_cast<uint8_t*>(dev_data);
   a.data_bytes = p->data_bytes;
-  a.rec = reinterpret_cast<const BlockRec*>(s + OFF_REC);
-  a.hostp = nullptr;  // no slot check in this variant
-  a.soff = reinterpret_cast<const uint64_t*>(s + OFF_SOFF);
-  a.tile_base = reinterpret_cast<const uint64_t*>(s + OFF_STATUS);
+  a.struct_bytes = p->struct_bytes;
+  a.rec = reinterpret_cast<const RelocRec*>(s + OFF_REC);
+  a.seg = reinterpret_cast<const RelocSeg*>(s + OFF_SEG);
+  a.tiles = reinterpret_cast<const RelocTile*>(s + OFF_TILE);
+  a.rec_host = nullptr;  // no slot check in this variant
+  a.rec_off = nullptr;
   a.ctrl = reinterpret_cast<uint32_t*>(s + OFF_CTRL);
-  a.nblocks = (uint32_t)nb;
-  a.nstruct_blocks = (uint32_t)p->nstruct_blocks;
-  a.ntiles = (uint32_t)((nb + RELOC_TILE - 1) / RELOC_TILE);
+  a.nrec = (uint32_t)nrec;
+  a.nseg = (uint32_t)nseg;
+  a.ntiles = (uint32_t)ntiles;
   a.verify = 0;
   DC_CUDA(launch_relocate(a, cs, sms));
   if (dev_status)

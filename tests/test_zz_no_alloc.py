@@ -42,8 +42,8 @@ def relocate_static(plan, ptr, nbytes, status):
 
 
 @pytest.mark.parametrize("make", [
-    lambda: tg.workload("dense"),                       # 564 blocks, one look-back tile
-    lambda: tg.node_tree(4, 16, tg.uniform(1, 40), seed=21),  # ~13,000 blocks, 13 tiles
+    lambda: tg.workload("dense"),                       # 564 blocks, 8.7 KB of structs: two tiles
+    lambda: tg.node_tree(4, 16, tg.uniform(1, 40), seed=21),  # ~13,000 blocks, 140 KB of structs: 18 tiles
 ], ids=["dense", "multi_tile"])
 def test_static_scratch_matches_dc_relocate_twice(make):
     t = make()
@@ -86,6 +86,22 @@ def test_static_scratch_rejects_plans_beyond_its_limit():
     rc = relocate_static(plan, dummy.data_ptr(), plan.info["data_bytes"], None)
     assert dc.STATUS[rc] == "DC_EBUDGET"
     assert b"at most 65536" in dc.lib.dc_last_error()
+    # 16,386 blocks, but a pointer slot in each of 16,385 tiles of 8 KiB: more tiles than the array lists
+    n = 16385
+    big = tg.Schema([tg.Type("Root", 16, 8, [tg.Field("n", tg.SCALAR, 0, 4),
+                                              tg.Field("kids", tg.CHILD, 8, count_field=0, child_type=1)]),
+                     tg.Type("Big", 8192, 8, [tg.Field("a", tg.ARRAY, 0, 4, count_const=1)])])
+    kids = (ctypes.c_uint8 * (n * 8192))()
+    vals = (ctypes.c_float * n)()
+    ptrs = np.frombuffer(kids, dtype=np.uint64).reshape(n, 1024)
+    ptrs[:, 0] = ctypes.addressof(vals) + 4 * np.arange(n, dtype=np.uint64)
+    root = (ctypes.c_uint64 * 2)(n, ctypes.addressof(kids))
+    p3 = dc.Plan(big, ctypes.addressof(root))
+    assert p3.info["nblocks"] == n + 2
+    rc = relocate_static(p3, dummy.data_ptr(), p3.info["data_bytes"], None)
+    assert dc.STATUS[rc] == "DC_EBUDGET"
+    assert b"relocation tiles" in dc.lib.dc_last_error()
+    p3.destroy()
     small = tg.workload("tiny")
     p2 = dc.Plan(small.schema, small.root)
     rc = relocate_static(p2, dummy.data_ptr(), 256, None)  # region smaller than the plan's
