@@ -57,7 +57,10 @@ WORKLOADS = {
 
 # DRAM bytes (read + write) per launch of the step's kernel from one ncu capture, by (workload, split);
 # the summary beside each gives the command.  An entry stands only while the kernel is unchanged.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    ("dense", 256, 4): (460_655_616, "profiles/fused_kernel_dense.md"),
+    ("reloc_stress", 256, 4): (195_031_296, "profiles/relocate_kernel_reloc_stress.md"),
+}
 
 
 def l2_policy(torch, step_bytes):
