@@ -85,6 +85,14 @@ def test_plan_counts_and_layout_match_oracle():
                 assert b["parent"] < info["nstruct_blocks"] and b["parent"] < i
             end, lane = b["offset"] + b["bytes"], b["lane"]
         assert info["data_bytes"] == (end + 15) // 16 * 16 == c["padded_bytes"]
+        # within each lane, consecutive blocks are pointed at by ascending slots
+        last = {}
+        for b in blocks:
+            if b["parent"] is None:
+                continue
+            slot = blocks[b["parent"]]["offset"] + b["slot_off"]
+            assert slot > last.get(b["lane"], -1), (t.name, b)
+            last[b["lane"]] = slot
         assert info["device_bytes"] >= info["data_bytes"]
         p.destroy()
         t.free()
