@@ -13,6 +13,7 @@
 
 #include "../../include/dc.h"
 #include "pool.hpp"
+#include "trace.hpp"
 
 namespace dc {
 
@@ -161,6 +162,7 @@ struct StreamArgs {
   const uint32_t* tile_seg;
   uint32_t nseg;
   uint64_t units;
+  uint64_t t_begin, t_end;  // the launch's tiles (of LEAF_TILE units)
   int kind, f64;
   double scale;
 };
@@ -303,6 +305,11 @@ struct dc_plan_s {
   dc::OpKey step_key;
   bool step_fused = false;
   Moves step_rest, step_xy, step_xback;
+  // the fused pass in tile groups: group g's tiles [step_cut[g], step_cut[g+1]) launch once its
+  // pieces in step_in[g] are marshalled; step_out[g] are scattered once they complete
+  std::vector<uint64_t> step_cut;
+  std::vector<Moves> step_in, step_out;
+  std::vector<cudaEvent_t> step_ev;
   uint64_t st_int_nd = 0, st_int_units = 0, st_run_nd = 0, st_run_units = 0, st_nseg = 0, st_units = 0;
   std::vector<uint32_t> step_written;
   uint64_t step_gen = 0;

@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(LEAF_THREADS) stream_kernel(StreamArgs a) {
   const T sc = (T)a.scale;
   const StreamSeg* seg = a.seg;
   auto ub = [&](uint32_t s) { return __ldg(&seg[s].ubeg); };
-  for (uint64_t t = blockIdx.x; t * LEAF_TILE < a.units; t += gridDim.x) {
+  for (uint64_t t = a.t_begin + blockIdx.x; t < a.t_end && t * LEAF_TILE < a.units; t += gridDim.x) {
     const uint64_t u0 = t * LEAF_TILE;
     const uint32_t lo = __ldg(&a.tile_seg[t]), hi = __ldg(&a.tile_seg[t + 1]);
     VT xv[LEAF_UNROLL], yv[LEAF_UNROLL];
@@ -692,8 +692,8 @@ cudaError_t launch_move(const MoveArgs& a, cudaStream_t s, int sm_count) {
 }
 
 cudaError_t launch_stream(const StreamArgs& a, cudaStream_t s, int sm_count) {
-  if (a.units == 0 || a.nseg == 0) return cudaSuccess;
-  uint64_t tiles = (a.units + LEAF_TILE - 1) / LEAF_TILE;
+  if (a.units == 0 || a.nseg == 0 || a.t_end <= a.t_begin) return cudaSuccess;
+  const uint64_t tiles = a.t_end - a.t_begin;
   auto go = [&](auto kernel) {
     static int occ = 0;
     if (!occ) occ = occupancy(kernel, LEAF_THREADS, 0);

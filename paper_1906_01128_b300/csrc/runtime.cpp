@@ -316,6 +316,10 @@ dc_status dc_plan_destroy(dc_plan_t p) {
   release_transfers(p);
   if (p->h2d_done) cudaEventDestroy(p->h2d_done);
   if (p->tab_done) cudaEventDestroy(p->tab_done);
+  for (cudaEvent_t e : p->step_ev) {
+    cudaEventSynchronize(e);
+    cudaEventDestroy(e);
+  }
   delete p;
   return DC_OK;
 }
@@ -561,7 +565,10 @@ dc_status dc_update_leaves(dc_plan_t p, const dc_op* op, dc_stream_t stream) {
   if (st) return st;
   if (!p->dev) return fail(DC_ESTATE, "no device buffer bound");
   cudaStream_t s = stream;
-  if ((st = build_leaf_table(p, op, s))) return st;
+  {
+    Trace tr("dc_update_leaves", "tables");
+    if ((st = build_leaf_table(p, op, s))) return st;
+  }
   p->written = &p->leaf_written;
   p->written_gen = p->leaf_gen;
   p->op_run = true;
@@ -674,6 +681,7 @@ dc_status dc_copy_back(dc_plan_t p, uint32_t flags, dc_stream_t stream) {
 dc_status dc_sync(dc_plan_t p, dc_stream_t stream) {
   if (!p) return fail(DC_EINVAL, "plan is NULL");
   if (!p->dev) return fail(DC_ESTATE, "no device buffer bound");
+  Trace tr("dc_sync", "wait");
   return device_error(p, stream);
 }
 

@@ -9,6 +9,10 @@
 // link instead of following each other.  Needs a DC_PLAN_MAP_HOST plan whose
 // selected arrays start on 16-byte host addresses; otherwise the call runs
 // dc_deep_copy, dc_update_leaves and dc_copy_back in turn (same results).
+//
+// The pass runs in tile groups (up to STEP_GROUPS launches): the host
+// marshals the array pieces that group g+1 reads from the pinned arena and
+// scatters the pieces group g-1 wrote there while the device streams group g.
 #include <algorithm>
 
 #include "internal.hpp"
@@ -16,6 +20,9 @@
 using namespace dc;
 
 namespace {
+
+constexpr uint64_t STEP_GROUPS = 8;
+constexpr uint64_t STEP_GROUP_MIN = 4ull << 20;  // x bytes per group at least
 
 // The op's blocks and the rest, their moves, and (when the fused kernel can
 // run: `direct` and 16-byte aligned host arrays) its device tables.
@@ -80,8 +87,37 @@ dc_status build_step(dc_plan_s* p, const dc_op* op, bool direct, cudaStream_t s)
   }
   p->st_nseg = seg.size();
   p->st_units = u;
+  const uint64_t ntiles = (u + LEAF_TILE - 1) / LEAF_TILE;
+  // tile groups: a piece in the pinned arena is marshalled for the group of its array's first
+  // tile and scattered after the group of its last tile
+  const uint64_t ng = std::max<uint64_t>(1, std::min<uint64_t>({STEP_GROUPS, ntiles, u * 16 / STEP_GROUP_MIN}));
+  p->step_cut.assign(ng + 1, 0);
+  for (uint64_t g = 0; g <= ng; g++) p->step_cut[g] = ntiles * g / ng;
+  auto group_of = [&](uint64_t t) {
+    return (uint64_t)(std::upper_bound(p->step_cut.begin(), p->step_cut.end(), t) - p->step_cut.begin()) - 1;
+  };
+  std::vector<std::vector<uint32_t>> in(ng), out(ng);
+  for (size_t i = 0; i < picks.size(); i++) {
+    const uint64_t nu = (p->blocks[picks[i].bx].count * esz + 15) / 16;
+    const uint64_t t0 = seg[i].ubeg / LEAF_TILE, t1 = (seg[i].ubeg + std::max<uint64_t>(nu, 1) - 1) / LEAF_TILE;
+    in[std::min(group_of(t0), ng - 1)].push_back(picks[i].bx);
+    if (axpy) in[std::min(group_of(t0), ng - 1)].push_back(picks[i].by);
+    out[std::min(group_of(t1), ng - 1)].push_back(picks[i].bx);
+  }
+  p->step_in.assign(ng, dc_plan_s::Moves());
+  p->step_out.assign(ng, dc_plan_s::Moves());
+  for (uint64_t g = 0; g < ng; g++) {
+    std::sort(in[g].begin(), in[g].end());
+    std::sort(out[g].begin(), out[g].end());
+    plan_moves(p, in[g], &p->step_in[g]);
+    plan_moves(p, out[g], &p->step_out[g]);
+  }
+  while (p->step_ev.size() < ng) {
+    cudaEvent_t e;
+    DC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    p->step_ev.push_back(e);
+  }
   if (!seg.empty()) {
-    const uint64_t ntiles = (u + LEAF_TILE - 1) / LEAF_TILE;
     if (ntiles + 1 > p->L.tseg_cap || seg.size() > p->L.seg_cap) return fail(DC_EINVAL, "step table larger than planned");
     std::vector<uint32_t> tiles;
     for (uint64_t t = 0, k = 0; t < ntiles; t++) {
@@ -106,7 +142,10 @@ dc_status prepare_step(dc_plan_s* p, const dc_op* op, cudaStream_t s) {
   return DC_OK;
 }
 
-dc_status launch_step_kernel(dc_plan_s* p, const dc_op* op, cudaStream_t s) {
+// The fused pass, group by group: marshal group g's pieces, launch its tiles, and while the
+// device streams it, scatter the pieces of group g-1.  Ends with the stream synchronized and the
+// device error word read.  On an error the caller's x arrays may hold part of the results.
+dc_status run_step_groups(dc_plan_s* p, const dc_op* op, cudaStream_t s) {
   StreamArgs a;
   a.seg = reinterpret_cast<const StreamSeg*>(p->dev + p->L.sts);
   a.tile_seg = reinterpret_cast<const uint32_t*>(p->dev + p->L.stst);
@@ -115,10 +154,33 @@ dc_status launch_step_kernel(dc_plan_s* p, const dc_op* op, cudaStream_t s) {
   a.kind = op->kind;
   a.f64 = p->schema.fields[op->type][op->x_field].elem_kind == DC_E_F64;
   a.scale = op->scale;
-  DC_CUDA(launch_stream(a, s, p->sm_count));
+  const uint64_t ng = p->step_in.size();
+  for (uint64_t g = 0; g < ng; g++) {
+    {
+      Trace tr("dc_roundtrip", "marshal");
+      host_copy(p, p->step_in[g], 0, p->step_in[g].units.size(), true);
+    }
+    a.t_begin = p->step_cut[g];
+    a.t_end = p->step_cut[g + 1];
+    DC_CUDA(launch_stream(a, s, p->sm_count));
+    DC_CUDA(cudaEventRecord(p->step_ev[g], s));
+    if (g) {
+      Trace tr("dc_roundtrip", "scatter");
+      DC_CUDA(cudaEventSynchronize(p->step_ev[g - 1]));
+      host_copy(p, p->step_out[g - 1], 0, p->step_out[g - 1].units.size(), false);
+    }
+  }
+  DC_CUDA(cudaEventRecord(p->h2d_done, s));  // the pinned arena is free once the pass has read it
   p->written = &p->step_written;
   p->written_gen = p->step_gen;
   p->op_run = true;
+  dc_status st;
+  {
+    Trace tr("dc_roundtrip", "device+wait");
+    if ((st = device_error(p, s))) return st;  // synchronizes the stream
+  }
+  Trace tr("dc_roundtrip", "scatter");
+  if (ng) host_copy(p, p->step_out[ng - 1], 0, p->step_out[ng - 1].units.size(), false);
   return DC_OK;
 }
 
@@ -131,7 +193,10 @@ extern "C" dc_status dc_roundtrip(dc_plan_t p, const dc_op* op, dc_stream_t stre
   if (!p->dev) return fail(DC_ESTATE, "no device buffer bound");
   cudaStream_t s = stream;
   pool_of(p);
-  if ((st = prepare_step(p, op, s))) return st;
+  {
+    Trace tr("dc_roundtrip", "tables");
+    if ((st = prepare_step(p, op, s))) return st;
+  }
   if (!p->step_fused) {
     if ((st = dc_deep_copy(p, stream))) return st;
     if ((st = dc_update_leaves(p, op, stream))) return st;
@@ -140,19 +205,16 @@ extern "C" dc_status dc_roundtrip(dc_plan_t p, const dc_op* op, dc_stream_t stre
   if ((st = wait_event(p->h2d_done))) return st;  // the pinned arena is rewritten below
   // blocks outside the op: as in dc_deep_copy
   if ((st = launch_table(p, p->L.sta, p->L.stat, p->st_int_nd, p->st_int_units, s))) return st;
-  host_copy(p, p->step_rest, 0, p->step_rest.units.size(), true);
-  host_copy(p, p->step_xy, 0, p->step_xy.units.size(), true);
-  size_t ns = 0;
-  null_slots_upto(p, &ns, ~0ull);
+  {
+    Trace tr("dc_roundtrip", "marshal");
+    host_copy(p, p->step_rest, 0, p->step_rest.units.size(), true);
+    size_t ns = 0;
+    null_slots_upto(p, &ns, ~0ull);
+  }
   if ((st = launch_table(p, p->L.stb, p->L.stbt, p->st_run_nd, p->st_run_units, s))) return st;
-  DC_CUDA(cudaEventRecord(p->h2d_done, s));
   if ((st = dc_relocate(p, stream))) return st;
-  // the selected arrays: host -> update -> arena and host, in one pass
-  if ((st = launch_step_kernel(p, op, s))) return st;
-  if ((st = device_error(p, s))) return st;  // synchronizes the stream
-  // x bytes that went through the pinned arena (outside mapped interiors)
-  host_copy(p, p->step_xback, 0, p->step_xback.units.size(), false);
-  return DC_OK;
+  // the selected arrays: host -> update -> arena and host, in one pass per tile group
+  return run_step_groups(p, op, s);
 }
 
 extern "C" dc_status dc_roundtrip_selected(dc_plan_t p, const dc_op* op, dc_stream_t stream) {
@@ -165,14 +227,8 @@ extern "C" dc_status dc_roundtrip_selected(dc_plan_t p, const dc_op* op, dc_stre
   if ((st = prepare_step(p, op, s))) return st;
   if ((st = wait_event(p->h2d_done))) return st;
   // only the op's arrays move, by their effective addresses (Sec. 3)
+  if (p->step_fused) return run_step_groups(p, op, s);
   host_copy(p, p->step_xy, 0, p->step_xy.units.size(), true);
-  if (p->step_fused) {
-    if ((st = launch_step_kernel(p, op, s))) return st;
-    DC_CUDA(cudaEventRecord(p->h2d_done, s));
-    if ((st = device_error(p, s))) return st;
-    host_copy(p, p->step_xback, 0, p->step_xback.units.size(), false);
-    return DC_OK;
-  }
   for (const auto& r : p->step_xy.runs)
     DC_CUDA(cudaMemcpyAsync(p->dev + r.lo, p->pinned + r.lo, r.hi - r.lo, cudaMemcpyHostToDevice, s));
   DC_CUDA(cudaEventRecord(p->h2d_done, s));

@@ -238,11 +238,15 @@ dc_status transfer_to_device(dc_plan_s* p, cudaStream_t s) {
   if (st) return st;
   size_t ns = 0;
   if (p->flags & DC_PLAN_MAP_HOST) {
-    host_copy(p, m, 0, m.units.size(), true);
-    null_slots_upto(p, &ns, ~0ull);
+    {
+      Trace tr("dc_deep_copy", "marshal");
+      host_copy(p, m, 0, m.units.size(), true);
+      null_slots_upto(p, &ns, ~0ull);
+    }
     return launch_table(p, p->L.mvb, p->L.mvbt, p->h2d_frag_nd, p->h2d_frag_units, s);
   }
   // Algorithm 1's contiguous buffer, marshalled and sent chunk by chunk
+  Trace tr("dc_deep_copy", "marshal+copies");
   for (const auto& c : m.chunks) {
     host_copy(p, m, c.ufirst, c.ulast, true);
     null_slots_upto(p, &ns, c.clast > c.cfirst ? m.copies[c.clast - 1].hi : 0);
@@ -269,7 +273,11 @@ dc_status transfer_back(dc_plan_s* p, const std::vector<uint32_t>& list, uint64_
   }
   dc_status st = launch_table(p, p->L.bk, p->L.bkt, p->bk_nd, p->bk_units, s);
   if (st) return st;
-  if ((st = device_error(p, s))) return st;  // synchronizes the stream
+  {
+    Trace tr("dc_copy_back", "device+wait");
+    if ((st = device_error(p, s))) return st;  // synchronizes the stream
+  }
+  Trace tr("dc_copy_back", "scatter");
   if (!p->back.units.empty()) host_copy(p, p->back, 0, p->back.units.size(), false);
   return DC_OK;
 }
