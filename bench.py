@@ -784,6 +784,11 @@ def main():
     for mode, r in (("staged", e2e_staged), ("map_host", e2e_mapped)):
         link[f"deep_copy_frac_of_h2d_peak_{mode}"] = round(r["deep_copy_gbs"] / link["h2d_gbs"], 4)
         link[f"copy_back_frac_of_d2h_peak_{mode}"] = round(r["copy_back_gbs"] / link["d2h_gbs"], 4)
+    # the round trip moves both directions at once: against the two copy engines' aggregate
+    rt_bytes = e2e_rt["h2d_bytes_per_step"] + e2e_rt["d2h_bytes_per_step"]
+    link["roundtrip_link_gbs"] = round(rt_bytes / (e2e_rt["ms_per_step"] * 1e-3) / 1e9, 2)
+    link["roundtrip_frac_of_bidirectional_peak"] = round(link["roundtrip_link_gbs"] /
+                                                         link["bidirectional"]["aggregate_gbs"], 4)
 
     # ---- comparison paths (same GPU) -----------------------------------------
     compare = None

@@ -343,7 +343,10 @@ dc_status check_op(const dc_plan_s* p, const dc_op* op);
 bool in_host_arena(const void* host, uint64_t bytes, uint64_t* dev);
 // transfer.cpp
 uint64_t interior_bytes(const HostBlock& b);
-void plan_moves(const dc_plan_s* p, const std::vector<uint32_t>& list, dc_plan_s::Moves* m);
+// host_order: hand out the host copies in host-address order (sequential on the
+// caller's side); such Moves have no DMA chunks.  Otherwise they follow the
+// arena, chunk by chunk.
+void plan_moves(const dc_plan_s* p, const std::vector<uint32_t>& list, dc_plan_s::Moves* m, bool host_order = true);
 void plan_transfers(dc_plan_s* p);
 void release_transfers(dc_plan_s* p);
 dc_status upload_h2d_tables(dc_plan_s* p, cudaStream_t s);

@@ -44,7 +44,7 @@ uint64_t interior_bytes(const HostBlock& b) {
   return hi > lo && hi - lo >= DC_MAP_MIN_BYTES ? hi - lo : 0;
 }
 
-void plan_moves(const dc_plan_s* p, const std::vector<uint32_t>& list, dc_plan_s::Moves* m) {
+void plan_moves(const dc_plan_s* p, const std::vector<uint32_t>& list, dc_plan_s::Moves* m, bool host_order) {
   *m = dc_plan_s::Moves();
   for (uint32_t b : list) {
     const HostBlock& B = p->blocks[b];
@@ -62,6 +62,10 @@ void plan_moves(const dc_plan_s* p, const std::vector<uint32_t>& list, dc_plan_s
   for (const auto& f : m->frags)
     for (uint64_t o = 0; o < f.len; o += PIECE_BYTES)
       m->pieces.push_back({f.off + o, std::min(PIECE_BYTES, f.len - o), f.host + o});
+  if (host_order)
+    std::sort(m->pieces.begin(), m->pieces.end(), [](const dc_plan_s::Frag& a, const dc_plan_s::Frag& b) {
+      return a.host < b.host;
+    });
   for (uint64_t i = 0; i < m->pieces.size();) {
     uint64_t j = i, bytes = 0;
     while (j < m->pieces.size() && bytes < UNIT_BYTES && j - i < UNIT_PIECES) bytes += m->pieces[j++].len;
@@ -75,6 +79,7 @@ void plan_moves(const dc_plan_s* p, const std::vector<uint32_t>& list, dc_plan_s
     else
       m->runs.push_back({f.off, f.off + f.len});
   }
+  if (host_order) return;
   // chunks of ~CHUNK_BYTES of staged bytes, with the runs clipped to them
   size_t r = 0;
   for (uint64_t u = 0; u < m->units.size();) {
@@ -144,7 +149,7 @@ void plan_transfers(dc_plan_s* p) {
   }
   std::vector<uint32_t> all(nb);
   for (uint32_t b = 0; b < nb; b++) all[b] = b;
-  plan_moves(p, all, &p->h2d);
+  plan_moves(p, all, &p->h2d, (p->flags & DC_PLAN_MAP_HOST) != 0);  // staged copies go chunk by chunk
   p->transfers_ready = true;
 }
 
