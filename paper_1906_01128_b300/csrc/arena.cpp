@@ -40,7 +40,7 @@ dc_status dc_host_arena_create(uint64_t bytes, dc_host_arena_t* out) {
   auto* a = new (std::nothrow) dc_host_arena_s;
   if (!a) return dc::fail(DC_ENOMEM, "out of host memory");
   a->bytes = dc::round_up(bytes, 256);
-  cudaError_t e = cudaHostAlloc((void**)&a->base, a->bytes, cudaHostAllocMapped);
+  cudaError_t e = dc::host_alloc((void**)&a->base, a->bytes, cudaHostAllocMapped);
   if (e != cudaSuccess) {
     delete a;
     return dc::fail(DC_ENOMEM, "host arena of %llu bytes: %s", (unsigned long long)bytes, cudaGetErrorString(e));

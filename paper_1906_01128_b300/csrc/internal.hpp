@@ -23,6 +23,9 @@ inline uint64_t round_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 
 // ---- error reporting ---------------------------------------------------------
 dc_status fail(dc_status s, const char* fmt, ...);
+// debug.cpp: DC_DEBUG=1 (every plan verifies) and DC_FAULT_HOST_ALLOC=1 (pinned allocations fail)
+bool debug_on();
+cudaError_t host_alloc(void** ptr, size_t bytes, unsigned int flags);
 dc_status cuda_fail(cudaError_t e, const char* what);
 const char* last_error();
 #define DC_CUDA(call)                                        \

@@ -102,10 +102,6 @@ Pool& dc::pool_of(dc_plan_s* p) {
   return *p->pool;
 }
 
-namespace {
-
-}  // namespace
-
 dc_status dc::device_error(dc_plan_s* p, cudaStream_t s) {
   uint32_t* word = reinterpret_cast<uint32_t*>(p->pin_tab + tab_words(p->L));
   DC_CUDA(cudaMemcpyAsync(word, p->dev + p->L.ctrl + CTRL_ERR * 4, 4, cudaMemcpyDeviceToHost, s));
@@ -118,10 +114,6 @@ dc_status dc::device_error(dc_plan_s* p, cudaStream_t s) {
   if (e & ERR_TIMEOUT) return fail(DC_ETIMEOUT, "a device-side wait gave up (0x%x)", e);
   return fail(DC_EVERIFY, "relocation check: a pointer slot did not hold the recorded host address");
 }
-
-namespace {
-
-}  // namespace
 
 OpKey dc::key_of(const dc_op* op) {
   OpKey k;
@@ -254,13 +246,14 @@ dc_status dc_plan_forest(const dc_schema* schema, const void* const* roots, uint
     return st;
   }
   p->L = make_layout(p);
+  if (debug_on()) p->flags |= DC_PLAN_VERIFY;
   *out = p;
   return DC_OK;
 }
 
 dc_status dc_plan_set_flags(dc_plan_t p, uint32_t flags) {
   if (!p) return fail(DC_EINVAL, "plan is NULL");
-  p->flags = flags;
+  p->flags = flags | (debug_on() ? DC_PLAN_VERIFY : 0u);
   return DC_OK;
 }
 
@@ -335,7 +328,7 @@ dc_status dc_bind_device(dc_plan_t p, void* dev, uint64_t bytes, dc_stream_t str
   DC_CUDA(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device));
   if (p->h2d_done) DC_CUDA(cudaEventSynchronize(p->h2d_done));
   if (!p->pinned) {
-    cudaError_t e = cudaHostAlloc((void**)&p->pinned, std::max<uint64_t>(p->data_bytes, 16), cudaHostAllocMapped);
+    cudaError_t e = host_alloc((void**)&p->pinned, std::max<uint64_t>(p->data_bytes, 16), cudaHostAllocMapped);
     if (e != cudaSuccess) {
       p->pinned = nullptr;
       return fail(DC_ENOMEM, "pinned arena of %llu bytes: %s", (unsigned long long)p->data_bytes,
@@ -354,7 +347,7 @@ dc_status dc_bind_device(dc_plan_t p, void* dev, uint64_t bytes, dc_stream_t str
   if (!p->pin_tab || p->pin_tab_bytes < tab_total(p->L)) {
     if (p->pin_tab && !p->borrowed_pinned) cudaFreeHost(p->pin_tab);
     p->pin_tab_bytes = tab_total(p->L);
-    cudaError_t e = cudaHostAlloc((void**)&p->pin_tab, p->pin_tab_bytes, cudaHostAllocDefault);
+    cudaError_t e = host_alloc((void**)&p->pin_tab, p->pin_tab_bytes, cudaHostAllocDefault);
     if (e != cudaSuccess) {
       p->pin_tab = nullptr;
       return fail(DC_ENOMEM, "pinned table staging: %s", cudaGetErrorString(e));

@@ -169,7 +169,7 @@ dc_status dc_server_create(const dc_schema* schema, void* dev_pool, uint64_t dev
   S->pin_bytes = round_up(std::max<uint64_t>(pinned_bytes, 256), 256);
   S->flags = flags;
   S->nslots = (flags & DC_SERVER_SEQUENTIAL) ? 1 : nslots;
-  cudaError_t e = cudaHostAlloc((void**)&S->pin, S->pin_bytes, cudaHostAllocMapped);
+  cudaError_t e = host_alloc((void**)&S->pin, S->pin_bytes, cudaHostAllocMapped);
   if (e != cudaSuccess) {
     delete S;
     return fail(DC_ENOMEM, "pinned pool of %llu bytes: %s", (unsigned long long)pinned_bytes, cudaGetErrorString(e));
