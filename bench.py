@@ -618,9 +618,21 @@ def main():
     payload = tree.payload_bytes
     nelem = tree.nelems("Node", "position")
     stream = torch.cuda.current_stream()
-    plan = dc.Plan(s, tree.root)
-    plan.bind()
+    t0 = time.perf_counter()
+    plan = dc.Plan(s, tree.root)  # the walk, layout and relocation tables (host)
+    t1 = time.perf_counter()
+    plan.bind()  # pinned arena, transfer plan, table uploads
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
     info = plan.info
+    host_side = {"plan_ms": round((t1 - t0) * 1e3, 3), "bind_ms": round((t2 - t1) * 1e3, 3)}
+    leaf_chain = tg.leaf_path(tg.WORKLOADS[args.workload][0])  # root -> ... -> the first leaf
+    plan.resolve(leaf_chain)
+    t0 = time.perf_counter()
+    for _ in range(1000):
+        plan.resolve(leaf_chain)
+    host_side["resolve_chain_us"] = round((time.perf_counter() - t0) * 1e3, 3)  # ms for 1000 calls = us per call
+    host_side["resolve_chain_steps"] = len(leaf_chain)
     if args.workload == "deep":  # only the leaf carries the long arrays: update through its chain
         op = dc.Op(sel=dc.SEL_CHAIN, path=tg.leaf_path(64))
         nelem = 1 << 26
@@ -851,6 +863,7 @@ def main():
                            "frac": round(reloc_bytes / reloc_avg / 1e9 / hbm, 4), "record_bytes_moved": reloc_moved},
             "two_launch_step_us": round((reloc_avg + leaf_avg) * 1e6, 2),
             "step_median_ms": round(step_median * 1e3, 4),
+            "host_side": host_side,
             "e2e": e2e, "e2e_three_calls_map_host": e2e_mapped, "e2e_staged": e2e_staged, "link": link, "compare": compare, "cpu_baseline": cpu,
             "clocks": clk,
             "gpu_launches": launches,
