@@ -90,7 +90,13 @@ dc_status build_step(dc_plan_s* p, const dc_op* op, bool direct, cudaStream_t s)
   const uint64_t ntiles = (u + LEAF_TILE - 1) / LEAF_TILE;
   // tile groups: a piece in the pinned arena is marshalled for the group of its array's first
   // tile and scattered after the group of its last tile
-  const uint64_t ng = std::max<uint64_t>(1, std::min<uint64_t>({STEP_GROUPS, ntiles, u * 16 / STEP_GROUP_MIN}));
+  // groups only pay when there are host copies to overlap: the bytes of x and y that go through
+  // the pinned arena (the rest is read and written in place by the kernel)
+  uint64_t staged = 0;
+  for (const auto& f : p->step_xy.frags) staged += f.len;
+  const uint64_t ng = staged < STEP_GROUP_MIN
+                          ? 1
+                          : std::max<uint64_t>(1, std::min<uint64_t>({STEP_GROUPS, ntiles, u * 16 / STEP_GROUP_MIN}));
   p->step_cut.assign(ng + 1, 0);
   for (uint64_t g = 0; g <= ng; g++) p->step_cut[g] = ntiles * g / ng;
   auto group_of = [&](uint64_t t) {

@@ -69,3 +69,31 @@ def test_served_full_configuration():
     for k in range(nkeys):
         ok, msg = oracle.trees_equal(s, src[k].root, ref[k].root)
         assert ok, (k, msg)
+
+
+@pytest.mark.parametrize("name", ["dense", "deep", "reloc_stress"])
+def test_bench_step_full_size(name):
+    """The bench's step for the single-tree workloads: dc_autotune picks the
+    split, then one dc_relocate_update launch (relocation + leaf update) on the
+    resident arena, then the copy back; the host tree must equal the oracle's."""
+    src, ref = tg.workload(name), tg.workload(name)
+    s = src.schema
+    op = dc.Op(sel=dc.SEL_CHAIN, path=tg.leaf_path(64)) if name == "deep" else dc.Op()
+    oop = oracle.Op(sel=oracle.SEL_CHAIN, path=tg.leaf_path(64)) if name == "deep" else oracle.Op()
+    plan = dc.Plan(s, src.root)
+    plan.bind()
+    plan.deep_copy()
+    plan.autotune(op)
+    plan.deep_copy()  # the tuning runs applied the update: start again from the host tree
+    plan.sync()
+    ok, msg, _ = oracle.check_image(s, src.root, plan.image(), plan.device_base)
+    assert ok, msg
+    plan.relocate_update(op)
+    plan.copy_back()
+    plan.sync()
+    cp = oracle.deep_copy(s, ref.root)
+    oracle.update(s, cp.root, oop)
+    oracle.copy_back(s, cp.root, ref.root, oop)
+    ok, msg = oracle.trees_equal(s, src.root, ref.root)
+    assert ok, msg
+    plan.destroy()
