@@ -35,6 +35,13 @@
 #include <stddef.h>
 #include <stdint.h>
 
+/* Every entry point below is exported from the library; nothing else is. */
+#if defined(__GNUC__)
+#define DC_API __attribute__((visibility("default")))
+#else
+#define DC_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -157,34 +164,34 @@ typedef struct {
  * (in type, field order), each in depth-first order; every block starts on a
  * 16-byte boundary.  Errors: DC_EINVAL (NULL pointer with a non-zero count,
  * negative count, bad schema), DC_EALIAS / DC_ECYCLE (not a tree), DC_ENOMEM. */
-dc_status dc_plan(const dc_schema* schema, const void* host_root, dc_plan_t* out);
+DC_API dc_status dc_plan(const dc_schema* schema, const void* host_root, dc_plan_t* out);
 /* dc_plan_forest — one plan (one arena, one relocation, one leaf stream) for
  * `nroots` independent trees of the same schema, laid out tree after tree
  * within each lane (the batched form of the deep copy).  SEL_ALL ops cover
  * every tree; SEL_CHAIN paths and dc_resolve_chain / dc_verify_chain start at
  * tree 0 (dc_resolve_chain_in takes a tree index).  The trees must not share
  * blocks (DC_EALIAS). */
-dc_status dc_plan_forest(const dc_schema* schema, const void* const* roots, uint64_t nroots, dc_plan_t* out);
+DC_API dc_status dc_plan_forest(const dc_schema* schema, const void* const* roots, uint64_t nroots, dc_plan_t* out);
 /* Offset of tree `tree`'s root struct in the data region. */
-dc_status dc_plan_root(dc_plan_t plan, uint64_t tree, uint64_t* offset);
-dc_status dc_plan_set_flags(dc_plan_t plan, uint32_t flags);
-dc_status dc_plan_info_get(dc_plan_t plan, dc_plan_info* out);
+DC_API dc_status dc_plan_root(dc_plan_t plan, uint64_t tree, uint64_t* offset);
+DC_API dc_status dc_plan_set_flags(dc_plan_t plan, uint32_t flags);
+DC_API dc_status dc_plan_info_get(dc_plan_t plan, dc_plan_info* out);
 /* Block `i` in arena order: its host address, arena offset, byte size, lane,
  * and its relocation entry — the struct block holding the pointer slot that
  * refers to it (UINT32_MAX for the root) and that slot's byte offset inside
  * it.  Any output pointer may be NULL. */
-dc_status dc_plan_block(dc_plan_t plan, uint64_t i, uint64_t* host_addr, uint64_t* offset,
+DC_API dc_status dc_plan_block(dc_plan_t plan, uint64_t i, uint64_t* host_addr, uint64_t* offset,
                         uint64_t* bytes, uint32_t* lane, uint32_t* parent, uint32_t* slot_off);
 /* Host threads used by marshal and copy-back scatter (0 = all online cores). */
-dc_status dc_plan_set_threads(dc_plan_t plan, uint32_t nthreads);
-dc_status dc_plan_destroy(dc_plan_t plan);
+DC_API dc_status dc_plan_set_threads(dc_plan_t plan, uint32_t nthreads);
+DC_API dc_status dc_plan_destroy(dc_plan_t plan);
 
 /* dc_bind_device — give the plan a caller-owned device buffer of at least
  * info.device_bytes bytes, 256-byte aligned (a torch CUDA uint8 tensor
  * qualifies).  Uploads the block table and clears the scratch on `stream`
  * (blocking), and allocates the plan's pinned staging arena on first use.
  * Errors: DC_EBUDGET, DC_EINVAL (misaligned), DC_ENOMEM, DC_ECUDA. */
-dc_status dc_bind_device(dc_plan_t plan, void* dev_buffer, uint64_t bytes, dc_stream_t stream);
+DC_API dc_status dc_bind_device(dc_plan_t plan, void* dev_buffer, uint64_t bytes, dc_stream_t stream);
 
 /* dc_deep_copy — move the tree into the arena (Fig 2 steps b-c), then run
  * the relocation kernel, which rebuilds every pointer slot to the device
@@ -198,14 +205,14 @@ dc_status dc_bind_device(dc_plan_t plan, void* dev_buffer, uint64_t bytes, dc_st
  * and the kernel are queued; with DC_PLAN_MAP_HOST the caller's arrays are
  * read until the stream gets there.  Errors: DC_ESTATE (nothing bound),
  * DC_ECUDA. */
-dc_status dc_deep_copy(dc_plan_t plan, dc_stream_t stream);
+DC_API dc_status dc_deep_copy(dc_plan_t plan, dc_stream_t stream);
 
 /* dc_relocate — the relocation kernel of dc_deep_copy alone (Fig 2 step d):
  * recompute every block's arena offset on the device and rewrite every pointer
  * slot of the data region already in device memory.  For a data region that
  * is already resident (filled by an earlier dc_deep_copy or by the caller);
  * the result is the same whatever the slots held.  Errors: DC_ESTATE, DC_ECUDA. */
-dc_status dc_relocate(dc_plan_t plan, dc_stream_t stream);
+DC_API dc_status dc_relocate(dc_plan_t plan, dc_stream_t stream);
 
 /* dc_resolve_chain — the effective device address of a pointer chain
  * (Sec. 3: extract it once, before the compute region): the struct the CHILD
@@ -214,16 +221,16 @@ dc_status dc_relocate(dc_plan_t plan, dc_stream_t stream);
  * of range, NULL link), DC_ESTATE (nothing bound).
  * dc_resolve_offset gives the same place as an offset in the data region
  * and needs no device buffer. */
-dc_status dc_resolve_chain(dc_plan_t plan, const dc_step* path, uint32_t len, uint64_t* dev_addr);
-dc_status dc_resolve_offset(dc_plan_t plan, const dc_step* path, uint32_t len, uint64_t* offset);
-dc_status dc_resolve_chain_in(dc_plan_t plan, uint64_t tree, const dc_step* path, uint32_t len, uint64_t* dev_addr);
-dc_status dc_resolve_offset_in(dc_plan_t plan, uint64_t tree, const dc_step* path, uint32_t len, uint64_t* offset);
+DC_API dc_status dc_resolve_chain(dc_plan_t plan, const dc_step* path, uint32_t len, uint64_t* dev_addr);
+DC_API dc_status dc_resolve_offset(dc_plan_t plan, const dc_step* path, uint32_t len, uint64_t* offset);
+DC_API dc_status dc_resolve_chain_in(dc_plan_t plan, uint64_t tree, const dc_step* path, uint32_t len, uint64_t* dev_addr);
+DC_API dc_status dc_resolve_offset_in(dc_plan_t plan, uint64_t tree, const dc_step* path, uint32_t len, uint64_t* offset);
 
 /* dc_update_leaves — run the leaf kernel on the device copy through resolved
  * addresses: the selected structs' chains are resolved on the host and the
  * kernel streams over (x, y, n) segments with no pointer loads.  Errors:
  * DC_EINVAL (op fields / path / counts), DC_ESTATE, DC_ECUDA. */
-dc_status dc_update_leaves(dc_plan_t plan, const dc_op* op, dc_stream_t stream);
+DC_API dc_status dc_update_leaves(dc_plan_t plan, const dc_op* op, dc_stream_t stream);
 
 /* dc_relocate_update — dc_relocate and dc_update_leaves(op) in one persistent
  * kernel launch: work items are the relocation's tiles, then the leaf
@@ -235,7 +242,7 @@ dc_status dc_update_leaves(dc_plan_t plan, const dc_op* op, dc_stream_t stream);
  * tables are on the device (after a first call) the call only launches a
  * kernel, so it can be captured in a CUDA graph.  Errors: as
  * dc_update_leaves. */
-dc_status dc_relocate_update(dc_plan_t plan, const dc_op* op, dc_stream_t stream);
+DC_API dc_status dc_relocate_update(dc_plan_t plan, const dc_op* op, dc_stream_t stream);
 
 /* dc_autotune — time dc_relocate_update's launch on the bound arena under each
  * work split (128, 256 or 512 threads per CTA, i.e. 8, 4 or 2 blocks or
@@ -245,18 +252,18 @@ dc_status dc_relocate_update(dc_plan_t plan, const dc_op* op, dc_stream_t stream
  * histogram of the selected arrays' lengths.  Blocking.  Each timing run applies
  * the update, so the arena's x arrays change: tune before the deep copy of
  * the data that matters, or deep copy again afterwards.  Outputs may be NULL. */
-dc_status dc_autotune(dc_plan_t plan, const dc_op* op, dc_stream_t stream, uint32_t* threads,
+DC_API dc_status dc_autotune(dc_plan_t plan, const dc_op* op, dc_stream_t stream, uint32_t* threads,
                       uint32_t* ctas_per_sm);
 
 /* dc_update_chase — the same update, computed the way an unresolved chain
  * is: every element walks root -> ... -> struct -> x/y with device loads the
  * compiler may not hoist (Listing 2's loop body; Sec. 3).  Comparison path. */
-dc_status dc_update_chase(dc_plan_t plan, const dc_op* op, dc_stream_t stream);
+DC_API dc_status dc_update_chase(dc_plan_t plan, const dc_op* op, dc_stream_t stream);
 
 /* dc_verify_chain — walk `path` on the device with one thread, reading the
  * relocated pointers, and return the address it reaches (blocking).  Lets a
  * caller check dc_resolve_chain against the device image. */
-dc_status dc_verify_chain(dc_plan_t plan, const dc_step* path, uint32_t len, dc_stream_t stream,
+DC_API dc_status dc_verify_chain(dc_plan_t plan, const dc_step* path, uint32_t len, dc_stream_t stream,
                           uint64_t* dev_addr);
 
 /* dc_copy_back — transfer back (Algorithm 2 step 5): the arrays the last
@@ -267,7 +274,7 @@ dc_status dc_verify_chain(dc_plan_t plan, const dc_step* path, uint32_t len, dc_
  * Errors: DC_ESTATE (no op run and no flag), DC_ECUDA, plus any device error
  * recorded by earlier kernels. */
 #define DC_COPY_ALL_ARRAYS 1u
-dc_status dc_copy_back(dc_plan_t plan, uint32_t flags, dc_stream_t stream);
+DC_API dc_status dc_copy_back(dc_plan_t plan, uint32_t flags, dc_stream_t stream);
 
 /* dc_roundtrip — dc_deep_copy, dc_update_leaves(op) and dc_copy_back(0) as one
  * call (Algorithm 2 steps 3-5: transfer, run the kernel once, transfer back),
@@ -279,7 +286,7 @@ dc_status dc_copy_back(dc_plan_t plan, uint32_t flags, dc_stream_t stream);
  * following each other.  Otherwise it runs the three calls in turn.
  * Blocking: returns when the host arrays hold the results.  Errors: as the
  * three calls. */
-dc_status dc_roundtrip(dc_plan_t plan, const dc_op* op, dc_stream_t stream);
+DC_API dc_status dc_roundtrip(dc_plan_t plan, const dc_op* op, dc_stream_t stream);
 
 /* dc_roundtrip_selected — the paper's pointerchain transfer scheme (Sec. 3;
  * Sec. 4.1.1 item 3): only the arrays the op reads and writes move, each to its
@@ -288,15 +295,15 @@ dc_status dc_roundtrip(dc_plan_t plan, const dc_op* op, dc_stream_t stream);
  * whatever an earlier deep copy left), so it suits kernels that work through
  * resolved addresses only.  The host result equals dc_roundtrip's.
  * Blocking.  Errors: as dc_roundtrip. */
-dc_status dc_roundtrip_selected(dc_plan_t plan, const dc_op* op, dc_stream_t stream);
+DC_API dc_status dc_roundtrip_selected(dc_plan_t plan, const dc_op* op, dc_stream_t stream);
 
 /* dc_sync — wait for the plan's work on `stream` and report (then clear) the
  * device error word: DC_EDEVICE_BOUNDS, DC_ETIMEOUT or DC_EVERIFY. */
-dc_status dc_sync(dc_plan_t plan, dc_stream_t stream);
+DC_API dc_status dc_sync(dc_plan_t plan, dc_stream_t stream);
 
 /* Device address of the bound buffer's data region (for callers that want
  * to read the device image, e.g. to check it). */
-dc_status dc_device_base(dc_plan_t plan, uint64_t* dev_base);
+DC_API dc_status dc_device_base(dc_plan_t plan, uint64_t* dev_base);
 
 /* ---- comparison path: Unified Virtual Memory (Sec. 2; Sec. 4.1.1 item 1) ----
  * dc_uvm_build replicates the host tree into managed memory, one
@@ -308,13 +315,13 @@ dc_status dc_device_base(dc_plan_t plan, uint64_t* dev_base);
  * the written arrays (all arrays with DC_COPY_ALL_ARRAYS) into the original
  * host tree: the host reads managed memory.  dc_uvm_root gives the managed
  * root's address. */
-dc_status dc_uvm_build(const dc_schema* schema, const void* host_root, dc_uvm_t* out);
-dc_status dc_uvm_root(dc_uvm_t uvm, uint64_t* managed_root);
-dc_status dc_uvm_prefetch(dc_uvm_t uvm, int to_device, dc_stream_t stream);
-dc_status dc_uvm_update(dc_uvm_t uvm, const dc_op* op, dc_stream_t stream);
-dc_status dc_uvm_copy_back(dc_uvm_t uvm, const void* host_root, uint32_t flags);
-dc_status dc_uvm_sync(dc_uvm_t uvm, dc_stream_t stream);
-dc_status dc_uvm_destroy(dc_uvm_t uvm);
+DC_API dc_status dc_uvm_build(const dc_schema* schema, const void* host_root, dc_uvm_t* out);
+DC_API dc_status dc_uvm_root(dc_uvm_t uvm, uint64_t* managed_root);
+DC_API dc_status dc_uvm_prefetch(dc_uvm_t uvm, int to_device, dc_stream_t stream);
+DC_API dc_status dc_uvm_update(dc_uvm_t uvm, const dc_op* op, dc_stream_t stream);
+DC_API dc_status dc_uvm_copy_back(dc_uvm_t uvm, const void* host_root, uint32_t flags);
+DC_API dc_status dc_uvm_sync(dc_uvm_t uvm, dc_stream_t stream);
+DC_API dc_status dc_uvm_destroy(dc_uvm_t uvm);
 
 /* ---- relocation that allocates nothing ---------------------------------------
  * The paper has no counterpart of this call; it exists for callers that
@@ -346,7 +353,7 @@ dc_status dc_uvm_destroy(dc_uvm_t uvm);
 #define DC_STATIC_MAX_BLOCKS 65536u
 #define DC_STATIC_MAX_TILES 16384u /* 8 KiB ranges of struct bytes that hold a pointer slot */
 #define DC_STATIC_SCRATCH_BYTES 1835776u /* 512 KiB records + 1 MiB lane groups + 256 KiB tile table + control words */
-dc_status dc_relocate_static(dc_plan_t plan, void* dev_data, uint64_t data_bytes, uint32_t* dev_status,
+DC_API dc_status dc_relocate_static(dc_plan_t plan, void* dev_data, uint64_t data_bytes, uint32_t* dev_status,
                              dc_stream_t stream);
 
 /* ---- host arenas (Algorithm 1's allocation requests served from one buffer) ----
@@ -361,11 +368,11 @@ dc_status dc_relocate_static(dc_plan_t plan, void* dev_data, uint64_t data_bytes
  * full; dc_host_arena_reset forgets every allocation (no plan may still use
  * them); an arena must outlive the plans that use it. */
 typedef struct dc_host_arena_s* dc_host_arena_t;
-dc_status dc_host_arena_create(uint64_t bytes, dc_host_arena_t* out);
-void* dc_host_arena_alloc(dc_host_arena_t arena, uint64_t bytes, uint64_t align);
-dc_status dc_host_arena_used(dc_host_arena_t arena, uint64_t* used);
-dc_status dc_host_arena_reset(dc_host_arena_t arena);
-dc_status dc_host_arena_destroy(dc_host_arena_t arena);
+DC_API dc_status dc_host_arena_create(uint64_t bytes, dc_host_arena_t* out);
+DC_API void* dc_host_arena_alloc(dc_host_arena_t arena, uint64_t bytes, uint64_t align);
+DC_API dc_status dc_host_arena_used(dc_host_arena_t arena, uint64_t* used);
+DC_API dc_status dc_host_arena_reset(dc_host_arena_t arena);
+DC_API dc_status dc_host_arena_destroy(dc_host_arena_t arena);
 
 /* ---- served requests (a request loop with continuous batching) ----------------
  * A server deep-copies and updates trees on request.  It owns `dev_pool`
@@ -398,22 +405,22 @@ typedef struct {
   double wall_s;                       /* time spent in dc_server_run */
 } dc_server_stats;
 #define DC_SERVER_SEQUENTIAL 1u
-dc_status dc_server_create(const dc_schema* schema, void* dev_pool, uint64_t dev_bytes, uint64_t pinned_bytes,
+DC_API dc_status dc_server_create(const dc_schema* schema, void* dev_pool, uint64_t dev_bytes, uint64_t pinned_bytes,
                            uint32_t nslots, uint32_t flags, dc_server_t* out);
 /* Run a request stream: each request is injected at its arrival time and
  * served with `op`; returns when all are done.  latency_ms[i] (may be NULL)
  * receives the time from request i's arrival to its results being in host
  * memory, or -1 if it failed (the first failure's status is returned). */
-dc_status dc_server_run(dc_server_t server, const dc_request* requests, uint64_t n, const dc_op* op,
+DC_API dc_status dc_server_run(dc_server_t server, const dc_request* requests, uint64_t n, const dc_op* op,
                         double* latency_ms);
-dc_status dc_server_stats_get(dc_server_t server, dc_server_stats* out);
-dc_status dc_server_destroy(dc_server_t server);
+DC_API dc_status dc_server_stats_get(dc_server_t server, dc_server_stats* out);
+DC_API dc_status dc_server_destroy(dc_server_t server);
 
 /* ---- misc ------------------------------------------------------------------ */
-const char* dc_last_error(void);
-const char* dc_status_name(dc_status s);
+DC_API const char* dc_last_error(void);
+DC_API const char* dc_status_name(dc_status s);
 /* Number of kernels this library has launched in this process (all paths). */
-uint64_t dc_kernel_launches(void);
+DC_API uint64_t dc_kernel_launches(void);
 
 #ifdef __cplusplus
 }

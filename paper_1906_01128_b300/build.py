@@ -29,7 +29,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not needs_build():
         return SO
     cmd = [NVCC, "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
-           "-shared", "-Xcompiler", "-fPIC,-O3,-pthread,-Wall", "-cudart", "shared",
+           "-shared", "-Xcompiler", "-fPIC,-O3,-pthread,-Wall,-fvisibility=hidden", "-cudart", "shared",
            "-Xlinker", "-rpath,/usr/local/cuda/lib64",
            "-o", SO + ".tmp"] + [os.path.join(CSRC, f) for f in SOURCES] + ["-lpthread"]
     if verbose:

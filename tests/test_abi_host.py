@@ -21,7 +21,8 @@ HEADER = os.path.join(ROOT, "include", "dc.h")
 
 def declared_functions():
     text = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:dc_status|const char\*|uint64_t|void\*)\s+(dc_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:DC_API\s+)?(?:dc_status|const char\*|uint64_t|void\*)\s+(dc_\w+)\s*\(",
+                                 text, re.M)))
 
 
 def test_library_exports_every_declared_symbol():
@@ -35,6 +36,9 @@ def test_library_exports_every_declared_symbol():
         assert getattr(dc.lib, n) is not None
     assert set(dc.SIGNATURES) | {"dc_last_error", "dc_status_name", "dc_kernel_launches",
                                  "dc_host_arena_alloc"} == set(names)
+    # and nothing but the C ABI: the library's own C++ functions stay hidden
+    internal = [line for line in out.splitlines() if " T " in line and not line.split()[-1].startswith("dc_")]
+    assert not internal, internal[:5]
 
 
 def host_image(plan, base):
