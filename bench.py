@@ -60,6 +60,8 @@ WORKLOADS = {
 NCU_TRAFFIC = {
     ("dense", 256, 4): (460_655_616, "profiles/fused_kernel_dense.md"),
     ("reloc_stress", 256, 4): (195_031_296, "profiles/relocate_kernel_reloc_stress.md"),
+    ("deep", 256, 4): (757_760_000, "profiles/fused_kernel_deep_batched.md"),
+    ("batched", 256, 4): (7_015_000_000, "profiles/fused_kernel_deep_batched.md"),
 }
 
 
@@ -294,7 +296,7 @@ def run_batched(args, rank, world):
     forest.deep_copy()
     forest.sync()
     do_flush, l2_line = l2_policy(torch, 12 * nelem + info["nrelocs"] * 20 + info["nblocks"] * 16)
-    singles = [dc.Plan(s, t.root, flags=dc.PLAN_MAP_HOST) for t in trees]
+    singles = [] if args.no_compare else [dc.Plan(s, t.root, flags=dc.PLAN_MAP_HOST) for t in trees]
     for p in singles:
         p.bind()
         p.deep_copy()
@@ -303,14 +305,15 @@ def run_batched(args, rank, world):
     clocks = Clocks()
     clocks.start()
 
-    def timed(fn, reps):
-        ts = []
+    def timed(fn, reps, label):
+        """CUDA events around each step; the timed steps sit in the NVTX range ``label``."""
         for _ in range(args.warmup):
             if do_flush:
                 flush.zero_()
             fn()
         torch.cuda.synchronize()
         torch.cuda._sleep(2_000_000)  # the device waits here, outside the events, while the host queues
+        torch.cuda.nvtx.range_push(label)
         ev = []
         for _ in range(reps):
             if do_flush:
@@ -320,19 +323,20 @@ def run_batched(args, rank, world):
             fn()
             e1.record()
             ev.append((e0, e1))
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         ts = [a.elapsed_time(b) * 1e-3 for a, b in ev]
         return statistics.median(ts), ts
 
     launches0 = dc.kernel_launches()
-    t_forest, ts_forest = timed(lambda: forest.relocate_update(op), args.steps)
-    launches = dc.kernel_launches() - launches0
+    t_forest, ts_forest = timed(lambda: forest.relocate_update(op), args.steps, "dc_step")
+    launches = dc.kernel_launches() - launches0 - args.warmup  # the timed steps' launches (one per step)
 
     def per_structure():
         for p in singles:
             p.relocate()
             p.update(op)
-    t_single, _ = timed(per_structure, max(3, args.steps // 4))
+    t_single = timed(per_structure, max(3, args.steps // 4), "dc_per_structure")[0] if singles else None
 
     def wall(fn, reps):
         ts = []
@@ -346,7 +350,7 @@ def run_batched(args, rank, world):
         return statistics.median(ts)
 
     e2e_forest = wall(lambda: forest.roundtrip(op), max(3, args.steps // 4))
-    e2e_single = wall(lambda: [p.roundtrip(op) for p in singles], 3)
+    e2e_single = wall(lambda: [p.roundtrip(op) for p in singles], 3) if singles else None
     clk = clocks.stop()
     hbm, peak_kind = peaks()
     reloc_bytes = info["nrelocs"] * 20 + info["nblocks"] * 16  # 12 B entry + 8 B slot; 8 B size + 8 B offset
@@ -376,16 +380,18 @@ def run_batched(args, rank, world):
                    "l2": l2_line},
         "roofline": {"bound": "hbm", "kernel": "fused_kernel<float, AXPY_HALF> (relocation + leaf update)",
                      "achieved": round(fused_bytes / t_mean / 1e9, 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(fused_bytes / t_mean / 1e9 / hbm, 4), "traffic": None,
+                     "frac": round(fused_bytes / t_mean / 1e9 / hbm, 4),
+                     "traffic": NCU_TRAFFIC.get(("batched", threads, ctas), (None,))[0],
                      "peak_kind": peak_kind, "algorithmic_bytes_per_launch": fused_bytes,
+                     "traffic_source": NCU_TRAFFIC.get(("batched", threads, ctas), (None, None))[1],
                      "avg_launch_us": round(t_mean * 1e6, 2)},
         "batched": {"autotuned_split": {"threads_per_cta": threads, "ctas_per_sm": ctas or "max"},
                     "device_step_ms": {"forest_one_launch": round(t_forest * 1e3, 4),
-                                       "per_structure_8192_launches": round(t_single * 1e3, 3)},
-                    "device_speedup": round(t_single / t_forest, 2),
+                                       "per_structure_8192_launches": t_single and round(t_single * 1e3, 3)},
+                    "device_speedup": t_single and round(t_single / t_forest, 2),
                     "e2e_ms": {"forest_roundtrip": round(e2e_forest * 1e3, 3),
-                               "per_structure_roundtrips": round(e2e_single * 1e3, 3)},
-                    "e2e_speedup": round(e2e_single / e2e_forest, 2)},
+                               "per_structure_roundtrips": e2e_single and round(e2e_single * 1e3, 3)},
+                    "e2e_speedup": e2e_single and round(e2e_single / e2e_forest, 2)},
         "e2e": {"value": round(payload * world / e2e_forest / 1e9, 3), "unit": "GB/s",
                 "h2d_bytes_per_step": info["data_bytes"], "d2h_bytes_per_step": 4 * nelem,
                 "api": "dc_roundtrip on the forest plan, DC_PLAN_MAP_HOST"},
