@@ -16,6 +16,8 @@
 //                     The copy back writes array interiors straight back.
 // Only pages wholly inside an array are registered, so no other object's bytes
 // are ever page-locked.
+#include <immintrin.h>
+
 #include <algorithm>
 #include <cstring>
 
@@ -197,14 +199,52 @@ dc_status launch_table(dc_plan_s* p, uint64_t desc_off, uint64_t tile_off, uint6
   return DC_OK;
 }
 
+namespace {
+
+// Copies of at least NT_MIN bytes use streaming stores: the destination lines are written without
+// being read first (a plain copy reads every destination line before writing it), and they do
+// not displace the cache.  The store fence at the end makes them visible before the copy returns.
+constexpr size_t NT_MIN = 4096;
+
+__attribute__((target("avx2"))) void copy_stream(uint8_t* dst, const uint8_t* src, size_t n) {
+  const size_t head = (32 - ((uintptr_t)dst & 31)) & 31;
+  memcpy(dst, src, head);
+  dst += head;
+  src += head;
+  n -= head;
+  size_t i = 0;
+  for (; i + 128 <= n; i += 128) {
+    const __m256i a = _mm256_loadu_si256(reinterpret_cast<const __m256i*>(src + i));
+    const __m256i b = _mm256_loadu_si256(reinterpret_cast<const __m256i*>(src + i + 32));
+    const __m256i c = _mm256_loadu_si256(reinterpret_cast<const __m256i*>(src + i + 64));
+    const __m256i d = _mm256_loadu_si256(reinterpret_cast<const __m256i*>(src + i + 96));
+    _mm256_stream_si256(reinterpret_cast<__m256i*>(dst + i), a);
+    _mm256_stream_si256(reinterpret_cast<__m256i*>(dst + i + 32), b);
+    _mm256_stream_si256(reinterpret_cast<__m256i*>(dst + i + 64), c);
+    _mm256_stream_si256(reinterpret_cast<__m256i*>(dst + i + 96), d);
+  }
+  memcpy(dst + i, src + i, n - i);
+  _mm_sfence();
+}
+
+void copy_block(uint8_t* dst, const uint8_t* src, size_t n) {
+  static const bool avx2 = __builtin_cpu_supports("avx2");
+  if (avx2 && n >= NT_MIN)
+    copy_stream(dst, src, n);
+  else
+    memcpy(dst, src, n);
+}
+
+}  // namespace
+
 void host_copy(dc_plan_s* p, const dc_plan_s::Moves& m, uint64_t ufirst, uint64_t ulast, bool to_arena) {
   auto unit = [&](uint64_t u) {
     for (uint64_t k = m.units[u].first; k < m.units[u].last; k++) {
       const auto& pc = m.pieces[k];
       if (to_arena)
-        memcpy(p->pinned + pc.off, pc.host, pc.len);
+        copy_block(p->pinned + pc.off, pc.host, pc.len);
       else
-        memcpy(pc.host, p->pinned + pc.off, pc.len);
+        copy_block(pc.host, p->pinned + pc.off, pc.len);
     }
   };
   Pool& pool = *p->pool;
