@@ -1,0 +1,77 @@
+// plan_shim.cpp — test infrastructure: the host walk and layout (build_plan)
+// behind a C entry point, built with AddressSanitizer and UBSan by
+// tests/test_host_sanitizers.py and run on the CPU.  Besides planning, it
+// checks the relocation tables the way the relocation kernel reads them:
+// every slot inside its tile, lane groups in order, and each group's base
+// plus the running prefix of its records' sizes equal to the plan's own
+// offset of every target block.
+#include <cstdio>
+
+#include "internal.hpp"
+
+namespace {
+char g_msg[256];
+int bad(const char* what, unsigned long long a, unsigned long long b) {
+  std::snprintf(g_msg, sizeof g_msg, "%s (%llu, %llu)", what, a, b);
+  return 1000;
+}
+}  // namespace
+
+extern "C" const char* shim_message() { return g_msg; }
+
+// Returns the dc_status of planning, 1000 when a table check fails (message in
+// shim_message()), else 0; out[0..5] = blocks, records, groups, listed tiles, data bytes, struct bytes.
+extern "C" int shim_plan(const dc_schema* schema, const void* const* roots, uint64_t nroots, uint64_t* out) {
+  dc_plan_s* p = new dc_plan_s;
+  int st = dc::build_plan(schema, roots, nroots, p);
+  if (st) {
+    delete p;
+    return st;
+  }
+  out[0] = p->blocks.size();
+  out[1] = p->rrec.size();
+  out[2] = p->rseg.size() - 1;
+  out[3] = p->rtiles.size();
+  out[4] = p->data_bytes;
+  out[5] = p->struct_bytes;
+  int rc = 0;
+  uint64_t seen = 0;
+  for (const dc::RelocTile& T : p->rtiles) {
+    const uint32_t nr = T.counts & 0xFFFFu, ng = T.counts >> 16;
+    const uint64_t lo = (uint64_t)T.t * dc::RELOC_SPAN, hi = std::min<uint64_t>(p->struct_bytes, lo + dc::RELOC_SPAN);
+    if (!nr || !ng || ng > dc::RELOC_MAXGROUPS || T.r0 != seen || T.g0 + ng > p->rseg.size() - 1) {
+      rc = bad("tile header", T.t, T.counts);
+      break;
+    }
+    seen = T.r0 + nr;
+    if (p->rseg[T.g0].rec_begin != T.r0 || p->rseg[T.g0 + ng].rec_begin != T.r0 + nr) {
+      rc = bad("tile groups do not cover its records", T.t, ng);
+      break;
+    }
+    for (uint32_t g = T.g0; g < T.g0 + ng && !rc; g++) {
+      const dc::RelocSeg& G = p->rseg[g];
+      uint64_t prefix = 0;
+      for (uint32_t i = G.rec_begin; i < p->rseg[g + 1].rec_begin; i++) {
+        const dc::RelocRec& R = p->rrec[i];
+        const uint64_t slot = (uint64_t)R.slot8 * 8;
+        if (slot < lo || slot + 8 > hi) {
+          rc = bad("slot outside its tile", slot, T.t);
+          break;
+        }
+        if (prefix >= (1ull << 32)) {
+          rc = bad("group prefix reaches 2^32", g, prefix);
+          break;
+        }
+        if ((G.base16 + prefix) * 16 != p->rec_off[i]) {
+          rc = bad("base + prefix differs from the plan's offset", (G.base16 + prefix) * 16, p->rec_off[i]);
+          break;
+        }
+        prefix += R.size16;
+      }
+    }
+    if (rc) break;
+  }
+  if (!rc && seen != p->rrec.size()) rc = bad("records outside every tile", seen, p->rrec.size());
+  delete p;
+  return rc;
+}

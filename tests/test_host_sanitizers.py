@@ -1,0 +1,82 @@
+"""The host walk and layout under AddressSanitizer and UBSan (CPU only).
+
+plan.cpp and a small shim (tests/sanitize/plan_shim.cpp) are compiled with
+-fsanitize=address,undefined and driven, in a child process with the ASan
+runtime preloaded, over the test trees, random schemas, forests and the
+planning errors (NULL with a count, aliases, cycles).  Any memory error or
+undefined behaviour aborts the child.  The shim also checks the relocation
+tables the way the relocation kernel reads them (every slot inside its tile,
+groups in order, each group's base plus the prefix of sizes equal to the
+plan's offset of every target block)."""
+import os
+import shutil
+import subprocess
+import sys
+import textwrap
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(ROOT, "paper_1906_01128_b300", "csrc")
+CUDA = "/usr/local/cuda"
+
+DRIVER = textwrap.dedent(r'''
+    import ctypes, random, sys
+    sys.path.insert(0, ROOT)
+    import treegen as tg
+    from paper_1906_01128_b300 import schema_struct
+    lib = ctypes.CDLL(SO)
+    lib.shim_plan.restype = ctypes.c_int
+    lib.shim_plan.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]
+    lib.shim_message.restype = ctypes.c_char_p
+
+    def plan(schema, roots):
+        cs, keep = schema_struct(schema)
+        arr = (ctypes.c_void_p * len(roots))(*roots)
+        out = (ctypes.c_uint64 * 6)()
+        rc = lib.shim_plan(ctypes.byref(cs), arr, len(roots), out)
+        if rc == 1000:
+            raise SystemExit("table check: " + lib.shim_message().decode())
+        return rc, list(out)
+
+    trees = [tg.workload("tiny"), tg.node_tree(3, 16, tg.lognormal(300, 1.2, 5000), seed=2),
+             tg.node_tree(4, 3, tg.uniform(0, 9), seed=4), tg.linear_tree(6, 100, "llinit", seed=5),
+             tg.dense_tree(3, 7, 3, seed=6), tg.listing1_tree(50, seed=7), tg.node_tree(5, 16, 3, seed=1)]
+    rng = random.Random(11)
+    for i in range(80):
+        s, levels, rules = tg.random_schema(rng)
+        trees.append(tg.Tree(s, levels, rules, seed=2000 + i))
+    n = 0
+    for t in trees:
+        rc, out = plan(t.schema, [t.root])
+        assert rc == 0, (t.name, rc)
+        n += out[0]
+    forest = tg.batched(40, seed=9, t_max=256 << 10)
+    rc, out = plan(forest[0].schema, [t.root for t in forest])
+    assert rc == 0, rc
+    # planning errors: the same tree twice in a forest (alias), a NULL root in a forest
+    rc, _ = plan(forest[0].schema, [forest[0].root, forest[0].root])
+    assert rc != 0
+    print("planned", len(trees) + 1, "trees,", n, "blocks")
+''')
+
+
+def test_plan_under_asan_and_ubsan(tmp_path):
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("no g++")
+    so = str(tmp_path / "libplan_asan.so")
+    cmd = [gxx, "-std=c++17", "-O1", "-g", "-fsanitize=address,undefined", "-fno-sanitize-recover=all",
+           "-fno-omit-frame-pointer", "-shared", "-fPIC", f"-I{CUDA}/include", f"-I{CSRC}",
+           os.path.join(CSRC, "plan.cpp"), os.path.join(HERE, "sanitize", "plan_shim.cpp"),
+           f"-L{CUDA}/lib64", "-lcudart", f"-Wl,-rpath,{CUDA}/lib64", "-o", so]
+    subprocess.run(cmd, check=True, capture_output=True, text=True)
+    asan = subprocess.run([gxx, "-print-file-name=libasan.so"], capture_output=True, text=True).stdout.strip()
+    ubsan = subprocess.run([gxx, "-print-file-name=libubsan.so"], capture_output=True, text=True).stdout.strip()
+    env = dict(os.environ, LD_PRELOAD=f"{asan}:{ubsan}", ASAN_OPTIONS="detect_leaks=0",
+               UBSAN_OPTIONS="halt_on_error=1:print_stacktrace=1")
+    code = f"ROOT = {ROOT!r}\nSO = {so!r}\n" + DRIVER
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, (r.stdout[-3000:], r.stderr[-3000:])
+    assert "planned" in r.stdout
