@@ -130,6 +130,7 @@ struct LeafArgs {
   int kind;        // dc_op_kind
   int f64;         // element type: 0 f32, 1 f64
   double scale;
+  uint32_t* ctrl;  // the plan's control words (error bits)
 };
 
 // One block to move between host and device memory: src and dst are device-

@@ -27,6 +27,10 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "internal.hpp"
 
@@ -381,6 +385,133 @@ __global__ void __launch_bounds__(LEAF_THREADS) leaf_kernel(LeafArgs a) {
 // two are independent (the leaf kernel works through addresses resolved on
 // the host, the relocation writes only pointer slots), so one launch over a
 // forest replaces two per structure.
+// ---- leaf update with its operands staged by 1-D bulk copies -----------------
+
+constexpr uint32_t LSTAGES = 3;  // tiles in flight per CTA
+constexpr size_t LEAF_TILE_BYTES = (size_t)LEAF_TILE * 16;
+
+// Dynamic shared memory of leaf_tma_kernel: per stage one tile of x (and of y
+// for AXPY_HALF), then the stage headers and barriers.
+template <int KIND>
+constexpr size_t leaf_tma_smem() {
+  return LSTAGES * (KIND == DC_OP_AXPY_HALF ? 2 : 1) * LEAF_TILE_BYTES + LSTAGES * (8 + 16);
+}
+
+// The producer (thread 0) stages tile t in stage s: a tile inside one segment
+// comes by bulk copies (its x and y units are contiguous and 16-byte
+// aligned); a tile across segments, or t past the end, is marked for the
+// direct path or as the end.
+template <int KIND>
+__device__ __forceinline__ void leaf_issue(const LeafArgs& a, uint4* buf, uint64_t* bar, uint4* hdr, uint32_t s,
+                                           uint64_t t, uint64_t ntiles) {
+  constexpr uint32_t NB = KIND == DC_OP_AXPY_HALF ? 2 : 1;
+  if (t >= ntiles) {
+    hdr[s] = make_uint4(NONE, NONE, 0, 0);
+    mbar_arrive_tx(&bar[s], 0);
+    return;
+  }
+  const uint32_t lo = __ldg(&a.tile_seg[t]), hi = __ldg(&a.tile_seg[t + 1]);
+  const uint64_t u0 = t * LEAF_TILE, u1 = min(u0 + LEAF_TILE, a.units);
+  if (lo != hi || lo >= a.nseg) {  // across segments: the direct path
+    hdr[s] = make_uint4((uint32_t)t, (uint32_t)(t >> 32), 0, 0);
+    mbar_arrive_tx(&bar[s], 0);
+    return;
+  }
+  const Segment g = a.seg[lo];
+  const uint32_t bytes = (uint32_t)((u1 - u0) * 16);
+  hdr[s] = make_uint4((uint32_t)t, (uint32_t)(t >> 32), 1, (uint32_t)(u1 - u0));
+  mbar_arrive_tx(&bar[s], NB * bytes);
+  bulk_load(buf + (size_t)s * NB * LEAF_TILE, reinterpret_cast<const void*>(g.x + (u0 - g.ubeg) * 16), bytes, &bar[s]);
+  if (KIND == DC_OP_AXPY_HALF)
+    bulk_load(buf + ((size_t)s * NB + 1) * LEAF_TILE, reinterpret_cast<const void*>(g.y + (u0 - g.ubeg) * 16), bytes,
+              &bar[s]);
+}
+
+// The leaf update with x and y of each tile brought into shared memory by the
+// tensor-memory-access engine, LSTAGES tiles in flight per CTA; the update
+// runs in registers and x goes back by coalesced 16-byte stores.  Tiles
+// t = blockIdx.x + k * gridDim.x.  Every wait has an iteration limit.
+template <typename T, int KIND, uint32_t THREADS>
+__global__ void __launch_bounds__(THREADS) leaf_tma_kernel(LeafArgs a) {
+  using VT = typename V16<T>::type;
+  constexpr int EPU = V16<T>::N;
+  constexpr uint32_t NB = KIND == DC_OP_AXPY_HALF ? 2 : 1;
+  constexpr uint32_t UNROLL = LEAF_TILE / THREADS;
+  extern __shared__ __align__(128) uint8_t dsm[];
+  uint4* buf = reinterpret_cast<uint4*>(dsm);
+  uint4* hdr = reinterpret_cast<uint4*>(dsm + LSTAGES * NB * LEAF_TILE_BYTES);  // 16-byte aligned
+  uint64_t* bar = reinterpret_cast<uint64_t*>(hdr + LSTAGES);
+  const uint32_t tid = threadIdx.x;
+  const T sc = (T)a.scale;
+  const uint64_t ntiles = (a.units + LEAF_TILE - 1) / LEAF_TILE;
+  if (blockIdx.x >= ntiles) return;
+  if (tid == 0) {
+    for (uint32_t s = 0; s < LSTAGES; s++) mbar_init(&bar[s]);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  uint64_t tn = blockIdx.x;  // the producer's next tile
+  if (tid == 0)
+    for (uint32_t s = 0; s < LSTAGES; s++, tn += gridDim.x) leaf_issue<KIND>(a, buf, bar, hdr, s, tn, ntiles);
+  for (uint32_t k = 0;; k++) {
+    const uint32_t s = k % LSTAGES, parity = (k / LSTAGES) & 1;
+    bool late = false;
+    uint32_t spins = 0;
+    while (!mbar_try_wait(&bar[s], parity))
+      if (++spins >= WAIT_LIMIT) {
+        late = true;
+        break;
+      }
+    if (__syncthreads_or(late)) {
+      if (tid == 0) {  // give the copies in flight another bounded wait before leaving
+        atomicOr(&a.ctrl[CTRL_ERR], ERR_TIMEOUT);
+        for (uint32_t q = 0; q < LSTAGES; q++) {
+          const uint32_t kq = k + q;
+          for (uint32_t n = 0; n < WAIT_LIMIT && !mbar_try_wait(&bar[kq % LSTAGES], (kq / LSTAGES) & 1); n++) {
+          }
+        }
+      }
+      break;
+    }
+    const uint4 h = hdr[s];
+    if (h.x == NONE && h.y == NONE) break;  // uniform
+    const uint64_t t = (uint64_t)h.x | ((uint64_t)h.y << 32);
+    if (h.z == 0) {
+      leaf_tile<T, KIND, THREADS>(a, t);
+    } else {
+      const Segment g = a.seg[__ldg(&a.tile_seg[t])];
+      const uint64_t u0 = t * LEAF_TILE;
+      const VT* xs = reinterpret_cast<const VT*>(buf + (size_t)s * NB * LEAF_TILE);
+      const VT* ys = reinterpret_cast<const VT*>(buf + ((size_t)s * NB + (NB - 1)) * LEAF_TILE);
+#pragma unroll
+      for (uint32_t i = 0; i < UNROLL; i++) {
+        const uint32_t j = tid + i * THREADS;
+        if (j >= h.w) break;
+        const uint64_t e0 = (u0 + j - g.ubeg) * EPU;
+        const uint64_t left = g.n - e0;
+        VT xv = xs[j];
+        const VT yv = ys[j];
+        T* x = reinterpret_cast<T*>(&xv);
+        const T* y = reinterpret_cast<const T*>(&yv);
+        if (left >= (uint64_t)EPU) {
+#pragma unroll
+          for (int q = 0; q < EPU; q++) x[q] = apply<T, KIND>(x[q], KIND == DC_OP_AXPY_HALF ? y[q] : T(0), sc);
+          stcs(reinterpret_cast<VT*>(g.x + e0 * sizeof(T)), xv);
+        } else {
+          T* xd = reinterpret_cast<T*>(g.x + e0 * sizeof(T));
+          for (uint32_t q = 0; q < (uint32_t)left; q++)
+            xd[q] = apply<T, KIND>(x[q], KIND == DC_OP_AXPY_HALF ? y[q] : T(0), sc);
+        }
+      }
+    }
+    __syncthreads();  // nobody reads stage s any more
+    if (tid == 0) {
+      leaf_issue<KIND>(a, buf, bar, hdr, s, tn, ntiles);
+      if (tn < ntiles) tn += gridDim.x;
+    }
+  }
+}
+
 template <typename T, int KIND, uint32_t THREADS>
 // CTAs take leaf tiles from a counter, so the ones that relocated take fewer.
 // The last CTA to finish resets the counter for the next launch (launches on
@@ -590,10 +721,22 @@ __global__ void walk_kernel(uint64_t root, const ChaseStep* steps, uint32_t nste
   *out = p + final_add;
 }
 
+// Resident CTAs per SM of `kernel` at `threads` threads and `smem` bytes of
+// dynamic shared memory, computed once per (kernel, threads, smem); a kernel
+// that needs more than the default 48 KiB of dynamic shared memory is allowed
+// it on first use.
 template <typename K>
 int occupancy(K kernel, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, int, size_t>, int> cache;
+  std::lock_guard<std::mutex> g(mu);
+  const auto key = std::make_tuple(reinterpret_cast<const void*>(kernel), threads, smem);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  if (smem > (48u << 10)) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1) n = 1;
+  cache.emplace(key, n);
   return n;
 }
 
@@ -601,7 +744,7 @@ int occupancy(K kernel, int threads, size_t smem) {
 
 cudaError_t launch_relocate(const RelocArgs& a, cudaStream_t s, int sm_count) {
   if (a.ntiles == 0) return cudaSuccess;
-  static int occ = occupancy(relocate_kernel<false>, RELOC_THREADS, 0);
+  const int occ = occupancy(relocate_kernel<false>, RELOC_THREADS, 0);
   const uint32_t grid = (uint32_t)std::min<uint64_t>(a.ntiles, (uint64_t)sm_count * occ);  // persistent CTAs
   if (a.verify)
     relocate_kernel<true><<<grid, RELOC_THREADS, 0, s>>>(a);
@@ -614,9 +757,29 @@ cudaError_t launch_relocate(const RelocArgs& a, cudaStream_t s, int sm_count) {
 cudaError_t launch_leaf(const LeafArgs& a, cudaStream_t s, int sm_count) {
   if (a.units == 0 || a.nseg == 0) return cudaSuccess;
   uint64_t tiles = (a.units + LEAF_TILE - 1) / LEAF_TILE;
+  static const bool tma = [] {
+    const char* v = getenv("DC_LEAF_TMA");
+    return v && *v && v[0] != '0';
+  }();
+  if (tma) {
+    auto go_tma = [&](auto kernel, size_t smem) {
+      const int occ = occupancy(kernel, LEAF_THREADS, smem);
+      uint32_t grid = (uint32_t)std::min<uint64_t>(tiles, (uint64_t)sm_count * occ);
+      kernel<<<grid, LEAF_THREADS, smem, s>>>(a);
+    };
+    if (a.f64)
+      a.kind == DC_OP_AXPY_HALF
+          ? go_tma(leaf_tma_kernel<double, DC_OP_AXPY_HALF, LEAF_THREADS>, leaf_tma_smem<DC_OP_AXPY_HALF>())
+          : go_tma(leaf_tma_kernel<double, DC_OP_SCALE, LEAF_THREADS>, leaf_tma_smem<DC_OP_SCALE>());
+    else
+      a.kind == DC_OP_AXPY_HALF
+          ? go_tma(leaf_tma_kernel<float, DC_OP_AXPY_HALF, LEAF_THREADS>, leaf_tma_smem<DC_OP_AXPY_HALF>())
+          : go_tma(leaf_tma_kernel<float, DC_OP_SCALE, LEAF_THREADS>, leaf_tma_smem<DC_OP_SCALE>());
+    count_launch();
+    return cudaGetLastError();
+  }
   auto go = [&](auto kernel) {
-    static int occ = 0;
-    if (!occ) occ = occupancy(kernel, LEAF_THREADS, 0);
+    const int occ = occupancy(kernel, LEAF_THREADS, 0);
     uint32_t grid = (uint32_t)std::min<uint64_t>(tiles, (uint64_t)sm_count * occ);
     kernel<<<grid, LEAF_THREADS, 0, s>>>(a);
   };
@@ -632,8 +795,7 @@ cudaError_t launch_chase(const ChaseArgs& a, cudaStream_t s, int sm_count) {
   if (a.elems == 0 || a.nseg == 0) return cudaSuccess;
   uint64_t tiles = (a.elems + CHASE_TILE - 1) / CHASE_TILE;
   auto go = [&](auto kernel) {
-    static int occ = 0;
-    if (!occ) occ = occupancy(kernel, CHASE_THREADS, 0);
+    const int occ = occupancy(kernel, CHASE_THREADS, 0);
     uint32_t grid = (uint32_t)std::min<uint64_t>(tiles, (uint64_t)sm_count * occ);
     kernel<<<grid, CHASE_THREADS, 0, s>>>(a);
   };
@@ -683,7 +845,7 @@ cudaError_t launch_fused(const RelocArgs& r, const LeafArgs& l, uint32_t threads
 
 cudaError_t launch_move(const MoveArgs& a, cudaStream_t s, int sm_count) {
   if (a.units == 0 || a.nd == 0) return cudaSuccess;
-  static int occ = occupancy(move_kernel, LEAF_THREADS, 0);
+  const int occ = occupancy(move_kernel, LEAF_THREADS, 0);
   uint64_t tiles = (a.units + LEAF_TILE - 1) / LEAF_TILE;
   uint32_t grid = (uint32_t)std::min<uint64_t>(tiles, (uint64_t)sm_count * occ);
   move_kernel<<<grid, LEAF_THREADS, 0, s>>>(a);
@@ -695,8 +857,7 @@ cudaError_t launch_stream(const StreamArgs& a, cudaStream_t s, int sm_count) {
   if (a.units == 0 || a.nseg == 0 || a.t_end <= a.t_begin) return cudaSuccess;
   const uint64_t tiles = a.t_end - a.t_begin;
   auto go = [&](auto kernel) {
-    static int occ = 0;
-    if (!occ) occ = occupancy(kernel, LEAF_THREADS, 0);
+    const int occ = occupancy(kernel, LEAF_THREADS, 0);
     uint32_t grid = (uint32_t)std::min<uint64_t>(tiles, (uint64_t)sm_count * occ);
     kernel<<<grid, LEAF_THREADS, 0, s>>>(a);
   };

@@ -529,6 +529,7 @@ LeafArgs dc::leaf_args(const dc_plan_s* p, const dc_op* op) {
   a.kind = op->kind;
   a.f64 = X.elem_kind == DC_E_F64;
   a.scale = op->scale;
+  a.ctrl = reinterpret_cast<uint32_t*>(p->dev + p->L.ctrl);
   return a;
 }
 
