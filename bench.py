@@ -97,7 +97,8 @@ class Clocks:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,"
+                 "clocks.mem,temperature.gpu,temperature.memory",
                  "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
             t0 = time.time()  # the timed region starts once the sampler is producing
             while time.time() - t0 < wait_s and os.path.getsize(self.path) == 0:
@@ -112,7 +113,7 @@ class Clocks:
         self.proc.wait()
         self.f.close()
         dev = int(os.environ.get("LOCAL_RANK", "0"))
-        sm, mx, reasons = [], [], set()
+        sm, mx, mem, temps, reasons = [], [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             c = [x.strip() for x in line.split(",")]
@@ -128,8 +129,18 @@ class Clocks:
             for n, v in zip(names, c[5:9]):
                 if v.lower() == "active":
                     reasons.add(n)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+            for lst, k in ((mem, 9), (temps, 10)):
+                try:
+                    lst.append(float(c[k]))
+                except (ValueError, IndexError):
+                    pass
+        out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+               "reasons": sorted(reasons), "samples": len(sm)}
+        if mem:
+            out["mem_mhz"] = {"min": min(mem), "median": statistics.median(mem)}
+        if temps:
+            out["gpu_temp_c_max"] = max(temps)
+        return out
 
 
 def rank_seed(workload: str, rank: int) -> int:
