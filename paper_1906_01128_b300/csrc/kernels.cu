@@ -387,39 +387,42 @@ __global__ void __launch_bounds__(LEAF_THREADS) leaf_kernel(LeafArgs a) {
 // forest replaces two per structure.
 // ---- leaf update with its operands staged by 1-D bulk copies -----------------
 
-constexpr uint32_t LSTAGES = 3;  // tiles in flight per CTA
+constexpr uint32_t LSTAGES = 2;  // tiles in flight per CTA
 constexpr size_t LEAF_TILE_BYTES = (size_t)LEAF_TILE * 16;
 
 // Dynamic shared memory of leaf_tma_kernel: per stage one tile of x (and of y
 // for AXPY_HALF), then the stage headers and barriers.
 template <int KIND>
 constexpr size_t leaf_tma_smem() {
-  return LSTAGES * (KIND == DC_OP_AXPY_HALF ? 2 : 1) * LEAF_TILE_BYTES + LSTAGES * (8 + 16);
+  return LSTAGES * (KIND == DC_OP_AXPY_HALF ? 2 : 1) * LEAF_TILE_BYTES + LSTAGES * (8 + 32);
 }
 
 // The producer (thread 0) stages tile t in stage s: a tile inside one segment
 // comes by bulk copies (its x and y units are contiguous and 16-byte
 // aligned); a tile across segments, or t past the end, is marked for the
-// direct path or as the end.
+// direct path or as the end.  hdr[2s] = (t, mode, units), hdr[2s+1] = the
+// destination of the tile's first unit and the elements left from it.
 template <int KIND>
 __device__ __forceinline__ void leaf_issue(const LeafArgs& a, uint4* buf, uint64_t* bar, uint4* hdr, uint32_t s,
                                            uint64_t t, uint64_t ntiles) {
   constexpr uint32_t NB = KIND == DC_OP_AXPY_HALF ? 2 : 1;
   if (t >= ntiles) {
-    hdr[s] = make_uint4(NONE, NONE, 0, 0);
+    hdr[2 * s] = make_uint4(NONE, NONE, 0, 0);
     mbar_arrive_tx(&bar[s], 0);
     return;
   }
   const uint32_t lo = __ldg(&a.tile_seg[t]), hi = __ldg(&a.tile_seg[t + 1]);
   const uint64_t u0 = t * LEAF_TILE, u1 = min(u0 + LEAF_TILE, a.units);
   if (lo != hi || lo >= a.nseg) {  // across segments: the direct path
-    hdr[s] = make_uint4((uint32_t)t, (uint32_t)(t >> 32), 0, 0);
+    hdr[2 * s] = make_uint4((uint32_t)t, (uint32_t)(t >> 32), 0, 0);
     mbar_arrive_tx(&bar[s], 0);
     return;
   }
   const Segment g = a.seg[lo];
   const uint32_t bytes = (uint32_t)((u1 - u0) * 16);
-  hdr[s] = make_uint4((uint32_t)t, (uint32_t)(t >> 32), 1, (uint32_t)(u1 - u0));
+  const uint64_t x0 = g.x + (u0 - g.ubeg) * 16, left = g.n - (u0 - g.ubeg) * (16 / (a.f64 ? 8 : 4));
+  hdr[2 * s] = make_uint4((uint32_t)t, (uint32_t)(t >> 32), 1, (uint32_t)(u1 - u0));
+  hdr[2 * s + 1] = make_uint4((uint32_t)x0, (uint32_t)(x0 >> 32), (uint32_t)left, (uint32_t)(left >> 32));
   mbar_arrive_tx(&bar[s], NB * bytes);
   bulk_load(buf + (size_t)s * NB * LEAF_TILE, reinterpret_cast<const void*>(g.x + (u0 - g.ubeg) * 16), bytes, &bar[s]);
   if (KIND == DC_OP_AXPY_HALF)
@@ -439,8 +442,8 @@ __global__ void __launch_bounds__(THREADS) leaf_tma_kernel(LeafArgs a) {
   constexpr uint32_t UNROLL = LEAF_TILE / THREADS;
   extern __shared__ __align__(128) uint8_t dsm[];
   uint4* buf = reinterpret_cast<uint4*>(dsm);
-  uint4* hdr = reinterpret_cast<uint4*>(dsm + LSTAGES * NB * LEAF_TILE_BYTES);  // 16-byte aligned
-  uint64_t* bar = reinterpret_cast<uint64_t*>(hdr + LSTAGES);
+  uint4* hdr = reinterpret_cast<uint4*>(dsm + LSTAGES * NB * LEAF_TILE_BYTES);  // 16-byte aligned, 2 per stage
+  uint64_t* bar = reinterpret_cast<uint64_t*>(hdr + 2 * LSTAGES);
   const uint32_t tid = threadIdx.x;
   const T sc = (T)a.scale;
   const uint64_t ntiles = (a.units + LEAF_TILE - 1) / LEAF_TILE;
@@ -473,22 +476,22 @@ __global__ void __launch_bounds__(THREADS) leaf_tma_kernel(LeafArgs a) {
       }
       break;
     }
-    const uint4 h = hdr[s];
+    const uint4 h = hdr[2 * s];
     if (h.x == NONE && h.y == NONE) break;  // uniform
     const uint64_t t = (uint64_t)h.x | ((uint64_t)h.y << 32);
     if (h.z == 0) {
       leaf_tile<T, KIND, THREADS>(a, t);
     } else {
-      const Segment g = a.seg[__ldg(&a.tile_seg[t])];
-      const uint64_t u0 = t * LEAF_TILE;
+      const uint4 h2 = hdr[2 * s + 1];
+      const uint64_t x0 = (uint64_t)h2.x | ((uint64_t)h2.y << 32), left0 = (uint64_t)h2.z | ((uint64_t)h2.w << 32);
       const VT* xs = reinterpret_cast<const VT*>(buf + (size_t)s * NB * LEAF_TILE);
       const VT* ys = reinterpret_cast<const VT*>(buf + ((size_t)s * NB + (NB - 1)) * LEAF_TILE);
 #pragma unroll
       for (uint32_t i = 0; i < UNROLL; i++) {
         const uint32_t j = tid + i * THREADS;
         if (j >= h.w) break;
-        const uint64_t e0 = (u0 + j - g.ubeg) * EPU;
-        const uint64_t left = g.n - e0;
+        const uint64_t e0 = (uint64_t)j * EPU;  // from the tile's first element
+        const uint64_t left = left0 - e0;
         VT xv = xs[j];
         const VT yv = ys[j];
         T* x = reinterpret_cast<T*>(&xv);
@@ -496,9 +499,9 @@ __global__ void __launch_bounds__(THREADS) leaf_tma_kernel(LeafArgs a) {
         if (left >= (uint64_t)EPU) {
 #pragma unroll
           for (int q = 0; q < EPU; q++) x[q] = apply<T, KIND>(x[q], KIND == DC_OP_AXPY_HALF ? y[q] : T(0), sc);
-          stcs(reinterpret_cast<VT*>(g.x + e0 * sizeof(T)), xv);
+          stcs(reinterpret_cast<VT*>(x0 + e0 * sizeof(T)), xv);
         } else {
-          T* xd = reinterpret_cast<T*>(g.x + e0 * sizeof(T));
+          T* xd = reinterpret_cast<T*>(x0 + e0 * sizeof(T));
           for (uint32_t q = 0; q < (uint32_t)left; q++)
             xd[q] = apply<T, KIND>(x[q], KIND == DC_OP_AXPY_HALF ? y[q] : T(0), sc);
         }
