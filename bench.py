@@ -65,6 +65,24 @@ NCU_TRAFFIC = {
 }
 
 
+def copy_check(torch, nbytes=1 << 30, reps=5):
+    """A plain device-to-device copy (torch) timed in this process just before the timed steps: the
+    HBM bandwidth the GPU gives right now, for comparison with the measured peak."""
+    a = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    b = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    best = 0.0
+    for _ in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.copy_(a)
+        e1.record()
+        e1.synchronize()
+        best = max(best, 2 * nbytes / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    del a, b
+    torch.cuda.empty_cache()
+    return round(best, 1)
+
+
 def l2_policy(torch, step_bytes):
     """Whether to flush L2 between timed steps, and the line that says so."""
     l2 = torch.cuda.get_device_properties(torch.cuda.current_device()).L2_cache_size
@@ -709,6 +727,7 @@ def main():
         barrier()
         return [[e[i].elapsed_time(e[i + 1]) * 1e-3 for e in ev] for i in range(len(parts))]
 
+    copy_now = copy_check(torch)
     clocks = Clocks()
     clocks.start()
     # ---- device-resident step: relocation + leaf update in one launch -------
@@ -738,6 +757,7 @@ def main():
                 "median_launch_us": round(fused_med * 1e6, 2),
                 "frac_at_median": round(fused_bytes / fused_med / 1e9 / hbm, 4),
                 "split": {"threads_per_cta": tuned[0], "ctas_per_sm": tuned[1]},
+                "step_us": [round(x * 1e6, 1) for x in t_fused],
                 "traffic_source": NCU_TRAFFIC.get((args.workload,) + tuple(tuned), (None, None))[1]}
     leaf = {"kernel": "leaf_kernel<float, AXPY_HALF>", "algorithmic_bytes": leaf_bytes,
             "avg_launch_us": round(leaf_avg * 1e6, 2), "median_launch_us": round(leaf_med * 1e6, 2),
@@ -880,6 +900,7 @@ def main():
                            "frac": round(reloc_bytes / reloc_avg / 1e9 / hbm, 4), "record_bytes_moved": reloc_moved},
             "two_launch_step_us": round((reloc_avg + leaf_avg) * 1e6, 2),
             "step_median_ms": round(step_median * 1e3, 4),
+            "hbm_copy_gbs_now": copy_now,
             "host_side": host_side,
             "e2e": e2e, "e2e_three_calls_map_host": e2e_mapped, "e2e_staged": e2e_staged, "link": link, "compare": compare, "cpu_baseline": cpu,
             "clocks": clk,
