@@ -43,15 +43,17 @@ const char* last_error();
 // relocation tile is such a range; its records are grouped by lane, each
 // group holding consecutive target blocks.
 //
-// One pointer slot: the target block's padded size in 16-byte units and the
-// slot's arena byte offset / 8 (slots are 8-byte aligned).
+// One pointer slot: the target block's arena offset / 16 relative to its lane
+// group's base, and where the slot is: its 8-byte word within the tile (low 16
+// bits) and its lane group's index within the tile (high 16 bits).
 struct RelocRec {
-  uint32_t size16;
-  uint32_t slot8;
+  uint32_t off16;
+  uint32_t where;
 };
 static_assert(sizeof(RelocRec) == 8, "RelocRec is 8 bytes");
 // One (tile, lane) group: the arena offset / 16 of its first target block and
-// the index of its first record.  The table ends with a group whose
+// the index of its first record; the plan starts a new group where a target
+// lies 2^32 units or more past the base.  The table ends with a group whose
 // rec_begin is the record count.
 struct RelocSeg {
   uint64_t base16;

@@ -2,12 +2,11 @@
 //
 //   relocate_kernel  Fig 2 step d / Algorithm 1's attach loop: one pass over
 //                    the struct lane in RELOC_SPAN-byte tiles.  A tile stages
-//                    its struct bytes in shared memory, computes the arena
-//                    offset of every block its slots point at (an exclusive
-//                    scan of the 16-byte block sizes with warp shuffles, on top
-//                    of each lane group's base offset), writes each block's
-//                    device address into its slot, and stores the tile back:
-//                    whole coalesced sectors instead of one 8-byte store per
+//                    its struct bytes in shared memory, writes into each of
+//                    its slots the device address of the block it points at
+//                    (the arena base + the slot's lane group base + the
+//                    record's offset), and stores the tile back: whole
+//                    coalesced sectors instead of one 8-byte store per
 //                    pointer.
 //   leaf_kernel      the leaf update through resolved effective addresses
 //                    (Sec. 3): x += 0.5*y or x *= scale over (x, y, n)
@@ -37,15 +36,6 @@
 namespace dc {
 
 namespace {
-
-__device__ __forceinline__ uint32_t warp_incl_scan32(uint32_t v, uint32_t lane) {
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const uint32_t o = __shfl_up_sync(0xffffffffu, v, d);
-    if (lane >= (uint32_t)d) v += o;
-  }
-  return v;
-}
 
 // ---- 1-D bulk copies (TMA) and mbarriers ------------------------------------
 
@@ -99,8 +89,6 @@ struct __align__(16) RelocSmem {
   RelocStage st[RSTAGES];
   uint64_t bar[RSTAGES];
   uint4 hdr[RSTAGES];  // the staged tile: (t, r0, r1, ng); t = NONE ends the CTA's tiles
-  uint4 gb[RELOC_MAXGROUPS];  // per lane group: base offset / 16 (x, y) and minus its first record's size prefix (z)
-  uint32_t warp_sum[32];
 };
 
 // The producer (thread 0) fills stage s with listed tile i of the CTA (or
@@ -134,18 +122,15 @@ __device__ __forceinline__ void issue_tile(const RelocArgs& a, RelocSmem& sm, ui
 // Every listed relocation tile i = blockIdx.x + k * gridDim.x, through a
 // two-stage pipeline: while the CTA rewrites the slots of one staged tile,
 // the bulk copies of the next are in flight, and the producer has the header
-// after that in a register.  The sizes are scanned with warp shuffles, slice
-// by slice, then across the warps.  Sizes and prefixes are 32-bit: the plan splits lane groups so that the blocks of one
-// group total less than 2^32 units, and a block's offset is its group's base
-// plus a difference of two prefixes, exact modulo 2^32.  The staged tile is
-// written back by one bulk store.  The loop's exits are uniform across the
+// after that in a register.  A slot's target lies at its lane group's base
+// plus the record's 32-bit offset (both in 16-byte units); the rewritten
+// staged tile goes back by one bulk store.  The loop's exits are uniform across the
 // CTA; every wait has an iteration limit.
 template <uint32_t THREADS, bool VERIFY>
 __device__ __forceinline__ void reloc_tiles(const RelocArgs& a, RelocSmem& sm) {
-  constexpr uint32_t NW = THREADS / 32;
   constexpr uint32_t ITEMS = RELOC_MAXREC / THREADS;
   static_assert(ITEMS * THREADS == RELOC_MAXREC, "tile shape");
-  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t tid = threadIdx.x;
   uint32_t* err = &a.ctrl[CTRL_ERR];
   if (blockIdx.x >= a.ntiles) return;
   const uint4* hdrs = reinterpret_cast<const uint4*>(a.tiles);
@@ -192,59 +177,27 @@ __device__ __forceinline__ void reloc_tiles(const RelocArgs& a, RelocSmem& sm) {
     const uint32_t t = h.x, r0 = h.y, nr = h.z - h.y, ng = h.w, sh = r0 & 1u;
     const uint64_t lo = (uint64_t)t * RELOC_SPAN, hi = min(a.struct_bytes, lo + RELOC_SPAN);
     if (nr) {  // uniform
-      // records warp-striped: warp w owns [w*32*ITEMS, (w+1)*32*ITEMS), its lane L the records k*32 + L
-      // (conflict-free shared loads; slot writes of consecutive records land 8 bytes x stride apart)
-      const uint32_t wb = warp * 32 * ITEMS;
+      // record j goes to thread j % THREADS: conflict-free shared loads, and the
+      // slot writes of a warp land in a few hundred consecutive bytes
       uint2 r[ITEMS];
 #pragma unroll
       for (uint32_t i = 0; i < ITEMS; i++) {
-        const uint32_t j = wb + i * 32 + lane;
+        const uint32_t j = tid + i * THREADS;
         r[i] = j < nr ? S.rec[sh + j] : make_uint2(0, 0);
       }
-      // exclusive prefix of the sizes inside the warp's span, slice by slice, then across warps
-      uint32_t ex[ITEMS];
-      uint32_t carry = 0;
-#pragma unroll
-      for (uint32_t i = 0; i < ITEMS; i++) {
-        const uint32_t incl = warp_incl_scan32(r[i].x, lane);
-        ex[i] = carry + incl - r[i].x;
-        carry += __shfl_sync(0xffffffffu, incl, 31);
-      }
-      if (lane == 0) sm.warp_sum[warp] = carry;
-      __syncthreads();
-      uint32_t wt = lane < NW ? sm.warp_sum[lane] : 0u;
-      wt = warp_incl_scan32(wt, lane);
-      const uint32_t wpre = warp ? __shfl_sync(0xffffffffu, wt, (warp - 1) & 31) : 0u;
-      // each record's lane group (ascending with the record index) and every group's start prefix
-      uint32_t grp[ITEMS];
-      uint32_t g = 0;
-#pragma unroll
-      for (uint32_t i = 0; i < ITEMS; i++) {
-        ex[i] += wpre;
-        const uint32_t j = wb + i * 32 + lane;
-        while (g + 1 < ng && S.grp[g + 1].rec_begin - r0 <= j) g++;
-        grp[i] = g;
-        if (j < nr && S.grp[g].rec_begin - r0 == j) {
-          const uint64_t b16 = S.grp[g].base16;
-          sm.gb[g] = make_uint4((uint32_t)b16, (uint32_t)(b16 >> 32), 0u - ex[i], 0u);
-        }
-      }
-      __syncthreads();  // every group's base and start prefix are in shared memory
       uint64_t* img64 = reinterpret_cast<uint64_t*>(S.img);
-      const uint32_t lo8 = (uint32_t)(lo / 8), n8 = (uint32_t)((hi - lo) / 8);
+      const uint32_t n8 = (uint32_t)((hi - lo) / 8);
 #pragma unroll
       for (uint32_t i = 0; i < ITEMS; i++) {
-        const uint32_t j = wb + i * 32 + lane;
+        const uint32_t j = tid + i * THREADS;
         if (j >= nr) continue;
-        // base + (prefix - prefix at the group start), the difference taken modulo 2^32
-        const uint4 G = sm.gb[grp[i]];
-        const uint64_t off = ((((uint64_t)G.y << 32) | G.x) + (uint32_t)(ex[i] + G.z)) * 16;
-        const uint32_t rel = r[i].y - lo8;  // the slot, in 8-byte words from the tile start
-        if (rel >= n8) {
+        const uint32_t w = r[i].y & 0xFFFFu, g = r[i].y >> 16;  // slot word in the tile, lane group
+        if (w >= n8 || g >= ng) {
           atomicOr(err, ERR_BOUNDS);
           continue;
         }
-        uint64_t* sp = img64 + rel;
+        const uint64_t off = (S.grp[g].base16 + r[i].x) * 16;
+        uint64_t* sp = img64 + w;
         if (VERIFY) {
           const uint32_t ri = r0 + j;
           if (*sp != __ldg(&a.rec_host[ri]) || off != __ldg(&a.rec_off[ri])) atomicOr(err, ERR_VERIFY);

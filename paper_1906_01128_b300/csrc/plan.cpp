@@ -372,9 +372,10 @@ dc_status build_plan(const dc_schema* schema, const void* const* roots, uint64_t
     const uint32_t tr0 = (uint32_t)p->rrec.size(), tg0 = (uint32_t)p->rseg.size();
     const uint64_t hi = (t + 1) * RELOC_SPAN;
     for (uint32_t l = 0; l < nl; l++) {
-      // a group's records must see size prefixes below 2^32 units (the kernel's
-      // prefixes are 32-bit): a longer run starts a new group
-      uint64_t run = ~0ull;
+      // a record holds its target's offset from the group base in 32 bits: a
+      // target 2^32 units or more past the base starts a new group
+      uint64_t base16 = 0;
+      bool open = false;
       for (; cur[l] < lane_start[l + 1] && slot(cur[l]) < hi; cur[l]++) {
         const HostBlock& b = p->blocks[cur[l]];
         const uint64_t sl = slot(cur[l]);
@@ -382,13 +383,14 @@ dc_status build_plan(const dc_schema* schema, const void* const* roots, uint64_t
           return fail(DC_EINVAL, "internal: lane %u is not in slot order at block %llu", l,
                       (unsigned long long)cur[l]);
         last[l] = sl + 8;
-        const uint64_t size16 = round_up(b.bytes, 16) / 16;
-        if (run > 0xFFFFFFFFull) {
-          p->rseg.push_back(RelocSeg{b.off / 16, (uint32_t)p->rrec.size(), 0});
-          run = 0;
+        if (!open || b.off / 16 - base16 > 0xFFFFFFFFull) {
+          base16 = b.off / 16;
+          open = true;
+          p->rseg.push_back(RelocSeg{base16, (uint32_t)p->rrec.size(), 0});
         }
-        run += size16;
-        p->rrec.push_back(RelocRec{(uint32_t)size16, (uint32_t)(sl / 8)});
+        const uint64_t g = p->rseg.size() - 1 - tg0;  // checked against RELOC_MAXGROUPS below
+        const uint64_t w = (sl - t * RELOC_SPAN) / 8;  // < RELOC_MAXREC
+        p->rrec.push_back(RelocRec{(uint32_t)(b.off / 16 - base16), (uint32_t)(w | std::min<uint64_t>(g, 0xFFFF) << 16)});
         p->rec_host.push_back((uint64_t)(uintptr_t)b.host);
         p->rec_off.push_back(b.off);
       }

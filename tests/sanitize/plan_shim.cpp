@@ -2,10 +2,12 @@
 // behind a C entry point, built with AddressSanitizer and UBSan by
 // tests/test_host_sanitizers.py and run on the CPU.  Besides planning, it
 // checks the relocation tables the way the relocation kernel reads them:
-// every slot inside its tile, lane groups in order, and each group's base
-// plus the running prefix of its records' sizes equal to the plan's own
-// offset of every target block.
+// every slot inside its tile, each record in the lane group it names, each
+// group's base plus the record's offset equal to the plan's own offset of the
+// target block, and the slot the record names being the one that points at
+// that block.
 #include <cstdio>
+#include <unordered_map>
 
 #include "internal.hpp"
 
@@ -36,6 +38,8 @@ extern "C" int shim_plan(const dc_schema* schema, const void* const* roots, uint
   out[5] = p->struct_bytes;
   int rc = 0;
   uint64_t seen = 0;
+  std::unordered_map<uint64_t, size_t> by_off;  // arena offset -> block
+  for (size_t i = 0; i < p->blocks.size(); i++) by_off.emplace(p->blocks[i].off, i);
   for (const dc::RelocTile& T : p->rtiles) {
     const uint32_t nr = T.counts & 0xFFFFu, ng = T.counts >> 16;
     const uint64_t lo = (uint64_t)T.t * dc::RELOC_SPAN, hi = std::min<uint64_t>(p->struct_bytes, lo + dc::RELOC_SPAN);
@@ -50,23 +54,28 @@ extern "C" int shim_plan(const dc_schema* schema, const void* const* roots, uint
     }
     for (uint32_t g = T.g0; g < T.g0 + ng && !rc; g++) {
       const dc::RelocSeg& G = p->rseg[g];
-      uint64_t prefix = 0;
       for (uint32_t i = G.rec_begin; i < p->rseg[g + 1].rec_begin; i++) {
         const dc::RelocRec& R = p->rrec[i];
-        const uint64_t slot = (uint64_t)R.slot8 * 8;
-        if (slot < lo || slot + 8 > hi) {
+        const uint64_t slot = lo + (uint64_t)(R.where & 0xFFFFu) * 8;
+        if (slot + 8 > hi) {
           rc = bad("slot outside its tile", slot, T.t);
           break;
         }
-        if (prefix >= (1ull << 32)) {
-          rc = bad("group prefix reaches 2^32", g, prefix);
+        if ((R.where >> 16) != g - T.g0) {
+          rc = bad("record names another lane group", R.where >> 16, g - T.g0);
           break;
         }
-        if ((G.base16 + prefix) * 16 != p->rec_off[i]) {
-          rc = bad("base + prefix differs from the plan's offset", (G.base16 + prefix) * 16, p->rec_off[i]);
+        if ((G.base16 + R.off16) * 16 != p->rec_off[i]) {
+          rc = bad("base + offset differs from the plan's offset", (G.base16 + R.off16) * 16, p->rec_off[i]);
           break;
         }
-        prefix += R.size16;
+        // the slot is the one that points at the block at that offset
+        const auto b = by_off.find(p->rec_off[i]);
+        if (b == by_off.end() || p->blocks[b->second].parent == dc::NONE ||
+            p->blocks[p->blocks[b->second].parent].off + p->blocks[b->second].slot_off != slot) {
+          rc = bad("the slot does not point at the record's target", slot, p->rec_off[i]);
+          break;
+        }
       }
     }
     if (rc) break;

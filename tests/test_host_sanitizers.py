@@ -6,8 +6,9 @@ runtime preloaded, over the test trees, random schemas, forests and the
 planning errors (NULL with a count, aliases, cycles).  Any memory error or
 undefined behaviour aborts the child.  The shim also checks the relocation
 tables the way the relocation kernel reads them (every slot inside its tile,
-groups in order, each group's base plus the prefix of sizes equal to the
-plan's offset of every target block)."""
+each record in the group it names, each group's base plus the record's offset
+equal to the plan's offset of the target block, and the record's slot being
+the one that points at that block)."""
 import os
 import shutil
 import subprocess
