@@ -5,8 +5,9 @@
          every pointer and runs the leaf update through resolved chains, in one
          persistent launch (dc_relocate_update).  GB/s = payload bytes / step
          time, CUDA events on the launching stream.  Between steps, L2 is
-         flushed (512 MiB write) unless one step streams more than twice the L2
-         (then no input of a step is still in L2 when the next step reads it).
+         flushed (a 512 MiB write, then a 512 MiB read of another buffer) unless
+         one step streams more than twice the L2 (then no input of a step is
+         still in L2 when the next step reads it).
   e2e    the same metric through the C ABI with host buffers: dc_deep_copy
          (transfer + relocation), dc_update_leaves, dc_copy_back (back into the
          host arrays), host clock around synchronized steps; reported for a plan
@@ -89,7 +90,25 @@ def l2_policy(torch, step_bytes):
     if step_bytes > 2 * l2:
         return False, (f"not flushed: inputs larger than L2 (one step streams {step_bytes / 1e6:.1f} MB in the same "
                        f"order every step; L2 {l2 / 1e6:.1f} MB)")
-    return True, "flushed: 512 MiB write before every timed step (outside the events)"
+    return True, ("flushed: 512 MiB write, then a 512 MiB read of another buffer, before every timed step "
+                  "(outside the events)")
+
+
+class L2Flush:
+    """Evicts the step's data from L2 between timed steps, outside the events: a 512 MiB write,
+    then a read of another 512 MiB buffer, so that a step starts with L2 holding only clean lines of
+    unrelated data.  (After the write alone L2 is full of dirty lines, and the timed kernel would
+    pay for writing them back.)"""
+
+    def __init__(self, torch):
+        self.torch = torch
+        self.w = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+        self.r = torch.ones(128 << 20, dtype=torch.float32, device="cuda")
+        self.out = torch.empty((), dtype=torch.float32, device="cuda")
+
+    def __call__(self):
+        self.w.zero_()
+        self.torch.sum(self.r, dim=0, out=self.out)
 
 
 def peaks():
@@ -316,7 +335,7 @@ def run_batched(args, rank, world):
     payload = sum(t.payload_bytes for t in trees)
     nelem = sum(t.nelems("Node", "position") for t in trees)
     op = dc.Op()
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    flush = L2Flush(torch)
     forest = dc.Plan(s, [t.root for t in trees], flags=dc.PLAN_MAP_HOST)
     forest.bind()
     info = forest.info
@@ -338,7 +357,7 @@ def run_batched(args, rank, world):
         """CUDA events around each step; the timed steps sit in the NVTX range ``label``."""
         for _ in range(args.warmup):
             if do_flush:
-                flush.zero_()
+                flush()
             fn()
         torch.cuda.synchronize()
         torch.cuda._sleep(2_000_000)  # the device waits here, outside the events, while the host queues
@@ -346,7 +365,7 @@ def run_batched(args, rank, world):
         ev = []
         for _ in range(reps):
             if do_flush:
-                flush.zero_()
+                flush()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             fn()
@@ -493,12 +512,12 @@ def run_paper(args, rank, world):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     n_lin = int(os.environ.get("DC_PAPER_N", str(10 ** 7)))
     reps = max(3, args.steps // 4)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    flush = L2Flush(torch)
 
     def wall(fn):
         ts = []
         for i in range(2 + reps):
-            flush.zero_()
+            flush()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             fn()
@@ -510,7 +529,7 @@ def run_paper(args, rank, world):
     def kernel_us(fn):
         ts = []
         for i in range(2 + reps):
-            flush.zero_()
+            flush()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             fn()
@@ -606,7 +625,8 @@ def run_paper(args, rank, world):
         "n_gpus": world, "steps": reps, "warmup": 2, "ms_per_step": None, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOADS["paper"],
-                   "l2": "flushed: 512 MiB write before every timed call (outside the timers)",
+                   "l2": "flushed: 512 MiB write, then a 512 MiB read of another buffer, before every timed "
+                         "call (outside the timers)",
                    "linear_plan": "DC_PLAN_MAP_HOST", "dense_plan": "staged"},
         "linear_allinit_llused": linear, "dense_llused": dense,
         "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None,
@@ -673,7 +693,7 @@ def main():
         nelem = 1 << 26
     else:
         op = dc.Op()
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    flush = L2Flush(torch)
 
     def barrier():
         torch.cuda.synchronize()
@@ -694,9 +714,9 @@ def main():
     plan.sync()
     leaf_bytes = 12 * nelem
     # relocation: 12-byte entry read + 8-byte slot written per pointer, 8-byte size read + 8-byte offset
-    # written per block; this library's records move 16 B per block + 8 B per slot + 8 B per struct block
+    # written per block; this library's relocation reads its tables and reads and writes the struct lane
     reloc_bytes = info["nrelocs"] * 20 + info["nblocks"] * 16
-    reloc_moved = info["nblocks"] * (16 + 8) + info["nstruct_blocks"] * 8
+    reloc_moved = info["reloc_table_bytes"] + 2 * info["struct_bytes"]
     fused_bytes = leaf_bytes + reloc_bytes
     do_flush, l2_line = l2_policy(torch, fused_bytes)
 
@@ -705,7 +725,7 @@ def main():
         in an NVTX range named ``label`` (an ncu capture can select them by it)."""
         for _ in range(args.warmup):
             if do_flush:
-                flush.zero_()
+                flush()
             for f in parts:
                 f()
         barrier()
@@ -716,7 +736,7 @@ def main():
         ev = []
         for _ in range(args.steps):
             if do_flush:
-                flush.zero_()  # outside the events
+                flush()  # outside the events
             e = [torch.cuda.Event(enable_timing=True) for _ in range(len(parts) + 1)]
             e[0].record()
             for i, f in enumerate(parts):
@@ -846,7 +866,7 @@ def main():
         t = []
         for i in range(5):
             if do_flush:
-                flush.zero_()
+                flush()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             plan.update_chase(op)
@@ -897,7 +917,7 @@ def main():
             "relocation": {"kernel": "relocate_kernel", "avg_launch_us": round(reloc_avg * 1e6, 2),
                            "median_launch_us": round(reloc_med * 1e6, 2),
                            "algorithmic_bytes": reloc_bytes, "achieved_gbs": round(reloc_bytes / reloc_avg / 1e9, 1),
-                           "frac": round(reloc_bytes / reloc_avg / 1e9 / hbm, 4), "record_bytes_moved": reloc_moved},
+                           "frac": round(reloc_bytes / reloc_avg / 1e9 / hbm, 4), "bytes_moved": reloc_moved},
             "two_launch_step_us": round((reloc_avg + leaf_avg) * 1e6, 2),
             "step_median_ms": round(step_median * 1e3, 4),
             "hbm_copy_gbs_now": copy_now,

@@ -134,11 +134,15 @@ typedef struct {
                               data region + block table + scratch */
   uint64_t payload_bytes;  /* sum of block sizes without padding */
   uint64_t nblocks;        /* root struct + non-empty arrays + non-empty child arrays */
-  uint64_t nrelocs;        /* pointer slots rewritten by the relocation (nblocks - 1) */
+  uint64_t nrelocs;        /* pointer slots rewritten by the relocation (nblocks - ntrees) */
   uint64_t nstructs;       /* struct instances in the tree */
   uint64_t nstruct_blocks; /* blocks that hold structs (root + child arrays) */
   uint64_t root_offset;    /* offset of the (first) root struct in the data region (0) */
   uint64_t ntrees;         /* trees in the plan (1, or the count given to dc_plan_forest) */
+  uint64_t struct_bytes;   /* bytes of lane 0 (every struct block, padded), at the start of
+                              the data region: the relocation reads and writes this range */
+  uint64_t reloc_table_bytes; /* the relocation's tables (8 B per slot, 16 B per lane group
+                                 of a tile, 16 B per tile that holds a slot) */
 } dc_plan_info;
 
 /* Plan flags (dc_plan_set_flags, before dc_bind_device). */
@@ -160,14 +164,17 @@ typedef struct {
  * determineTotalBytes, and its allocation requests; Fig 2 step a).  Host only:
  * touches no GPU.
  * Layout: blocks are grouped in lanes — lane 0 holds every struct block (the
- * root, then child arrays in depth-first order), then one lane per ARRAY field
- * (in type, field order), each in depth-first order; every block starts on a
- * 16-byte boundary.  Errors: DC_EINVAL (NULL pointer with a non-zero count,
+ * root, then the child arrays breadth first, each struct block's children in
+ * the order of their slots), then one lane per ARRAY field (in type, field
+ * order) holding its blocks in the order of their parents in lane 0, then of
+ * their slots.  So in every lane, consecutive blocks are pointed at by
+ * ascending slots.  Every block starts on a 16-byte boundary.  Errors: DC_EINVAL (NULL pointer with a non-zero count,
  * negative count, bad schema), DC_EALIAS / DC_ECYCLE (not a tree), DC_ENOMEM. */
 DC_API dc_status dc_plan(const dc_schema* schema, const void* host_root, dc_plan_t* out);
 /* dc_plan_forest — one plan (one arena, one relocation, one leaf stream) for
- * `nroots` independent trees of the same schema, laid out tree after tree
- * within each lane (the batched form of the deep copy).  SEL_ALL ops cover
+ * `nroots` independent trees of the same schema (the batched form of the deep
+ * copy): lane 0 starts with the roots in the order given, and the lanes hold
+ * every tree's blocks in the slot order above.  SEL_ALL ops cover
  * every tree; SEL_CHAIN paths and dc_resolve_chain / dc_verify_chain start at
  * tree 0 (dc_resolve_chain_in takes a tree index).  The trees must not share
  * blocks (DC_EALIAS). */

@@ -72,7 +72,7 @@ class _Op(ctypes.Structure):
 class _Info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("data_bytes", "device_bytes", "payload_bytes", "nblocks",
                                                "nrelocs", "nstructs", "nstruct_blocks", "root_offset",
-                                               "ntrees")]
+                                               "ntrees", "struct_bytes", "reloc_table_bytes")]
 
 
 class _Request(ctypes.Structure):

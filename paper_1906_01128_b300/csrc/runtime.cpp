@@ -271,11 +271,14 @@ dc_status dc_plan_info_get(dc_plan_t p, dc_plan_info* out) {
   out->device_bytes = p->L.total;
   out->payload_bytes = p->payload;
   out->nblocks = p->blocks.size();
-  out->nrelocs = p->blocks.size() - 1;
+  out->nrelocs = p->blocks.size() - p->roots.size();
   out->nstructs = p->nstructs;
   out->nstruct_blocks = p->nstruct_blocks;
   out->root_offset = 0;
   out->ntrees = p->roots.size();
+  out->struct_bytes = p->struct_bytes;
+  out->reloc_table_bytes =
+      p->rrec.size() * sizeof(RelocRec) + p->rseg.size() * sizeof(RelocSeg) + p->rtiles.size() * sizeof(RelocTile);
   return DC_OK;
 }
 

@@ -98,6 +98,10 @@ def test_plan_counts_and_layout_match_oracle():
             assert slot > last.get(b["lane"], -1), (t.name, b)
             last[b["lane"]] = slot
         assert info["device_bytes"] >= info["data_bytes"]
+        # the struct lane ends where the first array block starts; one 8-byte record per slot
+        n_s = info["nstruct_blocks"]
+        assert info["struct_bytes"] == (blocks[n_s - 1]["offset"] + blocks[n_s - 1]["bytes"] + 15) // 16 * 16
+        assert info["reloc_table_bytes"] >= 8 * info["nrelocs"] + 16
         p.destroy()
         t.free()
 
@@ -117,6 +121,17 @@ def hand_tree():
     root = CNode(2, 2, ctypes.addressof(pos), ctypes.addressof(vel), ctypes.addressof(kids))
     keep += [pos, vel, p0, v0, kids, root]
     return root, keep
+
+
+def test_forest_counts():
+    """A forest's roots are not pointed at: nrelocs = nblocks - ntrees."""
+    trees = tg.batched(5, seed=9, t_min=4 << 10, t_max=64 << 10)
+    p = dc.Plan(trees[0].schema, [t.root for t in trees])
+    info = p.info
+    assert info["ntrees"] == 5
+    assert info["nblocks"] == sum(oracle.count(t.schema, t.root)["nblocks"] for t in trees)
+    assert info["nrelocs"] == info["nblocks"] - 5 == sum(oracle.count(t.schema, t.root)["nptr"] for t in trees)
+    p.destroy()
 
 
 def test_hand_tree_lane_layout():
