@@ -59,10 +59,10 @@ WORKLOADS = {
 # DRAM bytes (read + write) per launch of the step's kernel from one ncu capture, by (workload, split);
 # the summary beside each gives the command.  An entry stands only while the kernel is unchanged.
 NCU_TRAFFIC = {
-    ("dense", 256, 4): (460_655_616, "profiles/fused_kernel_dense.md"),
-    ("reloc_stress", 256, 4): (195_031_296, "profiles/relocate_kernel_reloc_stress.md"),
-    ("deep", 256, 4): (757_760_000, "profiles/fused_kernel_deep_batched.md"),
-    ("batched", 256, 4): (7_015_000_000, "profiles/fused_kernel_deep_batched.md"),
+    ("dense", 256, 4): (460_959_872, "profiles/fused_kernel_dense.md"),
+    ("reloc_stress", 128, 4): (191_866_112, "profiles/relocate_kernel_reloc_stress.md"),
+    ("deep", 256, 4): (757_033_088, "profiles/fused_kernel_deep_batched.md"),
+    ("batched", 256, 4): (7_019_413_120, "profiles/fused_kernel_deep_batched.md"),
 }
 
 
