@@ -134,6 +134,29 @@ def test_forest_counts():
     p.destroy()
 
 
+def test_lane_groups_split_64_gib_past_their_base():
+    """Relocation records hold a target's offset from its lane group's base in
+    32 bits of 16-byte units: the plan must start a new group where a target
+    lies 2^32 units (64 GiB) or more past the base.  A 7-level Linear chain
+    whose A arrays are 16 GiB of reserved address space (never read) has its
+    level structs at 32 B each (lane 0, 224 B) and A_k at 224 + k (2^34 - 16):
+    A_0..A_4 share a group, A_5 and A_6 start another."""
+    nA = 2 ** 31 - 2
+    t = tg.ReservedChain(7, nA)
+    p = dc.Plan(t.schema, t.root)
+    info = p.info
+    a_bytes = 8 * nA
+    assert info["struct_bytes"] == 224 and info["nrelocs"] == 13
+    assert info["data_bytes"] == 224 + 7 * a_bytes
+    got = [(b["offset"], b["lane"]) for b in p.blocks()]
+    assert got == [(32 * k, 0) for k in range(7)] + [(224 + k * a_bytes, 1) for k in range(7)]
+    # 13 records, one tile, groups: lane 0, A_0..A_4, A_5..A_6 (and the closing entry)
+    assert info["reloc_table_bytes"] == 13 * 8 + (3 + 1) * 16 + 16
+    assert (224 + 5 * a_bytes - 224) // 16 > 0xFFFFFFFF >= (4 * a_bytes) // 16
+    p.destroy()
+    t.free()
+
+
 def test_hand_tree_lane_layout():
     # lane 0: root (32 B) @0, child array (64 B) @32; lane 1 (position):
     # root.pos (8 B) @96, c0.pos (4 B) @112; lane 2 (velocity): @128, @144

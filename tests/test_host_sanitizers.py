@@ -56,6 +56,10 @@ DRIVER = textwrap.dedent(r'''
     forest = tg.batched(40, seed=9, t_max=256 << 10)
     rc, out = plan(forest[0].schema, [t.root for t in forest])
     assert rc == 0, rc
+    # targets 64 GiB and more past their lane group's base (reserved address space, never read)
+    far = tg.ReservedChain(7, 2 ** 31 - 2)
+    rc, out = plan(far.schema, [far.root])
+    assert rc == 0 and out[2] == 3 and out[4] == 224 + 7 * 8 * (2 ** 31 - 2), (rc, out)
     # planning errors: the same tree twice in a forest (alias), a NULL root in a forest
     rc, _ = plan(forest[0].schema, [forest[0].root, forest[0].root])
     assert rc != 0

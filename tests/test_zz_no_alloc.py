@@ -108,3 +108,43 @@ def test_static_scratch_rejects_plans_beyond_its_limit():
     assert dc.STATUS[rc] == "DC_EINVAL"
     for x in (plan, p2):
         x.destroy()
+
+
+def test_static_relocation_of_targets_64_gib_past_their_group_base():
+    """Records hold a target's offset from its lane group's base in 32 bits of
+    16-byte units; the plan starts a new group 2^32 units (64 GiB) past the
+    base.  A 7-level Linear chain whose A arrays are 16 GiB of reserved host
+    address space (never read) lays out a 120 GB arena: A_5 and A_6 lie in a
+    second group.  Only the level structs (224 bytes at the start of the data
+    region) are written and relocated; every slot must hold the device
+    address the layout's closed form gives: level k at 32k, A_k at
+    224 + k (2^34 - 16)."""
+    nA, levels = 2 ** 31 - 2, 7
+    t = tg.ReservedChain(levels, nA)
+    plan = dc.Plan(t.schema, t.root)
+    n, sb = plan.info["data_bytes"], plan.info["struct_bytes"]
+    assert sb == 224 and n == 224 + levels * 8 * nA
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    if free < n + (8 << 30):
+        pytest.skip(f"needs {n / 1e9:.0f} GB of device memory, {free / 1e9:.0f} GB free")
+    buf = torch.empty(n, dtype=torch.uint8, device="cuda")
+    img = bytearray(sb)
+    for b in plan.blocks()[:plan.info["nstruct_blocks"]]:
+        img[b["offset"]:b["offset"] + b["bytes"]] = ctypes.string_at(b["host"], b["bytes"])
+    buf[:sb].copy_(torch.frombuffer(img, dtype=torch.uint8))
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    assert relocate_static(plan, buf.data_ptr(), n, status) == 0, dc.lib.dc_last_error()
+    torch.cuda.synchronize()
+    assert status.item() == 0
+    lv = np.frombuffer(buf[:sb].cpu().numpy().tobytes(), dtype=np.dtype(
+        [("nA", "<i4"), ("nLnext", "<i4"), ("A", "<u8"), ("Lnext", "<u8"), ("pad", "<u8")]))
+    base = buf.data_ptr()
+    for k in range(levels):
+        assert lv["nA"][k] == nA and lv["nLnext"][k] == (1 if k + 1 < levels else 0), k
+        assert int(lv["A"][k]) == base + 224 + k * 8 * nA, k
+        assert int(lv["Lnext"][k]) == (base + 32 * (k + 1) if k + 1 < levels else 0), k
+    del buf
+    torch.cuda.empty_cache()
+    plan.destroy()
+    t.free()

@@ -482,3 +482,54 @@ def batched(ntrees: int = 4096, seed: int = 4, t_min: int = 16 << 10, t_max: int
                 break
         trees.append(Tree(node_schema(), levels, rules, s, name=f"batched-{i}", nthreads=1))
     return trees
+
+
+# Address-only trees ----------------------------------------------------------------
+
+class ReservedChain:
+    """A Linear chain (``linear_schema``) of ``levels`` level structs whose A
+    arrays are address ranges reserved with no memory behind them
+    (``mmap(PROT_NONE, MAP_NORESERVE)``), each ``nA`` doubles long.  Planning
+    reads only the level structs, so such a tree lays out an arena far larger
+    than the host's memory (at nA = 2^31 - 2, 16 GiB per level) without
+    touching the arrays; it is for layout and relocation tests only: reading
+    an A array faults.  ``root`` is the level-0 struct's address."""
+
+    PROT_NONE, MAP_PRIVATE, MAP_ANONYMOUS, MAP_NORESERVE = 0, 0x02, 0x20, 0x4000
+
+    def __init__(self, levels: int, nA: int):
+        libc = ctypes.CDLL(None, use_errno=True)
+        libc.mmap.restype = ctypes.c_void_p
+        libc.mmap.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                              ctypes.c_long]
+        libc.munmap.restype = ctypes.c_int
+        libc.munmap.argtypes = [ctypes.c_void_p, ctypes.c_size_t]
+        self._libc, self.schema, self.levels, self.nA, self.name = libc, linear_schema(), levels, nA, "reserved"
+        self.span = (nA * 8 + 4095) // 4096 * 4096
+        self.region = libc.mmap(None, self.span * levels, self.PROT_NONE,
+                                self.MAP_PRIVATE | self.MAP_ANONYMOUS | self.MAP_NORESERVE, -1, 0)
+        if self.region in (None, ctypes.c_void_p(-1).value):
+            raise OSError(ctypes.get_errno(), "mmap of the reserved A arrays failed")
+
+        class L(ctypes.Structure):
+            _fields_ = [("nA", ctypes.c_int32), ("nLnext", ctypes.c_int32), ("A", ctypes.c_void_p),
+                        ("Lnext", ctypes.c_void_p)]
+
+        # one single-struct array per level (Lnext has count 1), the last with no next level
+        self.levels_c = [L() for _ in range(levels)]
+        for k, s in enumerate(self.levels_c):
+            s.nA, s.A = nA, self.region + k * self.span
+            if k + 1 < levels:
+                s.nLnext, s.Lnext = 1, ctypes.addressof(self.levels_c[k + 1])
+        self.root = ctypes.addressof(self.levels_c[0])
+
+    def free(self):
+        if getattr(self, "region", None):
+            self._libc.munmap(self.region, self.span * self.levels)
+            self.region, self.root = None, 0
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
