@@ -183,6 +183,12 @@ DC_API dc_status dc_plan_forest(const dc_schema* schema, const void* const* root
 DC_API dc_status dc_plan_root(dc_plan_t plan, uint64_t tree, uint64_t* offset);
 DC_API dc_status dc_plan_set_flags(dc_plan_t plan, uint32_t flags);
 DC_API dc_status dc_plan_info_get(dc_plan_t plan, dc_plan_info* out);
+/* dc_plan_arena_bytes — the three sizes a caller needs before dc_bind_device:
+ * the bytes the device buffer must hold (info.device_bytes: the data region of
+ * Algorithm 1's determineTotalBytes plus the plan's tables and scratch), the
+ * block count and the pointer slots the relocation rewrites.  Host only.  Any
+ * output pointer may be NULL.  Errors: DC_EINVAL (NULL plan). */
+DC_API dc_status dc_plan_arena_bytes(dc_plan_t plan, uint64_t* bytes, uint64_t* nblocks, uint64_t* nrelocs);
 /* Block `i` in arena order: its host address, arena offset, byte size, lane,
  * and its relocation entry — the struct block holding the pointer slot that
  * refers to it (UINT32_MAX for the root) and that slot's byte offset inside

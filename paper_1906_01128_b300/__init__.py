@@ -95,6 +95,7 @@ SIGNATURES = {
     "dc_plan_root": [_vp, _u64, _P(_u64)],
     "dc_plan_set_flags": [_vp, _u32],
     "dc_plan_info_get": [_vp, _P(_Info)],
+    "dc_plan_arena_bytes": [_vp, _P(_u64), _P(_u64), _P(_u64)],
     "dc_plan_block": [_vp, _u64, _P(_u64), _P(_u64), _P(_u64), _P(_u32), _P(_u32), _P(_u32)],
     "dc_plan_set_threads": [_vp, _u32],
     "dc_plan_destroy": [_vp],
@@ -239,6 +240,12 @@ class Plan:
         if threads:
             _check(lib.dc_plan_set_threads(self._h, threads))
         self.buffer: Optional[torch.Tensor] = None
+
+    def arena_bytes(self) -> tuple:
+        """(device buffer bytes for bind, blocks, pointer slots) — dc_plan_arena_bytes."""
+        b, n, r = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib.dc_plan_arena_bytes(self._h, ctypes.byref(b), ctypes.byref(n), ctypes.byref(r)))
+        return b.value, n.value, r.value
 
     @property
     def info(self) -> dict:

@@ -282,6 +282,14 @@ dc_status dc_plan_info_get(dc_plan_t p, dc_plan_info* out) {
   return DC_OK;
 }
 
+dc_status dc_plan_arena_bytes(dc_plan_t p, uint64_t* bytes, uint64_t* nblocks, uint64_t* nrelocs) {
+  if (!p) return fail(DC_EINVAL, "plan is NULL");
+  if (bytes) *bytes = p->L.total;
+  if (nblocks) *nblocks = p->blocks.size();
+  if (nrelocs) *nrelocs = p->blocks.size() - p->roots.size();
+  return DC_OK;
+}
+
 dc_status dc_plan_root(dc_plan_t p, uint64_t tree, uint64_t* offset) {
   if (!p || !offset) return fail(DC_EINVAL, "NULL argument");
   if (tree >= p->roots.size()) return fail(DC_EINVAL, "tree %llu out of range", (unsigned long long)tree);

@@ -129,6 +129,7 @@ def test_forest_counts():
     p = dc.Plan(trees[0].schema, [t.root for t in trees])
     info = p.info
     assert info["ntrees"] == 5
+    assert p.arena_bytes() == (info["device_bytes"], info["nblocks"], info["nrelocs"])
     assert info["nblocks"] == sum(oracle.count(t.schema, t.root)["nblocks"] for t in trees)
     assert info["nrelocs"] == info["nblocks"] - 5 == sum(oracle.count(t.schema, t.root)["nptr"] for t in trees)
     p.destroy()
