@@ -202,7 +202,8 @@ DC_API dc_status dc_plan_destroy(dc_plan_t plan);
 /* dc_bind_device — give the plan a caller-owned device buffer of at least
  * info.device_bytes bytes, 256-byte aligned (a torch CUDA uint8 tensor
  * qualifies).  Uploads the block table and clears the scratch on `stream`
- * (blocking), and allocates the plan's pinned staging arena on first use.
+ * (blocking).  The plan's first bind also allocates its pinned staging arena:
+ * info.data_bytes of page-locked host memory.
  * Errors: DC_EBUDGET, DC_EINVAL (misaligned), DC_ENOMEM, DC_ECUDA. */
 DC_API dc_status dc_bind_device(dc_plan_t plan, void* dev_buffer, uint64_t bytes, dc_stream_t stream);
 
@@ -221,8 +222,9 @@ DC_API dc_status dc_bind_device(dc_plan_t plan, void* dev_buffer, uint64_t bytes
 DC_API dc_status dc_deep_copy(dc_plan_t plan, dc_stream_t stream);
 
 /* dc_relocate — the relocation kernel of dc_deep_copy alone (Fig 2 step d):
- * recompute every block's arena offset on the device and rewrite every pointer
- * slot of the data region already in device memory.  For a data region that
+ * rewrite every pointer slot of the data region already in device memory to
+ * the device address of its target (the buffer's base + the target's arena
+ * offset, which the plan's relocation records hold).  For a data region that
  * is already resident (filled by an earlier dc_deep_copy or by the caller);
  * the result is the same whatever the slots held.  Errors: DC_ESTATE, DC_ECUDA. */
 DC_API dc_status dc_relocate(dc_plan_t plan, dc_stream_t stream);
