@@ -168,8 +168,12 @@ typedef struct {
  * the order of their slots), then one lane per ARRAY field (in type, field
  * order) holding its blocks in the order of their parents in lane 0, then of
  * their slots.  So in every lane, consecutive blocks are pointed at by
- * ascending slots.  Every block starts on a 16-byte boundary.  Errors: DC_EINVAL (NULL pointer with a non-zero count,
- * negative count, bad schema), DC_EALIAS / DC_ECYCLE (not a tree), DC_ENOMEM. */
+ * ascending slots.  Every block starts on a 16-byte boundary.
+ * Errors: DC_EINVAL (NULL pointer with a non-zero count, negative count, bad
+ * schema), DC_ECYCLE (a child pointer leads into an ancestor struct block),
+ * DC_EALIAS (any other two blocks overlap: the structure is not a tree),
+ * DC_ENOMEM.  With DC_TRACE=1 the walk, the overlap check, the lane order, the
+ * remap and the relocation tables are timed. */
 DC_API dc_status dc_plan(const dc_schema* schema, const void* host_root, dc_plan_t* out);
 /* dc_plan_forest — one plan (one arena, one relocation, one leaf stream) for
  * `nroots` independent trees of the same schema (the batched form of the deep

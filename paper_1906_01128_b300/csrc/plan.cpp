@@ -11,7 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
-#include <unordered_map>
+#include <optional>
 
 #include "internal.hpp"
 
@@ -118,6 +118,12 @@ static bool read_count(const dc_type& T, const uint8_t* s, const dc_field& F, ui
 
 namespace {
 
+// A block's host byte range and its emission index.
+struct Span {
+  uint64_t start, end;
+  uint32_t id;
+};
+
 struct Frame {
   uint32_t blk;    // emission index of the struct block
   uint64_t elem;   // element of that block
@@ -130,8 +136,10 @@ struct Walker {
   dc_plan_s* p;
   const SchemaCopy& S;
   std::vector<HostBlock> emitted;
-  std::unordered_map<uint64_t, uint32_t> starts;              // host start -> emission index
-  std::map<uint64_t, std::pair<uint64_t, uint32_t>> structs;  // struct ranges: start -> (end, id)
+  // struct ranges: start -> (end, id).  A struct block that overlaps one already
+  // emitted stops the walk at once, so a cycle of child pointers cannot make it
+  // loop; arrays are leaves, and the overlap pass after the walk checks them.
+  std::map<uint64_t, std::pair<uint64_t, uint32_t>> structs;
   std::vector<std::pair<uint32_t, uint64_t>> null_slots;      // (emission index, slot offset)
 
   explicit Walker(dc_plan_s* pl) : p(pl), S(pl->schema) {}
@@ -148,13 +156,6 @@ struct Walker {
     if (slot_off > 0xFFFFFFFFull) return fail(DC_EINVAL, "child array too large for a 32-bit slot offset");
     if (round_up(bytes, 16) / 16 > 0xFFFFFFFFull) return fail(DC_EINVAL, "block larger than 64 GiB");
     uint64_t a = (uint64_t)(uintptr_t)host;
-    auto hit = starts.find(a);
-    if (hit != starts.end()) {
-      if (field == NONE && is_ancestor(hit->second, parent))
-        return fail(DC_ECYCLE, "a pointer leads back to an ancestor struct block (host 0x%llx)",
-                    (unsigned long long)a);
-      return fail(DC_EALIAS, "host block 0x%llx is reached through two pointers", (unsigned long long)a);
-    }
     if (field == NONE) {  // a struct block: it must not overlap another struct block
       auto it = structs.upper_bound(a);
       uint32_t other = NONE;
@@ -165,12 +166,12 @@ struct Walker {
       }
       if (other != NONE) {
         if (parent != NONE && is_ancestor(other, parent))
-          return fail(DC_ECYCLE, "a child array overlaps an ancestor struct block");
+          return fail(DC_ECYCLE, "a pointer leads back into an ancestor struct block (host 0x%llx)",
+                      (unsigned long long)a);
         return fail(DC_EALIAS, "struct block at 0x%llx overlaps another", (unsigned long long)a);
       }
       structs.emplace(a, std::make_pair(a + bytes, (uint32_t)emitted.size()));
     }
-    starts.emplace(a, (uint32_t)emitted.size());
     HostBlock b{};
     b.host = host;
     b.bytes = bytes;
@@ -273,6 +274,8 @@ dc_status build_plan(const dc_schema* schema, const void* const* roots, uint64_t
   if (!roots || nroots == 0) return fail(DC_EINVAL, "no root");
   dc_status st = copy_schema(schema, &p->schema);
   if (st) return st;
+  std::optional<Trace> phase;  // one traced phase at a time
+  phase.emplace("dc_plan", "walk");
   Walker w(p);
   std::vector<uint32_t> root_ids;
   for (uint64_t i = 0; i < nroots; i++) {  // trees one after another; they must not share blocks
@@ -283,23 +286,31 @@ dc_status build_plan(const dc_schema* schema, const void* const* roots, uint64_t
   std::vector<HostBlock>& E = w.emitted;
   const uint64_t nb = E.size();
 
-  // every block must be disjoint from every other (arrays included)
+  // every block must be disjoint from every other (arrays included): sort the
+  // blocks' host ranges by start and compare neighbours
+  phase.emplace("dc_plan", "overlap");
   {
-    std::vector<uint32_t> by(nb);
-    for (uint64_t i = 0; i < nb; i++) by[i] = (uint32_t)i;
-    std::sort(by.begin(), by.end(), [&](uint32_t a, uint32_t b) { return E[a].host < E[b].host; });
+    std::vector<Span> by(nb);
+    for (uint64_t i = 0; i < nb; i++) {
+      const uint64_t a = (uint64_t)(uintptr_t)E[i].host;
+      by[i] = Span{a, a + E[i].bytes, (uint32_t)i};
+    }
+    std::sort(by.begin(), by.end(), [](const Span& x, const Span& y) { return x.start < y.start; });
     for (uint64_t i = 1; i < nb; i++) {
-      const HostBlock& a = E[by[i - 1]];
-      const HostBlock& b = E[by[i]];
-      if ((uint64_t)(uintptr_t)a.host + a.bytes > (uint64_t)(uintptr_t)b.host) {
-        bool cyc = (a.field == NONE && w.is_ancestor(by[i - 1], b.parent)) ||
-                   (b.field == NONE && w.is_ancestor(by[i], a.parent));
+      if (by[i - 1].end > by[i].start) {
+        const uint32_t ia = by[i - 1].id, ib = by[i].id;
+        const HostBlock& a = E[ia];
+        const HostBlock& b = E[ib];
+        // only child pointers can close a cycle: two struct blocks, one inside the other's ancestry
+        const bool cyc = a.field == NONE && b.field == NONE &&
+                         (w.is_ancestor(ia, b.parent) || w.is_ancestor(ib, a.parent));
         return fail(cyc ? DC_ECYCLE : DC_EALIAS, "host blocks at 0x%llx and 0x%llx overlap",
-                    (unsigned long long)(uintptr_t)a.host, (unsigned long long)(uintptr_t)b.host);
+                    (unsigned long long)by[i - 1].start, (unsigned long long)by[i].start);
       }
     }
   }
 
+  phase.emplace("dc_plan", "lanes");
   // Lanes in slot order: lane 0 holds the roots, then the child arrays breadth
   // first (each struct block's children by slot offset); every array lane holds
   // its blocks in the order of their parents, then of their slot offsets.  So
@@ -316,9 +327,13 @@ dc_status build_plan(const dc_schema* schema, const void* const* roots, uint64_t
     for (uint64_t i = 0; i < nb; i++)
       if (E[i].parent != NONE) kid[fill[E[i].parent]++] = (uint32_t)i;
   }
+  // the walk emits a struct block's children element by element, each element's
+  // in field order, so they are in slot order unless the schema lists its pointer
+  // fields out of offset order
+  auto by_slot = [&](uint32_t a, uint32_t b) { return E[a].slot_off < E[b].slot_off; };
   for (uint64_t i = 0; i < nb; i++)
-    std::sort(kid.begin() + kbeg[i], kid.begin() + kbeg[i + 1],
-              [&](uint32_t a, uint32_t b) { return E[a].slot_off < E[b].slot_off; });
+    if (!std::is_sorted(kid.begin() + kbeg[i], kid.begin() + kbeg[i + 1], by_slot))
+      std::sort(kid.begin() + kbeg[i], kid.begin() + kbeg[i + 1], by_slot);
   std::vector<std::vector<uint32_t>> lanes(nl);
   for (uint32_t r : root_ids) lanes[0].push_back(r);
   for (size_t q = 0; q < lanes[0].size(); q++)
@@ -327,32 +342,34 @@ dc_status build_plan(const dc_schema* schema, const void* const* roots, uint64_t
   for (uint32_t l = 0; l < nl; l++) lane_start[l + 1] = lane_start[l] + lanes[l].size();
   if (lane_start[nl] != nb) return fail(DC_EINVAL, "internal: %llu of %llu blocks reached in the lane order",
                                         (unsigned long long)lane_start[nl], (unsigned long long)nb);
+  phase.emplace("dc_plan", "remap");
   std::vector<uint32_t> new_id(nb);
   for (uint32_t l = 0; l < nl; l++)
     for (size_t j = 0; j < lanes[l].size(); j++) new_id[lanes[l][j]] = (uint32_t)(lane_start[l] + j);
+  // gather the blocks in arena order, each at the next 16-byte boundary
+  p->blocks.clear();
+  p->blocks.reserve(nb);
+  uint64_t off = 0;
+  for (uint32_t l = 0; l < nl; l++)
+    for (uint32_t old : lanes[l]) {
+      HostBlock b = E[old];
+      if (b.parent != NONE) b.parent = new_id[b.parent];
+      b.off = off;
+      off += round_up(b.bytes, 16);
+      p->blocks.push_back(b);
+    }
   lanes.clear();
-  p->blocks.resize(nb);
-  for (uint64_t i = 0; i < nb; i++) {
-    HostBlock b = E[i];
-    if (b.parent != NONE) b.parent = new_id[b.parent];
-    p->blocks[new_id[i]] = b;
-  }
   for (auto& t : p->ptr_target)
     if (t != NONE) t = new_id[t];
   p->roots.clear();
   for (uint32_t r : root_ids) p->roots.push_back(new_id[r]);
-  uint64_t off = 0;
-  for (uint64_t i = 0; i < nb; i++) {
-    HostBlock& b = p->blocks[i];
-    b.off = off;
-    off += round_up(b.bytes, 16);
-  }
   p->data_bytes = off;
   p->struct_bytes = p->nstruct_blocks ? p->blocks[p->nstruct_blocks - 1].off +
                                             round_up(p->blocks[p->nstruct_blocks - 1].bytes, 16)
                                       : 0;
   if (p->struct_bytes / 8 > 0xFFFFFFFFull) return fail(DC_EINVAL, "struct lane larger than 32 GiB");
 
+  phase.emplace("dc_plan", "reloc_tables");
   // Relocation tables: tile t covers the struct-lane bytes [t, t+1) * RELOC_SPAN;
   // its records are, lane by lane, the consecutive blocks whose slots lie there.
   const uint64_t ntiles = (p->struct_bytes + RELOC_SPAN - 1) / RELOC_SPAN;

@@ -243,6 +243,17 @@ def test_plan_rejects_non_trees_and_bad_inputs():
     k2[0] = CNode(4, 0, ctypes.addressof(big), ctypes.addressof(big) + 8, None)
     r2 = CNode(0, 1, None, None, ctypes.addressof(k2))
     assert _status(lambda: dc.Plan(s, ctypes.addressof(r2))) == "DC_EALIAS"
+    # an array that points into its own struct: arrays are leaves, so it is an alias, not a cycle
+    k3 = (CNode * 1)()
+    k3[0] = CNode(2, 0, ctypes.addressof(k3), None, None)
+    k3[0].velocity = ctypes.addressof(big)
+    r5 = CNode(0, 1, None, None, ctypes.addressof(k3))
+    assert _status(lambda: dc.Plan(s, ctypes.addressof(r5))) == "DC_EALIAS"
+    # a child pointer into the middle of an ancestor child array
+    loop2 = (CNode * 2)()
+    loop2[0] = CNode(0, 1, None, None, ctypes.addressof(loop2) + ctypes.sizeof(CNode))
+    top2 = CNode(0, 2, None, None, ctypes.addressof(loop2))
+    assert _status(lambda: dc.Plan(s, ctypes.addressof(top2))) == "DC_ECYCLE"
     # NULL with a count, negative count, NULL root
     r3 = CNode(3, 0, None, None, None)
     assert _status(lambda: dc.Plan(s, ctypes.addressof(r3))) == "DC_EINVAL"
@@ -253,7 +264,7 @@ def test_plan_rejects_non_trees_and_bad_inputs():
     bad = tg.Schema([tg.Type("B", 16, 8, [tg.Field("n", tg.SCALAR, 0, 4),
                                           tg.Field("a", tg.ARRAY, 4, 4, count_field=0)])])
     assert _status(lambda: dc.Plan(bad, ctypes.addressof(r3))) == "DC_EINVAL"
-    keep = (arr, kids, root, loop, top, big, k2, r2, r3, r4)  # noqa: F841
+    keep = (arr, kids, root, loop, top, big, k2, r2, r3, r4, k3, r5, loop2, top2)  # noqa: F841
 
 
 def test_count_zero_pointer_becomes_null_in_the_plan_image():

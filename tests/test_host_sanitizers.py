@@ -1,6 +1,7 @@
 """The host walk and layout under AddressSanitizer and UBSan (CPU only).
 
-plan.cpp and a small shim (tests/sanitize/plan_shim.cpp) are compiled with
+plan.cpp (with trace.cpp, its phase timer) and a small shim
+(tests/sanitize/plan_shim.cpp) are compiled with
 -fsanitize=address,undefined and driven, in a child process with the ASan
 runtime preloaded, over the test trees, random schemas, forests and the
 planning errors (NULL with a count, aliases, cycles).  Any memory error or
@@ -74,7 +75,8 @@ def test_plan_under_asan_and_ubsan(tmp_path):
     so = str(tmp_path / "libplan_asan.so")
     cmd = [gxx, "-std=c++17", "-O1", "-g", "-fsanitize=address,undefined", "-fno-sanitize-recover=all",
            "-fno-omit-frame-pointer", "-shared", "-fPIC", f"-I{CUDA}/include", f"-I{CSRC}",
-           os.path.join(CSRC, "plan.cpp"), os.path.join(HERE, "sanitize", "plan_shim.cpp"),
+           os.path.join(CSRC, "plan.cpp"), os.path.join(CSRC, "trace.cpp"),
+           os.path.join(HERE, "sanitize", "plan_shim.cpp"),
            f"-L{CUDA}/lib64", "-lcudart", f"-Wl,-rpath,{CUDA}/lib64", "-o", so]
     subprocess.run(cmd, check=True, capture_output=True, text=True)
     asan = subprocess.run([gxx, "-print-file-name=libasan.so"], capture_output=True, text=True).stdout.strip()
