@@ -74,6 +74,7 @@ def copy_check(torch, nbytes=1 << 30, reps=5):
     best = 0.0
     for _ in range(reps + 1):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        queue_ahead(torch, 100)
         e0.record()
         b.copy_(a)
         e1.record()
@@ -92,6 +93,13 @@ def l2_policy(torch, step_bytes):
                        f"order every step; L2 {l2 / 1e6:.1f} MB)")
     return True, ("flushed: 512 MiB write, then a 512 MiB read of another buffer, before every timed step "
                   "(outside the events)")
+
+
+def queue_ahead(torch, us: float):
+    """Keep the device busy for about ``us`` microseconds, outside any events, so that the host
+    has queued the launches and events that follow before the device reaches them: no timed
+    region then contains host time."""
+    torch.cuda._sleep(int(us * 2000))  # ~2,000 cycles per microsecond at the B300's SM clock
 
 
 class L2Flush:
@@ -283,6 +291,7 @@ def link_peaks(torch, nbytes=256 << 20, reps=5):
         for _ in range(reps + 1):
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            queue_ahead(torch, 100)
             e0.record()
             fn()
             e1.record()
@@ -360,17 +369,15 @@ def run_batched(args, rank, world):
                 flush()
             fn()
         torch.cuda.synchronize()
-        torch.cuda._sleep(2_000_000)  # the device waits here, outside the events, while the host queues
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        queue_ahead(torch, 1000 + 500 * reps)  # the host queues every timed step meanwhile
         torch.cuda.nvtx.range_push(label)
-        ev = []
-        for _ in range(reps):
+        for e0, e1 in ev:
             if do_flush:
                 flush()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             fn()
             e1.record()
-            ev.append((e0, e1))
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         ts = [a.elapsed_time(b) * 1e-3 for a, b in ev]
@@ -531,6 +538,7 @@ def run_paper(args, rank, world):
         for i in range(2 + reps):
             flush()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            queue_ahead(torch, 200)
             e0.record()
             fn()
             e1.record()
@@ -729,20 +737,18 @@ def main():
             for f in parts:
                 f()
         barrier()
-        # keep the device busy (outside the events) while the host queues the first steps, so that
-        # no timed step waits for the host to submit it
-        torch.cuda._sleep(2_000_000)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(parts) + 1)] for _ in range(args.steps)]
+        # keep the device busy (outside the events) while the host queues every timed step, so
+        # that no timed step waits for the host to submit it
+        queue_ahead(torch, 1000 + 500 * args.steps)
         torch.cuda.nvtx.range_push(label)
-        ev = []
-        for _ in range(args.steps):
+        for e in ev:
             if do_flush:
                 flush()  # outside the events
-            e = [torch.cuda.Event(enable_timing=True) for _ in range(len(parts) + 1)]
             e[0].record()
             for i, f in enumerate(parts):
                 f()
                 e[i + 1].record()
-            ev.append(e)
         torch.cuda.nvtx.range_pop()
         barrier()
         return [[e[i].elapsed_time(e[i + 1]) * 1e-3 for e in ev] for i in range(len(parts))]
@@ -868,6 +874,7 @@ def main():
             if do_flush:
                 flush()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            queue_ahead(torch, 200)
             e0.record()
             plan.update_chase(op)
             e1.record()
@@ -882,6 +889,7 @@ def main():
             u.prefetch(False)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            queue_ahead(torch, 200)
             e0.record()
             u.update(op)
             e1.record()
@@ -890,6 +898,7 @@ def main():
             u.prefetch(True)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            queue_ahead(torch, 200)
             e0.record()
             u.update(op)
             e1.record()
