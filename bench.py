@@ -60,6 +60,7 @@ WORKLOADS = {
 # the summary beside each gives the command.  An entry stands only while the kernel is unchanged.
 NCU_TRAFFIC = {
     ("dense", 256, 4): (460_959_872, "profiles/fused_kernel_dense.md"),
+    ("reloc_stress", 256, 4): (192_249_600, "profiles/relocate_kernel_reloc_stress.md"),
     ("reloc_stress", 128, 4): (191_866_112, "profiles/relocate_kernel_reloc_stress.md"),
     ("deep", 256, 4): (757_033_088, "profiles/fused_kernel_deep_batched.md"),
     ("batched", 256, 4): (7_019_413_120, "profiles/fused_kernel_deep_batched.md"),
@@ -93,6 +94,15 @@ def l2_policy(torch, step_bytes):
                        f"order every step; L2 {l2 / 1e6:.1f} MB)")
     return True, ("flushed: 512 MiB write, then a 512 MiB read of another buffer, before every timed step "
                   "(outside the events)")
+
+
+def pick_split(plan, op, args):
+    """The fused step's split: --split if given (dc_set_split), else dc_autotune's pick."""
+    if args.split:
+        threads, ctas = (int(v) for v in args.split.split(","))
+        plan.set_split(op, threads, ctas)
+        return threads, ctas
+    return plan.autotune(op)
 
 
 def queue_ahead(torch, us: float):
@@ -349,7 +359,7 @@ def run_batched(args, rank, world):
     forest.bind()
     info = forest.info
     forest.deep_copy()
-    threads, ctas = forest.autotune(op)
+    threads, ctas = pick_split(forest, op, args)
     forest.deep_copy()
     forest.sync()
     do_flush, l2_line = l2_policy(torch, 12 * nelem + info["nrelocs"] * 20 + info["nblocks"] * 16)
@@ -440,7 +450,8 @@ def run_batched(args, rank, world):
                      "peak_kind": peak_kind, "algorithmic_bytes_per_launch": fused_bytes,
                      "traffic_source": NCU_TRAFFIC.get(("batched", threads, ctas), (None, None))[1],
                      "avg_launch_us": round(t_mean * 1e6, 2)},
-        "batched": {"autotuned_split": {"threads_per_cta": threads, "ctas_per_sm": ctas or "max"},
+        "batched": {"autotuned_split": {"threads_per_cta": threads, "ctas_per_sm": ctas or "max",
+                                        "source": "--split" if args.split else "dc_autotune"},
                     "device_step_ms": {"forest_one_launch": round(t_forest * 1e3, 4),
                                        "per_structure_8192_launches": t_single and round(t_single * 1e3, 3)},
                     "device_speedup": t_single and round(t_single / t_forest, 2),
@@ -652,6 +663,8 @@ def main():
     ap.add_argument("--workload", default="dense", choices=sorted(WORKLOADS))
     ap.add_argument("--no-compare", action="store_true", help="skip the chase / UVM comparison paths")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--split", default="", help="THREADS,CTAS_PER_SM for the fused step (dc_set_split) instead "
+                    "of dc_autotune, e.g. 256,4: repeats a launch shape, as for an ncu capture")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "native" else args.warmup
 
@@ -717,7 +730,7 @@ def main():
 
     plan.deep_copy()
     plan.sync()
-    tuned = plan.autotune(op)  # the tuning runs apply the update: start again from the host tree
+    tuned = pick_split(plan, op, args)  # the tuning runs apply the update: start again from the host tree
     plan.deep_copy()
     plan.sync()
     leaf_bytes = 12 * nelem
@@ -782,7 +795,8 @@ def main():
                 "algorithmic_bytes_per_launch": fused_bytes, "avg_launch_us": round(fused_avg * 1e6, 2),
                 "median_launch_us": round(fused_med * 1e6, 2),
                 "frac_at_median": round(fused_bytes / fused_med / 1e9 / hbm, 4),
-                "split": {"threads_per_cta": tuned[0], "ctas_per_sm": tuned[1]},
+                "split": {"threads_per_cta": tuned[0], "ctas_per_sm": tuned[1],
+                          "source": "--split" if args.split else "dc_autotune"},
                 "step_us": [round(x * 1e6, 1) for x in t_fused],
                 "traffic_source": NCU_TRAFFIC.get((args.workload,) + tuple(tuned), (None, None))[1]}
     leaf = {"kernel": "leaf_kernel<float, AXPY_HALF>", "algorithmic_bytes": leaf_bytes,

@@ -266,13 +266,21 @@ DC_API dc_status dc_relocate_update(dc_plan_t plan, const dc_op* op, dc_stream_t
 /* dc_autotune — time dc_relocate_update's launch on the bound arena under each
  * work split (128, 256 or 512 threads per CTA, i.e. 8, 4 or 2 blocks or
  * 16-byte units per thread per tile; 1, 2, 4 or 8 CTAs per SM, as far as they
- * fit), keep the fastest for the plan and cache it for the process under a key
- * made of the op's kind and element size, the plan's block count and the log2
- * histogram of the selected arrays' lengths.  Blocking.  Each timing run applies
+ * fit; each timed over three back-to-back launches), keep the fastest for the
+ * plan and cache it for the process under a key made of the op's kind and
+ * element size, the plan's block count and the log2 histogram of the selected
+ * arrays' lengths.  Blocking.  Each timing run applies
  * the update, so the arena's x arrays change: tune before the deep copy of
  * the data that matters, or deep copy again afterwards.  Outputs may be NULL. */
 DC_API dc_status dc_autotune(dc_plan_t plan, const dc_op* op, dc_stream_t stream, uint32_t* threads,
                       uint32_t* ctas_per_sm);
+/* dc_set_split — use this split for dc_relocate_update(op) on this plan
+ * instead of timing the candidates: `threads` per CTA (128, 256 or 512) and
+ * `ctas_per_sm` CTAs per SM (0 = as many as fit; more than fit are clamped at
+ * launch).  For a split tuned earlier, or to repeat a run with the same launch
+ * shape.  Host only.  Errors: DC_EINVAL (NULL plan, bad op, other thread
+ * counts). */
+DC_API dc_status dc_set_split(dc_plan_t plan, const dc_op* op, uint32_t threads, uint32_t ctas_per_sm);
 
 /* dc_update_chase — the same update, computed the way an unresolved chain
  * is: every element walks root -> ... -> struct -> x/y with device loads the

@@ -109,6 +109,7 @@ SIGNATURES = {
     "dc_resolve_offset_in": [_vp, _u64, _P(_Step), _u32, _P(_u64)],
     "dc_relocate_update": [_vp, _P(_Op), _vp],
     "dc_autotune": [_vp, _P(_Op), _vp, _P(_u32), _P(_u32)],
+    "dc_set_split": [_vp, _P(_Op), _u32, _u32],
     "dc_update_leaves": [_vp, _P(_Op), _vp],
     "dc_update_chase": [_vp, _P(_Op), _vp],
     "dc_verify_chain": [_vp, _P(_Step), _u32, _vp, _P(_u64)],
@@ -308,6 +309,11 @@ class Plan:
         t, c = ctypes.c_uint32(), ctypes.c_uint32()
         _check(lib.dc_autotune(self._h, ctypes.byref(o), _stream(stream), ctypes.byref(t), ctypes.byref(c)))
         return t.value, c.value
+
+    def set_split(self, op=None, threads: int = 256, ctas_per_sm: int = 0):
+        """Pin the fused launch's split (dc_set_split) instead of timing candidates."""
+        o, keep = _op(op or Op())
+        _check(lib.dc_set_split(self._h, ctypes.byref(o), threads, ctas_per_sm))
 
     def resolve_offset(self, path) -> int:
         st, out = _steps(path), ctypes.c_uint64()

@@ -76,11 +76,14 @@ extern "C" dc_status dc_autotune(dc_plan_t p, const dc_op* op, dc_stream_t strea
     DC_CUDA(launch_fused(r, l, threads, 0, p->sm_count, s, &fit));
     for (uint32_t ctas : {1u, 2u, 4u, 8u}) {
       if (ctas > (uint32_t)fit) break;
+      // per sample: an untimed launch keeps the device busy while the host queues the timed
+      // ones, which run back to back as repeated steps do
+      constexpr int REP = 3;
       float t[3];
-      DC_CUDA(launch_fused(r, l, threads, ctas, p->sm_count, s, nullptr));  // warm
       for (float& ms : t) {
-        DC_CUDA(cudaEventRecord(e0, s));
         DC_CUDA(launch_fused(r, l, threads, ctas, p->sm_count, s, nullptr));
+        DC_CUDA(cudaEventRecord(e0, s));
+        for (int k = 0; k < REP; k++) DC_CUDA(launch_fused(r, l, threads, ctas, p->sm_count, s, nullptr));
         DC_CUDA(cudaEventRecord(e1, s));
         DC_CUDA(cudaEventSynchronize(e1));
         DC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
@@ -105,4 +108,16 @@ extern "C" dc_status dc_autotune(dc_plan_t p, const dc_op* op, dc_stream_t strea
   if (threads_out) *threads_out = bt;
   if (ctas_out) *ctas_out = bc;
   return device_error(p, s);
+}
+
+extern "C" dc_status dc_set_split(dc_plan_t p, const dc_op* op, uint32_t threads, uint32_t ctas_per_sm) {
+  if (!p) return fail(DC_EINVAL, "plan is NULL");
+  dc_status st = check_op(p, op);
+  if (st) return st;
+  if (threads != 128 && threads != 256 && threads != 512)
+    return fail(DC_EINVAL, "threads per CTA must be 128, 256 or 512 (got %u)", threads);
+  p->tuned_threads = threads;
+  p->tuned_ctas = ctas_per_sm;
+  p->tuned_key = key_of(op);
+  return DC_OK;
 }

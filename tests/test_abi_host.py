@@ -158,6 +158,17 @@ def test_lane_groups_split_64_gib_past_their_base():
     t.free()
 
 
+def test_set_split_checks_its_arguments():
+    t = tg.workload("tiny")
+    p = dc.Plan(t.schema, t.root)
+    p.set_split(dc.Op(), 512, 0)  # host only: no device buffer needed
+    for bad in ((dc.Op(), 100, 1), (dc.Op(), 0, 4), (dc.Op(x_field=9), 256, 4)):
+        with pytest.raises(dc.DcError) as e:
+            p.set_split(*bad)
+        assert e.value.name == "DC_EINVAL"
+    p.destroy()
+
+
 def test_hand_tree_lane_layout():
     # lane 0: root (32 B) @0, child array (64 B) @32; lane 1 (position):
     # root.pos (8 B) @96, c0.pos (4 B) @112; lane 2 (velocity): @128, @144

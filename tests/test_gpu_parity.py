@@ -396,6 +396,10 @@ def forest_parity(ntrees, t_max, mode, flags=0, seed=4):
             plan.autotune(dop)
             plan.deep_copy()  # the tuning runs applied the update: start again
             plan.relocate_update(dop)
+        elif mode.startswith("split"):  # a pinned launch shape: "split-THREADS-CTAS"
+            _, threads, ctas = mode.split("-")
+            plan.set_split(dop, int(threads), int(ctas))
+            plan.relocate_update(dop)
         elif mode == "graph":
             plan.relocate_update(dop)  # puts the op's tables on the device
             plan.sync()
@@ -422,7 +426,7 @@ def forest_parity(ntrees, t_max, mode, flags=0, seed=4):
     plan.destroy()
 
 
-@pytest.mark.parametrize("mode", ["plain", "fused", "tuned", "graph", "roundtrip"])
+@pytest.mark.parametrize("mode", ["plain", "fused", "tuned", "split-128-1", "split-512-64", "graph", "roundtrip"])
 def test_forest_of_uneven_trees(mode):
     forest_parity(300, 256 << 10, mode, flags=dc.PLAN_MAP_HOST if mode == "roundtrip" else 0)
 
