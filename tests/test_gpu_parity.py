@@ -464,6 +464,45 @@ def test_fused_single_tree_workloads():
         plan.destroy()
 
 
+FUSED_CASES = {
+    # Linear chain, fp64 A: x *= 1.5 on every level (the paper's kernel)
+    "linear_scale_f64": (lambda: tg.linear_tree(6, 100000, "allinit", seed=3), dict(kind=dc.OP_SCALE, x=2, scale=1.5)),
+    # the same on the last level only, reached by a chain
+    "linear_chain_f64": (lambda: tg.linear_tree(8, 70001, "allinit", seed=4),
+                         dict(kind=dc.OP_SCALE, sel=dc.SEL_CHAIN, x=2, scale=-0.75, path=[(3, 0)] * 7)),
+    # node tree, fp32: x *= scale, and x += 0.5*y on one node's chain
+    "node_scale_f32": (lambda: tg.node_tree(4, 6, tg.uniform(0, 3000), seed=8), dict(kind=dc.OP_SCALE, scale=3.0)),
+    "node_chain_axpy": (lambda: tg.node_tree(4, 6, tg.uniform(1, 3000), seed=9),
+                        dict(sel=dc.SEL_CHAIN, path=[(NODE_LEAF, 5), (NODE_LEAF, 2)])),
+}
+
+
+@pytest.mark.parametrize("threads", [128, 256, 512])
+@pytest.mark.parametrize("case", sorted(FUSED_CASES))
+def test_fused_launch_every_kind_and_width(case, threads):
+    """dc_relocate_update's instances beyond fp32 x += 0.5*y over every node:
+    fp64 and fp32 SCALE, chain selections, at each CTA size (pinned with
+    dc_set_split), twice in a row: the device image after each launch equals
+    the oracle's copy updated as many times."""
+    make, op_kw = FUSED_CASES[case]
+    src, ref = make(), make()
+    s = src.schema
+    plan = dc.Plan(s, src.root)
+    plan.bind()
+    plan.deep_copy()
+    dop, oop = ops_pair(**op_kw)
+    plan.set_split(dop, threads, 2)
+    cp = oracle.deep_copy(s, ref.root)
+    for _ in range(2):
+        plan.relocate_update(dop)
+        plan.sync()
+        oracle.update(s, cp.root, oop)
+        image_ok(plan, s, cp.root)
+    plan.destroy()
+    src.free()
+    ref.free()
+
+
 # ---- host arenas (allocation requests served from one pinned buffer) -----------------
 
 def arena_case(make_tree, op_kw, mode, arena_bytes):
