@@ -117,7 +117,8 @@ def test_deep_chain_to_leaf_full_size():
 
 
 def test_reloc_stress_many_tiles():
-    # 1,118,481 nodes, 2,306,868 blocks: the relocation's look-back spans ~2,250 tiles
+    # 1,118,481 nodes, 2,306,868 blocks: 4,370 relocation tiles over the 35.8 MB struct lane,
+    # several per CTA through the two-stage pipeline, with the device-side slot check on
     full_parity(lambda: tg.workload("reloc_stress"), {}, verify=True)
 
 
