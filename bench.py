@@ -286,6 +286,26 @@ def oracle_baseline(tree, workload, budget_s=10.0):
                       f"({tree.payload_bytes / 1e6:.1f} MB), {t_total:.1f} s on one host core"}
 
 
+def cpu_update_all_cores(tree, workload, leaf_bytes, reps=5):
+    """The leaf update alone on every host core (the oracle's update split into chunks over OpenMP
+    threads, bit-identical to it) over the host tree in place: the CPU counterpart of the device
+    step's leaf phase, with the tree already in host memory (no copy, no relocation)."""
+    import oracle
+    op = oracle_op(workload)
+    oracle.update_parallel(tree.schema, tree.root, op)  # warm: pages and threads
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.update_parallel(tree.schema, tree.root, op)
+        ts.append(time.perf_counter() - t0)
+    t = statistics.median(ts)
+    return {"value": round(tree.payload_bytes / t / 1e9, 3), "unit": "GB/s", "cores": oracle.threads(),
+            "kind": "oracle update on every host core (OpenMP)", "ms_per_step": round(t * 1e3, 3),
+            "leaf_gbs": round(leaf_bytes / t / 1e9, 2),
+            "sample": f"median of {reps} in-place updates of every selected array of the whole workload "
+                      f"({leaf_bytes / 1e6:.1f} MB moved each)"}
+
+
 def link_peaks(torch, nbytes=256 << 20, reps=5):
     """Pinned cudaMemcpyAsync peaks: each direction alone (best of `reps` at 256 MiB), both
     directions at once on two streams (an H2D of 2x and a D2H of 1x the bytes, the round trip's
@@ -923,6 +943,7 @@ def main():
         u.destroy()
 
     cpu = None if (args.no_cpu or rank != 0) else oracle_baseline(tree, args.workload)
+    cpu_all = None if (args.no_cpu or rank != 0) else cpu_update_all_cores(tree, args.workload, leaf_bytes)
 
     if rank == 0:
         out = {
@@ -946,6 +967,7 @@ def main():
             "hbm_copy_gbs_now": copy_now,
             "host_side": host_side,
             "e2e": e2e, "e2e_three_calls_map_host": e2e_mapped, "e2e_staged": e2e_staged, "link": link, "compare": compare, "cpu_baseline": cpu,
+            "cpu_baseline_all_cores": cpu_all,
             "clocks": clk,
             "gpu_launches": launches,
         }

@@ -34,7 +34,7 @@ def build_lib(force: bool = False) -> str:
     hdr = os.path.join(_HERE, "oracle.h")
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
             os.path.getmtime(src), os.path.getmtime(hdr)):
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-fPIC", "-shared",
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-fPIC", "-shared", "-fopenmp",
                                "-ffp-contract=off", "-fno-fast-math", "-o", _SO, src])
     return _SO
 
@@ -90,6 +90,8 @@ def lib():
         L.or_count.argtypes = [P(_Schema), ctypes.c_void_p, P(_Counts)]
         L.or_deep_copy.argtypes = [P(_Schema), ctypes.c_void_p, P(_Arena), P(ctypes.c_void_p)]
         L.or_update.argtypes = [P(_Schema), ctypes.c_void_p, P(_Op)]
+        L.or_update_parallel.argtypes = [P(_Schema), ctypes.c_void_p, P(_Op), ctypes.c_int]
+        L.or_threads.argtypes = []
         L.or_copy_back.argtypes = [P(_Schema), ctypes.c_void_p, ctypes.c_void_p, P(_Op), ctypes.c_int]
         L.or_trees_equal.argtypes = [P(_Schema), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_char_p,
                                      ctypes.c_size_t]
@@ -101,8 +103,8 @@ def lib():
                                        P(ctypes.c_uint64)]
         L.or_host_resolve.argtypes = [P(_Schema), ctypes.c_void_p, P(_Step), ctypes.c_uint32,
                                       P(ctypes.c_uint64)]
-        for f in ("or_count", "or_deep_copy", "or_update", "or_copy_back", "or_trees_equal",
-                  "or_check_image", "or_image_resolve", "or_host_resolve"):
+        for f in ("or_count", "or_deep_copy", "or_update", "or_update_parallel", "or_threads", "or_copy_back",
+                  "or_trees_equal", "or_check_image", "or_image_resolve", "or_host_resolve"):
             getattr(L, f).restype = ctypes.c_int
         _L = L
     return _L
@@ -206,6 +208,19 @@ def deep_copy(schema, src_root: int, ptr_base: int = 0) -> Copy:
 def update(schema, root: int, op: Op) -> None:
     o, keep = _op(op)
     _check(lib().or_update(ctypes.byref(_cs(schema).struct), root, ctypes.byref(o)), "update")
+
+
+def update_parallel(schema, root: int, op: Op, threads: int = 0) -> None:
+    """``update`` on ``threads`` host cores (0 = all): the multi-core CPU baseline,
+    bit-identical to ``update``."""
+    o, keep = _op(op)
+    _check(lib().or_update_parallel(ctypes.byref(_cs(schema).struct), root, ctypes.byref(o), threads),
+           "update_parallel")
+
+
+def threads() -> int:
+    """Host threads ``update_parallel`` uses by default."""
+    return lib().or_threads()
 
 
 def copy_back(schema, copy_root: int, src_root: int, op: Optional[Op], all_arrays: bool = False):

@@ -6,6 +6,7 @@
  */
 #include "oracle.h"
 
+#include <omp.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -265,6 +266,137 @@ int or_update(const or_schema* s, void* root, const or_op* op) {
   if (ti != op->type) return OR_EINVAL;
   return apply(s, op, node);
 }
+
+/* ---- the same update on every host core (the CPU baseline on N cores) ------
+ * Not a parity reference.  It collects the structs the op selects, as
+ * or_update visits them, then splits each one's arrays into chunks of
+ * 2^16 elements and applies the same per-element arithmetic as apply() to the
+ * chunks in parallel (OpenMP).  Elements are independent, so the result is
+ * bit-identical to or_update's. */
+
+typedef struct {
+  uint8_t** v;
+  uint64_t n, cap;
+} node_list;
+
+static int push_node(node_list* l, uint8_t* node) {
+  if (l->n == l->cap) {
+    uint64_t cap = l->cap ? 2 * l->cap : 1024;
+    uint8_t** v = (uint8_t**)realloc(l->v, cap * sizeof *v);
+    if (!v) return OR_ENOMEM;
+    l->v = v;
+    l->cap = cap;
+  }
+  l->v[l->n++] = node;
+  return OR_OK;
+}
+
+static int collect_all(const or_schema* sc, uint32_t ti, uint8_t* s, const or_op* op, node_list* out) {
+  const or_type* T = &sc->types[ti];
+  if (ti == op->type) {
+    int rc = push_node(out, s);
+    if (rc) return rc;
+  }
+  for (uint32_t fi = 0; fi < T->nfields; fi++) {
+    const or_field* f = &T->fields[fi];
+    if (f->kind != OR_CHILD) continue;
+    uint64_t n;
+    if (count_of(T, s, f, &n)) return OR_EINVAL;
+    uint8_t* c = (uint8_t*)ptr_at(s, f);
+    uint32_t cs = sc->types[f->child_type].size;
+    for (uint64_t j = 0; j < n; j++) {
+      int rc = collect_all(sc, (uint32_t)f->child_type, c + j * cs, op, out);
+      if (rc) return rc;
+    }
+  }
+  return OR_OK;
+}
+
+/* elements [lo, hi) of one selected struct's x (and y), as apply() does them */
+static void apply_range(const or_op* op, int kind, uint8_t* x, const uint8_t* y, uint64_t lo, uint64_t hi) {
+  if (op->kind == OR_OP_SCALE) {
+    if (kind == 0) {
+      float a = (float)op->scale;
+      float* xf = (float*)x;
+      for (uint64_t i = lo; i < hi; i++) xf[i] = xf[i] * a;
+    } else {
+      double* xd = (double*)x;
+      for (uint64_t i = lo; i < hi; i++) xd[i] = xd[i] * op->scale;
+    }
+  } else if (kind == 0) {
+    float* xf = (float*)x;
+    const float* yf = (const float*)y;
+    for (uint64_t i = lo; i < hi; i++) {
+      float half = 0.5f * yf[i];
+      xf[i] = xf[i] + half;
+    }
+  } else {
+    double* xd = (double*)x;
+    const double* yd = (const double*)y;
+    for (uint64_t i = lo; i < hi; i++) {
+      double half = 0.5 * yd[i];
+      xd[i] = xd[i] + half;
+    }
+  }
+}
+
+int or_update_parallel(const or_schema* s, void* root, const or_op* op, int nthreads) {
+  if (!s || !root || !op || op->type >= s->ntypes) return OR_EINVAL;
+  const or_type* T = &s->types[op->type];
+  if (op->x_field >= T->nfields) return OR_EINVAL;
+  if (op->kind == OR_OP_AXPY_HALF && op->y_field >= T->nfields) return OR_EINVAL;
+  node_list nodes = {0};
+  int rc;
+  if (op->sel == OR_SEL_ALL) {
+    rc = collect_all(s, s->root_type, (uint8_t*)root, op, &nodes);
+  } else {
+    uint8_t* node;
+    uint32_t ti;
+    rc = walk_chain(s, (uint8_t*)root, op->path, op->path_len, &node, &ti);
+    if (!rc) rc = ti != op->type ? OR_EINVAL : push_node(&nodes, node);
+  }
+  /* the chunks: (node, first element) pairs, checked as apply() checks them */
+  const uint64_t CH = 1u << 16;
+  uint64_t nchunks = 0;
+  const or_field* fx = &T->fields[op->x_field];
+  const or_field* fy = op->kind == OR_OP_AXPY_HALF ? &T->fields[op->y_field] : NULL;
+  for (uint64_t k = 0; !rc && k < nodes.n; k++) {
+    uint64_t n, ny;
+    if (fx->kind != OR_ARRAY || count_of(T, nodes.v[k], fx, &n) || fx->elem_kind > 1) rc = OR_EINVAL;
+    else if (fy && (fy->kind != OR_ARRAY || count_of(T, nodes.v[k], fy, &ny) || ny != n ||
+                    fy->elem_kind != fx->elem_kind)) rc = OR_EINVAL;
+    else nchunks += (n + CH - 1) / CH;
+  }
+  uint64_t* chunk = NULL;  /* per chunk: node index, first element, end */
+  if (!rc && nchunks) {
+    chunk = (uint64_t*)malloc(3 * nchunks * sizeof *chunk);
+    if (!chunk) rc = OR_ENOMEM;
+  }
+  if (!rc) {
+    uint64_t c = 0;
+    for (uint64_t k = 0; k < nodes.n; k++) {
+      uint64_t n = 0;
+      count_of(T, nodes.v[k], fx, &n);
+      for (uint64_t lo = 0; lo < n; lo += CH, c++) {
+        chunk[3 * c] = k;
+        chunk[3 * c + 1] = lo;
+        chunk[3 * c + 2] = lo + CH < n ? lo + CH : n;
+      }
+    }
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t c2 = 0; c2 < (int64_t)nchunks; c2++) {
+      uint8_t* node = nodes.v[chunk[3 * c2]];
+      apply_range(op, fx->elem_kind, (uint8_t*)ptr_at(node, fx), fy ? (const uint8_t*)ptr_at(node, fy) : NULL,
+                  chunk[3 * c2 + 1], chunk[3 * c2 + 2]);
+    }
+  }
+  free(chunk);
+  free(nodes.v);
+  return rc;
+}
+
+int or_threads(void) { return omp_get_max_threads(); }
 
 /* ---- copy back (Alg 2 step 5) ---------------------------------------------- */
 

@@ -17,6 +17,8 @@
  *                     paper's scaling kernel x[i] *= scale (Sec. 4.1.2 item 1,
  *                     Listing 2), on every struct (allused) or on the struct a
  *                     pointer chain reaches (LLused / Listing 2's chain).
+ *   or_update_parallel  the same on every host core (OpenMP): the benchmark's
+ *                     multi-core CPU baseline, pinned to or_update.
  *   or_copy_back      transfer back of the arrays the kernel wrote (Alg 2 step 5).
  *   or_trees_equal    the results check (Alg 2 step 6): two trees have the same
  *                     shape, the same scalar/padding bytes and the same arrays.
@@ -99,6 +101,12 @@ typedef struct {
 int or_count(const or_schema* s, const void* root, or_counts* out);
 int or_deep_copy(const or_schema* s, const void* src_root, or_arena* a, void** dst_root);
 int or_update(const or_schema* s, void* root, const or_op* op);
+/* The same update with the selected arrays split into 2^16-element chunks
+ * that `nthreads` OpenMP threads (0 = all) apply in parallel: the CPU
+ * baseline on every host core.  Not a parity reference; its results equal
+ * or_update's bit for bit.  or_threads() = the threads it uses by default. */
+int or_update_parallel(const or_schema* s, void* root, const or_op* op, int nthreads);
+int or_threads(void);
 int or_copy_back(const or_schema* s, const void* copy_root, void* src_root, const or_op* op,
                  int all_arrays);
 int or_trees_equal(const or_schema* s, const void* a, const void* b, char* msg, size_t msglen);

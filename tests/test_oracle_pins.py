@@ -453,3 +453,31 @@ def test_generator_is_deterministic():
     assert np.all(np.ldexp(v.astype(np.float64), 23) == np.round(np.ldexp(v.astype(np.float64), 23)))
     for t in (a, b, c):
         t.free()
+
+
+PARALLEL_CASES = [
+    # (tree, op): f32 axpy over every node with multi-chunk and empty arrays; f64 scale over every
+    # level and on a chain; an axpy on one node reached by a chain
+    (lambda: tg.node_tree(3, 5, tg.uniform(0, 200000), seed=31), oracle.Op()),
+    (lambda: tg.linear_tree(5, 150001, "allinit", seed=32), oracle.Op(kind=oracle.OP_SCALE, x_field=2, scale=1.5)),
+    (lambda: tg.linear_tree(6, 70000, "llinit", seed=33),
+     oracle.Op(kind=oracle.OP_SCALE, sel=oracle.SEL_CHAIN, x_field=2, scale=-0.75, path=[(3, 0)] * 5)),
+    (lambda: tg.node_tree(3, 4, tg.uniform(1, 90000), seed=34),
+     oracle.Op(sel=oracle.SEL_CHAIN, path=[(4, 3), (4, 1)])),
+]
+
+
+@pytest.mark.parametrize("threads", [1, 3, 0])
+@pytest.mark.parametrize("case", range(len(PARALLEL_CASES)))
+def test_parallel_update_equals_the_sequential_update(case, threads):
+    """The multi-core CPU baseline (update_parallel) is pinned to the oracle's
+    update: on the same inputs every array is bit-identical afterwards, for
+    any thread count."""
+    make, op = PARALLEL_CASES[case]
+    a, b = make(), make()
+    oracle.update(a.schema, a.root, op)
+    oracle.update_parallel(b.schema, b.root, op, threads)
+    ok, msg = oracle.trees_equal(a.schema, a.root, b.root)
+    assert ok, msg
+    a.free()
+    b.free()
