@@ -210,17 +210,56 @@ def rank_seed(workload: str, rank: int) -> int:
 
 
 def aggregate(payload_bytes: int, steps: int, t_local: float, world: int, dist=None):
-    """Whole-job throughput: bytes all ranks moved / the slowest rank's time.
-    Returns (GB/s, max time)."""
-    t = t_local
+    """Whole-job throughput: the bytes all ranks moved (each rank's own payload, summed) / the
+    slowest rank's time.  Returns (GB/s, max time)."""
+    t, total = t_local, payload_bytes
     if world > 1:
         import torch
-        x = torch.tensor([t_local], dtype=torch.float64)
         dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
-        x = x.to(dev)
+        x = torch.tensor([t_local], dtype=torch.float64, device=dev)
         dist.all_reduce(x, op=dist.ReduceOp.MAX)
         t = float(x.item())
-    return payload_bytes * world * steps / t / 1e9, t
+        y = torch.tensor([payload_bytes], dtype=torch.float64, device=dev)
+        dist.all_reduce(y, op=dist.ReduceOp.SUM)
+        total = float(y.item())
+    return total * steps / t / 1e9, t
+
+
+class Ranks:
+    """The ranks of a torchrun job, one per GPU: a barrier, and max / sum over ranks.  With one
+    rank every call is local.  The data path has no collective; these only time the job."""
+
+    def __init__(self, torch, world: int):
+        self.torch, self.world, self.dist = torch, world, None
+        if world > 1:
+            import torch.distributed as dist
+            if not dist.is_initialized():
+                dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo", init_method="env://")
+            self.dist = dist
+
+    def barrier(self):
+        if self.torch.cuda.is_available():
+            self.torch.cuda.synchronize()
+        if self.dist:
+            self.dist.barrier()
+
+    def _reduce(self, x: float, op) -> float:
+        if not self.dist:
+            return x
+        dev = "cuda" if self.dist.get_backend() == "nccl" else "cpu"
+        t = self.torch.tensor([x], dtype=self.torch.float64, device=dev)
+        self.dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    def max(self, x: float) -> float:
+        return self._reduce(x, self.dist.ReduceOp.MAX) if self.dist else x
+
+    def sum(self, x: float) -> float:
+        return self._reduce(x, self.dist.ReduceOp.SUM) if self.dist else x
+
+    def close(self):
+        if self.dist:
+            self.dist.destroy_process_group()
 
 
 def run_reference(args, rank, world):
@@ -360,16 +399,24 @@ def link_peaks(torch, nbytes=256 << 20, reps=5):
     return out
 
 
-def run_batched(args, rank, world):
+def run_batched(args, rank, world, ranks):
     """One forest plan over 4,096 trees (one fused relocation + update launch;
     one round trip) against 4,096 per-structure plans (two launches each; one
-    round trip each), on the same GPU."""
+    round trip each), on the same GPU.  With N ranks, 4,096 x N trees are drawn
+    (sizes only) and assigned to the ranks by bytes (greedy LPT,
+    dc_partition_by_bytes); each rank builds and runs its own share."""
     import torch
     import treegen as tg
     import paper_1906_01128_b300 as dc
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     ntrees = int(os.environ.get("DC_BATCH_TREES", "4096"))
-    trees = tg.batched(ntrees, seed=rank_seed("batched", rank))
+    if world > 1:
+        specs = tg.batched_specs(ntrees * world, seed=rank_seed("batched", 0))
+        part, part_bytes = dc.partition_by_bytes([sp.bytes for sp in specs], world)
+        trees = [sp.build() for sp, k in zip(specs, part) if k == rank]
+        ntrees = len(trees)
+    else:
+        trees = tg.batched(ntrees, seed=rank_seed("batched", 0))
+        part_bytes = [sum(t.payload_bytes for t in trees)]
     s = trees[0].schema
     payload = sum(t.payload_bytes for t in trees)
     nelem = sum(t.nelems("Node", "position") for t in trees)
@@ -414,14 +461,16 @@ def run_batched(args, rank, world):
         return statistics.median(ts), ts
 
     launches0 = dc.kernel_launches()
+    ranks.barrier()
     t_forest, ts_forest = timed(lambda: forest.relocate_update(op), args.steps, "dc_step")
+    ranks.barrier()
     launches = dc.kernel_launches() - launches0 - args.warmup  # the timed steps' launches (one per step)
 
     def per_structure():
         for p in singles:
             p.relocate()
             p.update(op)
-    t_single = timed(per_structure, max(3, args.steps // 4), "dc_per_structure")[0] if singles else None
+    t_single = ranks.max(timed(per_structure, max(3, args.steps // 4), "dc_per_structure")[0]) if singles else None
 
     def wall(fn, reps):
         ts = []
@@ -434,15 +483,18 @@ def run_batched(args, rank, world):
                 ts.append(time.perf_counter() - t0)
         return statistics.median(ts)
 
-    e2e_forest = wall(lambda: forest.roundtrip(op), max(3, args.steps // 4))
-    e2e_single = wall(lambda: [p.roundtrip(op) for p in singles], 3) if singles else None
+    ranks.barrier()
+    e2e_forest = ranks.max(wall(lambda: forest.roundtrip(op), max(3, args.steps // 4)))
+    e2e_single = ranks.max(wall(lambda: [p.roundtrip(op) for p in singles], 3)) if singles else None
     clk = clocks.stop()
     hbm, peak_kind = peaks()
     reloc_bytes = info["nrelocs"] * 20 + info["nblocks"] * 16  # 12 B entry + 8 B slot; 8 B size + 8 B offset
     fused_bytes = 12 * nelem + reloc_bytes
-    t_mean = statistics.mean(ts_forest)
+    t_mean = ranks.max(statistics.mean(ts_forest))  # the slowest rank's step
+    t_forest = ranks.max(t_forest)
+    job_payload = ranks.sum(payload)  # the bytes all ranks' steps process
     cpu = None
-    if not args.no_cpu:
+    if not args.no_cpu and rank == 0:
         import oracle
         t_cpu, n = 0.0, 0
         for t in trees[:512]:  # a bounded sample: the first 512 trees
@@ -456,13 +508,17 @@ def run_batched(args, rank, world):
                "sample": f"the first 512 of the {ntrees} trees ({n / 1e6:.1f} MB), deep copy + update + copy back, "
                          f"one core"}
     out = {
-        "metric": METRIC, "value": round(payload * world / t_mean / 1e9, 2), "unit": "GB/s", "n_gpus": world,
+        "metric": METRIC, "value": round(job_payload / t_mean / 1e9, 2), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_mean * 1e3, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOADS["batched"], "trees": ntrees, "nodes": info["nstructs"],
                    "blocks": info["nblocks"], "payload_bytes": payload,
                    "step": "dc_relocate_update on the forest (one persistent launch)",
-                   "l2": l2_line},
+                   "l2": l2_line,
+                   "parallelism": (f"{world} ranks, one per GPU; {len(part)} trees assigned by bytes "
+                                   f"(greedy LPT), per-rank payload "
+                                   f"{min(part_bytes) / 1e9:.3f}-{max(part_bytes) / 1e9:.3f} GB"
+                                   if world > 1 else "1 rank")},
         "roofline": {"bound": "hbm", "kernel": "fused_kernel<float, AXPY_HALF> (relocation + leaf update)",
                      "achieved": round(fused_bytes / t_mean / 1e9, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(fused_bytes / t_mean / 1e9 / hbm, 4),
@@ -478,7 +534,7 @@ def run_batched(args, rank, world):
                     "e2e_ms": {"forest_roundtrip": round(e2e_forest * 1e3, 3),
                                "per_structure_roundtrips": e2e_single and round(e2e_single * 1e3, 3)},
                     "e2e_speedup": e2e_single and round(e2e_single / e2e_forest, 2)},
-        "e2e": {"value": round(payload * world / e2e_forest / 1e9, 3), "unit": "GB/s",
+        "e2e": {"value": round(job_payload / e2e_forest / 1e9, 3), "unit": "GB/s",
                 "h2d_bytes_per_step": info["data_bytes"], "d2h_bytes_per_step": 4 * nelem,
                 "api": "dc_roundtrip on the forest plan, DC_PLAN_MAP_HOST"},
         "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,
@@ -490,13 +546,12 @@ def run_batched(args, rank, world):
     forest.destroy()
 
 
-def run_served(args, rank, world):
+def run_served(args, rank, world, ranks):
     """The request server (8 slots, continuous batching, resident trees)
     against the same stream handled sequentially with nothing resident."""
     import torch
     import treegen as tg
     import paper_1906_01128_b300 as dc
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     duration = float(os.environ.get("DC_SERVED_SECONDS", "2"))
     reqs, nkeys = tg.poisson_requests(duration, 2000.0, 0.3, seed=5 + rank)
     trees = tg.batched(nkeys, seed=5 + rank, t_min=16 << 10, t_max=64 << 20)
@@ -507,15 +562,18 @@ def run_served(args, rank, world):
     results = {}
     clocks = Clocks()
     clocks.start()
+    job_payload = ranks.sum(payload)  # every rank serves its own stream
     for mode, slots, flags in (("served", 8, 0), ("sequential", 1, dc.SERVER_SEQUENTIAL)):
         srv = dc.Server(s, pool, pinned_bytes=pinned, slots=slots, flags=flags)
+        ranks.barrier()
         lat = srv.run([(k, trees[k].root, a, r) for k, a, r in reqs])
         st = srv.stats
         srv.destroy()
+        wall_s = ranks.max(st["wall_s"])  # the slowest rank's stream
         lat.sort()
         results[mode] = {"p50_ms": round(lat[len(lat) // 2], 3), "p99_ms": round(lat[int(len(lat) * 0.99)], 3),
-                         "max_ms": round(lat[-1], 3), "wall_s": round(st["wall_s"], 3),
-                         "gbs": round(payload / st["wall_s"] / 1e9, 3), "resident_hits": st["resident_hits"],
+                         "max_ms": round(lat[-1], 3), "wall_s": round(wall_s, 3),
+                         "gbs": round(job_payload / wall_s / 1e9, 3), "resident_hits": st["resident_hits"],
                          "evictions": st["evictions"], "deep_copied_bytes": st["h2d_bytes"],
                          "copied_back_bytes": st["d2h_bytes"], "peak_resident_bytes": st["peak_resident_bytes"]}
     clk = clocks.stop()
@@ -537,7 +595,7 @@ def run_served(args, rank, world):
         print(json.dumps(out))
 
 
-def run_paper(args, rank, world):
+def run_paper(args, rank, world, ranks):
     """The paper's transfer-scheme comparison (Sec. 4-6) measured on this GPU:
     wall time of transfer + kernel + transfer back for marshalling (a full deep
     copy), pointerchain (only the effective-address array moves) and UVM, the
@@ -547,7 +605,6 @@ def run_paper(args, rank, world):
     import torch
     import treegen as tg
     import paper_1906_01128_b300 as dc
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     n_lin = int(os.environ.get("DC_PAPER_N", str(10 ** 7)))
     reps = max(3, args.steps // 4)
     flush = L2Flush(torch)
@@ -692,12 +749,6 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
-    if args.workload == "batched":
-        return run_batched(args, rank, world)
-    if args.workload == "served":
-        return run_served(args, rank, world)
-    if args.workload == "paper":
-        return run_paper(args, rank, world)
 
     import torch
     import torch.distributed as dist
@@ -706,8 +757,11 @@ def main():
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", init_method="env://")
+    ranks = Ranks(torch, world)
+    if args.workload in ("batched", "served", "paper"):
+        {"batched": run_batched, "served": run_served, "paper": run_paper}[args.workload](args, rank, world, ranks)
+        ranks.close()
+        return
     # each rank deep-copies its own independent tree (weak scaling, no data-path collective)
     tree = tg.node_tree(*tg.WORKLOADS[args.workload][:4], seed=rank_seed(args.workload, rank))
     s = tree.schema
@@ -736,17 +790,8 @@ def main():
         op = dc.Op()
     flush = L2Flush(torch)
 
-    def barrier():
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    barrier = ranks.barrier
+    max_over_ranks = ranks.max
 
     plan.deep_copy()
     plan.sync()
@@ -973,8 +1018,7 @@ def main():
         }
         print(json.dumps(out))
     plan.destroy()
-    if world > 1:
-        dist.destroy_process_group()
+    ranks.close()
 
 
 if __name__ == "__main__":

@@ -350,6 +350,18 @@ DC_API dc_status dc_uvm_copy_back(dc_uvm_t uvm, const void* host_root, uint32_t 
 DC_API dc_status dc_uvm_sync(dc_uvm_t uvm, dc_stream_t stream);
 DC_API dc_status dc_uvm_destroy(dc_uvm_t uvm);
 
+/* ---- several GPUs -------------------------------------------------------------
+ * dc_partition_by_bytes — assign n independent trees (payload sizes
+ * bytes[0..n)) to nparts GPUs with no exchange between them: greedy LPT,
+ * trees in decreasing size (stable), each to the part with the fewest bytes
+ * so far (the lower part index on ties).  part_of[i] receives tree i's part;
+ * part_bytes (nparts entries, may be NULL) each part's total.  No part
+ * exceeds the mean by more than the largest tree, and the result depends on
+ * the inputs alone, so every rank can compute it independently.  Host only.
+ * Errors: DC_EINVAL (nparts = 0, NULL arrays with n > 0, total overflow). */
+DC_API dc_status dc_partition_by_bytes(const uint64_t* bytes, uint64_t n, uint32_t nparts, uint32_t* part_of,
+                                       uint64_t* part_bytes);
+
 /* ---- relocation that allocates nothing ---------------------------------------
  * The paper has no counterpart of this call; it exists for callers that
  * cannot allocate memory at the point where they relocate.  Examples: code

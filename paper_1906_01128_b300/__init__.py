@@ -19,7 +19,7 @@ from __future__ import annotations
 import ctypes
 import os
 from dataclasses import dataclass
-from typing import Optional, Sequence, Tuple
+from typing import List, Optional, Sequence, Tuple
 
 import torch  # loads the CUDA runtime that libdc.so then shares
 
@@ -110,6 +110,7 @@ SIGNATURES = {
     "dc_relocate_update": [_vp, _P(_Op), _vp],
     "dc_autotune": [_vp, _P(_Op), _vp, _P(_u32), _P(_u32)],
     "dc_set_split": [_vp, _P(_Op), _u32, _u32],
+    "dc_partition_by_bytes": [_P(_u64), _u64, _u32, _P(_u32), _P(_u64)],
     "dc_update_leaves": [_vp, _P(_Op), _vp],
     "dc_update_chase": [_vp, _P(_Op), _vp],
     "dc_verify_chain": [_vp, _P(_Step), _u32, _vp, _P(_u64)],
@@ -167,6 +168,16 @@ def _check(status: int):
 def kernel_launches() -> int:
     """Kernels this library has launched in this process."""
     return lib.dc_kernel_launches()
+
+
+def partition_by_bytes(sizes: Sequence[int], nparts: int) -> Tuple[List[int], List[int]]:
+    """dc_partition_by_bytes: (part of each tree, bytes of each part), greedy LPT."""
+    n = len(sizes)
+    b = (ctypes.c_uint64 * max(n, 1))(*sizes)
+    part = (ctypes.c_uint32 * max(n, 1))()
+    load = (ctypes.c_uint64 * max(nparts, 1))()
+    _check(lib.dc_partition_by_bytes(b, n, nparts, part, load))
+    return list(part[:n]), list(load[:nparts])
 
 
 def _stream(stream) -> int:

@@ -3,6 +3,7 @@ relocation tables, the arena layout, chain resolution and error paths.  The
 device relocation is modelled on the host from the plan's tables and checked
 with the oracle's image checker."""
 import ctypes
+import itertools
 import os
 import random
 import re
@@ -298,3 +299,29 @@ def test_device_calls_need_a_bound_buffer():
     assert _status(lambda: p.update(dc.Op(y_field=2), stream=0)) == "DC_EINVAL"  # x == y
     p.destroy()
     t.free()
+
+
+def test_partition_by_bytes_is_greedy_lpt():
+    """dc_partition_by_bytes against LPT's definition and its bound.  Graham's
+    tight example (3 parts, sizes 5,5,4,4,3,3,3) worked by hand: 5->0, 5->1,
+    4->2, 4->2, 3->0, 3->1, 3->0 (ties to the lower part), makespan 11 against
+    the optimum 9 = (4/3 - 1/9) * 9.  On small random inputs the makespan stays
+    within Graham's bound of the brute-force optimum, and the assignment is a
+    function of the input."""
+    part, loads = dc.partition_by_bytes([5, 5, 4, 4, 3, 3, 3], 3)
+    assert part == [0, 1, 2, 2, 0, 1, 0] and loads == [11, 8, 8]
+    assert dc.partition_by_bytes([], 4) == ([], [0, 0, 0, 0])
+    with pytest.raises(dc.DcError) as e:
+        dc.partition_by_bytes([1, 2], 0)
+    assert e.value.name == "DC_EINVAL"
+    rng = random.Random(5)
+    for _ in range(200):
+        n, k = rng.randint(1, 8), rng.randint(1, 3)
+        sizes = [rng.randint(0, 50) for _ in range(n)]
+        part, loads = dc.partition_by_bytes(sizes, k)
+        assert (part, loads) == dc.partition_by_bytes(sizes, k)
+        assert all(0 <= p < k for p in part)
+        assert [sum(s for s, p in zip(sizes, part) if p == j) for j in range(k)] == loads
+        best = min(max(sum(s for s, a in zip(sizes, assign) if a == j) for j in range(k))
+                   for assign in itertools.product(range(k), repeat=n))
+        assert 3 * k * max(loads) <= (4 * k - 1) * best or max(loads) == best

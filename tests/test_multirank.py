@@ -48,3 +48,42 @@ def test_two_gloo_ranks_weak_scaling():
         seed, value, t_max, payload = res[r]
         assert t_max == pytest.approx(1.5)  # the slowest rank's time
         assert value == pytest.approx(payload * world * 4 / 1.5 / 1e9)
+
+
+def _lpt_rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    import torch
+    import bench
+    import treegen as tg
+    import paper_1906_01128_b300 as dc
+    ranks = bench.Ranks(torch, world)  # gloo: no GPU here
+    specs = tg.batched_specs(60, seed=9, t_max=256 << 10)
+    part, loads = dc.partition_by_bytes([sp.bytes for sp in specs], world)
+    mine = [sp for sp, k in zip(specs, part) if k == rank]
+    trees = [sp.build() for sp in mine]
+    assert all(t.payload_bytes == sp.bytes for t, sp in zip(trees, mine))  # sizes counted without building
+    out[rank] = (part, loads, [sp.index for sp in mine], ranks.sum(len(mine)), ranks.sum(sum(sp.bytes for sp in mine)),
+                 ranks.max(float(rank)))
+    ranks.barrier()
+    ranks.close()
+
+
+def test_two_gloo_ranks_take_disjoint_lpt_shares():
+    """The batched bench path with N ranks: every rank draws the same tree sizes,
+    computes the same greedy-LPT assignment on its own, and builds only its
+    share; together the shares cover every tree once, with byte totals that
+    differ by at most the largest tree."""
+    world = 2
+    port = _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_lpt_rank, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    assert res[0][0] == res[1][0] and res[0][1] == res[1][1]  # the same assignment on both ranks
+    assert sorted(res[0][2] + res[1][2]) == list(range(60))
+    loads = res[0][1]
+    import treegen as tg
+    sizes = [sp.bytes for sp in tg.batched_specs(60, seed=9, t_max=256 << 10)]
+    assert sum(loads) == sum(sizes) and max(loads) - min(loads) <= max(sizes)
+    for r in range(world):
+        assert res[r][3] == 60 and res[r][4] == sum(sizes) and res[r][5] == world - 1

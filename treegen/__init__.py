@@ -464,24 +464,49 @@ def poisson_requests(duration: float, rate: float = 2000.0, retouch: float = 0.3
     return reqs, nkeys
 
 
-def batched(ntrees: int = 4096, seed: int = 4, t_min: int = 16 << 10, t_max: int = 7 << 20,
-            median: int = 4096, sigma: float = 1.0, cap: int = 1 << 20):
-    """``ntrees`` independent node trees of uneven shape: per tree, levels
-    uniform in 1-5 and fanout uniform in 1-8; array lengths lognormal (median
-    ``median``, sigma ``sigma``, capped at ``cap``); a tree whose payload falls
-    outside [t_min, t_max] bytes is redrawn with the next seed."""
+@dataclass
+class TreeSpec:
+    """One tree of the batched workload before it is built: its shape, its
+    seed and its payload bytes (counted without allocating)."""
+    levels: int
+    rules: List[Rule]
+    seed: int
+    bytes: int
+    index: int
+
+    def build(self, name: str = "") -> Tree:
+        return Tree(node_schema(), self.levels, self.rules, self.seed, name=name or f"batched-{self.index}",
+                    nthreads=1)
+
+
+def batched_specs(ntrees: int = 4096, seed: int = 4, t_min: int = 16 << 10, t_max: int = 7 << 20,
+                  median: int = 4096, sigma: float = 1.0, cap: int = 1 << 20) -> List[TreeSpec]:
+    """The shapes of ``batched(...)``'s trees, drawn the same way, without
+    building them: per tree, levels uniform in 1-5 and fanout uniform in 1-8;
+    array lengths lognormal (median ``median``, sigma ``sigma``, capped at
+    ``cap``); a tree whose payload falls outside [t_min, t_max] bytes is
+    redrawn with the next seed.  The first k specs of a longer draw are the
+    specs of a draw of k."""
     import random as _random
     rng = _random.Random(seed)
-    trees = []
+    specs = []
     for i in range(ntrees):
         while True:
             levels, fanout, s = rng.randint(1, 5), rng.randint(1, 8), rng.getrandbits(63)
             n = lognormal(median, sigma, cap)
             rules = [Rule(0, 0, n, n), Rule(0, 1, const(fanout), const(0))]
-            if t_min <= dry_bytes(node_schema(), levels, rules, s) <= t_max:
+            b = dry_bytes(node_schema(), levels, rules, s)
+            if t_min <= b <= t_max:
                 break
-        trees.append(Tree(node_schema(), levels, rules, s, name=f"batched-{i}", nthreads=1))
-    return trees
+        specs.append(TreeSpec(levels, rules, s, b, i))
+    return specs
+
+
+def batched(ntrees: int = 4096, seed: int = 4, t_min: int = 16 << 10, t_max: int = 7 << 20,
+            median: int = 4096, sigma: float = 1.0, cap: int = 1 << 20):
+    """``ntrees`` independent node trees of uneven shape (``batched_specs``),
+    built."""
+    return [sp.build() for sp in batched_specs(ntrees, seed, t_min, t_max, median, sigma, cap)]
 
 
 # Address-only trees ----------------------------------------------------------------
