@@ -383,8 +383,8 @@ int or_update_parallel(const or_schema* s, void* root, const or_op* op, int nthr
         chunk[3 * c + 2] = lo + CH < n ? lo + CH : n;
       }
     }
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 1)
+    const int nt = nthreads > 0 ? nthreads : omp_get_num_procs();  /* this call only */
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
     for (int64_t c2 = 0; c2 < (int64_t)nchunks; c2++) {
       uint8_t* node = nodes.v[chunk[3 * c2]];
       apply_range(op, fx->elem_kind, (uint8_t*)ptr_at(node, fx), fy ? (const uint8_t*)ptr_at(node, fy) : NULL,
@@ -396,7 +396,7 @@ int or_update_parallel(const or_schema* s, void* root, const or_op* op, int nthr
   return rc;
 }
 
-int or_threads(void) { return omp_get_max_threads(); }
+int or_threads(void) { return omp_get_num_procs(); }
 
 /* ---- copy back (Alg 2 step 5) ---------------------------------------------- */
 
