@@ -53,8 +53,9 @@ typedef enum {
   DC_EINVAL = 1,         /* bad argument, schema, path or structure */
   DC_ENOMEM = 2,         /* host or pinned allocation failed */
   DC_ECUDA = 3,          /* a CUDA runtime call failed (message has the CUDA error) */
-  DC_EALIAS = 4,         /* a block is reachable twice or overlaps another: not a tree */
-  DC_ECYCLE = 5,         /* a pointer leads back into one of its ancestors */
+  DC_EALIAS = 4,         /* two blocks overlap (one reached twice, an array pointing into a
+                            struct, ...): not a tree */
+  DC_ECYCLE = 5,         /* a child pointer leads into an ancestor struct block */
   DC_EBUDGET = 6,        /* the bound device buffer is smaller than the plan needs */
   DC_ETIMEOUT = 7,       /* a device-side wait gave up after its iteration limit */
   DC_EDEVICE_BOUNDS = 8, /* a kernel found an index or offset outside its buffers */
@@ -305,12 +306,15 @@ DC_API dc_status dc_copy_back(dc_plan_t plan, uint32_t flags, dc_stream_t stream
 
 /* dc_roundtrip — dc_deep_copy, dc_update_leaves(op) and dc_copy_back(0) as one
  * call (Algorithm 2 steps 3-5: transfer, run the kernel once, transfer back),
- * with the same results.  With a DC_PLAN_MAP_HOST plan whose selected arrays
- * start on 16-byte host addresses, the blocks the op does not touch move as in
- * dc_deep_copy, and one kernel then reads each selected x and y element from
- * host memory, applies the update, writes x and y into the arena and the new x
- * straight back to the host: the two directions of the link overlap instead of
- * following each other.  Otherwise it runs the three calls in turn.
+ * with the same results.  With a DC_PLAN_MAP_HOST plan, or a tree built in
+ * dc_host_arena memory, whose selected arrays start on 16-byte host addresses,
+ * the blocks the op does not touch move as in dc_deep_copy, and one kernel
+ * then reads each selected x and y element from host memory, applies the
+ * update, writes x and y into the arena and the new x straight back to the
+ * host: the two directions of the link overlap instead of following each
+ * other.  The kernel runs in up to eight tile groups while host threads stage
+ * the next group's array heads and tails and return the previous group's.
+ * Otherwise it runs the three calls in turn.
  * Blocking: returns when the host arrays hold the results.  Errors: as the
  * three calls. */
 DC_API dc_status dc_roundtrip(dc_plan_t plan, const dc_op* op, dc_stream_t stream);
