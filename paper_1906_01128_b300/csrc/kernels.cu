@@ -328,9 +328,36 @@ __device__ __forceinline__ void leaf_tile(const LeafArgs& a, uint64_t t) {
   }
 }
 
+// With many tiles per CTA (`dynamic`), tiles come from an atomic counter in the
+// plan's control words, since tiles take uneven times (those that straddle
+// segments search for theirs); the last CTA to finish resets it for the next
+// launch (launches on one stream never overlap).  With a few tiles per CTA
+// there is little to balance, and CTA b takes tiles b, b + grid, ... without
+// the per-tile atomic and barriers.
 template <typename T, int KIND>
-__global__ void __launch_bounds__(LEAF_THREADS) leaf_kernel(LeafArgs a) {
-  for (uint64_t t = blockIdx.x; t * LEAF_TILE < a.units; t += gridDim.x) leaf_tile<T, KIND, LEAF_THREADS>(a, t);
+__global__ void __launch_bounds__(LEAF_THREADS) leaf_kernel(LeafArgs a, int dynamic) {
+  const uint64_t ntiles = (a.units + LEAF_TILE - 1) / LEAF_TILE;
+  if (!dynamic) {  // uniform across the grid
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) leaf_tile<T, KIND, LEAF_THREADS>(a, t);
+    return;
+  }
+  __shared__ unsigned long long s_t;
+  unsigned long long* next = reinterpret_cast<unsigned long long*>(&a.ctrl[CTRL_NEXT]);
+  for (;;) {
+    if (threadIdx.x == 0) s_t = atomicAdd(next, 1ull);
+    __syncthreads();
+    const uint64_t t = s_t;
+    __syncthreads();
+    if (t >= ntiles) break;
+    leaf_tile<T, KIND, LEAF_THREADS>(a, t);
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&a.ctrl[CTRL_DONE], 1u) == gridDim.x - 1) {
+      atomicExch(next, 0ull);
+      atomicExch(&a.ctrl[CTRL_DONE], 0u);
+    }
+  }
 }
 
 // Relocation and leaf update in one persistent launch: work item w < the
@@ -737,7 +764,7 @@ cudaError_t launch_leaf(const LeafArgs& a, cudaStream_t s, int sm_count) {
   auto go = [&](auto kernel) {
     const int occ = occupancy(kernel, LEAF_THREADS, 0);
     uint32_t grid = (uint32_t)std::min<uint64_t>(tiles, (uint64_t)sm_count * occ);
-    kernel<<<grid, LEAF_THREADS, 0, s>>>(a);
+    kernel<<<grid, LEAF_THREADS, 0, s>>>(a, tiles >= 8ull * grid ? 1 : 0);
   };
   if (a.f64)
     a.kind == DC_OP_AXPY_HALF ? go(leaf_kernel<double, DC_OP_AXPY_HALF>) : go(leaf_kernel<double, DC_OP_SCALE>);
