@@ -844,6 +844,15 @@ def main():
     # the same step as two launches: each kernel on its own
     t_reloc, t_leaf = timed_loop([plan.relocate, lambda: plan.update(op)], "dc_two_launch_step")
     plan.sync()
+    # the same relocation with size records: offsets from warp-shuffle prefix sums on the device
+    plan_scan = dc.Plan(s, tree.root, flags=dc.PLAN_DEVICE_SCAN)
+    plan_scan.bind()
+    plan_scan.deep_copy()
+    plan_scan.sync()
+    (t_reloc_scan,) = timed_loop([plan_scan.relocate], "dc_relocate_device_scan")
+    plan_scan.sync()
+    plan_scan.destroy()
+    del plan_scan
 
     hbm, peak_kind = peaks()
     leaf_avg = statistics.mean(t_leaf)
@@ -1024,6 +1033,11 @@ def main():
                            "median_launch_us": round(reloc_med * 1e6, 2),
                            "algorithmic_bytes": reloc_bytes, "achieved_gbs": round(reloc_bytes / reloc_avg / 1e9, 1),
                            "frac": round(reloc_bytes / reloc_avg / 1e9 / hbm, 4), "bytes_moved": reloc_moved},
+            "relocation_device_scan": {
+                "kernel": "relocate_kernel, DC_PLAN_DEVICE_SCAN (offsets from prefix sums of the targets' sizes)",
+                "avg_launch_us": round(statistics.mean(t_reloc_scan) * 1e6, 2),
+                "median_launch_us": round(statistics.median(t_reloc_scan) * 1e6, 2),
+                "frac": round(reloc_bytes / statistics.mean(t_reloc_scan) / 1e9 / hbm, 4)},
             "two_launch_step_us": round((reloc_avg + leaf_avg) * 1e6, 2),
             "step_median_ms": round(step_median * 1e3, 4),
             "hbm_copy_gbs_now": copy_now,

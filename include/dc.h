@@ -159,6 +159,13 @@ typedef struct {
                              caller that starts inside such a page range and runs past
                              its end fails. */
 #define DC_MAP_MIN_BYTES (64u << 10)
+#define DC_PLAN_DEVICE_SCAN 4u /* the relocation computes every target's arena offset on
+                             the device: its records carry the targets' padded sizes,
+                             and warp-shuffle prefix sums over them, added to each lane
+                             group's base, give the offsets.  Without it (the default)
+                             the records carry the offsets the plan's layout assigned,
+                             which is faster; the device image is the same.  Read at
+                             dc_bind_device; dc_relocate_static ignores it. */
 
 /* dc_plan — walk the host structure from `host_root` (one struct of
  * schema->root_type) and lay out its device arena (Algorithm 1's first step,

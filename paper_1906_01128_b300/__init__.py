@@ -30,6 +30,7 @@ OP_AXPY_HALF, OP_SCALE = 0, 1
 SEL_ALL, SEL_CHAIN = 0, 1
 PLAN_VERIFY = 1
 PLAN_MAP_HOST = 2
+PLAN_DEVICE_SCAN = 4
 COPY_ALL_ARRAYS = 1
 
 STATUS = {0: "DC_OK", 1: "DC_EINVAL", 2: "DC_ENOMEM", 3: "DC_ECUDA", 4: "DC_EALIAS", 5: "DC_ECYCLE",

@@ -118,6 +118,7 @@ struct RelocArgs {
   const uint64_t* rec_off;     // DC_PLAN_VERIFY: arena offset of each record's target
   uint32_t* ctrl;
   uint32_t nrec, nseg, ntiles, verify;
+  uint32_t scan;  // records hold sizes (DC_PLAN_DEVICE_SCAN), not offsets
 };
 
 constexpr uint32_t LEAF_THREADS = 256;
@@ -251,6 +252,8 @@ struct dc_plan_s {
   std::vector<dc::RelocTile> rtiles;     // per relocation tile: its records and lane groups
   std::vector<uint64_t> rec_host;        // per record: the target's host address (DC_PLAN_VERIFY)
   std::vector<uint64_t> rec_off;         // per record: the target's arena offset (DC_PLAN_VERIFY)
+  std::vector<uint32_t> rec_size16;      // per record: the target's padded size / 16 (DC_PLAN_DEVICE_SCAN)
+  bool rec_scan = false;                 // the bound buffer holds size records
   uint64_t struct_bytes = 0;             // bytes of the struct lane (lane 0)
   std::vector<uint64_t> null_slots;      // arena offsets of slots with count 0 but a non-NULL host value
   std::vector<uint32_t> roots;           // arena index of each tree's root struct block

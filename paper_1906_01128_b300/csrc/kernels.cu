@@ -91,6 +91,118 @@ struct __align__(16) RelocSmem {
   uint4 hdr[RSTAGES];  // the staged tile: (t, r0, r1, ng); t = NONE ends the CTA's tiles
 };
 
+__device__ __forceinline__ uint32_t warp_incl_scan32(uint32_t v, uint32_t lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t o = __shfl_up_sync(0xffffffffu, v, d);
+    if (lane >= (uint32_t)d) v += o;
+  }
+  return v;
+}
+
+// One staged tile's slots from offset records (the default): a slot's target
+// lies at its lane group's base plus the record's 32-bit offset, both in
+// 16-byte units.  Record j goes to thread j % THREADS: conflict-free shared
+// loads, and a warp's slot writes land in a few hundred consecutive bytes.
+template <uint32_t THREADS, bool VERIFY>
+__device__ __forceinline__ void reloc_apply_offsets(const RelocArgs& a, RelocStage& S, uint32_t r0, uint32_t nr,
+                                                    uint32_t ng, uint32_t sh, uint32_t n8, uint64_t base) {
+  constexpr uint32_t ITEMS = RELOC_MAXREC / THREADS;
+  const uint32_t tid = threadIdx.x;
+  uint2 r[ITEMS];
+#pragma unroll
+  for (uint32_t i = 0; i < ITEMS; i++) {
+    const uint32_t j = tid + i * THREADS;
+    r[i] = j < nr ? S.rec[sh + j] : make_uint2(0, 0);
+  }
+  uint64_t* img64 = reinterpret_cast<uint64_t*>(S.img);
+#pragma unroll
+  for (uint32_t i = 0; i < ITEMS; i++) {
+    const uint32_t j = tid + i * THREADS;
+    if (j >= nr) continue;
+    const uint32_t w = r[i].y & 0xFFFFu, g = r[i].y >> 16;  // slot word in the tile, lane group
+    if (w >= n8 || g >= ng) {
+      atomicOr(&a.ctrl[CTRL_ERR], ERR_BOUNDS);
+      continue;
+    }
+    const uint64_t off = (S.grp[g].base16 + r[i].x) * 16;
+    uint64_t* sp = img64 + w;
+    if (VERIFY) {
+      const uint32_t ri = r0 + j;
+      if (*sp != __ldg(&a.rec_host[ri]) || off != __ldg(&a.rec_off[ri])) atomicOr(&a.ctrl[CTRL_ERR], ERR_VERIFY);
+    }
+    *sp = base + off;
+  }
+}
+
+// One staged tile's slots from size records (DC_PLAN_DEVICE_SCAN): a target's
+// offset is its lane group's base plus the exclusive prefix of the padded sizes
+// before it in its group.  The records are warp-striped (warp w owns a
+// contiguous run of 32 x ITEMS records, its lane L record 32k + L); warp-shuffle
+// scans run slice by slice inside each warp, then over the warps' totals.  The
+// prefixes are 32-bit: a group's offsets stay below 2^32 units (the plan starts
+// a new group otherwise), so a difference of two prefixes modulo 2^32 is exact.
+// Every thread reaches both barriers (the call is uniform across the CTA).  Its
+// shared arrays exist only in the kernels built with this form.
+template <uint32_t THREADS, bool VERIFY>
+__device__ __forceinline__ void reloc_apply_scan(const RelocArgs& a, RelocStage& S, uint32_t r0, uint32_t nr,
+                                                 uint32_t ng, uint32_t sh, uint32_t n8, uint64_t base) {
+  constexpr uint32_t NW = THREADS / 32, ITEMS = RELOC_MAXREC / THREADS;
+  // per lane group: its base offset / 16 (x, y) and minus the size prefix at its
+  // first record (z); per warp: its records' size total
+  __shared__ uint4 gb[RELOC_MAXGROUPS];
+  __shared__ uint32_t warp_sum[32];
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, wb = warp * 32 * ITEMS;
+  uint2 r[ITEMS];
+#pragma unroll
+  for (uint32_t i = 0; i < ITEMS; i++) {
+    const uint32_t j = wb + i * 32 + lane;
+    r[i] = j < nr ? S.rec[sh + j] : make_uint2(0, 0);
+  }
+  uint32_t ex[ITEMS];
+  uint32_t carry = 0;
+#pragma unroll
+  for (uint32_t i = 0; i < ITEMS; i++) {
+    const uint32_t incl = warp_incl_scan32(r[i].x, lane);
+    ex[i] = carry + incl - r[i].x;
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (lane == 0) warp_sum[warp] = carry;
+  __syncthreads();
+  uint32_t wt = lane < NW ? warp_sum[lane] : 0u;
+  wt = warp_incl_scan32(wt, lane);
+  const uint32_t wpre = warp ? __shfl_sync(0xffffffffu, wt, (warp - 1) & 31) : 0u;
+#pragma unroll
+  for (uint32_t i = 0; i < ITEMS; i++) {
+    ex[i] += wpre;
+    const uint32_t j = wb + i * 32 + lane, g = r[i].y >> 16;
+    if (j < nr && g < ng && S.grp[g].rec_begin - r0 == j) {  // the group's first record
+      const uint64_t b16 = S.grp[g].base16;
+      gb[g] = make_uint4((uint32_t)b16, (uint32_t)(b16 >> 32), 0u - ex[i], 0u);
+    }
+  }
+  __syncthreads();  // every group's base and start prefix are in shared memory
+  uint64_t* img64 = reinterpret_cast<uint64_t*>(S.img);
+#pragma unroll
+  for (uint32_t i = 0; i < ITEMS; i++) {
+    const uint32_t j = wb + i * 32 + lane;
+    if (j >= nr) continue;
+    const uint32_t w = r[i].y & 0xFFFFu, g = r[i].y >> 16;
+    if (w >= n8 || g >= ng) {
+      atomicOr(&a.ctrl[CTRL_ERR], ERR_BOUNDS);
+      continue;
+    }
+    const uint4 G = gb[g];
+    const uint64_t off = ((((uint64_t)G.y << 32) | G.x) + (uint32_t)(ex[i] + G.z)) * 16;
+    uint64_t* sp = img64 + w;
+    if (VERIFY) {
+      const uint32_t ri = r0 + j;
+      if (*sp != __ldg(&a.rec_host[ri]) || off != __ldg(&a.rec_off[ri])) atomicOr(&a.ctrl[CTRL_ERR], ERR_VERIFY);
+    }
+    *sp = base + off;
+  }
+}
+
 // The producer (thread 0) fills stage s with listed tile i of the CTA (or
 // marks the CTA's tiles done, i = NONE), after checking the tile's header
 // against the tables; a header that fails is recorded and its stage skipped.
@@ -123,10 +235,11 @@ __device__ __forceinline__ void issue_tile(const RelocArgs& a, RelocSmem& sm, ui
 // two-stage pipeline: while the CTA rewrites the slots of one staged tile,
 // the bulk copies of the next are in flight, and the producer has the header
 // after that in a register.  A slot's target lies at its lane group's base
-// plus the record's 32-bit offset (both in 16-byte units); the rewritten
-// staged tile goes back by one bulk store.  The loop's exits are uniform across the
-// CTA; every wait has an iteration limit.
-template <uint32_t THREADS, bool VERIFY>
+// plus its offset in the group (both in 16-byte units): the record's own
+// offset, or with DC_PLAN_DEVICE_SCAN a prefix sum of the records' sizes.  The
+// rewritten staged tile goes back by one bulk store.  The loop's exits are
+// uniform across the CTA; every wait has an iteration limit.
+template <uint32_t THREADS, bool VERIFY, bool SCAN>
 __device__ __forceinline__ void reloc_tiles(const RelocArgs& a, RelocSmem& sm) {
   constexpr uint32_t ITEMS = RELOC_MAXREC / THREADS;
   static_assert(ITEMS * THREADS == RELOC_MAXREC, "tile shape");
@@ -177,33 +290,11 @@ __device__ __forceinline__ void reloc_tiles(const RelocArgs& a, RelocSmem& sm) {
     const uint32_t t = h.x, r0 = h.y, nr = h.z - h.y, ng = h.w, sh = r0 & 1u;
     const uint64_t lo = (uint64_t)t * RELOC_SPAN, hi = min(a.struct_bytes, lo + RELOC_SPAN);
     if (nr) {  // uniform
-      // record j goes to thread j % THREADS: conflict-free shared loads, and the
-      // slot writes of a warp land in a few hundred consecutive bytes
-      uint2 r[ITEMS];
-#pragma unroll
-      for (uint32_t i = 0; i < ITEMS; i++) {
-        const uint32_t j = tid + i * THREADS;
-        r[i] = j < nr ? S.rec[sh + j] : make_uint2(0, 0);
-      }
-      uint64_t* img64 = reinterpret_cast<uint64_t*>(S.img);
       const uint32_t n8 = (uint32_t)((hi - lo) / 8);
-#pragma unroll
-      for (uint32_t i = 0; i < ITEMS; i++) {
-        const uint32_t j = tid + i * THREADS;
-        if (j >= nr) continue;
-        const uint32_t w = r[i].y & 0xFFFFu, g = r[i].y >> 16;  // slot word in the tile, lane group
-        if (w >= n8 || g >= ng) {
-          atomicOr(err, ERR_BOUNDS);
-          continue;
-        }
-        const uint64_t off = (S.grp[g].base16 + r[i].x) * 16;
-        uint64_t* sp = img64 + w;
-        if (VERIFY) {
-          const uint32_t ri = r0 + j;
-          if (*sp != __ldg(&a.rec_host[ri]) || off != __ldg(&a.rec_off[ri])) atomicOr(err, ERR_VERIFY);
-        }
-        *sp = base + off;
-      }
+      if (SCAN)
+        reloc_apply_scan<THREADS, VERIFY>(a, S, r0, nr, ng, sh, n8, base);
+      else
+        reloc_apply_offsets<THREADS, VERIFY>(a, S, r0, nr, ng, sh, n8, base);
       fence_async_smem();  // the slot writes are seen by the bulk store
     }
     __syncthreads();  // nobody reads stage s any more
@@ -224,10 +315,10 @@ __device__ __forceinline__ void reloc_tiles(const RelocArgs& a, RelocSmem& sm) {
   __syncthreads();  // shared memory may be reused
 }
 
-template <bool VERIFY>
+template <bool VERIFY, bool SCAN>
 __global__ void __launch_bounds__(RELOC_THREADS) relocate_kernel(RelocArgs a) {
   __shared__ RelocSmem sm;
-  reloc_tiles<RELOC_THREADS, VERIFY>(a, sm);
+  reloc_tiles<RELOC_THREADS, VERIFY, SCAN>(a, sm);
 }
 
 // ---- leaf update over resolved segments -------------------------------------
@@ -495,7 +586,7 @@ __global__ void __launch_bounds__(THREADS) leaf_tma_kernel(LeafArgs a) {
   }
 }
 
-template <typename T, int KIND, uint32_t THREADS>
+template <typename T, int KIND, uint32_t THREADS, bool SCAN>
 // CTAs take leaf tiles from a counter, so the ones that relocated take fewer.
 // The last CTA to finish resets the counter for the next launch (launches on
 // one stream never overlap).
@@ -503,9 +594,9 @@ __global__ void __launch_bounds__(THREADS) fused_kernel(RelocArgs r, LeafArgs l,
   __shared__ RelocSmem sm;
   __shared__ unsigned long long s_w;
   if (r.verify)
-    reloc_tiles<THREADS, true>(r, sm);
+    reloc_tiles<THREADS, true, SCAN>(r, sm);
   else
-    reloc_tiles<THREADS, false>(r, sm);
+    reloc_tiles<THREADS, false, SCAN>(r, sm);
   unsigned long long* next = reinterpret_cast<unsigned long long*>(&r.ctrl[CTRL_NEXT]);
   for (;;) {
     if (threadIdx.x == 0) s_w = atomicAdd(next, 1ull);
@@ -727,12 +818,15 @@ int occupancy(K kernel, int threads, size_t smem) {
 
 cudaError_t launch_relocate(const RelocArgs& a, cudaStream_t s, int sm_count) {
   if (a.ntiles == 0) return cudaSuccess;
-  const int occ = occupancy(relocate_kernel<false>, RELOC_THREADS, 0);
-  const uint32_t grid = (uint32_t)std::min<uint64_t>(a.ntiles, (uint64_t)sm_count * occ);  // persistent CTAs
-  if (a.verify)
-    relocate_kernel<true><<<grid, RELOC_THREADS, 0, s>>>(a);
+  auto go = [&](auto kernel) {
+    const int occ = occupancy(kernel, RELOC_THREADS, 0);
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(a.ntiles, (uint64_t)sm_count * occ);  // persistent CTAs
+    kernel<<<grid, RELOC_THREADS, 0, s>>>(a);
+  };
+  if (a.scan)
+    a.verify ? go(relocate_kernel<true, true>) : go(relocate_kernel<false, true>);
   else
-    relocate_kernel<false><<<grid, RELOC_THREADS, 0, s>>>(a);
+    a.verify ? go(relocate_kernel<true, false>) : go(relocate_kernel<false, false>);
   count_launch();
   return cudaGetLastError();
 }
@@ -809,10 +903,17 @@ cudaError_t fused_go(const RelocArgs& r, const LeafArgs& l, uint32_t threads, ui
     count_launch();
     return cudaGetLastError();
   };
+  if (r.scan) {
+    switch (threads) {
+      case 128: return go(fused_kernel<T, KIND, 128, true>, 128);
+      case 512: return go(fused_kernel<T, KIND, 512, true>, 512);
+      default: return go(fused_kernel<T, KIND, 256, true>, 256);
+    }
+  }
   switch (threads) {
-    case 128: return go(fused_kernel<T, KIND, 128>, 128);
-    case 512: return go(fused_kernel<T, KIND, 512>, 512);
-    default: return go(fused_kernel<T, KIND, 256>, 256);
+    case 128: return go(fused_kernel<T, KIND, 128, false>, 128);
+    case 512: return go(fused_kernel<T, KIND, 512, false>, 512);
+    default: return go(fused_kernel<T, KIND, 256, false>, 256);
   }
 }
 }  // namespace

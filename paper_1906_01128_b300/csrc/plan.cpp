@@ -382,6 +382,8 @@ dc_status build_plan(const dc_schema* schema, const void* const* roots, uint64_t
   p->rtiles.clear();
   p->rec_host.clear();
   p->rec_off.clear();
+  p->rec_size16.clear();
+  p->rec_size16.reserve(nb - nr);
   p->rrec.reserve(nb - nr);
   p->rec_host.reserve(nb - nr);
   p->rec_off.reserve(nb - nr);
@@ -410,6 +412,7 @@ dc_status build_plan(const dc_schema* schema, const void* const* roots, uint64_t
         p->rrec.push_back(RelocRec{(uint32_t)(b.off / 16 - base16), (uint32_t)(w | std::min<uint64_t>(g, 0xFFFF) << 16)});
         p->rec_host.push_back((uint64_t)(uintptr_t)b.host);
         p->rec_off.push_back(b.off);
+        p->rec_size16.push_back((uint32_t)(round_up(b.bytes, 16) / 16));  // < 2^32: blocks stay below 64 GiB
       }
     }
     if (p->rseg.size() - tg0 > RELOC_MAXGROUPS)

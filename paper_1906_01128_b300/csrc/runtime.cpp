@@ -369,8 +369,15 @@ dc_status dc_bind_device(dc_plan_t p, void* dev, uint64_t bytes, dc_stream_t str
   p->dev = (uint8_t*)dev;
   p->dev_bytes = bytes;
   const uint64_t nrec = p->rrec.size();
+  p->rec_scan = (p->flags & DC_PLAN_DEVICE_SCAN) != 0;
+  std::vector<RelocRec> size_rec;  // DC_PLAN_DEVICE_SCAN: the same records with sizes for offsets
+  if (nrec && p->rec_scan) {
+    size_rec.resize(nrec);
+    for (uint64_t i = 0; i < nrec; i++) size_rec[i] = RelocRec{p->rec_size16[i], p->rrec[i].where};
+  }
   if (nrec) {
-    DC_CUDA(cudaMemcpyAsync(p->dev + p->L.rec, p->rrec.data(), nrec * sizeof(RelocRec), cudaMemcpyHostToDevice, s));
+    DC_CUDA(cudaMemcpyAsync(p->dev + p->L.rec, p->rec_scan ? size_rec.data() : p->rrec.data(), nrec * sizeof(RelocRec),
+                            cudaMemcpyHostToDevice, s));
     DC_CUDA(cudaMemcpyAsync(p->dev + p->L.hostp, p->rec_host.data(), nrec * 8, cudaMemcpyHostToDevice, s));
     DC_CUDA(cudaMemcpyAsync(p->dev + p->L.soff, p->rec_off.data(), nrec * 8, cudaMemcpyHostToDevice, s));
   }
@@ -559,6 +566,7 @@ RelocArgs dc::reloc_args(const dc_plan_s* p) {
   a.nseg = (uint32_t)(p->rseg.size() - 1);
   a.ntiles = (uint32_t)p->L.ntiles;
   a.verify = (p->flags & DC_PLAN_VERIFY) ? 1u : 0u;
+  a.scan = p->rec_scan ? 1u : 0u;
   return a;
 }
 

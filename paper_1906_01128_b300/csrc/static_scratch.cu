@@ -100,6 +100,7 @@ extern "C" dc_status dc_relocate_static(dc_plan_t p, void* dev_data, uint64_t da
   a.nseg = (uint32_t)nseg;
   a.ntiles = (uint32_t)ntiles;
   a.verify = 0;
+  a.scan = 0;  // the offsets the plan assigned
   DC_CUDA(launch_relocate(a, cs, sms));
   if (dev_status)
     DC_CUDA(cudaMemcpyAsync(dev_status, s + OFF_CTRL + CTRL_ERR * 4, 4, cudaMemcpyDeviceToDevice, cs));

@@ -4,8 +4,9 @@
 // checks the relocation tables the way the relocation kernel reads them:
 // every slot inside its tile, each record in the lane group it names, each
 // group's base plus the record's offset equal to the plan's own offset of the
-// target block, and the slot the record names being the one that points at
-// that block.
+// target block, the slot the record names being the one that points at that
+// block, and the running sum of the records' sizes within each group equal to
+// the record's offset (what the device-scan relocation computes).
 #include <cstdio>
 #include <unordered_map>
 
@@ -54,8 +55,14 @@ extern "C" int shim_plan(const dc_schema* schema, const void* const* roots, uint
     }
     for (uint32_t g = T.g0; g < T.g0 + ng && !rc; g++) {
       const dc::RelocSeg& G = p->rseg[g];
+      uint64_t prefix = 0;  // the device-scan form: sizes summed from the group's first record
       for (uint32_t i = G.rec_begin; i < p->rseg[g + 1].rec_begin; i++) {
         const dc::RelocRec& R = p->rrec[i];
+        if (prefix != R.off16) {
+          rc = bad("prefix of the group's sizes differs from the record's offset", prefix, R.off16);
+          break;
+        }
+        prefix += p->rec_size16[i];
         const uint64_t slot = lo + (uint64_t)(R.where & 0xFFFFu) * 8;
         if (slot + 8 > hi) {
           rc = bad("slot outside its tile", slot, T.t);

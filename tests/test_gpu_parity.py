@@ -116,6 +116,21 @@ def test_deep_chain_to_leaf_full_size():
     full_parity(lambda: tg.workload("deep"), dict(sel=dc.SEL_CHAIN, path=tg.leaf_path(64)))
 
 
+def test_device_scan_relocation():
+    """DC_PLAN_DEVICE_SCAN: the relocation derives every offset from the targets'
+    sizes with warp-shuffle prefix sums; the device image and the results are
+    the oracle's, as with the default offset records (dense: two tiles; a
+    ragged tree of ~13,000 blocks: 18 tiles and lane groups of uneven runs)."""
+    full_parity(lambda: tg.workload("dense"), {}, flags=dc.PLAN_DEVICE_SCAN)
+    full_parity(lambda: tg.node_tree(4, 16, tg.uniform(1, 40), seed=21), {}, verify=True,
+                flags=dc.PLAN_DEVICE_SCAN)
+
+
+def test_reloc_stress_device_scan():
+    # the 2.3M-slot tree through the scan form, with the device-side slot check on
+    full_parity(lambda: tg.workload("reloc_stress"), {}, verify=True, flags=dc.PLAN_DEVICE_SCAN)
+
+
 def test_reloc_stress_many_tiles():
     # 1,118,481 nodes, 2,306,868 blocks: 4,370 relocation tiles over the 35.8 MB struct lane,
     # several per CTA through the two-stage pipeline, with the device-side slot check on
@@ -430,6 +445,12 @@ def forest_parity(ntrees, t_max, mode, flags=0, seed=4):
 @pytest.mark.parametrize("mode", ["plain", "fused", "tuned", "split-128-1", "split-512-64", "graph", "roundtrip"])
 def test_forest_of_uneven_trees(mode):
     forest_parity(300, 256 << 10, mode, flags=dc.PLAN_MAP_HOST if mode == "roundtrip" else 0)
+
+
+@pytest.mark.parametrize("mode", ["fused", "split-128-1"])
+def test_forest_fused_launch_with_device_scan(mode):
+    # the persistent relocation + update launch with size records
+    forest_parity(300, 256 << 10, mode, flags=dc.PLAN_DEVICE_SCAN)
 
 
 def test_forest_resolution_per_tree():
