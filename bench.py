@@ -59,11 +59,10 @@ WORKLOADS = {
 # DRAM bytes (read + write) per launch of the step's kernel from one ncu capture, by (workload, split);
 # the summary beside each gives the command.  An entry stands only while the kernel is unchanged.
 NCU_TRAFFIC = {
-    ("dense", 256, 4): (460_959_872, "profiles/fused_kernel_dense.md"),
-    ("reloc_stress", 256, 4): (192_249_600, "profiles/relocate_kernel_reloc_stress.md"),
-    ("reloc_stress", 128, 4): (191_866_112, "profiles/relocate_kernel_reloc_stress.md"),
-    ("deep", 256, 4): (757_033_088, "profiles/fused_kernel_deep_batched.md"),
-    ("batched", 256, 4): (7_019_413_120, "profiles/fused_kernel_deep_batched.md"),
+    ("dense", 256, 4): (460_444_928, "profiles/fused_kernel_dense.md"),
+    ("reloc_stress", 256, 4): (191_952_256, "profiles/relocate_kernel_reloc_stress.md"),
+    ("deep", 256, 4): (757_099_392, "profiles/fused_kernel_deep_batched.md"),
+    ("batched", 256, 4): (7_019_651_200, "profiles/fused_kernel_deep_batched.md"),
 }
 
 
