@@ -563,18 +563,20 @@ __global__ void __launch_bounds__(THREADS) leaf_tma_kernel(LeafArgs a) {
         if (j >= h.w) break;
         const uint64_t e0 = (uint64_t)j * EPU;  // from the tile's first element
         const uint64_t left = left0 - e0;
-        VT xv = xs[j];
-        const VT yv = ys[j];
-        T* x = reinterpret_cast<T*>(&xv);
-        const T* y = reinterpret_cast<const T*>(&yv);
         if (left >= (uint64_t)EPU) {
+          VT xv = xs[j];
+          const VT yv = ys[j];
+          T* x = reinterpret_cast<T*>(&xv);  // static indices only: the vector stays in registers
+          const T* y = reinterpret_cast<const T*>(&yv);
 #pragma unroll
           for (int q = 0; q < EPU; q++) x[q] = apply<T, KIND>(x[q], KIND == DC_OP_AXPY_HALF ? y[q] : T(0), sc);
           stcs(reinterpret_cast<VT*>(x0 + e0 * sizeof(T)), xv);
-        } else {
+        } else {  // the segment's last elements, read from the staged copy
+          const T* xsm = reinterpret_cast<const T*>(xs + j);
+          const T* ysm = reinterpret_cast<const T*>(ys + j);
           T* xd = reinterpret_cast<T*>(x0 + e0 * sizeof(T));
           for (uint32_t q = 0; q < (uint32_t)left; q++)
-            xd[q] = apply<T, KIND>(x[q], KIND == DC_OP_AXPY_HALF ? y[q] : T(0), sc);
+            xd[q] = apply<T, KIND>(xsm[q], KIND == DC_OP_AXPY_HALF ? ysm[q] : T(0), sc);
         }
       }
     }
