@@ -872,7 +872,9 @@ def main():
                           "source": "--split" if args.split else "dc_autotune"},
                 "step_us": [round(x * 1e6, 1) for x in t_fused],
                 "traffic_source": NCU_TRAFFIC.get((args.workload,) + tuple(tuned), (None, None))[1]}
-    leaf = {"kernel": "leaf_kernel<float, AXPY_HALF>", "algorithmic_bytes": leaf_bytes,
+    leaf_name = ("leaf_kernel<float, AXPY_HALF> (direct loads, DC_LEAF_TMA=0)" if os.environ.get("DC_LEAF_TMA") == "0"
+                 else "leaf_tma_kernel<float, AXPY_HALF> (bulk copies into shared memory)")
+    leaf = {"kernel": leaf_name, "algorithmic_bytes": leaf_bytes,
             "avg_launch_us": round(leaf_avg * 1e6, 2), "median_launch_us": round(leaf_med * 1e6, 2),
             "achieved_gbs": round(leaf_bytes / leaf_avg / 1e9, 1), "frac": round(leaf_bytes / leaf_avg / 1e9 / hbm, 4),
             "frac_at_median": round(leaf_bytes / leaf_med / 1e9 / hbm, 4)}

@@ -458,77 +458,110 @@ __global__ void __launch_bounds__(LEAF_THREADS) leaf_kernel(LeafArgs a, int dyna
 // forest replaces two per structure.
 // ---- leaf update with its operands staged by 1-D bulk copies -----------------
 
-constexpr uint32_t LSTAGES = 2;  // tiles in flight per CTA
-constexpr size_t LEAF_TILE_BYTES = (size_t)LEAF_TILE * 16;
+constexpr uint32_t LSTAGES = 3;                    // sub-tiles in flight per CTA
+constexpr uint32_t LSUB = LEAF_TILE / 2;           // 16-byte units per sub-tile (half a leaf tile)
+constexpr size_t LSUB_BYTES = (size_t)LSUB * 16;  // 8 KiB per operand
 
-// Dynamic shared memory of leaf_tma_kernel: per stage one tile of x (and of y
-// for AXPY_HALF), then the stage headers and barriers.
+// Dynamic shared memory of leaf_tma_kernel: per stage one sub-tile of x (and of
+// y for AXPY_HALF), then the stage headers and barriers.
 template <int KIND>
 constexpr size_t leaf_tma_smem() {
-  return LSTAGES * (KIND == DC_OP_AXPY_HALF ? 2 : 1) * LEAF_TILE_BYTES + LSTAGES * (8 + 32);
+  return LSTAGES * (KIND == DC_OP_AXPY_HALF ? 2 : 1) * LSUB_BYTES + LSTAGES * (8 + 32);
 }
 
-// The producer (thread 0) stages tile t in stage s: a tile inside one segment
-// comes by bulk copies (its x and y units are contiguous and 16-byte
-// aligned); a tile across segments, or t past the end, is marked for the
-// direct path or as the end.  hdr[2s] = (t, mode, units), hdr[2s+1] = the
-// destination of the tile's first unit and the elements left from it.
+// The table entries a sub-tile's copies need: its leaf tile's segment range
+// and, when that is one segment, the segment.  The producer loads them in two
+// steps a refill ahead: the range at one refill, the segment (whose index the
+// range gives) at the start of the next iteration, so that no load on the
+// refill path waits for another.
+struct LeafNext {
+  uint32_t lo, hi;
+  Segment g;
+};
+__device__ __forceinline__ void leaf_next_range(const LeafArgs& a, uint64_t w, uint64_t nsub, LeafNext* n) {
+  n->lo = n->hi = NONE;
+  if (w >= nsub) return;
+  n->lo = __ldg(&a.tile_seg[w / 2]);
+  n->hi = __ldg(&a.tile_seg[w / 2 + 1]);
+}
+__device__ __forceinline__ void leaf_next_seg(const LeafArgs& a, LeafNext* n) {
+  const uint32_t k = n->lo < a.nseg ? n->lo : 0u;  // unused unless lo == hi < nseg
+  n->g = a.seg[k];
+}
+
+// The producer (thread 0) stages sub-tile w (units [w, w+1) * LSUB, in leaf
+// tile w / 2) in stage s.  A leaf tile inside one segment comes by bulk copies
+// (its x and y units are contiguous and 16-byte aligned, the last one inside
+// its block's 16-byte padding); a tile across segments goes to the direct path,
+// whole, from its first half (its second half is then empty); w past the end
+// marks the end.  hdr[2s] = (w, mode, units), hdr[2s+1] = the destination of
+// the sub-tile's first unit and the elements left from it.
 template <int KIND>
 __device__ __forceinline__ void leaf_issue(const LeafArgs& a, uint4* buf, uint64_t* bar, uint4* hdr, uint32_t s,
-                                           uint64_t t, uint64_t ntiles) {
+                                           uint64_t w, uint64_t nsub, const LeafNext& n) {
   constexpr uint32_t NB = KIND == DC_OP_AXPY_HALF ? 2 : 1;
-  if (t >= ntiles) {
+  if (w >= nsub) {
     hdr[2 * s] = make_uint4(NONE, NONE, 0, 0);
     mbar_arrive_tx(&bar[s], 0);
     return;
   }
-  const uint32_t lo = __ldg(&a.tile_seg[t]), hi = __ldg(&a.tile_seg[t + 1]);
-  const uint64_t u0 = t * LEAF_TILE, u1 = min(u0 + LEAF_TILE, a.units);
-  if (lo != hi || lo >= a.nseg) {  // across segments: the direct path
-    hdr[2 * s] = make_uint4((uint32_t)t, (uint32_t)(t >> 32), 0, 0);
+  const uint64_t u0 = w * LSUB, u1 = min(u0 + LSUB, a.units);
+  if (n.lo != n.hi || n.lo >= a.nseg) {  // across segments: the direct path takes the whole tile once
+    hdr[2 * s] = make_uint4((uint32_t)w, (uint32_t)(w >> 32), (w & 1) ? 3u : 0u, 0);
     mbar_arrive_tx(&bar[s], 0);
     return;
   }
-  const Segment g = a.seg[lo];
+  const Segment& g = n.g;
   const uint32_t bytes = (uint32_t)((u1 - u0) * 16);
   const uint64_t x0 = g.x + (u0 - g.ubeg) * 16, left = g.n - (u0 - g.ubeg) * (16 / (a.f64 ? 8 : 4));
-  hdr[2 * s] = make_uint4((uint32_t)t, (uint32_t)(t >> 32), 1, (uint32_t)(u1 - u0));
+  hdr[2 * s] = make_uint4((uint32_t)w, (uint32_t)(w >> 32), 1, (uint32_t)(u1 - u0));
   hdr[2 * s + 1] = make_uint4((uint32_t)x0, (uint32_t)(x0 >> 32), (uint32_t)left, (uint32_t)(left >> 32));
   mbar_arrive_tx(&bar[s], NB * bytes);
-  bulk_load(buf + (size_t)s * NB * LEAF_TILE, reinterpret_cast<const void*>(g.x + (u0 - g.ubeg) * 16), bytes, &bar[s]);
+  bulk_load(buf + (size_t)s * NB * LSUB, reinterpret_cast<const void*>(g.x + (u0 - g.ubeg) * 16), bytes, &bar[s]);
   if (KIND == DC_OP_AXPY_HALF)
-    bulk_load(buf + ((size_t)s * NB + 1) * LEAF_TILE, reinterpret_cast<const void*>(g.y + (u0 - g.ubeg) * 16), bytes,
+    bulk_load(buf + ((size_t)s * NB + 1) * LSUB, reinterpret_cast<const void*>(g.y + (u0 - g.ubeg) * 16), bytes,
               &bar[s]);
 }
 
-// The leaf update with x and y of each tile brought into shared memory by the
-// tensor-memory-access engine, LSTAGES tiles in flight per CTA; the update
-// runs in registers and x goes back by coalesced 16-byte stores.  Tiles
-// t = blockIdx.x + k * gridDim.x.  Every wait has an iteration limit.
+// The leaf update with x and y brought into shared memory by 1-D bulk copies
+// (the tensor-memory-access engine), in half tiles of 8 KiB per operand with
+// LSTAGES of them in flight per CTA: while the CTA updates one, the copies of
+// the next two are under way.  The update runs in registers and x goes back
+// by coalesced 16-byte stores.  Sub-tiles w = blockIdx.x + k * gridDim.x.
+// Every wait has an iteration limit.
 template <typename T, int KIND, uint32_t THREADS>
-__global__ void __launch_bounds__(THREADS) leaf_tma_kernel(LeafArgs a) {
+__global__ void __launch_bounds__(THREADS, 3) leaf_tma_kernel(LeafArgs a) {
   using VT = typename V16<T>::type;
   constexpr int EPU = V16<T>::N;
   constexpr uint32_t NB = KIND == DC_OP_AXPY_HALF ? 2 : 1;
-  constexpr uint32_t UNROLL = LEAF_TILE / THREADS;
+  constexpr uint32_t UNROLL = LSUB / THREADS;
+  static_assert(UNROLL * THREADS == LSUB, "sub-tile shape");
   extern __shared__ __align__(128) uint8_t dsm[];
   uint4* buf = reinterpret_cast<uint4*>(dsm);
-  uint4* hdr = reinterpret_cast<uint4*>(dsm + LSTAGES * NB * LEAF_TILE_BYTES);  // 16-byte aligned, 2 per stage
+  uint4* hdr = reinterpret_cast<uint4*>(dsm + LSTAGES * NB * LSUB_BYTES);  // 16-byte aligned, 2 per stage
   uint64_t* bar = reinterpret_cast<uint64_t*>(hdr + 2 * LSTAGES);
   const uint32_t tid = threadIdx.x;
   const T sc = (T)a.scale;
-  const uint64_t ntiles = (a.units + LEAF_TILE - 1) / LEAF_TILE;
-  if (blockIdx.x >= ntiles) return;
+  const uint64_t nsub = (a.units + LSUB - 1) / LSUB;
+  if (blockIdx.x >= nsub) return;
   if (tid == 0) {
     for (uint32_t s = 0; s < LSTAGES; s++) mbar_init(&bar[s]);
     mbar_init_fence();
   }
   __syncthreads();
-  uint64_t tn = blockIdx.x;  // the producer's next tile
-  if (tid == 0)
-    for (uint32_t s = 0; s < LSTAGES; s++, tn += gridDim.x) leaf_issue<KIND>(a, buf, bar, hdr, s, tn, ntiles);
+  uint64_t wn = blockIdx.x;  // the producer's next sub-tile, and its table entries
+  LeafNext nx{NONE, NONE, {0, 0, 0, 0}};
+  if (tid == 0) {
+    for (uint32_t s = 0; s < LSTAGES; s++, wn += gridDim.x) {
+      leaf_next_range(a, wn, nsub, &nx);
+      leaf_next_seg(a, &nx);
+      leaf_issue<KIND>(a, buf, bar, hdr, s, wn, nsub, nx);
+    }
+    leaf_next_range(a, wn, nsub, &nx);
+  }
   for (uint32_t k = 0;; k++) {
     const uint32_t s = k % LSTAGES, parity = (k / LSTAGES) & 1;
+    if (tid == 0) leaf_next_seg(a, &nx);  // the range arrived during the last iteration
     bool late = false;
     uint32_t spins = 0;
     while (!mbar_try_wait(&bar[s], parity))
@@ -549,19 +582,19 @@ __global__ void __launch_bounds__(THREADS) leaf_tma_kernel(LeafArgs a) {
     }
     const uint4 h = hdr[2 * s];
     if (h.x == NONE && h.y == NONE) break;  // uniform
-    const uint64_t t = (uint64_t)h.x | ((uint64_t)h.y << 32);
+    const uint64_t w = (uint64_t)h.x | ((uint64_t)h.y << 32);
     if (h.z == 0) {
-      leaf_tile<T, KIND, THREADS>(a, t);
-    } else {
+      leaf_tile<T, KIND, THREADS>(a, w / 2);  // the whole leaf tile, by direct loads
+    } else if (h.z == 1) {
       const uint4 h2 = hdr[2 * s + 1];
       const uint64_t x0 = (uint64_t)h2.x | ((uint64_t)h2.y << 32), left0 = (uint64_t)h2.z | ((uint64_t)h2.w << 32);
-      const VT* xs = reinterpret_cast<const VT*>(buf + (size_t)s * NB * LEAF_TILE);
-      const VT* ys = reinterpret_cast<const VT*>(buf + ((size_t)s * NB + (NB - 1)) * LEAF_TILE);
+      const VT* xs = reinterpret_cast<const VT*>(buf + (size_t)s * NB * LSUB);
+      const VT* ys = reinterpret_cast<const VT*>(buf + ((size_t)s * NB + (NB - 1)) * LSUB);
 #pragma unroll
       for (uint32_t i = 0; i < UNROLL; i++) {
         const uint32_t j = tid + i * THREADS;
         if (j >= h.w) break;
-        const uint64_t e0 = (uint64_t)j * EPU;  // from the tile's first element
+        const uint64_t e0 = (uint64_t)j * EPU;  // from the sub-tile's first element
         const uint64_t left = left0 - e0;
         if (left >= (uint64_t)EPU) {
           VT xv = xs[j];
@@ -579,11 +612,12 @@ __global__ void __launch_bounds__(THREADS) leaf_tma_kernel(LeafArgs a) {
             xd[q] = apply<T, KIND>(xsm[q], KIND == DC_OP_AXPY_HALF ? ysm[q] : T(0), sc);
         }
       }
-    }
+    }  // h.z == 3: the second half of a tile the direct path took whole
     __syncthreads();  // nobody reads stage s any more
     if (tid == 0) {
-      leaf_issue<KIND>(a, buf, bar, hdr, s, tn, ntiles);
-      if (tn < ntiles) tn += gridDim.x;
+      leaf_issue<KIND>(a, buf, bar, hdr, s, wn, nsub, nx);
+      if (wn < nsub) wn += gridDim.x;
+      leaf_next_range(a, wn, nsub, &nx);  // its segment is loaded next iteration
     }
   }
 }
@@ -833,17 +867,18 @@ cudaError_t launch_relocate(const RelocArgs& a, cudaStream_t s, int sm_count) {
   return cudaGetLastError();
 }
 
+// The leaf update's kernel: leaf_tma_kernel (bulk copies into shared memory)
+// unless DC_LEAF_TMA=0, read at every launch, selects leaf_kernel (direct loads).
 cudaError_t launch_leaf(const LeafArgs& a, cudaStream_t s, int sm_count) {
   if (a.units == 0 || a.nseg == 0) return cudaSuccess;
   uint64_t tiles = (a.units + LEAF_TILE - 1) / LEAF_TILE;
-  static const bool tma = [] {
-    const char* v = getenv("DC_LEAF_TMA");
-    return v && *v && v[0] != '0';
-  }();
+  const char* v = getenv("DC_LEAF_TMA");
+  const bool tma = !(v && v[0] == '0');
   if (tma) {
     auto go_tma = [&](auto kernel, size_t smem) {
       const int occ = occupancy(kernel, LEAF_THREADS, smem);
-      uint32_t grid = (uint32_t)std::min<uint64_t>(tiles, (uint64_t)sm_count * occ);
+      const uint64_t nsub = (a.units + LSUB - 1) / LSUB;  // the kernel's work items: half tiles
+      uint32_t grid = (uint32_t)std::min<uint64_t>(nsub, (uint64_t)sm_count * occ);
       kernel<<<grid, LEAF_THREADS, smem, s>>>(a);
     };
     if (a.f64)

@@ -116,6 +116,21 @@ def test_deep_chain_to_leaf_full_size():
     full_parity(lambda: tg.workload("deep"), dict(sel=dc.SEL_CHAIN, path=tg.leaf_path(64)))
 
 
+@pytest.mark.parametrize("case", ["dense", "deep_chain", "reloc_stress", "linear_scale_f64", "ragged"])
+def test_direct_load_leaf_kernel(case, monkeypatch):
+    """DC_LEAF_TMA=0 selects the direct-load leaf kernel instead of the default
+    bulk-copy one; its results are the oracle's too."""
+    monkeypatch.setenv("DC_LEAF_TMA", "0")
+    make, op = {
+        "dense": (lambda: tg.workload("dense"), {}),
+        "deep_chain": (lambda: tg.workload("deep"), dict(sel=dc.SEL_CHAIN, path=tg.leaf_path(64))),
+        "reloc_stress": (lambda: tg.workload("reloc_stress"), {}),
+        "linear_scale_f64": (lambda: tg.linear_tree(6, 100001, "allinit", seed=3), dict(kind=dc.OP_SCALE, x=2, scale=1.5)),
+        "ragged": (lambda: tg.node_tree(4, 6, tg.uniform(0, 3000), seed=8), {}),
+    }[case]
+    full_parity(make, op, repeat=2)
+
+
 def test_device_scan_relocation():
     """DC_PLAN_DEVICE_SCAN: the relocation derives every offset from the targets'
     sizes with warp-shuffle prefix sums; the device image and the results are
