@@ -485,8 +485,7 @@ __device__ __forceinline__ void leaf_next_range(const LeafArgs& a, uint64_t w, u
   n->hi = __ldg(&a.tile_seg[w / 2 + 1]);
 }
 __device__ __forceinline__ void leaf_next_seg(const LeafArgs& a, LeafNext* n) {
-  const uint32_t k = n->lo < a.nseg ? n->lo : 0u;  // unused unless lo == hi < nseg
-  n->g = a.seg[k];
+  if (n->lo < a.nseg) n->g = a.seg[n->lo];  // used only when lo == hi < nseg
 }
 
 // The producer (thread 0) stages sub-tile w (units [w, w+1) * LSUB, in leaf
@@ -496,31 +495,76 @@ __device__ __forceinline__ void leaf_next_seg(const LeafArgs& a, LeafNext* n) {
 // whole, from its first half (its second half is then empty); w past the end
 // marks the end.  hdr[2s] = (w, mode, units), hdr[2s+1] = the destination of
 // the sub-tile's first unit and the elements left from it.
+// (xd, yd: the stage's 8 KiB buffers for x and y; hdr: its two header slots.)
 template <int KIND>
-__device__ __forceinline__ void leaf_issue(const LeafArgs& a, uint4* buf, uint64_t* bar, uint4* hdr, uint32_t s,
+__device__ __forceinline__ void leaf_issue(const LeafArgs& a, uint4* xd, uint4* yd, uint64_t* bar, uint4* hdr,
                                            uint64_t w, uint64_t nsub, const LeafNext& n) {
   constexpr uint32_t NB = KIND == DC_OP_AXPY_HALF ? 2 : 1;
   if (w >= nsub) {
-    hdr[2 * s] = make_uint4(NONE, NONE, 0, 0);
-    mbar_arrive_tx(&bar[s], 0);
+    hdr[0] = make_uint4(NONE, NONE, 0, 0);
+    mbar_arrive_tx(bar, 0);
     return;
   }
   const uint64_t u0 = w * LSUB, u1 = min(u0 + LSUB, a.units);
   if (n.lo != n.hi || n.lo >= a.nseg) {  // across segments: the direct path takes the whole tile once
-    hdr[2 * s] = make_uint4((uint32_t)w, (uint32_t)(w >> 32), (w & 1) ? 3u : 0u, 0);
-    mbar_arrive_tx(&bar[s], 0);
+    hdr[0] = make_uint4((uint32_t)w, (uint32_t)(w >> 32), (w & 1) ? 3u : 0u, 0);
+    mbar_arrive_tx(bar, 0);
     return;
   }
   const Segment& g = n.g;
   const uint32_t bytes = (uint32_t)((u1 - u0) * 16);
   const uint64_t x0 = g.x + (u0 - g.ubeg) * 16, left = g.n - (u0 - g.ubeg) * (16 / (a.f64 ? 8 : 4));
-  hdr[2 * s] = make_uint4((uint32_t)w, (uint32_t)(w >> 32), 1, (uint32_t)(u1 - u0));
-  hdr[2 * s + 1] = make_uint4((uint32_t)x0, (uint32_t)(x0 >> 32), (uint32_t)left, (uint32_t)(left >> 32));
-  mbar_arrive_tx(&bar[s], NB * bytes);
-  bulk_load(buf + (size_t)s * NB * LSUB, reinterpret_cast<const void*>(g.x + (u0 - g.ubeg) * 16), bytes, &bar[s]);
-  if (KIND == DC_OP_AXPY_HALF)
-    bulk_load(buf + ((size_t)s * NB + 1) * LSUB, reinterpret_cast<const void*>(g.y + (u0 - g.ubeg) * 16), bytes,
-              &bar[s]);
+  hdr[0] = make_uint4((uint32_t)w, (uint32_t)(w >> 32), 1, (uint32_t)(u1 - u0));
+  hdr[1] = make_uint4((uint32_t)x0, (uint32_t)(x0 >> 32), (uint32_t)left, (uint32_t)(left >> 32));
+  mbar_arrive_tx(bar, NB * bytes);
+  bulk_load(xd, reinterpret_cast<const void*>(g.x + (u0 - g.ubeg) * 16), bytes, bar);
+  if (KIND == DC_OP_AXPY_HALF) bulk_load(yd, reinterpret_cast<const void*>(g.y + (u0 - g.ubeg) * 16), bytes, bar);
+}
+
+// One staged sub-tile's update (header h, h2 as leaf_issue wrote them): mode 0
+// runs the whole leaf tile by direct loads, mode 1 the staged units, mode 3
+// nothing.  x goes back by 16-byte stores; a segment's last elements are read
+// from the staged copy, so the register vectors take static indices only.
+template <typename T, int KIND, uint32_t THREADS>
+__device__ __forceinline__ void leaf_staged_apply(const LeafArgs& a, const uint4* xbuf, const uint4* ybuf, uint4 h,
+                                                  uint4 h2) {
+  using VT = typename V16<T>::type;
+  constexpr int EPU = V16<T>::N;
+  constexpr uint32_t UNROLL = LSUB / THREADS;
+  static_assert(UNROLL * THREADS == LSUB, "sub-tile shape");
+  const uint32_t tid = threadIdx.x;
+  const T sc = (T)a.scale;
+  const uint64_t w = (uint64_t)h.x | ((uint64_t)h.y << 32);
+  if (h.z == 0) {
+    leaf_tile<T, KIND, THREADS>(a, w / 2);  // the whole leaf tile, by direct loads
+    return;
+  }
+  if (h.z != 1) return;  // the second half of a tile the direct path took whole
+  const uint64_t x0 = (uint64_t)h2.x | ((uint64_t)h2.y << 32), left0 = (uint64_t)h2.z | ((uint64_t)h2.w << 32);
+  const VT* xs = reinterpret_cast<const VT*>(xbuf);
+  const VT* ys = reinterpret_cast<const VT*>(KIND == DC_OP_AXPY_HALF ? ybuf : xbuf);
+#pragma unroll
+  for (uint32_t i = 0; i < UNROLL; i++) {
+    const uint32_t j = tid + i * THREADS;
+    if (j >= h.w) break;
+    const uint64_t e0 = (uint64_t)j * EPU;  // from the sub-tile's first element
+    const uint64_t left = left0 - e0;
+    if (left >= (uint64_t)EPU) {
+      VT xv = xs[j];
+      const VT yv = ys[j];
+      T* x = reinterpret_cast<T*>(&xv);  // static indices only: the vector stays in registers
+      const T* y = reinterpret_cast<const T*>(&yv);
+#pragma unroll
+      for (int q = 0; q < EPU; q++) x[q] = apply<T, KIND>(x[q], KIND == DC_OP_AXPY_HALF ? y[q] : T(0), sc);
+      stcs(reinterpret_cast<VT*>(x0 + e0 * sizeof(T)), xv);
+    } else {  // the segment's last elements, read from the staged copy
+      const T* xsm = reinterpret_cast<const T*>(xs + j);
+      const T* ysm = reinterpret_cast<const T*>(ys + j);
+      T* xd = reinterpret_cast<T*>(x0 + e0 * sizeof(T));
+      for (uint32_t q = 0; q < (uint32_t)left; q++)
+        xd[q] = apply<T, KIND>(xsm[q], KIND == DC_OP_AXPY_HALF ? ysm[q] : T(0), sc);
+    }
+  }
 }
 
 // The leaf update with x and y brought into shared memory by 1-D bulk copies
@@ -531,19 +575,16 @@ __device__ __forceinline__ void leaf_issue(const LeafArgs& a, uint4* buf, uint64
 // Every wait has an iteration limit.
 template <typename T, int KIND, uint32_t THREADS>
 __global__ void __launch_bounds__(THREADS, 3) leaf_tma_kernel(LeafArgs a) {
-  using VT = typename V16<T>::type;
-  constexpr int EPU = V16<T>::N;
   constexpr uint32_t NB = KIND == DC_OP_AXPY_HALF ? 2 : 1;
-  constexpr uint32_t UNROLL = LSUB / THREADS;
-  static_assert(UNROLL * THREADS == LSUB, "sub-tile shape");
   extern __shared__ __align__(128) uint8_t dsm[];
   uint4* buf = reinterpret_cast<uint4*>(dsm);
   uint4* hdr = reinterpret_cast<uint4*>(dsm + LSTAGES * NB * LSUB_BYTES);  // 16-byte aligned, 2 per stage
   uint64_t* bar = reinterpret_cast<uint64_t*>(hdr + 2 * LSTAGES);
   const uint32_t tid = threadIdx.x;
-  const T sc = (T)a.scale;
   const uint64_t nsub = (a.units + LSUB - 1) / LSUB;
   if (blockIdx.x >= nsub) return;
+  auto xbuf = [&](uint32_t s) { return buf + (size_t)s * NB * LSUB; };
+  auto ybuf = [&](uint32_t s) { return buf + ((size_t)s * NB + (NB - 1)) * LSUB; };
   if (tid == 0) {
     for (uint32_t s = 0; s < LSTAGES; s++) mbar_init(&bar[s]);
     mbar_init_fence();
@@ -555,7 +596,7 @@ __global__ void __launch_bounds__(THREADS, 3) leaf_tma_kernel(LeafArgs a) {
     for (uint32_t s = 0; s < LSTAGES; s++, wn += gridDim.x) {
       leaf_next_range(a, wn, nsub, &nx);
       leaf_next_seg(a, &nx);
-      leaf_issue<KIND>(a, buf, bar, hdr, s, wn, nsub, nx);
+      leaf_issue<KIND>(a, xbuf(s), ybuf(s), &bar[s], &hdr[2 * s], wn, nsub, nx);
     }
     leaf_next_range(a, wn, nsub, &nx);
   }
@@ -582,40 +623,10 @@ __global__ void __launch_bounds__(THREADS, 3) leaf_tma_kernel(LeafArgs a) {
     }
     const uint4 h = hdr[2 * s];
     if (h.x == NONE && h.y == NONE) break;  // uniform
-    const uint64_t w = (uint64_t)h.x | ((uint64_t)h.y << 32);
-    if (h.z == 0) {
-      leaf_tile<T, KIND, THREADS>(a, w / 2);  // the whole leaf tile, by direct loads
-    } else if (h.z == 1) {
-      const uint4 h2 = hdr[2 * s + 1];
-      const uint64_t x0 = (uint64_t)h2.x | ((uint64_t)h2.y << 32), left0 = (uint64_t)h2.z | ((uint64_t)h2.w << 32);
-      const VT* xs = reinterpret_cast<const VT*>(buf + (size_t)s * NB * LSUB);
-      const VT* ys = reinterpret_cast<const VT*>(buf + ((size_t)s * NB + (NB - 1)) * LSUB);
-#pragma unroll
-      for (uint32_t i = 0; i < UNROLL; i++) {
-        const uint32_t j = tid + i * THREADS;
-        if (j >= h.w) break;
-        const uint64_t e0 = (uint64_t)j * EPU;  // from the sub-tile's first element
-        const uint64_t left = left0 - e0;
-        if (left >= (uint64_t)EPU) {
-          VT xv = xs[j];
-          const VT yv = ys[j];
-          T* x = reinterpret_cast<T*>(&xv);  // static indices only: the vector stays in registers
-          const T* y = reinterpret_cast<const T*>(&yv);
-#pragma unroll
-          for (int q = 0; q < EPU; q++) x[q] = apply<T, KIND>(x[q], KIND == DC_OP_AXPY_HALF ? y[q] : T(0), sc);
-          stcs(reinterpret_cast<VT*>(x0 + e0 * sizeof(T)), xv);
-        } else {  // the segment's last elements, read from the staged copy
-          const T* xsm = reinterpret_cast<const T*>(xs + j);
-          const T* ysm = reinterpret_cast<const T*>(ys + j);
-          T* xd = reinterpret_cast<T*>(x0 + e0 * sizeof(T));
-          for (uint32_t q = 0; q < (uint32_t)left; q++)
-            xd[q] = apply<T, KIND>(xsm[q], KIND == DC_OP_AXPY_HALF ? ysm[q] : T(0), sc);
-        }
-      }
-    }  // h.z == 3: the second half of a tile the direct path took whole
+    leaf_staged_apply<T, KIND, THREADS>(a, xbuf(s), ybuf(s), h, hdr[2 * s + 1]);
     __syncthreads();  // nobody reads stage s any more
     if (tid == 0) {
-      leaf_issue<KIND>(a, buf, bar, hdr, s, wn, nsub, nx);
+      leaf_issue<KIND>(a, xbuf(s), ybuf(s), &bar[s], &hdr[2 * s], wn, nsub, nx);
       if (wn < nsub) wn += gridDim.x;
       leaf_next_range(a, wn, nsub, &nx);  // its segment is loaded next iteration
     }
@@ -623,26 +634,84 @@ __global__ void __launch_bounds__(THREADS, 3) leaf_tma_kernel(LeafArgs a) {
 }
 
 template <typename T, int KIND, uint32_t THREADS, bool SCAN>
-// CTAs take leaf tiles from a counter, so the ones that relocated take fewer.
+// After its relocation tiles, a CTA takes half tiles of the leaf update from a
+// counter (so the CTAs that relocated take fewer) and stages them in its two
+// relocation stages by bulk copies: x in a stage's struct buffer, y in its
+// record buffer (8 KiB each).  Thread 0 grabs sub-tile indices two refills
+// ahead, loads their segment range one refill ahead and the segment at the
+// start of an iteration, so that no load on the refill path waits for another.
 // The last CTA to finish resets the counter for the next launch (launches on
-// one stream never overlap).
+// one stream never overlap).  Every wait has an iteration limit.
 __global__ void __launch_bounds__(THREADS) fused_kernel(RelocArgs r, LeafArgs l, uint64_t leaf_tiles) {
+  static_assert(sizeof(RelocStage::img) >= LSUB_BYTES && sizeof(RelocStage::rec) >= LSUB_BYTES,
+                "a relocation stage holds a half tile of x and of y");
   __shared__ RelocSmem sm;
-  __shared__ unsigned long long s_w;
+  __shared__ uint64_t lbar[RSTAGES];
+  __shared__ uint4 lhdr[2 * RSTAGES];
+  (void)leaf_tiles;  // the launch's grid size counts them; the CTAs count half tiles
   if (r.verify)
     reloc_tiles<THREADS, true, SCAN>(r, sm);
   else
     reloc_tiles<THREADS, false, SCAN>(r, sm);
+  // The relocation's stages are free: its loop ended with every stage's copies
+  // complete and its stores drained (or the CTA had no relocation tile).
+  const uint32_t tid = threadIdx.x;
   unsigned long long* next = reinterpret_cast<unsigned long long*>(&r.ctrl[CTRL_NEXT]);
-  for (;;) {
-    if (threadIdx.x == 0) s_w = atomicAdd(next, 1ull);
-    __syncthreads();
-    const uint64_t w = s_w;
-    __syncthreads();
-    if (w >= leaf_tiles) break;
-    leaf_tile<T, KIND, THREADS>(l, w);
+  const uint64_t nsub = (l.units + LSUB - 1) / LSUB;
+  auto xbuf = [&](uint32_t s) { return sm.st[s].img; };
+  auto ybuf = [&](uint32_t s) { return reinterpret_cast<uint4*>(sm.st[s].rec); };
+  if (tid == 0) {
+    for (uint32_t s = 0; s < RSTAGES; s++) mbar_init(&lbar[s]);
+    mbar_init_fence();
   }
-  if (threadIdx.x == 0) {
+  __syncthreads();
+  uint64_t cur = 0, ahead = 0;  // the producer's next two sub-tiles
+  LeafNext nx{NONE, NONE, {0, 0, 0, 0}};
+  if (tid == 0) {
+    for (uint32_t s = 0; s < RSTAGES; s++) {
+      const uint64_t w = atomicAdd(next, 1ull);
+      leaf_next_range(l, w, nsub, &nx);
+      leaf_next_seg(l, &nx);
+      leaf_issue<KIND>(l, xbuf(s), ybuf(s), &lbar[s], &lhdr[2 * s], w, nsub, nx);
+    }
+    cur = atomicAdd(next, 1ull);
+    leaf_next_range(l, cur, nsub, &nx);
+    ahead = atomicAdd(next, 1ull);
+  }
+  for (uint32_t k = 0;; k++) {
+    const uint32_t s = k % RSTAGES, parity = (k / RSTAGES) & 1;
+    if (tid == 0) leaf_next_seg(l, &nx);  // the range arrived during the last iteration
+    bool late = false;
+    uint32_t spins = 0;
+    while (!mbar_try_wait(&lbar[s], parity))
+      if (++spins >= WAIT_LIMIT) {
+        late = true;
+        break;
+      }
+    if (__syncthreads_or(late)) {
+      if (tid == 0) {  // give the copies in flight another bounded wait before leaving
+        atomicOr(&r.ctrl[CTRL_ERR], ERR_TIMEOUT);
+        for (uint32_t q = 0; q < RSTAGES; q++) {
+          const uint32_t kq = k + q;
+          for (uint32_t n = 0; n < WAIT_LIMIT && !mbar_try_wait(&lbar[kq % RSTAGES], (kq / RSTAGES) & 1); n++) {
+          }
+        }
+      }
+      break;
+    }
+    const uint4 h = lhdr[2 * s];
+    // the counter hands each CTA increasing indices: past the end, every later one is too
+    if (h.x == NONE && h.y == NONE) break;  // uniform
+    leaf_staged_apply<T, KIND, THREADS>(l, xbuf(s), ybuf(s), h, lhdr[2 * s + 1]);
+    __syncthreads();  // nobody reads stage s any more
+    if (tid == 0) {
+      leaf_issue<KIND>(l, xbuf(s), ybuf(s), &lbar[s], &lhdr[2 * s], cur, nsub, nx);
+      cur = ahead;
+      leaf_next_range(l, cur, nsub, &nx);  // its segment is loaded next iteration
+      ahead = atomicAdd(next, 1ull);
+    }
+  }
+  if (tid == 0) {
     __threadfence();
     if (atomicAdd(&r.ctrl[CTRL_DONE], 1u) == gridDim.x - 1) {
       atomicExch(next, 0ull);
