@@ -59,10 +59,10 @@ WORKLOADS = {
 # DRAM bytes (read + write) per launch of the step's kernel from one ncu capture, by (workload, split);
 # the summary beside each gives the command.  An entry stands only while the kernel is unchanged.
 NCU_TRAFFIC = {
-    ("dense", 256, 4): (460_444_928, "profiles/fused_kernel_dense.md"),
-    ("reloc_stress", 256, 4): (191_952_256, "profiles/relocate_kernel_reloc_stress.md"),
-    ("deep", 256, 4): (757_099_392, "profiles/fused_kernel_deep_batched.md"),
-    ("batched", 256, 4): (7_019_651_200, "profiles/fused_kernel_deep_batched.md"),
+    ("dense", 128, 4): (452_643_712, "profiles/fused_kernel_dense.md"),
+    ("reloc_stress", 128, 4): (196_395_520, "profiles/relocate_kernel_reloc_stress.md"),
+    ("deep", 128, 4): (751_302_656, "profiles/fused_kernel_deep_batched.md"),
+    ("batched", 128, 4): (7_016_776_448, "profiles/fused_kernel_deep_batched.md"),
 }
 
 
