@@ -5,12 +5,20 @@
 //                    its struct bytes in shared memory, writes into each of
 //                    its slots the device address of the block it points at
 //                    (the arena base + the slot's lane group base + the
-//                    record's offset), and stores the tile back: whole
-//                    coalesced sectors instead of one 8-byte store per
-//                    pointer.
-//   leaf_kernel      the leaf update through resolved effective addresses
+//                    target's offset in the group: the record's, or a
+//                    prefix sum of sizes with DC_PLAN_DEVICE_SCAN), and
+//                    stores the tile back: whole coalesced sectors instead
+//                    of one 8-byte store per pointer.
+//   leaf_tma_kernel  the leaf update through resolved effective addresses
 //                    (Sec. 3): x += 0.5*y or x *= scale over (x, y, n)
-//                    segments, 16-byte vector loads/stores, no pointer loads.
+//                    segments, no pointer loads; x and y come into shared
+//                    memory by 1-D bulk copies, half a tile at a time in
+//                    three stages (the default for dc_update_leaves).
+//   leaf_kernel      the same update by direct 16-byte vector loads
+//                    (DC_LEAF_TMA=0).
+//   fused_kernel     relocation tiles, then the leaf update's half tiles from
+//                    an atomic counter, staged by bulk copies in the
+//                    relocation's two stages (dc_relocate_update).
 //   chase_kernel     the same update with every element walking its pointer
 //                    chain from the root (Listing 2's loop body), with loads
 //                    that may not be hoisted out of the element loop.
