@@ -255,8 +255,11 @@ DC_API dc_status dc_resolve_offset_in(dc_plan_t plan, uint64_t tree, const dc_st
 
 /* dc_update_leaves — run the leaf kernel on the device copy through resolved
  * addresses: the selected structs' chains are resolved on the host and the
- * kernel streams over (x, y, n) segments with no pointer loads.  Errors:
- * DC_EINVAL (op fields / path / counts), DC_ESTATE, DC_ECUDA. */
+ * kernel streams over (x, y, n) segments with no pointer loads, bringing x
+ * and y into shared memory by 1-D bulk copies (with DC_LEAF_TMA=0 in the
+ * environment, read at every call, by direct 16-byte loads instead; the
+ * results are the same).  Errors: DC_EINVAL (op fields / path / counts),
+ * DC_ESTATE, DC_ECUDA. */
 DC_API dc_status dc_update_leaves(dc_plan_t plan, const dc_op* op, dc_stream_t stream);
 
 /* dc_relocate_update — dc_relocate and dc_update_leaves(op) in one persistent
