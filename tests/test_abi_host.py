@@ -325,3 +325,31 @@ def test_partition_by_bytes_is_greedy_lpt():
         best = min(max(sum(s for s, a in zip(sizes, assign) if a == j) for j in range(k))
                    for assign in itertools.product(range(k), repeat=n))
         assert 3 * k * max(loads) <= (4 * k - 1) * best or max(loads) == best
+
+
+def test_package_without_its_library_fails_to_import(tmp_path):
+    """A copy of the binding with no libdc.so beside it must refuse to import (no fallback)."""
+    pkg = tmp_path / "paper_1906_01128_b300"
+    pkg.mkdir()
+    src = os.path.join(ROOT, "paper_1906_01128_b300", "__init__.py")
+    (pkg / "__init__.py").write_text(open(src).read())
+    code = ("import sys; sys.path.insert(0, sys.argv[1])\n"
+            "try:\n"
+            "    import paper_1906_01128_b300\n"
+            "except ImportError as e:\n"
+            "    print('refused:', e); sys.exit(0)\n"
+            "sys.exit(1)\n")
+    r = subprocess.run([os.sys.executable, "-c", code, str(tmp_path)], capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "not built" in r.stdout and "no fallback" in r.stdout
+
+
+def test_product_package_never_reaches_the_oracle():
+    """The binding and the native sources name no oracle module, so no call can route through it."""
+    pkg = os.path.join(ROOT, "paper_1906_01128_b300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cpp", ".hpp", ".h", ".cuh")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b|\boracle/|\boracle\.[A-Za-z_]|liboracle", text, re.M), f
