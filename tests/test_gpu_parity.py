@@ -219,8 +219,8 @@ def test_dense_listing2_chain_scale():
                 mode="chase")
 
 
-def test_dense_paper_all_levels_axpy_f64():
-    # an AXPY needs two arrays: scale every level's A instead, level type by type
+def test_dense_paper_all_levels_scale_f64():
+    # the Dense struct has one array per level: scale every level's A, level type by type
     for lvl in range(4):
         full_parity(lambda: tg.dense_tree(4, 300, 3, seed=5),
                     dict(kind=dc.OP_SCALE, type_=lvl, x=2 if lvl < 3 else 1, scale=0.75))
@@ -501,7 +501,71 @@ def test_fused_single_tree_workloads():
         plan.destroy()
 
 
+def node64_tree(levels, fanout, n, seed):
+    """The node struct with fp64 position and velocity arrays (an AXPY in fp64
+    needs two arrays of one struct)."""
+    sch = tg.node_schema()
+    for f in sch.types[0].fields[2:4]:
+        f.elem_size, f.elem_kind = 8, tg.F64
+    rules = [tg.Rule(0, 0, n if isinstance(n, tuple) else tg.const(n), n if isinstance(n, tuple) else tg.const(n)),
+             tg.Rule(0, 1, tg.const(fanout), tg.const(0))]
+    return tg.Tree(sch, levels, rules, seed, name=f"node64-{levels}-{fanout}")
+
+
+# fp64 x += 0.5*y, and fp32 x *= scale with scales that are not fp32 numbers
+# (the kernel must multiply by the scale rounded to float, once)
+ROUNDING_CASES = {
+    "node64_axpy": (lambda: node64_tree(3, 7, tg.uniform(0, 5000), seed=31), {}),
+    "node64_chain_axpy": (lambda: node64_tree(3, 7, tg.uniform(1, 5000), seed=32),
+                          dict(sel=dc.SEL_CHAIN, path=[(NODE_LEAF, 3), (NODE_LEAF, 1)])),
+    "listing1_axpy_f64": (lambda: tg.listing1_tree(100003, seed=33), dict(type_=2, x=1, y=2)),
+    "node_scale_f32_inexact": (lambda: tg.node_tree(3, 7, tg.uniform(0, 5000), seed=34),
+                               dict(kind=dc.OP_SCALE, scale=1.1)),
+    "node_chain_scale_f32_inexact": (lambda: tg.node_tree(3, 7, tg.uniform(1, 5000), seed=35),
+                                     dict(kind=dc.OP_SCALE, sel=dc.SEL_CHAIN, scale=-0.7,
+                                          path=[(NODE_LEAF, 6), (NODE_LEAF, 0)])),
+}
+
+
+@pytest.mark.parametrize("case", sorted(ROUNDING_CASES))
+def test_axpy_f64_and_inexact_f32_scale(case, monkeypatch):
+    """Every path that runs the update, against the oracle at 0 ULP: the
+    bulk-copy leaf kernel (dc_update_leaves, twice), the direct-load one, the
+    pointer chase, and the one-call round trip (dc_roundtrip) on mapped and
+    staged plans.  dc_relocate_update takes the same cases in
+    test_fused_launch_every_kind_and_width."""
+    make, kw = ROUNDING_CASES[case]
+    full_parity(make, kw, repeat=2)
+    full_parity(make, kw, mode="chase")
+    step_parity(make, kw, dc.PLAN_MAP_HOST, repeat=2)
+    step_parity(make, kw, 0)
+    monkeypatch.setenv("DC_LEAF_TMA", "0")
+    full_parity(make, kw)
+
+
+def test_axpy_f64_dense_shape_full_size():
+    # the dense workload's shape and lengths (3 levels, fanout 16, lognormal
+    # median 65,536) with fp64 arrays: 677 MB, through the leaf update, the
+    # persistent fused launch and the round trip
+    make = lambda: node64_tree(3, 16, tg.lognormal(65536, 1.2, 4194304), seed=2)
+    full_parity(make, {})
+    step_parity(make, {}, dc.PLAN_MAP_HOST)
+    src, ref = make(), make()
+    s = src.schema
+    plan = dc.Plan(s, src.root)
+    plan.bind()
+    plan.deep_copy()
+    dop, oop = ops_pair()
+    plan.relocate_update(dop)
+    plan.sync()
+    cp = oracle.deep_copy(s, ref.root)
+    oracle.update(s, cp.root, oop)
+    image_ok(plan, s, cp.root)
+    plan.destroy()
+
+
 FUSED_CASES = {
+    **ROUNDING_CASES,
     # Linear chain, fp64 A: x *= 1.5 on every level (the paper's kernel)
     "linear_scale_f64": (lambda: tg.linear_tree(6, 100000, "allinit", seed=3), dict(kind=dc.OP_SCALE, x=2, scale=1.5)),
     # the same on the last level only, reached by a chain

@@ -319,6 +319,100 @@ def test_scale_listing2_chain_last_element():
     t2.free()
 
 
+def f32_round(fr: Fraction) -> np.float32:
+    """The fp32 value nearest to the exact rational `fr` (ties to even), for
+    rationals that a double holds exactly (products of two fp32 values): the
+    double conversion is then exact and the fp32 cast is the one rounding."""
+    d = float(fr)
+    assert Fraction(d) == fr, "not exact in a double"
+    return np.float32(d)
+
+
+@pytest.mark.parametrize("scale", [1.1, -0.7, 1.0 / 3.0])
+def test_scale_f32_uses_the_scale_rounded_to_float(scale):
+    # The paper's scaling kernel (Sec. 4.1.2, Listing 2) on fp32 arrays: the
+    # scale is an fp32 operand, so x*scale is the exact product of x and
+    # float(scale), rounded once to fp32.  Scales that are not fp32 numbers
+    # separate this from multiplying by the double and rounding twice.
+    t = tg.node_tree(3, 4, 777, seed=21)
+    s = t.schema
+    before = node_arrays(t.root)
+    cp = oracle.deep_copy(s, t.root)
+    oracle.update(s, cp.root, oracle.Op(kind=oracle.OP_SCALE, x_field=2, scale=scale))
+    after = node_arrays(cp.root)
+    sf = Fraction(float(np.float32(scale)))
+    differs = 0
+    for path, (p, v) in before.items():
+        want = np.array([f32_round(Fraction(float(x)) * sf) for x in p], dtype=np.float32)
+        assert same_bits(after[path][0], want), path
+        assert same_bits(after[path][1], v), path  # velocity is not an operand
+        twice = (p.astype(np.float64) * scale).astype(np.float32)  # the double product, rounded again
+        differs += int((twice != want).sum())
+    assert differs > 100  # the pin tells the two readings apart
+    t.free()
+
+
+class CTraits(ctypes.Structure):
+    """Listing 1's Traits struct: {int n; double* positions0..2}, 32 bytes."""
+    _fields_ = [("n", ctypes.c_int32), ("pad", ctypes.c_int32), ("p0", ctypes.c_void_p), ("p1", ctypes.c_void_p),
+                ("p2", ctypes.c_void_p)]
+
+
+def test_axpy_f64_special_values():
+    # x + 0.5*y in fp64 with each operation rounded once (ties to even), values
+    # computed by hand.  Halving is exact except below the normal range, where
+    # the product itself rounds: 0.5 * 2^-1074 is a tie between 0 and 2^-1074,
+    # and goes to 0.
+    e = 2.0 ** -52
+    tiny = 2.0 ** -1074
+    xs = [1.0, 1.0 + e, -1.0, 0.25, 0.75, tiny, 3.0, -0.5]
+    ys = [e, e, -e, -0.5, 0.5, tiny, 2.0 ** 53, 1.0]
+    # 1 + 2^-53: tie -> 1 (even); 1 + 2^-52 + 2^-53: tie -> 1 + 2^-51 (even);
+    # -1 - 2^-53 -> -1; 0.25 - 0.25 = +0; 0.75 + 0.25 = 1; 2^-1074 + 0;
+    # 3 + 2^52 is exact; -0.5 + 0.5 = +0
+    want = [1.0, 1.0 + 2 * e, -1.0, 0.0, 1.0, tiny, 3.0 + 2.0 ** 52, 0.0]
+    n = len(xs)
+    x = (ctypes.c_double * n)(*xs)
+    y = (ctypes.c_double * n)(*ys)
+    z = (ctypes.c_double * n)(*([7.0] * n))
+    node = CTraits(n, 0, ctypes.addressof(x), ctypes.addressof(y), ctypes.addressof(z))
+    s = tg.Schema([tg.listing1_schema().types[2]])
+    oracle.update(s, ctypes.addressof(node), oracle.Op(kind=oracle.OP_AXPY_HALF, type=0, x_field=1, y_field=2))
+    got = np.frombuffer(bytes(x), dtype=np.float64)
+    assert [float(g) for g in got] == want
+    assert not np.signbit(got[3]) and not np.signbit(got[7])  # RN: a + (-a) = +0
+    assert list(np.frombuffer(bytes(y), dtype=np.float64)) == ys
+    assert list(np.frombuffer(bytes(z), dtype=np.float64)) == [7.0] * n
+
+
+@pytest.mark.parametrize("sel", ["all", "chain"])
+def test_axpy_f64_is_correctly_rounded(sel):
+    # Listing 1's Simulation->Atoms->Traits chain with positions0 += 0.5 *
+    # positions1 in fp64: the generated values are multiples of 2^-52 in
+    # [-1, 1), so halving is exact and each result is the exact sum rounded once
+    # (Python's int/int division, under float(Fraction), rounds correctly).
+    t = tg.listing1_tree(3000, seed=23)
+    s = t.schema
+    traits = oracle.host_resolve(s, t.root, [(1, 0), (1, 0)])
+    x0, y0, z0 = (f64_view(u64(traits + off), 3000).copy() for off in (8, 16, 24))
+    cp = oracle.deep_copy(s, t.root)
+    op = oracle.Op(kind=oracle.OP_AXPY_HALF, type=2, x_field=1, y_field=2)
+    if sel == "chain":
+        op = oracle.Op(kind=oracle.OP_AXPY_HALF, sel=oracle.SEL_CHAIN, path=[(1, 0), (1, 0)], type=2, x_field=1,
+                       y_field=2)
+    oracle.update(s, cp.root, op)
+    ct = oracle.host_resolve(s, cp.root, [(1, 0), (1, 0)])
+    x1, y1, z1 = (f64_view(u64(ct + off), 3000) for off in (8, 16, 24))
+    want = np.array([float(Fraction(float(a)) + Fraction(float(b)) / 2) for a, b in zip(x0, y0)])
+    assert same_bits(x1, want)
+    assert same_bits(y1, y0) and same_bits(z1, z0)
+    rounded = sum(Fraction(float(a)) + Fraction(float(b)) / 2 != Fraction(float(w)) for a, b, w in zip(x0, y0, want))
+    # sums at or above 1 in magnitude whose exact value needs 54 bits round:
+    # about one in fourteen here, enough to exercise ties and rounding
+    assert rounded > 100
+    t.free()
+
+
 # ---------------------------------------------------------------------------
 # copy back and the results check
 # ---------------------------------------------------------------------------
