@@ -98,13 +98,16 @@ def lib():
         L.or_check_image.argtypes = [P(_Schema), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
                                      ctypes.c_uint64, ctypes.c_uint64, P(_Counts), ctypes.c_char_p,
                                      ctypes.c_size_t]
+        L.or_check_chain_image.argtypes = [P(_Schema), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                                           ctypes.c_uint64, ctypes.c_uint64, P(_Step), ctypes.c_uint32,
+                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_char_p, ctypes.c_size_t]
         L.or_image_resolve.argtypes = [P(_Schema), ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
                                        ctypes.c_uint64, P(_Step), ctypes.c_uint32,
                                        P(ctypes.c_uint64)]
         L.or_host_resolve.argtypes = [P(_Schema), ctypes.c_void_p, P(_Step), ctypes.c_uint32,
                                       P(ctypes.c_uint64)]
         for f in ("or_count", "or_deep_copy", "or_update", "or_update_parallel", "or_threads", "or_copy_back",
-                  "or_trees_equal", "or_check_image", "or_image_resolve", "or_host_resolve"):
+                  "or_trees_equal", "or_check_image", "or_check_chain_image", "or_image_resolve", "or_host_resolve"):
             getattr(L, f).restype = ctypes.c_int
         _L = L
     return _L
@@ -251,6 +254,21 @@ def check_image(schema, src_root: int, image: np.ndarray, dev_base: int, root_of
     if rc not in (0, 3):
         raise RuntimeError(f"oracle check_image: invalid input (status {rc})")
     return rc == 0, msg.value.decode(), _counts_dict(c)
+
+
+def check_chain_image(schema, src_root: int, image: np.ndarray, dev_base: int, path, x_field: int,
+                      y_field: int = -1, root_off: int = 0):
+    """Check a host copy of a device arena that holds a selective deep copy of
+    one chain (the struct blocks it passes through, the x / y arrays of the
+    struct it reaches) against the source tree, along that chain only."""
+    image = np.ascontiguousarray(image, dtype=np.uint8)
+    steps = _steps(path)
+    msg = ctypes.create_string_buffer(1024)
+    rc = lib().or_check_chain_image(ctypes.byref(_cs(schema).struct), src_root, image.ctypes.data, image.nbytes,
+                                    dev_base, root_off, steps, len(path), x_field, y_field, msg, 1024)
+    if rc not in (0, 3):
+        raise RuntimeError(f"oracle check_chain_image: invalid input (status {rc})")
+    return rc == 0, msg.value.decode()
 
 
 def image_resolve(schema, image: np.ndarray, dev_base: int, path, root_off: int = 0) -> int:

@@ -641,6 +641,112 @@ int or_check_image(const or_schema* s, const void* src_root, const void* image,
   return rc;
 }
 
+/* ---- selective deep copy of one chain (Sec. 2) ---------------------------- */
+
+/* One pointer of the chain in the image: `p` must be a device address inside
+ * the arena with the whole `b`-byte block after it, 16-byte aligned (the
+ * layout's block alignment), and not the source's own address. */
+static int chain_ptr(uint64_t p, uint64_t b, const void* src_ptr, uint64_t image_bytes, uint64_t dev_base,
+                     const char* what, char* msg, size_t msglen) {
+  if (p == (uint64_t)(uintptr_t)src_ptr) {
+    say(msg, msglen, "%s: still the source address", what);
+    return OR_MISMATCH;
+  }
+  if (p < dev_base || p - dev_base > image_bytes || b > image_bytes - (p - dev_base)) {
+    say(msg, msglen, "%s: pointer 0x%llx outside the arena", what, (unsigned long long)p);
+    return OR_MISMATCH;
+  }
+  if ((p - dev_base) % 16) {
+    say(msg, msglen, "%s: block offset %llu not 16-byte aligned", what, (unsigned long long)(p - dev_base));
+    return OR_MISMATCH;
+  }
+  return OR_OK;
+}
+
+/* Every struct of a struct block on the chain carries its source's bytes
+ * outside its pointer slots. */
+static int chain_block(const or_schema* sc, uint32_t ti, const uint8_t* src, const uint8_t* im, uint64_t n,
+                       uint32_t step, char* msg, size_t msglen) {
+  const or_type* T = &sc->types[ti];
+  for (uint64_t j = 0; j < n; j++)
+    for (uint32_t k = 0; k < T->size; k++)
+      if (!in_pointer_slot(T, k) && im[j * T->size + k] != src[j * T->size + k]) {
+        say(msg, msglen, "chain block %u, struct %llu: byte %u differs from the source", step,
+            (unsigned long long)j, k);
+        return OR_MISMATCH;
+      }
+  return OR_OK;
+}
+
+int or_check_chain_image(const or_schema* s, const void* src_root, const void* image, uint64_t image_bytes,
+                         uint64_t dev_base, uint64_t root_off, const or_step* path, uint32_t len, int32_t x_field,
+                         int32_t y_field, char* msg, size_t msglen) {
+  if (!s || !src_root || !image) return OR_EINVAL;
+  const uint8_t* img = (const uint8_t*)image;
+  uint32_t ti = s->root_type;
+  if (root_off % 16 || root_off > image_bytes || s->types[ti].size > image_bytes - root_off) {
+    say(msg, msglen, "root block outside the arena");
+    return OR_MISMATCH;
+  }
+  /* the struct block the walk is in: its source, its image offset, its length
+   * in structs, and the struct of it the chain takes */
+  const uint8_t* blk_src = (const uint8_t*)src_root;
+  uint64_t blk_off = root_off, blk_n = 1, at = 0;
+  for (uint32_t k = 0;; k++) {
+    const or_type* T = &s->types[ti];
+    int rc = chain_block(s, ti, blk_src, img + blk_off, blk_n, k, msg, msglen);
+    if (rc) return rc;
+    const uint8_t* cur_src = blk_src + at * T->size;
+    const uint8_t* cur_img = img + blk_off + at * T->size;
+    if (k == len) { /* the struct the chain reaches: its x and y arrays */
+      int32_t fields[2] = {x_field, y_field};
+      for (int a = 0; a < 2; a++) {
+        if (fields[a] < 0) continue;
+        if ((uint32_t)fields[a] >= T->nfields) return OR_EINVAL;
+        const or_field* f = &T->fields[fields[a]];
+        uint64_t n;
+        if (f->kind != OR_ARRAY || count_of(T, cur_src, f, &n)) return OR_EINVAL;
+        uint64_t p = u64_at(cur_img, f->offset);
+        if (n == 0) {
+          if (p != 0) {
+            say(msg, msglen, "field%d: count 0 but pointer 0x%llx", fields[a], (unsigned long long)p);
+            return OR_MISMATCH;
+          }
+          continue;
+        }
+        const uint8_t* sp = (const uint8_t*)ptr_at(cur_src, f);
+        if (!sp) return OR_EINVAL;
+        uint64_t b = block_bytes(s, f, n);
+        char what[64];
+        snprintf(what, sizeof what, "field%d of the chain's last struct", fields[a]);
+        if ((rc = chain_ptr(p, b, sp, image_bytes, dev_base, what, msg, msglen))) return rc;
+        if (memcmp(img + (p - dev_base), sp, b)) {
+          say(msg, msglen, "%s: array bytes differ from the source", what);
+          return OR_MISMATCH;
+        }
+      }
+      say(msg, msglen, "ok");
+      return OR_OK;
+    }
+    if (path[k].field >= T->nfields) return OR_EINVAL;
+    const or_field* f = &T->fields[path[k].field];
+    uint64_t n;
+    if (f->kind != OR_CHILD || count_of(T, cur_src, f, &n) || path[k].index >= n) return OR_EINVAL;
+    const uint8_t* sp = (const uint8_t*)ptr_at(cur_src, f);
+    if (!sp) return OR_EINVAL;
+    const uint32_t cs = s->types[f->child_type].size;
+    uint64_t p = u64_at(cur_img, f->offset);
+    char what[64];
+    snprintf(what, sizeof what, "chain step %u (field %u)", k, path[k].field);
+    if ((rc = chain_ptr(p, n * cs, sp, image_bytes, dev_base, what, msg, msglen))) return rc;
+    blk_src = sp;
+    blk_off = p - dev_base;
+    blk_n = n;
+    at = path[k].index;
+    ti = (uint32_t)f->child_type;
+  }
+}
+
 /* ---- effective addresses of pointer chains (Sec. 3) ------------------------ */
 
 int or_image_resolve(const or_schema* s, const void* image, uint64_t image_bytes,

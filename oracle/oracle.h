@@ -25,6 +25,15 @@
  *   or_check_image    checks a device image of a deep copy against its source:
  *                     same shape, byte-equal data, every pointer inside the
  *                     arena, 16-byte aligned, and no two blocks overlapping.
+ *   or_check_chain_image  checks a device image of a selective deep copy of
+ *                     one pointer chain (Sec. 2: only what the chain reaches is
+ *                     replicated) along that chain: each struct block the chain
+ *                     passes through holds its source's non-pointer bytes,
+ *                     every pointer the chain follows and the x / y array
+ *                     pointers of the struct it reaches lie inside the arena
+ *                     (16-byte aligned, not the source address), and those
+ *                     arrays hold the source's bytes.  Off the chain nothing
+ *                     is read.
  *   or_image_resolve  follows a pointer chain through a device image (the
  *                     effective address of Sec. 3) by reading its pointers.
  *   or_host_resolve   the same chain in a host tree.
@@ -113,6 +122,10 @@ int or_trees_equal(const or_schema* s, const void* a, const void* b, char* msg, 
 int or_check_image(const or_schema* s, const void* src_root, const void* image,
                    uint64_t image_bytes, uint64_t dev_base, uint64_t root_off, or_counts* seen,
                    char* msg, size_t msglen);
+/* y_field < 0: the op has no y array.  The path's steps are CHILD fields. */
+int or_check_chain_image(const or_schema* s, const void* src_root, const void* image, uint64_t image_bytes,
+                         uint64_t dev_base, uint64_t root_off, const or_step* path, uint32_t len, int32_t x_field,
+                         int32_t y_field, char* msg, size_t msglen);
 int or_image_resolve(const or_schema* s, const void* image, uint64_t image_bytes,
                      uint64_t dev_base, uint64_t root_off, const or_step* path, uint32_t len,
                      uint64_t* dev_addr);

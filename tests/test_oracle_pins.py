@@ -516,6 +516,98 @@ def test_check_image_catches_planted_mistakes(mistake):
     t.free()
 
 
+# ---------------------------------------------------------------------------
+# the image of a selective deep copy of one chain (Sec. 2)
+# ---------------------------------------------------------------------------
+
+def _le(img, off, n=8, signed=False):
+    return int.from_bytes(img[off:off + n].tobytes(), "little", signed=signed)
+
+
+def _dense_chain():
+    """The Dense tree (Fig 4) with q = 4, D = 3 and Listing 2's chain
+    a0->Lnext[q-1].Lnext[q-1].Lnext[q-1]; returns the tree, a full deep copy's
+    image at a device-like base, the path and the byte spans a selective copy
+    of that chain holds (the root struct, each Lnext block on the path, the
+    last struct's A array), found by reading the image by hand."""
+    q, D = 4, 3
+    t = tg.dense_tree(q, 50, D, seed=31)
+    base = 0x7D0000000000
+    img = oracle.deep_copy(t.schema, t.root, ptr_base=base).image().copy()
+    path = [(3, q - 1)] * D
+    spans, off = [(0, 24)], 0
+    for k in range(D):
+        b = _le(img, off + 16) - base  # Lnext of an L0..L(D-1) struct (offset 16)
+        size = 24 if k + 1 < D else 16  # the last level is the half-size struct
+        spans.append((b, b + q * size))
+        off = b + (q - 1) * size
+    a, n = _le(img, off + 8) - base, _le(img, off, 4, signed=True)  # {int nA; double* A}
+    spans.append((a, a + 8 * n))
+    return t, base, img, path, spans, D
+
+
+def test_chain_image_accepts_a_selective_copy_and_nothing_else_is_read():
+    t, base, img, path, spans, D = _dense_chain()
+    s = t.schema
+    ok, msg = oracle.check_chain_image(s, t.root, img, base, path, x_field=1)
+    assert ok, msg
+    # overwrite every byte off the chain: the chain check still passes, the
+    # full deep-copy check does not
+    sel = np.full_like(img, 0xAB)
+    for lo, hi in spans:
+        sel[lo:hi] = img[lo:hi]
+    assert sum(hi - lo for lo, hi in spans) < len(img) // 10
+    ok, msg = oracle.check_chain_image(s, t.root, sel, base, path, x_field=1)
+    assert ok, msg
+    assert not oracle.check_image(s, t.root, sel, base)[0]
+    # a mistake off the chain is not looked at: the root's own A array
+    sel[_le(img, 8) - base + 3] ^= 1
+    assert oracle.check_chain_image(s, t.root, sel, base, path, x_field=1)[0]
+    t.free()
+
+
+@pytest.mark.parametrize("mistake", ["array_byte", "path_struct_byte", "sibling_struct_byte", "ptr_plus16",
+                                     "ptr_to_source", "outside", "misaligned_array", "short_block"])
+def test_chain_image_catches_planted_mistakes(mistake):
+    t, base, img, path, spans, D = _dense_chain()
+    s = t.schema
+    (r0, _), (b1, _), (b2, _), (b3, _), (a, a_end) = spans
+    if mistake == "array_byte":
+        img[a + 13] ^= 1
+    elif mistake == "path_struct_byte":
+        img[b2 + 3 * 24 + 4] ^= 1  # Lnext[3].Lnext[3].nLnext
+    elif mistake == "sibling_struct_byte":
+        img[b1 + 0] ^= 1  # Lnext[0].nA: off the path, in a block the chain passes through
+    elif mistake == "ptr_plus16":
+        _plant(img, b1 + 3 * 24 + 16, _le(img, b1 + 3 * 24 + 16) + 16)
+    elif mistake == "ptr_to_source":
+        _plant(img, 16, u64(t.root + 16))  # the root's Lnext still the host's
+    elif mistake == "outside":
+        _plant(img, b3 + 3 * 16 + 8, base + len(img) - 8)  # the last struct's A runs past the arena
+    elif mistake == "misaligned_array":
+        _plant(img, b3 + 3 * 16 + 8, base + a + 8)
+    elif mistake == "short_block":
+        _plant(img, 16, base + len(img) - 2 * 24)  # room for 2 of the root's 4 children
+    ok, msg = oracle.check_chain_image(s, t.root, img, base, path, x_field=1)
+    assert not ok, mistake
+    t.free()
+
+
+def test_chain_image_with_x_and_y_on_a_node_chain():
+    # the node struct's chain root->child[2]->child[1] with x = position, y = velocity
+    t = tg.node_tree(3, 3, 40, seed=22)
+    s = t.schema
+    base = 0x7E0000000000
+    img = oracle.deep_copy(s, t.root, ptr_base=base).image().copy()
+    path = [(4, 2), (4, 1)]
+    assert oracle.check_chain_image(s, t.root, img, base, path, x_field=2, y_field=3)[0]
+    vel = oracle.image_resolve(s, img, base, path + [(3, 0)]) - base
+    img[vel + 7] ^= 1  # the chain's y array
+    assert not oracle.check_chain_image(s, t.root, img, base, path, x_field=2, y_field=3)[0]
+    assert oracle.check_chain_image(s, t.root, img, base, path, x_field=2)[0]  # y not asked for
+    t.free()
+
+
 def test_random_schemas_copy_and_image_agree():
     rng = random.Random(1234)
     for i in range(150):
