@@ -20,7 +20,12 @@
  *   - Device work is asynchronous and stream-ordered.  Errors a kernel finds
  *     (an index outside its buffers, a device-side wait that gave up, a
  *     failed relocation check) are recorded in a device word and reported by
- *     the next dc_sync() (or dc_copy_back()) on that plan.
+ *     the next dc_sync() (or dc_copy_back()) on that plan.  The only device-
+ *     side waits are a kernel's waits for its own bulk copies; each gives up
+ *     after about a second, records DC_ETIMEOUT, waits (bounded) for the
+ *     copies still in flight and returns.  For tests, DC_WAIT_LIMIT=N in the
+ *     environment (read at every launch) lowers the first wait of every
+ *     pipeline step to N try-wait rounds (0: give up at once).
  *   - Ownership: the caller owns the host tree and must not change its shape
  *     (pointers, counts) or free it before dc_plan_destroy, nor write its
  *     arrays while a dc_deep_copy is in flight (until dc_sync, or any later
@@ -223,8 +228,11 @@ DC_API dc_status dc_bind_device(dc_plan_t plan, void* dev_buffer, uint64_t bytes
  * the relocation kernel, which rebuilds every pointer slot to the device
  * address of its target (Fig 2 step d; Algorithm 1's attach loop).  By
  * default every block is marshalled into the pinned arena (Algorithm 1: one
- * contiguous buffer) by host threads and sent by DMA chunk by chunk while the
- * marshal goes on; with DC_PLAN_MAP_HOST the interiors of large arrays are
+ * contiguous buffer) by the plan's host threads, which take work units of
+ * about 256 KiB in arena order; each 16 MiB chunk of the arena goes by DMA as
+ * soon as its last unit is marshalled, while the threads go on with the next
+ * chunks (the call returns once every chunk is queued); with DC_PLAN_MAP_HOST
+ * the interiors of large arrays are
  * read straight from the caller's pages by one kernel launch (one transfer
  * per effective-address array, as in the paper's pointerchain scheme,
  * Sec. 4.1.1 item 3) while the rest is marshalled.  Returns once the copies
@@ -232,6 +240,24 @@ DC_API dc_status dc_bind_device(dc_plan_t plan, void* dev_buffer, uint64_t bytes
  * read until the stream gets there.  Errors: DC_ESTATE (nothing bound),
  * DC_ECUDA. */
 DC_API dc_status dc_deep_copy(dc_plan_t plan, dc_stream_t stream);
+
+/* dc_deep_copy_selected — a selective deep copy (Sec. 2: only what the
+ * computation reaches is replicated; the allinit-LLused and LLinit-LLused
+ * layouts of Sec. 4.1.2 and Listing 2's chain): for `op`, the struct blocks
+ * on the way from the root to every struct the op selects (with DC_SEL_CHAIN,
+ * the blocks its chain passes through: the root struct and each child array
+ * it indexes into) and those structs' x (and y) arrays are marshalled into the
+ * pinned arena and sent to the device; then the relocation runs only over the
+ * 8 KiB ranges of the struct lane that hold those blocks' pointer slots.  No
+ * other byte of the data region is written, so the device holds a walkable
+ * copy of the chain (dc_verify_chain, dc_update_chase) and the op's arrays
+ * (dc_update_leaves, dc_copy_back); other arrays and structs are not current,
+ * and pointer slots of unselected structs in the same 8 KiB ranges are set to
+ * their targets' device addresses whatever those hold.  Every block goes
+ * through the pinned arena (DC_PLAN_MAP_HOST's mapped pages are not used);
+ * no DC_PLAN_VERIFY check.  Returns once the copies and the kernel are
+ * queued.  Errors: DC_EINVAL (op), DC_ESTATE (nothing bound), DC_ECUDA. */
+DC_API dc_status dc_deep_copy_selected(dc_plan_t plan, const dc_op* op, dc_stream_t stream);
 
 /* dc_relocate — the relocation kernel of dc_deep_copy alone (Fig 2 step d):
  * rewrite every pointer slot of the data region already in device memory to
@@ -258,8 +284,11 @@ DC_API dc_status dc_resolve_offset_in(dc_plan_t plan, uint64_t tree, const dc_st
  * kernel streams over (x, y, n) segments with no pointer loads, bringing x
  * and y into shared memory by 1-D bulk copies (with DC_LEAF_TMA=0 in the
  * environment, read at every call, by direct 16-byte loads instead; the
- * results are the same).  Errors: DC_EINVAL (op fields / path / counts),
- * DC_ESTATE, DC_ECUDA. */
+ * results are the same).  Arrays that follow each other in the arena with
+ * only block padding between them (and whose y arrays do the same) are one
+ * segment: the update then also rewrites the padding bytes between them (up
+ * to 15 per block), which belong to no block.  Errors: DC_EINVAL (op fields /
+ * path / counts), DC_ESTATE, DC_ECUDA. */
 DC_API dc_status dc_update_leaves(dc_plan_t plan, const dc_op* op, dc_stream_t stream);
 
 /* dc_relocate_update — dc_relocate and dc_update_leaves(op) in one persistent
@@ -307,10 +336,15 @@ DC_API dc_status dc_verify_chain(dc_plan_t plan, const dc_step* path, uint32_t l
 /* dc_copy_back — transfer back (Algorithm 2 step 5): the arrays the last
  * dc_update_* wrote (the x arrays of the selected structs), or every ARRAY
  * block with DC_COPY_ALL_ARRAYS, are copied device -> pinned arena -> the
- * original host arrays.  Pointers, scalars and struct bytes on the host are
- * never written.  Blocking: returns when the host arrays hold the results.
- * Errors: DC_ESTATE (no op run and no flag), DC_ECUDA, plus any device error
- * recorded by earlier kernels. */
+ * original host arrays: by DMA in chunks of about 8 MiB, each scattered into
+ * the host arrays by the plan's host threads while the later chunks are still
+ * in transfer (array interiors in pages DC_PLAN_MAP_HOST mapped go straight
+ * into those pages by one kernel launch).  Pointers, scalars and struct bytes
+ * on the host are never written.  Blocking: returns when the host arrays hold
+ * the results.  The device's error word is read before any host byte is
+ * written: if an earlier kernel recorded an error, nothing is scattered and
+ * that error is returned.  Errors: DC_ESTATE (no op run and no flag),
+ * DC_ECUDA, plus any device error recorded by earlier kernels. */
 #define DC_COPY_ALL_ARRAYS 1u
 DC_API dc_status dc_copy_back(dc_plan_t plan, uint32_t flags, dc_stream_t stream);
 
@@ -401,8 +435,10 @@ DC_API dc_status dc_partition_by_bytes(const uint64_t* bytes, uint64_t n, uint32
  * keeps the previous call's contents (the call clears what must start at
  * zero), so calls whose work overlaps on the GPU race: order them on one
  * stream.  If `dev_status` is not NULL, the device word it points to receives
- * the kernel's error bits once the work completes (0 = success, 1 = an offset
- * outside the buffers). */
+ * the kernel's error bits once the work completes: 0 = success; bit 0 (1) = an
+ * offset outside the buffers (what dc_sync reports as DC_EDEVICE_BOUNDS); bit 1
+ * (2) = a wait for the kernel's own bulk copies gave up (DC_ETIMEOUT).  Test
+ * the bits, not equality: both can be set. */
 #define DC_STATIC_MAX_BLOCKS 65536u
 #define DC_STATIC_MAX_TILES 16384u /* 8 KiB ranges of struct bytes that hold a pointer slot */
 #define DC_STATIC_SCRATCH_BYTES 1835776u /* 512 KiB records + 1 MiB lane groups + 256 KiB tile table + control words */

@@ -102,6 +102,7 @@ SIGNATURES = {
     "dc_plan_destroy": [_vp],
     "dc_bind_device": [_vp, _vp, _u64, _vp],
     "dc_deep_copy": [_vp, _vp],
+    "dc_deep_copy_selected": [_vp, _P(_Op), _vp],
     "dc_relocate": [_vp, _vp],
     "dc_relocate_static": [_vp, _vp, _u64, _vp, _vp],
     "dc_resolve_chain": [_vp, _P(_Step), _u32, _P(_u64)],
@@ -291,6 +292,11 @@ class Plan:
 
     def deep_copy(self, stream=None):
         _check(lib.dc_deep_copy(self._h, _stream(stream)))
+
+    def deep_copy_selected(self, op=None, stream=None):
+        """Selective deep copy: the struct blocks on the op's chain(s) and its arrays."""
+        o, keep = _op(op or Op())
+        _check(lib.dc_deep_copy_selected(self._h, ctypes.byref(o), _stream(stream)))
 
     def relocate(self, stream=None):
         _check(lib.dc_relocate(self._h, _stream(stream)))

@@ -26,6 +26,12 @@ dc_status fail(dc_status s, const char* fmt, ...);
 // debug.cpp: DC_DEBUG=1 (every plan verifies) and DC_FAULT_HOST_ALLOC=1 (pinned allocations fail)
 bool debug_on();
 cudaError_t host_alloc(void** ptr, size_t bytes, unsigned int flags);
+
+// try_wait rounds before an mbarrier wait gives up (well over a second)
+constexpr uint32_t WAIT_LIMIT = 1u << 22;
+// The limit of the first wait of every pipeline step of the bulk-copy kernels:
+// WAIT_LIMIT unless DC_WAIT_LIMIT (decimal, read at every launch) lowers it.
+uint32_t first_wait_limit();
 dc_status cuda_fail(cudaError_t e, const char* what);
 const char* last_error();
 #define DC_CUDA(call)                                        \
@@ -119,6 +125,7 @@ struct RelocArgs {
   uint32_t* ctrl;
   uint32_t nrec, nseg, ntiles, verify;
   uint32_t scan;  // records hold sizes (DC_PLAN_DEVICE_SCAN), not offsets
+  uint32_t wait_limit = WAIT_LIMIT;  // try_wait rounds of a tile's first wait (0: give up at once)
 };
 
 constexpr uint32_t LEAF_THREADS = 256;
@@ -134,6 +141,7 @@ struct LeafArgs {
   int f64;         // element type: 0 f32, 1 f64
   double scale;
   uint32_t* ctrl;  // the plan's control words (error bits)
+  uint32_t wait_limit = WAIT_LIMIT;  // try_wait rounds of a sub-tile's first wait (0: give up at once)
 };
 
 // One block to move between host and device memory: src and dst are device-
@@ -227,7 +235,7 @@ dc_status copy_schema(const dc_schema* s, SchemaCopy* out);
 
 // Layout of the caller's device buffer (byte offsets).
 struct DevLayout {
-  uint64_t data = 0, rec = 0, hostp = 0, soff = 0, status = 0, rtile = 0, ctrl = 0;
+  uint64_t data = 0, rec = 0, hostp = 0, soff = 0, status = 0, rtile = 0, seltile = 0, ctrl = 0;
   uint64_t seg = 0, tseg = 0, cseg = 0, steps = 0, walk = 0, total = 0;
   uint64_t mva = 0, mvat = 0, mvb = 0, mvbt = 0, bk = 0, bkt = 0;  // move tables + their tile tables
   uint64_t sta = 0, stat = 0, stb = 0, stbt = 0, sts = 0, stst = 0;  // fused-step tables
@@ -310,6 +318,13 @@ struct dc_plan_s {
   uint64_t back_key = ~0ull;          // generation of the block list `back` was built for (0 = all arrays)
   Moves back;
   uint64_t bk_nd = 0, bk_units = 0;
+  Moves sel;                          // the last selective deep copy's blocks
+  dc::OpKey sel_key;
+  std::vector<dc::RelocTile> sel_tiles;  // relocation tiles holding its struct blocks' slots
+  // the copy back's events: the error word's read, then one per DMA chunk of `back`
+  cudaEvent_t back_err = nullptr;
+  std::vector<cudaEvent_t> back_ev;
+  cudaEvent_t sync_ev = nullptr;      // sync_stream's marker
   // the fused round trip (step.cpp), cached per op
   dc::OpKey step_key;
   bool step_fused = false;
@@ -355,7 +370,13 @@ uint64_t interior_bytes(const HostBlock& b);
 // host_order: hand out the host copies in host-address order (sequential on the
 // caller's side); such Moves have no DMA chunks.  Otherwise they follow the
 // arena, chunk by chunk.
-void plan_moves(const dc_plan_s* p, const std::vector<uint32_t>& list, dc_plan_s::Moves* m, bool host_order = true);
+// Split a block list's staged bytes into pieces, host work units and (unless
+// host_order) DMA chunks of about chunk_bytes (0: the deep copy's chunk size).
+void plan_moves(const dc_plan_s* p, const std::vector<uint32_t>& list, dc_plan_s::Moves* m, bool host_order = true,
+                uint64_t chunk_bytes = 0, bool stage_all = false);
+// Marshal a chunked move list (plan_moves with host_order false) into the
+// pinned arena and queue each chunk's DMA to the device as it completes.
+dc_status send_staged(dc_plan_s* p, const dc_plan_s::Moves& m, cudaStream_t s);
 void plan_transfers(dc_plan_s* p);
 void release_transfers(dc_plan_s* p);
 dc_status upload_h2d_tables(dc_plan_s* p, cudaStream_t s);
@@ -370,9 +391,14 @@ void host_copy(dc_plan_s* p, const dc_plan_s::Moves& m, uint64_t ufirst, uint64_
 void null_slots_upto(dc_plan_s* p, size_t* ns, uint64_t hi);
 // runtime.cpp
 dc_status device_error(dc_plan_s* p, cudaStream_t s);
+// The pinned host word that device_error reads the device's error word into.
+uint32_t* pinned_error_word(dc_plan_s* p);
 Pool& pool_of(dc_plan_s* p);
 OpKey key_of(const dc_op* op);
 dc_status wait_event(cudaEvent_t e);
+// Wait until the plan's work queued on `s` so far has completed (an event
+// recorded on `s`, waited for as wait_event does).
+dc_status sync_stream(dc_plan_s* p, cudaStream_t s);
 // x (and y) target blocks of the structs an op selects; structs whose x is empty are skipped
 struct Pick {
   uint32_t sblk;
@@ -387,6 +413,10 @@ RelocArgs reloc_args(const dc_plan_s* p);
 // memory lent by the caller (the request server's pool; mapped).
 uint64_t pinned_need(const dc_plan_s* p);
 dc_status bind_borrowed(dc_plan_s* p, void* dev, uint64_t bytes, uint8_t* pinned, uint8_t* pinned_dev, cudaStream_t s);
+// Give a plan bound with borrowed pinned memory another pinned range of the
+// same size (pinned_need) for its next calls; the caller makes sure nothing
+// of the plan's earlier calls is in flight.  Not for DC_PLAN_MAP_HOST plans.
+dc_status lend_pinned(dc_plan_s* p, uint8_t* pinned, uint8_t* pinned_dev);
 // The chain of (field, index) steps from the root to struct (block, elem).
 void path_to(const dc_plan_s* p, uint32_t block, uint64_t elem, std::vector<dc_step>* out);
 }  // namespace dc

@@ -1,6 +1,15 @@
 // pool.hpp — a small fixed thread pool for the host-side marshal and scatter.
 // parallel_for(n, fn) runs fn(i) for i in [0, n) on the workers and the
-// calling thread, and returns when every item is done.
+// calling thread, and returns when every item is done.  One job runs at a
+// time (callers on several threads take turns); a job whose items wait (the
+// copy back's, for its chunks' transfers) holds the pool meanwhile, so such
+// waits are kept short: the transfer runs ahead of the copying.
+//
+// Waking sleeping threads costs tens of microseconds on a virtual machine, so
+// workers spin for a short while (SPIN rounds of a pause instruction) after a
+// job before they sleep, and the caller spins the same way for the workers to
+// finish: back-to-back jobs (a transfer's chunks) then start within a few
+// microseconds.  Jobs of one or two items run on the calling thread alone.
 #pragma once
 
 #include <atomic>
@@ -11,10 +20,24 @@
 #include <thread>
 #include <vector>
 
+#if defined(DC_POOL_YIELD) && DC_POOL_YIELD
+#define DC_POOL_PAUSE() std::this_thread::yield()
+#elif defined(__x86_64__) || defined(__i386__)
+#include <immintrin.h>
+#define DC_POOL_PAUSE() _mm_pause()
+#else
+#define DC_POOL_PAUSE() std::this_thread::yield()
+#endif
+
 namespace dc {
 
 class Pool {
  public:
+#ifndef DC_POOL_SPIN
+#define DC_POOL_SPIN 4096
+#endif
+  static constexpr unsigned SPIN = DC_POOL_SPIN;  // pause rounds before sleeping (tens of microseconds)
+
   explicit Pool(unsigned nthreads) {
     if (nthreads == 0) nthreads = 1;
     for (unsigned i = 1; i < nthreads; i++) workers_.emplace_back([this] { loop(); });
@@ -23,7 +46,7 @@ class Pool {
     {
       std::lock_guard<std::mutex> g(m_);
       stop_ = true;
-      gen_++;
+      gen_.fetch_add(1, std::memory_order_release);
     }
     cv_.notify_all();
     for (auto& t : workers_) t.join();
@@ -32,30 +55,33 @@ class Pool {
 
   void parallel_for(uint64_t n, const std::function<void(uint64_t)>& fn) {
     if (n == 0) return;
-    if (workers_.empty() || n == 1) {
+    if (workers_.empty() || n <= 2) {
       for (uint64_t i = 0; i < n; i++) fn(i);
       return;
     }
     std::lock_guard<std::mutex> one_job(job_);  // callers on several threads take turns
+    fn_ = &fn;
+    n_ = n;
+    next_.store(0, std::memory_order_relaxed);
+    active_.store((unsigned)workers_.size(), std::memory_order_relaxed);
+    gen_.fetch_add(1, std::memory_order_release);  // publishes the job to spinning workers
     {
-      std::lock_guard<std::mutex> g(m_);
-      fn_ = &fn;
-      n_ = n;
-      next_.store(0);
-      active_ = (unsigned)workers_.size();
-      gen_++;
+      std::lock_guard<std::mutex> g(m_);  // a worker between its check and its sleep holds m_
     }
     cv_.notify_all();
     drain();
-    std::unique_lock<std::mutex> lk(m_);
-    done_cv_.wait(lk, [this] { return active_ == 0; });
+    for (unsigned k = 0; k < SPIN && active_.load(std::memory_order_acquire); k++) DC_POOL_PAUSE();
+    if (active_.load(std::memory_order_acquire)) {
+      std::unique_lock<std::mutex> lk(m_);
+      done_cv_.wait(lk, [this] { return active_.load(std::memory_order_acquire) == 0; });
+    }
     fn_ = nullptr;
   }
 
  private:
   void drain() {
     for (;;) {
-      uint64_t i = next_.fetch_add(1);
+      const uint64_t i = next_.fetch_add(1, std::memory_order_relaxed);
       if (i >= n_) break;
       (*fn_)(i);
     }
@@ -63,16 +89,17 @@ class Pool {
   void loop() {
     uint64_t seen = 0;
     for (;;) {
-      {
+      for (unsigned k = 0; k < SPIN && gen_.load(std::memory_order_acquire) == seen; k++) DC_POOL_PAUSE();
+      if (gen_.load(std::memory_order_acquire) == seen) {
         std::unique_lock<std::mutex> lk(m_);
-        cv_.wait(lk, [&] { return gen_ != seen; });
-        seen = gen_;
-        if (stop_) return;
+        cv_.wait(lk, [&] { return gen_.load(std::memory_order_acquire) != seen; });
       }
+      seen = gen_.load(std::memory_order_acquire);
+      if (stop_) return;
       drain();
-      {
-        std::lock_guard<std::mutex> g(m_);
-        if (--active_ == 0) done_cv_.notify_all();
+      if (active_.fetch_sub(1, std::memory_order_acq_rel) == 1) {
+        { std::lock_guard<std::mutex> g(m_); }
+        done_cv_.notify_all();
       }
     }
   }
@@ -84,8 +111,8 @@ class Pool {
   const std::function<void(uint64_t)>* fn_ = nullptr;
   uint64_t n_ = 0;
   std::atomic<uint64_t> next_{0};
-  unsigned active_ = 0;
-  uint64_t gen_ = 0;
+  std::atomic<unsigned> active_{0};
+  std::atomic<uint64_t> gen_{0};
   bool stop_ = false;
 };
 

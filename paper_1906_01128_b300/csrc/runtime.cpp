@@ -38,6 +38,8 @@ DevLayout make_layout(const dc_plan_s* p) {
   o = align256(o + p->rseg.size() * sizeof(RelocSeg));
   L.rtile = o;  // per tile: its records and groups
   o = align256(o + std::max<uint64_t>(1, p->rtiles.size()) * sizeof(RelocTile));
+  L.seltile = o;  // the tiles a selective deep copy relocates (a subset of the above)
+  o = align256(o + std::max<uint64_t>(1, p->rtiles.size()) * sizeof(RelocTile));
   L.ctrl = o;
   o = align256(o + CTRL_WORDS * 4);
   L.seg_cap = std::max<uint64_t>(1, p->nstructs);
@@ -102,14 +104,17 @@ Pool& dc::pool_of(dc_plan_s* p) {
   return *p->pool;
 }
 
+uint32_t* dc::pinned_error_word(dc_plan_s* p) { return reinterpret_cast<uint32_t*>(p->pin_tab + tab_words(p->L)); }
+
 dc_status dc::device_error(dc_plan_s* p, cudaStream_t s) {
-  uint32_t* word = reinterpret_cast<uint32_t*>(p->pin_tab + tab_words(p->L));
+  uint32_t* word = pinned_error_word(p);
   DC_CUDA(cudaMemcpyAsync(word, p->dev + p->L.ctrl + CTRL_ERR * 4, 4, cudaMemcpyDeviceToHost, s));
-  DC_CUDA(cudaStreamSynchronize(s));
+  dc_status st = sync_stream(p, s);
+  if (st) return st;
   uint32_t e = *word;
   if (!e) return DC_OK;
   DC_CUDA(cudaMemsetAsync(p->dev + p->L.ctrl + CTRL_ERR * 4, 0, 4, s));
-  DC_CUDA(cudaStreamSynchronize(s));
+  if ((st = sync_stream(p, s))) return st;
   if (e & ERR_BOUNDS) return fail(DC_EDEVICE_BOUNDS, "a kernel found an offset outside its buffers (0x%x)", e);
   if (e & ERR_TIMEOUT) return fail(DC_ETIMEOUT, "a device-side wait gave up (0x%x)", e);
   return fail(DC_EVERIFY, "relocation check: a pointer slot did not hold the recorded host address");
@@ -173,9 +178,32 @@ uint32_t chain_steps(const dc_plan_s* p, uint32_t sblk, uint64_t elem, std::vect
 
 }  // namespace
 
+// Host waits for the GPU.  cudaEventSynchronize spins a core while it waits;
+// the library's host threads (a server's slots, the pool) then keep cores from
+// the threads that marshal and scatter.  With DC_YIELD_WAITS (the default) a
+// waiting thread polls the event and yields the core between polls.
+#ifndef DC_YIELD_WAITS
+#define DC_YIELD_WAITS 1
+#endif
 dc_status dc::wait_event(cudaEvent_t e) {
-  if (e) DC_CUDA(cudaEventSynchronize(e));
+  if (!e) return DC_OK;
+#if DC_YIELD_WAITS
+  for (;;) {
+    const cudaError_t r = cudaEventQuery(e);
+    if (r == cudaSuccess) return DC_OK;
+    if (r != cudaErrorNotReady) return cuda_fail(r, "cudaEventQuery");
+    std::this_thread::yield();
+  }
+#else
+  DC_CUDA(cudaEventSynchronize(e));
   return DC_OK;
+#endif
+}
+
+dc_status dc::sync_stream(dc_plan_s* p, cudaStream_t s) {
+  if (!p->sync_ev) DC_CUDA(cudaEventCreateWithFlags(&p->sync_ev, cudaEventDisableTiming));
+  DC_CUDA(cudaEventRecord(p->sync_ev, s));
+  return wait_event(p->sync_ev);
 }
 
 namespace {
@@ -324,6 +352,9 @@ dc_status dc_plan_destroy(dc_plan_t p) {
     cudaEventSynchronize(e);
     cudaEventDestroy(e);
   }
+  if (p->back_err) cudaEventDestroy(p->back_err);
+  if (p->sync_ev) cudaEventDestroy(p->sync_ev);
+  for (cudaEvent_t e : p->back_ev) cudaEventDestroy(e);
   delete p;
   return DC_OK;
 }
@@ -417,6 +448,16 @@ dc_status dc::bind_borrowed(dc_plan_s* p, void* dev, uint64_t bytes, uint8_t* pi
   return dc_bind_device(p, dev, bytes, s);
 }
 
+dc_status dc::lend_pinned(dc_plan_s* p, uint8_t* pinned, uint8_t* pinned_dev) {
+  if (!p->borrowed_pinned) return fail(DC_ESTATE, "the plan owns its pinned arena");
+  if (p->flags & DC_PLAN_MAP_HOST) return fail(DC_ESTATE, "mapped plans keep the pinned range they were bound with");
+  p->pinned = pinned;
+  p->pinned_dev = pinned_dev;
+  p->pin_tab = pinned + round_up(p->data_bytes, 256);
+  p->step_key = OpKey();  // the round trip's device tables hold pinned addresses: rebuild them
+  return DC_OK;
+}
+
 extern "C" {
 
 dc_status dc_device_base(dc_plan_t p, uint64_t* base) {
@@ -447,6 +488,62 @@ dc_status dc_deep_copy(dc_plan_t p, dc_stream_t stream) {
   if ((st = transfer_to_device(p, s))) return st;
   DC_CUDA(cudaEventRecord(p->h2d_done, s));
   return dc_relocate(p, stream);
+}
+
+// A selective deep copy (Sec. 2): the struct blocks on the way to every struct
+// the op selects (for SEL_CHAIN: the blocks its chain passes through) and the
+// op's x and y arrays of those structs go through the pinned arena to the
+// device; then only the relocation tiles that hold those struct blocks' slots
+// run.  Nothing else of the data region is written.
+dc_status dc_deep_copy_selected(dc_plan_t p, const dc_op* op, dc_stream_t stream) {
+  if (!p) return fail(DC_EINVAL, "plan is NULL");
+  dc_status st = check_op(p, op);
+  if (st) return st;
+  if (!p->dev) return fail(DC_ESTATE, "no device buffer bound");
+  cudaStream_t s = stream;
+  OpKey key = key_of(op);
+  if (!(key == p->sel_key)) {
+    std::vector<std::pair<uint32_t, uint64_t>> structs;
+    if ((st = select_structs(p, op, &structs))) return st;
+    std::vector<Pick> picks;
+    if ((st = pick(p, op, &picks))) return st;
+    const uint64_t nb = p->blocks.size();
+    std::vector<uint8_t> mark(nb, 0);
+    for (const auto& se : structs)  // the struct block and every struct block above it
+      for (uint32_t b = se.first; b != NONE && !mark[b]; b = p->blocks[b].parent) mark[b] = 1;
+    for (const auto& k : picks) {
+      mark[k.bx] = 1;
+      if (k.by != NONE) mark[k.by] = 1;
+    }
+    std::vector<uint32_t> list;
+    for (uint32_t b = 0; b < nb; b++)
+      if (mark[b]) list.push_back(b);
+    plan_moves(p, list, &p->sel, false, 0, true);  // every selected byte through the pinned arena
+    // the listed relocation tiles (ascending t) that overlap a selected struct block
+    p->sel_tiles.clear();
+    for (uint32_t b : list) {
+      const HostBlock& B = p->blocks[b];
+      if (B.lane != 0 || !B.bytes) continue;
+      const uint64_t t0 = B.off / RELOC_SPAN, t1 = (B.off + B.bytes - 1) / RELOC_SPAN;
+      auto it = std::lower_bound(p->rtiles.begin(), p->rtiles.end(), t0,
+                                 [](const RelocTile& a, uint64_t t) { return a.t < t; });
+      for (; it != p->rtiles.end() && it->t <= t1; ++it)
+        if (p->sel_tiles.empty() || p->sel_tiles.back().t < it->t) p->sel_tiles.push_back(*it);
+    }
+    if (!p->sel_tiles.empty())
+      DC_CUDA(cudaMemcpyAsync(p->dev + p->L.seltile, p->sel_tiles.data(), p->sel_tiles.size() * sizeof(RelocTile),
+                              cudaMemcpyHostToDevice, s));
+    p->sel_key = key;
+  }
+  if ((st = wait_event(p->h2d_done))) return st;  // an earlier transfer may still read the pinned arena
+  if ((st = send_staged(p, p->sel, s))) return st;
+  DC_CUDA(cudaEventRecord(p->h2d_done, s));
+  RelocArgs a = reloc_args(p);
+  a.tiles = reinterpret_cast<const RelocTile*>(p->dev + p->L.seltile);
+  a.ntiles = (uint32_t)p->sel_tiles.size();
+  a.verify = 0;  // the tiles' other structs were not copied: their slots hold no host address
+  DC_CUDA(launch_relocate(a, s, p->sm_count));
+  return DC_OK;
 }
 
 dc_status dc_resolve_offset(dc_plan_t p, const dc_step* path, uint32_t len, uint64_t* offset) {

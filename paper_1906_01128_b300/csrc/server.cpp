@@ -5,8 +5,12 @@
 // threads, each with its own CUDA stream, take requests as they arrive and as
 // slots and memory free up (continuous batching: the work of requests on
 // different slots overlaps on the device).  A served tree stays resident (its
-// plan, arena and pinned staging) until memory is needed, then the least
-// recently used idle tree is evicted.  Requests on one key keep their order.
+// plan and its device arena) until device memory is needed, then the least
+// recently used idle tree is evicted.  Pinned staging is held only while a
+// request runs: a request borrows it from the pinned pool for its transfers and
+// returns it when it completes, so resident trees never hold host memory and
+// the device budget alone decides what stays.  Requests on one key keep their
+// order.
 // A re-touch of a resident tree skips the deep copy: the copy back leaves the
 // host and device copies identical, so only the update and the copy back run.
 // With DC_SERVER_SEQUENTIAL the same requests are handled one at a time in
@@ -16,6 +20,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <list>
 #include <map>
 #include <mutex>
 #include <string>
@@ -30,51 +35,80 @@ using clk = std::chrono::steady_clock;
 
 namespace {
 
-// First-fit allocator over [0, cap) in 256-byte units.
+// Best-fit allocator over [0, cap) in 256-byte units: free ranges by offset
+// (for merging neighbours) and by size (for the smallest range that fits).
 class RangeAlloc {
  public:
+  static uint64_t extent(uint64_t bytes) { return round_up(std::max<uint64_t>(bytes, 1), 256); }
   void reset(uint64_t cap) {
     free_.clear();
-    if (cap) free_[0] = cap;
+    by_size_.clear();
+    if (cap) add(0, cap);
   }
   bool alloc(uint64_t bytes, uint64_t* off) {
-    bytes = round_up(std::max<uint64_t>(bytes, 1), 256);
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second < bytes) continue;
-      *off = it->first;
-      const uint64_t rest = it->second - bytes, at = it->first + bytes;
-      free_.erase(it);
-      if (rest) free_[at] = rest;
-      return true;
-    }
-    return false;
+    bytes = extent(bytes);
+    auto it = by_size_.lower_bound(bytes);
+    if (it == by_size_.end()) return false;
+    const uint64_t at = it->second, len = it->first;
+    remove(at, len);
+    if (len > bytes) add(at + bytes, len - bytes);
+    *off = at;
+    return true;
   }
   void release(uint64_t off, uint64_t bytes) {
-    bytes = round_up(std::max<uint64_t>(bytes, 1), 256);
-    auto it = free_.emplace(off, bytes).first;
-    auto nx = std::next(it);
-    if (nx != free_.end() && it->first + it->second == nx->first) {
-      it->second += nx->second;
-      free_.erase(nx);
+    uint64_t lo = off, hi = off + extent(bytes);
+    auto nx = free_.lower_bound(hi);
+    if (nx != free_.end() && nx->first == hi) {
+      hi += nx->second;
+      remove(nx->first, nx->second);
     }
-    if (it != free_.begin()) {
-      auto pv = std::prev(it);
-      if (pv->first + pv->second == it->first) {
-        pv->second += it->second;
-        free_.erase(it);
+    auto pv = free_.lower_bound(lo);
+    if (pv != free_.begin()) {
+      --pv;
+      if (pv->first + pv->second == lo) {
+        lo = pv->first;
+        remove(pv->first, pv->second);
       }
     }
+    add(lo, hi - lo);
+  }
+  // the free range that starts at `at`, or ends at `at` (0 if none)
+  uint64_t free_from(uint64_t at) const {
+    auto it = free_.find(at);
+    return it == free_.end() ? 0 : it->second;
+  }
+  uint64_t free_until(uint64_t at) const {
+    auto it = free_.lower_bound(at);
+    if (it == free_.begin()) return 0;
+    --it;
+    return it->first + it->second == at ? it->second : 0;
   }
 
  private:
-  std::map<uint64_t, uint64_t> free_;
+  void add(uint64_t at, uint64_t len) {
+    free_[at] = len;
+    by_size_.emplace(len, at);
+  }
+  void remove(uint64_t at, uint64_t len) {
+    free_.erase(at);
+    auto r = by_size_.equal_range(len);
+    for (auto it = r.first; it != r.second; ++it)
+      if (it->second == at) {
+        by_size_.erase(it);
+        break;
+      }
+  }
+  std::map<uint64_t, uint64_t> free_;          // offset -> length
+  std::multimap<uint64_t, uint64_t> by_size_;  // length -> offset
 };
 
 struct Resident {
   dc_plan_s* plan = nullptr;
-  uint64_t dev_off = 0, dev_len = 0, pin_off = 0, pin_len = 0;
+  uint64_t dev_off = 0, dev_len = 0;
   uint64_t last_use = 0;
   bool busy = false;
+  bool idle_listed = false;
+  std::list<uint64_t>::iterator idle_it;  // its place in the idle list (when idle_listed)
 };
 
 }  // namespace
@@ -92,7 +126,10 @@ struct dc_server_s {
   uint32_t nslots = 1, flags = 0;
   std::vector<cudaStream_t> streams;
   std::unordered_map<uint64_t, Resident> cache;
+  std::list<uint64_t> idle;               // resident idle keys, least recently used first
+  std::map<uint64_t, uint64_t> by_addr;   // device offset -> key, every resident
   uint64_t tick = 0, resident_bytes = 0;
+  uint32_t pin_holders = 0;  // requests holding pinned staging
   std::mutex m;
   std::condition_variable cv;
   dc_server_stats stats{};
@@ -102,36 +139,91 @@ struct dc_server_s {
 
 namespace {
 
-// Free memory for `dev_len` + `pin_len` bytes by evicting idle residents, least
-// recently used first.  Called with the lock held.
-bool make_room(dc_server_s* S, uint64_t dev_len, uint64_t pin_len, uint64_t* doff, uint64_t* poff) {
-  for (;;) {
-    uint64_t d, q;
-    if (S->dalloc.alloc(dev_len, &d)) {
-      if (S->palloc.alloc(pin_len, &q)) {
-        *doff = d;
-        *poff = q;
-        return true;
-      }
-      S->dalloc.release(d, dev_len);
-    }
-    uint64_t victim = 0, oldest = ~0ull;
-    bool found = false;
-    for (auto& kv : S->cache)
-      if (!kv.second.busy && kv.second.plan && kv.second.last_use < oldest) {
-        oldest = kv.second.last_use;
-        victim = kv.first;
-        found = true;
-      }
-    if (!found) return false;
-    Resident& r = S->cache[victim];
-    dc_plan_destroy(r.plan);
-    S->dalloc.release(r.dev_off, r.dev_len);
-    S->palloc.release(r.pin_off, r.pin_len);
-    S->resident_bytes -= r.dev_len;
-    S->cache.erase(victim);
-    S->stats.evictions++;
+void unlist_idle(dc_server_s* S, Resident& r) {
+  if (r.idle_listed) {
+    S->idle.erase(r.idle_it);
+    r.idle_listed = false;
   }
+}
+
+void list_idle(dc_server_s* S, uint64_t key, Resident& r) {
+  unlist_idle(S, r);
+  r.idle_it = S->idle.insert(S->idle.end(), key);
+  r.idle_listed = true;
+}
+
+// Drop a resident: its device range back to the pool, its plan to `victims`.
+void evict(dc_server_s* S, uint64_t key, std::vector<dc_plan_s*>* victims) {
+  Resident& r = S->cache[key];
+  unlist_idle(S, r);
+  victims->push_back(r.plan);
+  S->dalloc.release(r.dev_off, r.dev_len);
+  S->by_addr.erase(r.dev_off);
+  S->resident_bytes -= r.dev_len;
+  S->cache.erase(key);
+  S->stats.evictions++;
+}
+
+// Device memory for `dev_len` bytes.  If no free range fits, the hole is made
+// around an idle resident, least recently used first: the window grows over
+// the free ranges and idle residents next to it (in address order) until it
+// holds dev_len bytes, and exactly the residents inside it are evicted; a seed
+// whose window is closed off by busy residents before that is passed over.
+// The evicted plans go to `victims`, to be destroyed once the lock is released
+// (nothing of theirs is in flight: an idle resident's requests have completed).
+// Called with the lock held.
+bool make_room(dc_server_s* S, uint64_t dev_len, uint64_t* doff, std::vector<dc_plan_s*>* victims) {
+  if (S->dalloc.alloc(dev_len, doff)) return true;
+  const uint64_t need = RangeAlloc::extent(dev_len);
+  auto idle_at = [&](uint64_t off, uint64_t* key, uint64_t* len) {
+    auto it = S->by_addr.find(off);
+    if (it == S->by_addr.end()) return false;
+    const Resident& r = S->cache[it->second];
+    if (r.busy) return false;
+    *key = it->second;
+    *len = RangeAlloc::extent(r.dev_len);
+    return true;
+  };
+  for (uint64_t seed : S->idle) {
+    const Resident& r = S->cache[seed];
+    uint64_t lo = r.dev_off, hi = lo + RangeAlloc::extent(r.dev_len);
+    std::vector<uint64_t> take{seed};
+    bool open_hi = true, open_lo = true;
+    while (hi - lo < need && (open_hi || open_lo)) {
+      if (open_hi) {  // grow up: a free range, else an idle resident, starting at hi
+        uint64_t k, len = S->dalloc.free_from(hi);
+        if (len) {
+          hi += len;
+        } else if (hi < S->dev_bytes && idle_at(hi, &k, &len)) {
+          take.push_back(k);
+          hi += len;
+        } else {
+          open_hi = false;
+        }
+        continue;
+      }
+      uint64_t len = S->dalloc.free_until(lo);  // grow down: a free range, else an idle resident, ending at lo
+      if (len) {
+        lo -= len;
+        continue;
+      }
+      auto it = S->by_addr.lower_bound(lo);
+      if (it != S->by_addr.begin()) {
+        --it;
+        uint64_t k;
+        if (idle_at(it->first, &k, &len) && it->first + len == lo) {
+          take.push_back(k);
+          lo = it->first;
+          continue;
+        }
+      }
+      open_lo = false;
+    }
+    if (hi - lo < need) continue;
+    for (uint64_t k : take) evict(S, k, victims);
+    return S->dalloc.alloc(dev_len, doff);
+  }
+  return false;
 }
 
 void note_error(dc_server_s* S, dc_status st) {
@@ -229,18 +321,21 @@ dc_status dc_server_run(dc_server_t S, const dc_request* reqs, uint64_t n, const
       Resident& r = S->cache[rq.key];
       const bool resident = r.plan != nullptr;
       r.busy = true;
+      unlist_idle(S, r);  // a busy resident is never evicted
+      dc_plan_s* p = r.plan;  // read under the lock: other slots may grow the map
+      uint64_t dev_off = r.dev_off, dev_len = r.dev_len;
       lk.unlock();
       dc_status st = DC_OK;
-      bool admitted = resident;
-      if (!resident) {  // plan outside the lock, then admit by memory
-        dc_plan_s* p = nullptr;
+      std::vector<dc_plan_s*> victims;
+      if (!resident) {  // plan outside the lock, then admit by device memory
         st = dc_plan(&S->schema, rq.host_root, &p);
         if (!st) {
-          const uint64_t dl = p->L.total, pl = pinned_need(p);
+          const uint64_t dl = p->L.total;
+          uint64_t doff = 0;
+          bool admitted = false;
           lk.lock();
-          uint64_t doff = 0, poff = 0;
           for (;;) {
-            if (make_room(S, dl, pl, &doff, &poff)) {
+            if (make_room(S, dl, &doff, &victims)) {
               admitted = true;
               break;
             }
@@ -250,31 +345,55 @@ dc_status dc_server_run(dc_server_t S, const dc_request* reqs, uint64_t n, const
             if (!others_busy) break;  // nothing held elsewhere will be freed: larger than the budget
             S->cv.wait(lk);          // wait for another slot to finish
           }
-          Resident& rr = S->cache[rq.key];
           if (admitted) {
+            Resident& rr = S->cache[rq.key];
             rr.plan = p;
-            rr.dev_off = doff;
-            rr.dev_len = dl;
-            rr.pin_off = poff;
-            rr.pin_len = pl;
+            rr.dev_off = dev_off = doff;
+            rr.dev_len = dev_len = dl;
+            S->by_addr[doff] = rq.key;
             S->resident_bytes += dl;
             S->stats.peak_resident_bytes = std::max(S->stats.peak_resident_bytes, S->resident_bytes);
           }
           lk.unlock();
-          if (admitted) {
-            st = bind_borrowed(p, S->dev + doff, dl, S->pin + poff, S->pin_dev + poff, cs);
-          } else {
+          if (!admitted) {
             dc_plan_destroy(p);
+            p = nullptr;
             st = fail(DC_EBUDGET, "request %llu needs %llu device bytes: more than the budget",
                       (unsigned long long)pick, (unsigned long long)dl);
           }
         }
       }
-      lk.lock();
-      Resident& rr = S->cache[rq.key];
-      dc_plan_s* p = rr.plan;
-      lk.unlock();
+      for (dc_plan_s* v : victims) dc_plan_destroy(v);
+      // pinned staging for this request's transfers, returned when it completes
+      uint64_t poff = 0, plen = 0;
+      if (!st && p) {
+        const uint64_t need = pinned_need(p);
+        bool got = false;
+        lk.lock();
+        for (;;) {
+          if (S->palloc.alloc(need, &poff)) {
+            got = true;
+            S->pin_holders++;
+            break;
+          }
+          if (!S->pin_holders) break;  // nothing will be returned: larger than the pinned pool
+          S->cv.wait(lk);              // another request returns its staging when it completes
+        }
+        lk.unlock();
+        if (got)
+          plen = need;
+        else
+          st = fail(DC_EBUDGET, "request %llu needs %llu bytes of pinned staging: more than the pool",
+                    (unsigned long long)pick, (unsigned long long)need);
+      }
       uint64_t h2d = 0, d2h = 0;
+      if (!st && p) {
+        if (!resident) {
+          st = bind_borrowed(p, S->dev + dev_off, dev_len, S->pin + poff, S->pin_dev + poff, cs);
+        } else {
+          st = lend_pinned(p, S->pin + poff, S->pin_dev + poff);
+        }
+      }
       if (!st && p) {
         if (resident && rq.retouch) {  // the device copy equals the host tree: update and copy back only
           st = dc_update_leaves(p, op, cs);
@@ -288,6 +407,10 @@ dc_status dc_server_run(dc_server_t S, const dc_request* reqs, uint64_t n, const
       }
       const double lat = std::chrono::duration<double, std::milli>(clk::now() - at(pick)).count();
       lk.lock();
+      if (plen) {  // the request's transfers are complete
+        S->palloc.release(poff, plen);
+        S->pin_holders--;
+      }
       if (latency_ms) latency_ms[pick] = st ? -1.0 : lat;
       if (st) {
         note_error(S, st);
@@ -300,16 +423,25 @@ dc_status dc_server_run(dc_server_t S, const dc_request* reqs, uint64_t n, const
       Resident& done = S->cache[rq.key];
       done.busy = false;
       done.last_use = ++S->tick;
+      dc_plan_s* drop = nullptr;
       if ((st || (S->flags & DC_SERVER_SEQUENTIAL)) && done.plan) {  // nothing kept resident
-        dc_plan_destroy(done.plan);
+        drop = done.plan;
         S->dalloc.release(done.dev_off, done.dev_len);
-        S->palloc.release(done.pin_off, done.pin_len);
+        S->by_addr.erase(done.dev_off);
         S->resident_bytes -= done.dev_len;
         done.plan = nullptr;
       }
-      if (!done.plan) S->cache.erase(rq.key);
+      if (done.plan)
+        list_idle(S, rq.key, done);
+      else
+        S->cache.erase(rq.key);
       finished++;
       S->cv.notify_all();
+      if (drop) {
+        lk.unlock();
+        dc_plan_destroy(drop);
+        lk.lock();
+      }
     }
   };
 

@@ -161,6 +161,7 @@ dc_status run_step_groups(dc_plan_s* p, const dc_op* op, cudaStream_t s) {
   a.f64 = p->schema.fields[op->type][op->x_field].elem_kind == DC_E_F64;
   a.scale = op->scale;
   const uint64_t ng = p->step_in.size();
+  dc_status st0;
   for (uint64_t g = 0; g < ng; g++) {
     {
       Trace tr("dc_roundtrip", "marshal");
@@ -172,7 +173,7 @@ dc_status run_step_groups(dc_plan_s* p, const dc_op* op, cudaStream_t s) {
     DC_CUDA(cudaEventRecord(p->step_ev[g], s));
     if (g) {
       Trace tr("dc_roundtrip", "scatter");
-      DC_CUDA(cudaEventSynchronize(p->step_ev[g - 1]));
+      if ((st0 = wait_event(p->step_ev[g - 1]))) return st0;
       host_copy(p, p->step_out[g - 1], 0, p->step_out[g - 1].units.size(), false);
     }
   }

@@ -19,7 +19,9 @@
 #include <immintrin.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
+#include <memory>
 
 #include "internal.hpp"
 
@@ -27,10 +29,24 @@ namespace dc {
 
 namespace {
 
-constexpr uint64_t PIECE_BYTES = 2ull << 20;  // largest memcpy one host thread does at once
-constexpr uint64_t UNIT_BYTES = 1ull << 20;   // host work handed out at once
+// The host side's granularity (overridable when building, for measurements).
+#ifndef DC_PIECE_BYTES
+#define DC_PIECE_BYTES (512ull << 10)
+#endif
+#ifndef DC_UNIT_BYTES
+#define DC_UNIT_BYTES (256ull << 10)
+#endif
+#ifndef DC_CHUNK_BYTES
+#define DC_CHUNK_BYTES (16ull << 20)
+#endif
+#ifndef DC_BACK_CHUNK_BYTES
+#define DC_BACK_CHUNK_BYTES (8ull << 20)
+#endif
+constexpr uint64_t PIECE_BYTES = DC_PIECE_BYTES;  // largest memcpy one host thread does at once
+constexpr uint64_t UNIT_BYTES = DC_UNIT_BYTES;    // host work handed out at once
 constexpr uint64_t UNIT_PIECES = 4096;
-constexpr uint64_t CHUNK_BYTES = 32ull << 20; // staged bytes per DMA chunk
+constexpr uint64_t CHUNK_BYTES = DC_CHUNK_BYTES;  // staged bytes per DMA chunk
+constexpr uint64_t BACK_CHUNK_BYTES = DC_BACK_CHUNK_BYTES;  // copied-back bytes per DMA chunk
 constexpr uint64_t PAGE = 4096;
 
 uint64_t page_up(uint64_t x) { return (x + PAGE - 1) / PAGE * PAGE; }
@@ -46,12 +62,14 @@ uint64_t interior_bytes(const HostBlock& b) {
   return hi > lo && hi - lo >= DC_MAP_MIN_BYTES ? hi - lo : 0;
 }
 
-void plan_moves(const dc_plan_s* p, const std::vector<uint32_t>& list, dc_plan_s::Moves* m, bool host_order) {
+void plan_moves(const dc_plan_s* p, const std::vector<uint32_t>& list, dc_plan_s::Moves* m, bool host_order,
+                uint64_t chunk_bytes, bool stage_all) {
   *m = dc_plan_s::Moves();
+  if (!chunk_bytes) chunk_bytes = CHUNK_BYTES;
   for (uint32_t b : list) {
     const HostBlock& B = p->blocks[b];
     uint8_t* host = const_cast<uint8_t*>(B.host);
-    if (p->ihi[b] > p->ilo[b]) {
+    if (!stage_all && p->ihi[b] > p->ilo[b]) {
       m->interiors.push_back(b);
       const uint64_t head = p->ilo[b] - (uint64_t)(uintptr_t)host;
       const uint64_t tail = p->ihi[b] - (uint64_t)(uintptr_t)host;
@@ -86,7 +104,7 @@ void plan_moves(const dc_plan_s* p, const std::vector<uint32_t>& list, dc_plan_s
   size_t r = 0;
   for (uint64_t u = 0; u < m->units.size();) {
     uint64_t v = u, bytes = 0;
-    while (v < m->units.size() && bytes < CHUNK_BYTES) {
+    while (v < m->units.size() && bytes < chunk_bytes) {
       for (uint64_t k = m->units[v].first; k < m->units[v].last; k++) bytes += m->pieces[k].len;
       v++;
     }
@@ -204,7 +222,10 @@ namespace {
 // Copies of at least NT_MIN bytes use streaming stores: the destination lines are written without
 // being read first (a plain copy reads every destination line before writing it), and they do
 // not displace the cache.  The store fence at the end makes them visible before the copy returns.
-constexpr size_t NT_MIN = 4096;
+#ifndef DC_NT_MIN
+#define DC_NT_MIN 4096
+#endif
+constexpr size_t NT_MIN = DC_NT_MIN;
 
 __attribute__((target("avx2"))) void copy_stream(uint8_t* dst, const uint8_t* src, size_t n) {
   const size_t head = (32 - ((uintptr_t)dst & 31)) & 31;
@@ -290,41 +311,127 @@ dc_status transfer_to_device(dc_plan_s* p, cudaStream_t s) {
     }
     return launch_table(p, p->L.mvb, p->L.mvbt, p->h2d_frag_nd, p->h2d_frag_units, s);
   }
-  // Algorithm 1's contiguous buffer, marshalled and sent chunk by chunk
+  return send_staged(p, m, s);
+}
+
+// Algorithm 1's contiguous buffer.  The pool's threads take the work units in
+// arena order without stopping at chunk ends; the thread that finishes a
+// chunk's last unit zeroes the chunk's NULL slots and queues its DMA, so the
+// link starts on a chunk as soon as its bytes are in the pinned arena.
+dc_status send_staged(dc_plan_s* p, const dc_plan_s::Moves& m, cudaStream_t s) {
   Trace tr("dc_deep_copy", "marshal+copies");
-  for (const auto& c : m.chunks) {
-    host_copy(p, m, c.ufirst, c.ulast, true);
-    null_slots_upto(p, &ns, c.clast > c.cfirst ? m.copies[c.clast - 1].hi : 0);
-    for (uint64_t k = c.cfirst; k < c.clast; k++)
-      DC_CUDA(cudaMemcpyAsync(p->dev + m.copies[k].lo, p->pinned + m.copies[k].lo, m.copies[k].hi - m.copies[k].lo,
-                              cudaMemcpyHostToDevice, s));
+  const size_t nc = m.chunks.size();
+  if (!nc) return DC_OK;
+  std::vector<uint32_t> unit_chunk(m.units.size());
+  std::unique_ptr<std::atomic<uint64_t>[]> left(new std::atomic<uint64_t>[nc]);
+  std::vector<size_t> nbeg(nc + 1, p->null_slots.size());
+  for (size_t c = 0, ns = 0; c < nc; c++) {
+    const auto& ch = m.chunks[c];
+    for (uint64_t u = ch.ufirst; u < ch.ulast; u++) unit_chunk[u] = (uint32_t)c;
+    left[c].store(ch.ulast - ch.ufirst);
+    const uint64_t lo = m.pieces[m.units[ch.ufirst].first].off;  // chunk c's bytes start here
+    while (ns < p->null_slots.size() && p->null_slots[ns] < lo) ns++;
+    nbeg[c] = ns;
   }
+  std::atomic<int> failed{0};
+  cudaError_t first = cudaSuccess;
+  auto finish_chunk = [&](size_t c) {
+    for (size_t k = nbeg[c]; k < nbeg[c + 1]; k++) memset(p->pinned + p->null_slots[k], 0, 8);
+    const auto& ch = m.chunks[c];
+    for (uint64_t k = ch.cfirst; k < ch.clast; k++) {
+      const cudaError_t e = cudaMemcpyAsync(p->dev + m.copies[k].lo, p->pinned + m.copies[k].lo,
+                                            m.copies[k].hi - m.copies[k].lo, cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess && failed.exchange(1) == 0) first = e;
+    }
+  };
+  auto unit = [&](uint64_t u) {
+    for (uint64_t k = m.units[u].first; k < m.units[u].last; k++) {
+      const auto& pc = m.pieces[k];
+      copy_block(p->pinned + pc.off, pc.host, pc.len);
+    }
+    const uint32_t c = unit_chunk[u];
+    if (left[c].fetch_sub(1, std::memory_order_acq_rel) == 1) finish_chunk(c);
+  };
+  pool_of(p).parallel_for(m.units.size(), unit);
+  if (failed.load()) return cuda_fail(first, "cudaMemcpyAsync (deep copy chunk)");
   return DC_OK;
 }
 
+// The copy back: array interiors in mapped caller pages go by one move-kernel
+// launch straight into those pages; every other written byte goes by DMA into
+// the pinned arena in chunks of about BACK_CHUNK_BYTES, each with an event, and
+// the pool scatters chunk c into the caller's arrays while the chunks after it
+// are still on the link.  The device's error word is read first (after
+// every kernel queued before the copy back): if a kernel recorded an error,
+// nothing is scattered and the error is returned.
 dc_status transfer_back(dc_plan_s* p, const std::vector<uint32_t>& list, uint64_t key, cudaStream_t s) {
   if (key != p->back_key) {
-    plan_moves(p, list, &p->back);
+    std::vector<uint32_t> sorted(list);  // chunks follow arena order
+    std::sort(sorted.begin(), sorted.end());
+    plan_moves(p, sorted, &p->back, false, BACK_CHUNK_BYTES);
     const uint64_t base = (uint64_t)(uintptr_t)p->dev;
     std::vector<MoveDesc> d;
     for (uint32_t b : p->back.interiors)  // interiors straight into the caller's pages
       push_desc(&d, base + p->blocks[b].off + (p->ilo[b] - (uint64_t)(uintptr_t)p->blocks[b].host), p->idev[b],
                 p->ihi[b] - p->ilo[b]);
-    for (const auto& r : p->back.runs)  // the rest into the mapped pinned arena
-      push_desc(&d, base + r.lo, (uint64_t)(uintptr_t)p->pinned_dev + r.lo, r.hi - r.lo);
     dc_status st = upload(p, d, p->L.bk, p->L.bkt, p->L.tab_cap, &p->bk_nd, &p->bk_units, s);
     if (st) return st;
     p->back_key = key;
   }
-  dc_status st = launch_table(p, p->L.bk, p->L.bkt, p->bk_nd, p->bk_units, s);
-  if (st) return st;
-  {
-    Trace tr("dc_copy_back", "device+wait");
-    if ((st = device_error(p, s))) return st;  // synchronizes the stream
+  const dc_plan_s::Moves& m = p->back;
+  if (!p->back_err) DC_CUDA(cudaEventCreateWithFlags(&p->back_err, cudaEventDisableTiming));
+  while (p->back_ev.size() < m.chunks.size()) {
+    cudaEvent_t e;
+    DC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    p->back_ev.push_back(e);
   }
+  uint32_t* word = pinned_error_word(p);
+  {
+    Trace tr("dc_copy_back", "enqueue");
+    DC_CUDA(cudaMemcpyAsync(word, p->dev + p->L.ctrl + CTRL_ERR * 4, 4, cudaMemcpyDeviceToHost, s));
+    DC_CUDA(cudaEventRecord(p->back_err, s));
+    dc_status st = launch_table(p, p->L.bk, p->L.bkt, p->bk_nd, p->bk_units, s);
+    if (st) return st;
+    for (size_t c = 0; c < m.chunks.size(); c++) {
+      for (uint64_t k = m.chunks[c].cfirst; k < m.chunks[c].clast; k++)
+        DC_CUDA(cudaMemcpyAsync(p->pinned + m.copies[k].lo, p->dev + m.copies[k].lo, m.copies[k].hi - m.copies[k].lo,
+                                cudaMemcpyDeviceToHost, s));
+      DC_CUDA(cudaEventRecord(p->back_ev[c], s));
+    }
+  }
+  {
+    Trace tr("dc_copy_back", "error word");
+    dc_status st = wait_event(p->back_err);
+    if (st) return st;
+  }
+  if (*word) return device_error(p, s);  // waits for the stream, clears the word and reports it
   Trace tr("dc_copy_back", "scatter");
-  if (!p->back.units.empty()) host_copy(p, p->back, 0, p->back.units.size(), false);
-  return DC_OK;
+  // One pass of the pool over every unit in arena order, with no stop between
+  // chunks: the first thread to take a unit of chunk c waits for c's event
+  // (polling and yielding its core) and marks c ready for the others.
+  const size_t nc = m.chunks.size();
+  std::vector<uint32_t> unit_chunk(m.units.size());
+  for (size_t c = 0; c < nc; c++)
+    for (uint64_t u = m.chunks[c].ufirst; u < m.chunks[c].ulast; u++) unit_chunk[u] = (uint32_t)c;
+  std::unique_ptr<std::atomic<uint8_t>[]> ready(new std::atomic<uint8_t>[nc]);
+  for (size_t c = 0; c < nc; c++) ready[c].store(0);
+  std::atomic<int> failed{0};
+  pool_of(p).parallel_for(m.units.size(), [&](uint64_t u) {
+    const uint32_t c = unit_chunk[u];
+    if (!ready[c].load(std::memory_order_acquire)) {
+      if (wait_event(p->back_ev[c]) != DC_OK) {
+        failed.store(1);
+        return;
+      }
+      ready[c].store(1, std::memory_order_release);
+    }
+    for (uint64_t k = m.units[u].first; k < m.units[u].last; k++) {
+      const auto& pc = m.pieces[k];
+      copy_block(pc.host, p->pinned + pc.off, pc.len);
+    }
+  });
+  if (failed.load()) return fail(DC_ECUDA, "copy back: a chunk's transfer failed");
+  return sync_stream(p, s);  // the interiors' launch, when no chunk follows it
 }
 
 }  // namespace dc

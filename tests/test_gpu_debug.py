@@ -8,6 +8,12 @@
   deep copy passes the device-side check; relocating the same arena again
   finds device addresses where the check expects the host's, and dc_sync
   reports DC_EVERIFY.
+- DC_WAIT_LIMIT=0: the first mbarrier wait of every pipeline step of the
+  bulk-copy kernels gives up at once.  Each kernel records DC_ETIMEOUT, waits
+  (at the full limit) for the bulk copies it has in flight, and returns; the
+  status reaches the host through dc_sync and the context stays usable: with
+  the switch off, the same plan's deep copy, update and copy back match the
+  oracle.
 """
 import pytest
 import torch
@@ -67,3 +73,43 @@ def test_debug_switch_turns_on_verification(monkeypatch):
         p.sync()
     assert e.value.name == "DC_EVERIFY"
     p.destroy()
+
+
+def _timeout_then_parity(kernel, monkeypatch):
+    make = lambda: tg.node_tree(3, 16, tg.uniform(1, 5000), seed=51)  # 273 nodes, 4 relocation tiles' worth of slots
+    src, ref = make(), make()
+    s = src.schema
+    p = dc.Plan(s, src.root)
+    p.bind()
+    op = dc.Op()
+    if kernel != "relocate":
+        p.deep_copy()
+        p.sync()
+    monkeypatch.setenv("DC_WAIT_LIMIT", "0")
+    {"relocate": p.deep_copy, "leaf_tma": lambda: p.update(op), "fused": lambda: p.relocate_update(op)}[kernel]()
+    with pytest.raises(dc.DcError) as e:
+        p.sync()
+    assert e.value.name == "DC_ETIMEOUT"
+    p.sync()  # the status was reported once and cleared
+    monkeypatch.delenv("DC_WAIT_LIMIT")
+    p.deep_copy()  # start again from the host tree, at the default limit
+    p.sync()
+    ok, msg, _ = oracle.check_image(s, src.root, p.image(), p.device_base)
+    assert ok, msg
+    if kernel == "fused":
+        p.relocate_update(op)
+    else:
+        p.update(op)
+    p.copy_back()
+    cp = oracle.deep_copy(s, ref.root)
+    oracle.update(s, cp.root, oracle.Op())
+    oracle.copy_back(s, cp.root, ref.root, oracle.Op())
+    ok, msg = oracle.trees_equal(s, src.root, ref.root)
+    assert ok, msg
+    p.destroy()
+
+
+@pytest.mark.parametrize("kernel", ["relocate", "leaf_tma", "fused"])
+def test_a_wait_that_runs_out_reports_a_timeout(kernel, monkeypatch):
+    monkeypatch.delenv("DC_LEAF_TMA", raising=False)  # the bulk-copy leaf kernel
+    _timeout_then_parity(kernel, monkeypatch)

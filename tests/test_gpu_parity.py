@@ -670,3 +670,62 @@ def test_roundtrip_selected_matches_the_oracle(flags):
         plan.destroy()
         src.free()
         ref.free()
+
+
+# ---- the selective deep copy of a chain (Sec. 2; Sec. 4.1.2's LLused layouts) ----------
+
+SELECTIVE_CASES = {
+    # Linear allinit-LLused: every level has its A, the kernel scales the last level's
+    "linear_allinit_llused": (lambda: tg.linear_tree(10, 10 ** 5, "allinit", seed=8),
+                              dict(kind=dc.OP_SCALE, sel=dc.SEL_CHAIN, x=2, scale=1.5, path=[(3, 0)] * 9),
+                              2, -1, [(2, 0)]),
+    # Dense, Listing 2's a0->Lnext[q-1].Lnext[q-1].Lnext[q-1]->A
+    "dense_listing2": (lambda: tg.dense_tree(8, 1000, 3, seed=4),
+                       dict(kind=dc.OP_SCALE, sel=dc.SEL_CHAIN, type_=3, x=1, scale=1.25, path=[(3, 7)] * 3),
+                       1, -1, [(2, 0)]),
+    # the node struct, x += 0.5*y at root->child[5]->child[2]
+    "node_chain_axpy": (lambda: tg.node_tree(4, 6, tg.uniform(1, 3000), seed=9),
+                        dict(sel=dc.SEL_CHAIN, path=[(NODE_LEAF, 5), (NODE_LEAF, 2)]), 2, 3, [(2, 0)]),
+}
+
+
+@pytest.mark.parametrize("flags", [0, dc.PLAN_MAP_HOST])
+@pytest.mark.parametrize("case", sorted(SELECTIVE_CASES))
+def test_selective_deep_copy_of_a_chain(case, flags):
+    """dc_deep_copy_selected moves only the chain's struct blocks and the op's
+    arrays: the device image passes the oracle's check along the chain, an
+    array off the chain still holds the bytes the buffer was filled with, the
+    device walk of the chain reaches the resolved address, and the pointer
+    chase and the resolved update, each followed by the copy back, give the
+    oracle's host tree."""
+    make, kw, xf, yf, off_chain = SELECTIVE_CASES[case]
+    src, ref = make(), make()
+    s = src.schema
+    plan = dc.Plan(s, src.root, flags=flags)
+    buf = plan.bind()
+    info = plan.info
+    buf[:info["data_bytes"]].fill_(0xAB)
+    dop, oop = ops_pair(**kw)
+    path = list(kw["path"])
+    plan.deep_copy_selected(dop)
+    plan.sync()
+    img, base = plan.image(), plan.device_base
+    ok, msg = oracle.check_chain_image(s, src.root, img, base, path, xf, yf)
+    assert ok, msg
+    o = plan.resolve_offset(off_chain)  # the root's first array (at least one element): not on the chain
+    assert (img[o:o + 4] == 0xAB).all()
+    assert not oracle.check_image(s, src.root, img, base)[0]  # not a full copy
+    assert plan.verify_chain(path) == plan.resolve(path)
+    for mode in ("chase", "leaf"):
+        if mode == "leaf":
+            plan.deep_copy_selected(dop)  # again, from the host tree the first round wrote back
+        (plan.update_chase if mode == "chase" else plan.update)(dop)
+        plan.copy_back()
+        cp = oracle.deep_copy(s, ref.root)
+        oracle.update(s, cp.root, oop)
+        oracle.copy_back(s, cp.root, ref.root, oop)
+        ok, msg = oracle.trees_equal(s, src.root, ref.root)
+        assert ok, (mode, msg)
+    plan.destroy()
+    src.free()
+    ref.free()
