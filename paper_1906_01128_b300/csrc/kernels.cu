@@ -105,30 +105,34 @@ struct __align__(16) RelocSmem {
   uint4 hdr[RSTAGES];  // the staged tile: (t, r0, r1, ng); t = NONE ends the CTA's tiles
 };
 
+__device__ __forceinline__ uint32_t warp_incl_scan32(uint32_t v, uint32_t lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t o = __shfl_up_sync(0xffffffffu, v, d);
+    if (lane >= (uint32_t)d) v += o;
+  }
+  return v;
+}
+
 // One staged tile's slots from offset records (the default): a slot's target
 // lies at its lane group's base plus the record's 32-bit offset, both in
-// 16-byte units.  Record j goes to thread j % THREADS (or, WARP_OWN, warp w
-// takes its own records [w, w + 1) * 32 * ITEMS, lane L the L-th of every 32):
-// conflict-free shared loads either way, and a warp's slot writes land in a
-// few hundred consecutive bytes.
-template <uint32_t THREADS, bool VERIFY, bool WARP_OWN = false>
+// 16-byte units.  Record j goes to thread j % THREADS: conflict-free shared
+// loads, and a warp's slot writes land in a few hundred consecutive bytes.
+template <uint32_t THREADS, bool VERIFY>
 __device__ __forceinline__ void reloc_apply_offsets(const RelocArgs& a, RelocStage& S, uint32_t r0, uint32_t nr,
                                                     uint32_t ng, uint32_t sh, uint32_t n8, uint64_t base) {
   constexpr uint32_t ITEMS = RELOC_MAXREC / THREADS;
   const uint32_t tid = threadIdx.x;
-  auto rec_of = [&](uint32_t i) {
-    return WARP_OWN ? (tid >> 5) * 32 * ITEMS + i * 32 + (tid & 31) : tid + i * THREADS;
-  };
   uint2 r[ITEMS];
 #pragma unroll
   for (uint32_t i = 0; i < ITEMS; i++) {
-    const uint32_t j = rec_of(i);
+    const uint32_t j = tid + i * THREADS;
     r[i] = j < nr ? S.rec[sh + j] : make_uint2(0, 0);
   }
   uint64_t* img64 = reinterpret_cast<uint64_t*>(S.img);
 #pragma unroll
   for (uint32_t i = 0; i < ITEMS; i++) {
-    const uint32_t j = rec_of(i);
+    const uint32_t j = tid + i * THREADS;
     if (j >= nr) continue;
     const uint32_t w = r[i].y & 0xFFFFu, g = r[i].y >> 16;  // slot word in the tile, lane group
     if (w >= n8 || g >= ng) {
@@ -147,86 +151,70 @@ __device__ __forceinline__ void reloc_apply_offsets(const RelocArgs& a, RelocSta
 
 // One staged tile's slots from size records (DC_PLAN_DEVICE_SCAN): a target's
 // offset is its lane group's base plus the exclusive prefix of the padded sizes
-// of the records before it in its group; a group's records are contiguous, so
-// a group starts wherever the group index changes.  Warp w owns the records
-// [w * 32 * ITEMS, (w + 1) * 32 * ITEMS).  Phase 1, before the CTA barrier that
-// follows every stage's wait: each thread scans its ITEMS consecutive records
-// in registers (restarting at group starts), one segmented warp scan combines
-// the threads' trailing sums, and lane 31 publishes the warp's trailing sum
-// and whether the warp holds a group start.  Phase 2, after that barrier: the
-// records before the warp's first group start take the trailing sums of the
-// warps before it back to the one that opened their group, each thread writes
-// its records' in-group prefixes over their sizes in the staged records, and
-// after a warp barrier (the warp's own records) the slots are written as in
-// the offset form.  Prefixes are 32-bit: a group's offsets stay below 2^32
-// units (the plan starts a new group otherwise).
-template <uint32_t THREADS>
-struct ScanState {
-  static constexpr uint32_t ITEMS = RELOC_MAXREC / THREADS;
-  uint32_t ex[ITEMS];  // in-group prefix, before the carry from earlier threads
-  uint32_t open;       // bit i: record i lies before this thread's first group start
-  uint32_t cin;        // the open group's sum in the earlier threads of this warp
-  bool warp_open;      // no group starts in the earlier threads of this warp
-};
-
-template <uint32_t THREADS>
-__device__ __forceinline__ void reloc_scan_phase1(const RelocStage& S, uint32_t nr, uint32_t sh,
-                                                  ScanState<THREADS>& st, uint2* warp_agg) {
-  constexpr uint32_t ITEMS = ScanState<THREADS>::ITEMS;
-  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, j0 = tid * ITEMS;
-  uint32_t gprev = j0 ? S.rec[sh + j0 - 1].y >> 16 : 0xFFFFFFFFu;  // the group of the record before
-  uint32_t run = 0;
-  bool headed = false;
-  st.open = 0;
-#pragma unroll
-  for (uint32_t i = 0; i < ITEMS; i++) {
-    const uint32_t j = j0 + i;
-    const uint2 r = j < nr ? S.rec[sh + j] : make_uint2(0, 0xFFFFFFFFu);
-    const uint32_t g = r.y >> 16;
-    const bool head = j < nr && g != gprev;
-    gprev = g;
-    run = head ? 0u : run;
-    headed = headed || head;
-    st.ex[i] = run;
-    st.open |= headed ? 0u : 1u << i;
-    run += r.x;
-  }
-  // segmented inclusive scan of (trailing sum, holds a group start) over the warp's threads
-  uint32_t v = run, f = headed ? 1u : 0u;
-#pragma unroll
-  for (uint32_t d = 1; d < 32; d <<= 1) {
-    const uint32_t vu = __shfl_up_sync(0xffffffffu, v, d), fu = __shfl_up_sync(0xffffffffu, f, d);
-    if (lane >= d) {
-      v = f ? v : v + vu;
-      f |= fu;
-    }
-  }
-  const uint32_t vp = __shfl_up_sync(0xffffffffu, v, 1), fp = __shfl_up_sync(0xffffffffu, f, 1);
-  st.cin = lane ? vp : 0u;
-  st.warp_open = lane ? fp == 0u : true;
-  if (lane == 31) warp_agg[warp] = make_uint2(v, f);
-}
-
+// before it in its group.  The records are warp-striped (warp w owns a
+// contiguous run of 32 x ITEMS records, its lane L record 32k + L); warp-shuffle
+// scans run slice by slice inside each warp, then over the warps' totals.  The
+// prefixes are 32-bit: a group's offsets stay below 2^32 units (the plan starts
+// a new group otherwise), so a difference of two prefixes modulo 2^32 is exact.
+// Every thread reaches both barriers (the call is uniform across the CTA).  Its
+// shared arrays exist only in the kernels built with this form.
 template <uint32_t THREADS, bool VERIFY>
-__device__ __forceinline__ void reloc_scan_phase2(const RelocArgs& a, RelocStage& S, uint32_t r0, uint32_t nr,
-                                                  uint32_t ng, uint32_t sh, uint32_t n8, uint64_t base,
-                                                  const ScanState<THREADS>& st, const uint2* warp_agg) {
-  constexpr uint32_t ITEMS = ScanState<THREADS>::ITEMS;
-  const uint32_t tid = threadIdx.x, warp = tid >> 5, j0 = tid * ITEMS;
-  uint32_t carry = st.cin;
-  if (st.warp_open)  // the group open at this thread's start began in an earlier warp
-    for (uint32_t w = warp; w-- > 0;) {
-      const uint2 ag = warp_agg[w];
-      carry += ag.x;
-      if (ag.y) break;
-    }
+__device__ __forceinline__ void reloc_apply_scan(const RelocArgs& a, RelocStage& S, uint32_t r0, uint32_t nr,
+                                                 uint32_t ng, uint32_t sh, uint32_t n8, uint64_t base) {
+  constexpr uint32_t NW = THREADS / 32, ITEMS = RELOC_MAXREC / THREADS;
+  // per lane group: its base offset / 16 (x, y) and minus the size prefix at its
+  // first record (z); per warp: its records' size total
+  __shared__ uint4 gb[RELOC_MAXGROUPS];
+  __shared__ uint32_t warp_sum[32];
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, wb = warp * 32 * ITEMS;
+  uint2 r[ITEMS];
 #pragma unroll
   for (uint32_t i = 0; i < ITEMS; i++) {
-    const uint32_t j = j0 + i;
-    if (j < nr) S.rec[sh + j].x = st.ex[i] + ((st.open >> i) & 1u ? carry : 0u);
+    const uint32_t j = wb + i * 32 + lane;
+    r[i] = j < nr ? S.rec[sh + j] : make_uint2(0, 0);
   }
-  __syncwarp();  // the warp's records now hold in-group offsets
-  reloc_apply_offsets<THREADS, VERIFY, true>(a, S, r0, nr, ng, sh, n8, base);
+  uint32_t ex[ITEMS];
+  uint32_t carry = 0;
+#pragma unroll
+  for (uint32_t i = 0; i < ITEMS; i++) {
+    const uint32_t incl = warp_incl_scan32(r[i].x, lane);
+    ex[i] = carry + incl - r[i].x;
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (lane == 0) warp_sum[warp] = carry;
+  __syncthreads();
+  uint32_t wt = lane < NW ? warp_sum[lane] : 0u;
+  wt = warp_incl_scan32(wt, lane);
+  const uint32_t wpre = warp ? __shfl_sync(0xffffffffu, wt, (warp - 1) & 31) : 0u;
+#pragma unroll
+  for (uint32_t i = 0; i < ITEMS; i++) {
+    ex[i] += wpre;
+    const uint32_t j = wb + i * 32 + lane, g = r[i].y >> 16;
+    if (j < nr && g < ng && S.grp[g].rec_begin - r0 == j) {  // the group's first record
+      const uint64_t b16 = S.grp[g].base16;
+      gb[g] = make_uint4((uint32_t)b16, (uint32_t)(b16 >> 32), 0u - ex[i], 0u);
+    }
+  }
+  __syncthreads();  // every group's base and start prefix are in shared memory
+  uint64_t* img64 = reinterpret_cast<uint64_t*>(S.img);
+#pragma unroll
+  for (uint32_t i = 0; i < ITEMS; i++) {
+    const uint32_t j = wb + i * 32 + lane;
+    if (j >= nr) continue;
+    const uint32_t w = r[i].y & 0xFFFFu, g = r[i].y >> 16;
+    if (w >= n8 || g >= ng) {
+      atomicOr(&a.ctrl[CTRL_ERR], ERR_BOUNDS);
+      continue;
+    }
+    const uint4 G = gb[g];
+    const uint64_t off = ((((uint64_t)G.y << 32) | G.x) + (uint32_t)(ex[i] + G.z)) * 16;
+    uint64_t* sp = img64 + w;
+    if (VERIFY) {
+      const uint32_t ri = r0 + j;
+      if (*sp != __ldg(&a.rec_host[ri]) || off != __ldg(&a.rec_off[ri])) atomicOr(&a.ctrl[CTRL_ERR], ERR_VERIFY);
+    }
+    *sp = base + off;
+  }
 }
 
 // The producer (thread 0) fills stage s with listed tile i of the CTA (or
@@ -290,18 +278,9 @@ __device__ __forceinline__ void reloc_tiles(const RelocArgs& a, RelocSmem& sm) {
     if (in != NONE) hn = __ldg(hdrs + in);
   }
   const uint64_t base = reinterpret_cast<uint64_t>(a.arena);
-  // the scan form's per-warp aggregates (phase 1 -> phase 2); unused otherwise
-  __shared__ uint2 warp_agg[SCAN ? THREADS / 32 : 1];
-  ScanState<THREADS> st;
   for (uint32_t k = 0;; k++) {
     const uint32_t s = k % RSTAGES, parity = (k / RSTAGES) & 1;
     const bool late = !mbar_wait(&sm.bar[s], parity, a.wait_limit);
-    // the scan form scans its records before the barrier, in warps whose every
-    // lane saw stage s complete (a late lane sends the whole CTA to the timeout)
-    if (SCAN && !__any_sync(0xffffffffu, late)) {
-      const uint4 h = sm.hdr[s];
-      if (h.x != NONE && h.z > h.y) reloc_scan_phase1<THREADS>(sm.st[s], h.z - h.y, h.y & 1u, st, warp_agg);
-    }
     if (__syncthreads_or(late)) {
       if (tid == 0) {  // give the copies in flight another bounded wait before leaving
         atomicOr(err, ERR_TIMEOUT);
@@ -320,7 +299,7 @@ __device__ __forceinline__ void reloc_tiles(const RelocArgs& a, RelocSmem& sm) {
     if (nr) {  // uniform
       const uint32_t n8 = (uint32_t)((hi - lo) / 8);
       if (SCAN)
-        reloc_scan_phase2<THREADS, VERIFY>(a, S, r0, nr, ng, sh, n8, base, st, warp_agg);
+        reloc_apply_scan<THREADS, VERIFY>(a, S, r0, nr, ng, sh, n8, base);
       else
         reloc_apply_offsets<THREADS, VERIFY>(a, S, r0, nr, ng, sh, n8, base);
       fence_async_smem();  // the slot writes are seen by the bulk store
