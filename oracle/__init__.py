@@ -98,6 +98,9 @@ def lib():
         L.or_check_image.argtypes = [P(_Schema), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
                                      ctypes.c_uint64, ctypes.c_uint64, P(_Counts), ctypes.c_char_p,
                                      ctypes.c_size_t]
+        L.or_check_image_packed.argtypes = [P(_Schema), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                                            ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, P(_Counts),
+                                            ctypes.c_char_p, ctypes.c_size_t]
         L.or_check_chain_image.argtypes = [P(_Schema), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
                                            ctypes.c_uint64, ctypes.c_uint64, P(_Step), ctypes.c_uint32,
                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_char_p, ctypes.c_size_t]
@@ -107,7 +110,8 @@ def lib():
         L.or_host_resolve.argtypes = [P(_Schema), ctypes.c_void_p, P(_Step), ctypes.c_uint32,
                                       P(ctypes.c_uint64)]
         for f in ("or_count", "or_deep_copy", "or_update", "or_update_parallel", "or_threads", "or_copy_back",
-                  "or_trees_equal", "or_check_image", "or_check_chain_image", "or_image_resolve", "or_host_resolve"):
+                  "or_trees_equal", "or_check_image", "or_check_image_packed", "or_check_chain_image", "or_image_resolve",
+                  "or_host_resolve"):
             getattr(L, f).restype = ctypes.c_int
         _L = L
     return _L
@@ -244,13 +248,14 @@ def trees_equal(schema, a: int, b: int) -> Tuple[bool, str]:
     return rc == 0, msg.value.decode()
 
 
-def check_image(schema, src_root: int, image: np.ndarray, dev_base: int, root_off: int = 0):
-    """Check a host copy of a device arena's data region against the source tree."""
+def check_image(schema, src_root: int, image: np.ndarray, dev_base: int, root_off: int = 0, pack_below: int = 0):
+    """Check a host copy of a device arena's data region against the source tree.
+    ``pack_below``: arrays of fewer bytes may start on their element alignment."""
     image = np.ascontiguousarray(image, dtype=np.uint8)
     msg = ctypes.create_string_buffer(1024)
     c = _Counts()
-    rc = lib().or_check_image(ctypes.byref(_cs(schema).struct), src_root, image.ctypes.data,
-                              image.nbytes, dev_base, root_off, ctypes.byref(c), msg, 1024)
+    rc = lib().or_check_image_packed(ctypes.byref(_cs(schema).struct), src_root, image.ctypes.data,
+                                     image.nbytes, dev_base, root_off, pack_below, ctypes.byref(c), msg, 1024)
     if rc not in (0, 3):
         raise RuntimeError(f"oracle check_image: invalid input (status {rc})")
     return rc == 0, msg.value.decode(), _counts_dict(c)

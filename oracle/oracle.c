@@ -518,6 +518,7 @@ typedef struct {
   or_counts* seen;
   char* msg;
   size_t len;
+  uint64_t pack_below; /* arrays of fewer bytes may start on their element alignment */
 } img_ctx;
 
 static int add_span(img_ctx* c, uint64_t lo, uint64_t hi) {
@@ -573,9 +574,12 @@ static int img_struct(img_ctx* c, uint32_t ti, const uint8_t* src, uint64_t off,
       return OR_MISMATCH;
     }
     uint64_t o = p - c->base;
-    if (o % 16) {
-      say(c->msg, c->len, "%s.field%u: block offset %llu not 16-byte aligned", where, fi,
-          (unsigned long long)o);
+    /* every block starts on 16 bytes; in a packed layout an array of fewer than
+     * pack_below bytes may start on 8 bytes (f64) or 4 (other elements) */
+    const uint64_t al = (f->kind == OR_ARRAY && b < c->pack_below) ? (f->elem_kind == 1 ? 8 : 4) : 16;
+    if (o % al) {
+      say(c->msg, c->len, "%s.field%u: block offset %llu not %llu-byte aligned", where, fi, (unsigned long long)o,
+          (unsigned long long)al);
       return OR_MISMATCH;
     }
     int rc = add_span(c, o, o + b);
@@ -611,6 +615,12 @@ static int span_cmp(const void* a, const void* b) {
 int or_check_image(const or_schema* s, const void* src_root, const void* image,
                    uint64_t image_bytes, uint64_t dev_base, uint64_t root_off, or_counts* seen,
                    char* msg, size_t msglen) {
+  return or_check_image_packed(s, src_root, image, image_bytes, dev_base, root_off, 0, seen, msg, msglen);
+}
+
+int or_check_image_packed(const or_schema* s, const void* src_root, const void* image,
+                          uint64_t image_bytes, uint64_t dev_base, uint64_t root_off, uint64_t pack_below,
+                          or_counts* seen, char* msg, size_t msglen) {
   or_counts local;
   if (!seen) seen = &local;
   memset(seen, 0, sizeof *seen);
@@ -620,7 +630,7 @@ int or_check_image(const or_schema* s, const void* src_root, const void* image,
     say(msg, msglen, "root block outside the arena");
     return OR_MISMATCH;
   }
-  img_ctx c = {s, (const uint8_t*)image, image_bytes, dev_base, NULL, 0, 0, seen, msg, msglen};
+  img_ctx c = {s, (const uint8_t*)image, image_bytes, dev_base, NULL, 0, 0, seen, msg, msglen, pack_below};
   int rc = add_span(&c, root_off, root_off + rs);
   seen->nblocks = 1;
   seen->payload_bytes = rs;

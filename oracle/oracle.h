@@ -25,6 +25,9 @@
  *   or_check_image    checks a device image of a deep copy against its source:
  *                     same shape, byte-equal data, every pointer inside the
  *                     arena, 16-byte aligned, and no two blocks overlapping.
+ *                     or_check_image_packed allows arrays of fewer than
+ *                     pack_below bytes to start on their element alignment (8
+ *                     bytes for f64, else 4), the packed layout's promise.
  *   or_check_chain_image  checks a device image of a selective deep copy of
  *                     one pointer chain (Sec. 2: only what the chain reaches is
  *                     replicated) along that chain: each struct block the chain
@@ -122,6 +125,9 @@ int or_trees_equal(const or_schema* s, const void* a, const void* b, char* msg, 
 int or_check_image(const or_schema* s, const void* src_root, const void* image,
                    uint64_t image_bytes, uint64_t dev_base, uint64_t root_off, or_counts* seen,
                    char* msg, size_t msglen);
+int or_check_image_packed(const or_schema* s, const void* src_root, const void* image,
+                          uint64_t image_bytes, uint64_t dev_base, uint64_t root_off, uint64_t pack_below,
+                          or_counts* seen, char* msg, size_t msglen);
 /* y_field < 0: the op has no y array.  The path's steps are CHILD fields. */
 int or_check_chain_image(const or_schema* s, const void* src_root, const void* image, uint64_t image_bytes,
                          uint64_t dev_base, uint64_t root_off, const or_step* path, uint32_t len, int32_t x_field,

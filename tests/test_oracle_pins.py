@@ -608,6 +608,33 @@ def test_chain_image_with_x_and_y_on_a_node_chain():
     t.free()
 
 
+@pytest.mark.parametrize("case", ["f32_small_4", "f32_small_2", "f64_small_4", "f64_small_8", "f32_large_4"])
+def test_check_image_packed_alignment(case):
+    # The packed layout's promise: an array of fewer than 64 bytes may start on
+    # its element alignment (8 bytes for f64, else 4); every other block on 16.
+    # Move the root's first array up into its padding and check both readings.
+    if case.startswith("f32"):
+        n = 10 if "small" in case else 17           # 40 B (8 B of padding) or 68 B (12 B of padding)
+        t = tg.node_tree(2, 3, n, seed=41)
+        field_off, nbytes = 8, 4 * n               # Node.position
+    else:
+        t = tg.linear_tree(2, 5, "allinit", seed=42)  # A: 5 doubles = 40 B
+        field_off, nbytes = 8, 40
+    by = int(case.rsplit("_", 1)[1])
+    base = 0x7F0000000000
+    img = oracle.deep_copy(t.schema, t.root, ptr_base=base).image().copy()
+    p = int.from_bytes(img[field_off:field_off + 8].tobytes(), "little")
+    o = p - base
+    assert o % 16 == 0
+    img[o + by:o + by + nbytes] = img[o:o + nbytes].copy()
+    _plant(img, field_off, p + by)
+    s = t.schema
+    assert not oracle.check_image(s, t.root, img, base)[0]  # 16-byte blocks everywhere
+    ok = oracle.check_image(s, t.root, img, base, pack_below=64)[0]
+    assert ok == (case in ("f32_small_4", "f64_small_8")), case
+    t.free()
+
+
 def test_random_schemas_copy_and_image_agree():
     rng = random.Random(1234)
     for i in range(150):
