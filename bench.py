@@ -953,6 +953,23 @@ def main():
     plan_scan.sync()
     plan_scan.destroy()
     del plan_scan
+    # The same tree on a DC_PLAN_PACK_SMALL plan (arrays below 64 bytes at their element
+    # alignment), when that shortens the arena: its device step and leaf update, same split
+    packed = None
+    plan_p = dc.Plan(s, tree.root, flags=dc.PLAN_PACK_SMALL)
+    if plan_p.info["data_bytes"] < info["data_bytes"]:
+        plan_p.bind()
+        plan_p.deep_copy()
+        plan_p.sync()
+        plan_p.set_split(op, *tuned)
+        (t_pstep,) = timed_loop([lambda: plan_p.relocate_update(op)], "dc_step_packed")
+        (t_pleaf,) = timed_loop([lambda: plan_p.update(op)], "dc_leaf_packed")
+        plan_p.sync()
+        packed = {"plan": "DC_PLAN_PACK_SMALL", "arena_bytes": plan_p.info["data_bytes"],
+                  "step_avg_us": round(statistics.mean(t_pstep) * 1e6, 2),
+                  "leaf_avg_us": round(statistics.mean(t_pleaf) * 1e6, 2)}
+    plan_p.destroy()
+    del plan_p
     # Both relocation forms once more, as back-to-back launches over copies of the arena that
     # together stream more than twice the L2 (so no launch finds its inputs there), one event
     # pair around the batch: a launch of a few microseconds is below the event timer's
@@ -1204,6 +1221,9 @@ def main():
                 **({"batched_us": round(reloc_batch["device_scan"] * 1e6, 2),
                     "batched_frac": round(reloc_bytes / reloc_batch["device_scan"] / 1e9 / hbm, 4)}
                    if reloc_batch else {})},
+            "packed": packed and {**packed,
+                                  "step_frac": round(fused_bytes / (packed["step_avg_us"] * 1e-6) / 1e9 / hbm, 4),
+                                  "leaf_frac": round(leaf_bytes / (packed["leaf_avg_us"] * 1e-6) / 1e9 / hbm, 4)},
             "two_launch_step_us": round((reloc_avg + leaf_avg) * 1e6, 2),
             "step_median_ms": round(step_median * 1e3, 4),
             "hbm_copy_gbs_now": copy_now,

@@ -171,6 +171,20 @@ typedef struct {
                              the records carry the offsets the plan's layout assigned,
                              which is faster; the device image is the same.  Read at
                              dc_bind_device; dc_relocate_static ignores it. */
+#define DC_PLAN_PACK_SMALL 8u /* lay array blocks of fewer than DC_PACK_BYTES bytes out
+                             at their element alignment (8 bytes for f64, else 4)
+                             instead of on 16 bytes, so that many small arrays lie
+                             back to back and the leaf update streams over them
+                             without padding (the relocation tables then count in
+                             4-byte units: a lane group spans at most 16 GiB and a
+                             block less than 16 GiB).  Struct blocks and larger
+                             arrays stay on 16 bytes; every lane starts on 16 bytes.
+                             Changing it reruns the plan's layout, so it is set before
+                             dc_bind_device (DC_ESTATE after).  dc_plan_arena_bytes
+                             and dc_plan_block give the packed offsets.  dc_roundtrip
+                             takes its three-call path when a selected array is not
+                             on 16 bytes in the arena. */
+#define DC_PACK_BYTES 64u
 
 /* dc_plan — walk the host structure from `host_root` (one struct of
  * schema->root_type) and lay out its device arena (Algorithm 1's first step,

@@ -31,6 +31,7 @@ SEL_ALL, SEL_CHAIN = 0, 1
 PLAN_VERIFY = 1
 PLAN_MAP_HOST = 2
 PLAN_DEVICE_SCAN = 4
+PLAN_PACK_SMALL = 8
 COPY_ALL_ARRAYS = 1
 
 STATUS = {0: "DC_OK", 1: "DC_EINVAL", 2: "DC_ENOMEM", 3: "DC_ECUDA", 4: "DC_EALIAS", 5: "DC_ECYCLE",
@@ -249,6 +250,7 @@ class Plan:
             _check(lib.dc_plan_forest(ctypes.byref(self._schema_c), roots, len(host_root), ctypes.byref(h)))
         self._h = h.value
         self.host_root = host_root if isinstance(host_root, int) else host_root[0]
+        self.flags = flags
         if flags:
             _check(lib.dc_plan_set_flags(self._h, flags))
         if threads:
@@ -280,6 +282,11 @@ class Plan:
 
     def set_threads(self, n: int):
         _check(lib.dc_plan_set_threads(self._h, n))
+
+    def set_flags(self, flags: int):
+        """dc_plan_set_flags (DC_PLAN_PACK_SMALL lays the plan out again)."""
+        _check(lib.dc_plan_set_flags(self._h, flags))
+        self.flags = flags
 
     def bind(self, buffer: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
         need = self.info["device_bytes"]

@@ -49,20 +49,23 @@ const char* last_error();
 // relocation tile is such a range; its records are grouped by lane, each
 // group holding consecutive target blocks.
 //
-// One pointer slot: the target block's arena offset / 16 relative to its lane
-// group's base, and where the slot is: its 8-byte word within the tile (low 16
-// bits) and its lane group's index within the tile (high 16 bits).
+// Offsets in the relocation tables are in record units: 16 bytes, or 4 bytes
+// for DC_PLAN_PACK_SMALL plans (the plan's unit_shift: 4 or 2).
+// One pointer slot: the target block's arena offset in units relative to its
+// lane group's base (or, DC_PLAN_DEVICE_SCAN, the target's size in units), and
+// where the slot is: its 8-byte word within the tile (low 16 bits) and its lane
+// group's index within the tile (high 16 bits).
 struct RelocRec {
-  uint32_t off16;
+  uint32_t off;
   uint32_t where;
 };
 static_assert(sizeof(RelocRec) == 8, "RelocRec is 8 bytes");
-// One (tile, lane) group: the arena offset / 16 of its first target block and
-// the index of its first record; the plan starts a new group where a target
+// One (tile, lane) group: the arena offset in units of its first target block
+// and the index of its first record; the plan starts a new group where a target
 // lies 2^32 units or more past the base.  The table ends with a group whose
 // rec_begin is the record count.
 struct RelocSeg {
-  uint64_t base16;
+  uint64_t base;
   uint32_t rec_begin, pad;
 };
 static_assert(sizeof(RelocSeg) == 16, "RelocSeg is 16 bytes");
@@ -126,6 +129,7 @@ struct RelocArgs {
   uint32_t nrec, nseg, ntiles, verify;
   uint32_t scan;  // records hold sizes (DC_PLAN_DEVICE_SCAN), not offsets
   uint32_t wait_limit = WAIT_LIMIT;  // try_wait rounds of a tile's first wait (0: give up at once)
+  uint32_t unit_shift = 4;           // offsets in the tables are in units of 1 << unit_shift bytes
 };
 
 constexpr uint32_t LEAF_THREADS = 256;
@@ -260,7 +264,9 @@ struct dc_plan_s {
   std::vector<dc::RelocTile> rtiles;     // per relocation tile: its records and lane groups
   std::vector<uint64_t> rec_host;        // per record: the target's host address (DC_PLAN_VERIFY)
   std::vector<uint64_t> rec_off;         // per record: the target's arena offset (DC_PLAN_VERIFY)
-  std::vector<uint32_t> rec_size16;      // per record: the target's padded size / 16 (DC_PLAN_DEVICE_SCAN)
+  std::vector<uint32_t> rec_size;        // per record: units to the next block of the lane (DC_PLAN_DEVICE_SCAN)
+  std::vector<uint64_t> lane_start;      // lane l's blocks are [lane_start[l], lane_start[l+1])
+  uint32_t unit_shift = 4;               // the tables' units: 16 bytes, or 4 with DC_PLAN_PACK_SMALL
   bool rec_scan = false;                 // the bound buffer holds size records
   uint64_t struct_bytes = 0;             // bytes of the struct lane (lane 0)
   std::vector<uint64_t> null_slots;      // arena offsets of slots with count 0 but a non-NULL host value
@@ -354,6 +360,8 @@ struct dc_uvm_s {
 };
 
 namespace dc {
+// Block offsets and relocation tables from the blocks in lane order (plan.cpp).
+dc_status layout(dc_plan_s* p);
 dc_status build_plan(const dc_schema* schema, const void* const* roots, uint64_t nroots, dc_plan_s* p);
 // Resolve a chain over the plan tables to (block, byte offset in block, type
 // of the struct reached or NONE when the last step was an ARRAY step, element).

@@ -115,8 +115,8 @@ __device__ __forceinline__ uint32_t warp_incl_scan32(uint32_t v, uint32_t lane) 
 }
 
 // One staged tile's slots from offset records (the default): a slot's target
-// lies at its lane group's base plus the record's 32-bit offset, both in
-// 16-byte units.  Record j goes to thread j % THREADS: conflict-free shared
+// lies at its lane group's base plus the record's 32-bit offset, both in the
+// plan's record units (16 bytes, or 4 with DC_PLAN_PACK_SMALL).  Record j goes to thread j % THREADS: conflict-free shared
 // loads, and a warp's slot writes land in a few hundred consecutive bytes.
 template <uint32_t THREADS, bool VERIFY>
 __device__ __forceinline__ void reloc_apply_offsets(const RelocArgs& a, RelocStage& S, uint32_t r0, uint32_t nr,
@@ -139,7 +139,7 @@ __device__ __forceinline__ void reloc_apply_offsets(const RelocArgs& a, RelocSta
       atomicOr(&a.ctrl[CTRL_ERR], ERR_BOUNDS);
       continue;
     }
-    const uint64_t off = (S.grp[g].base16 + r[i].x) * 16;
+    const uint64_t off = (S.grp[g].base + r[i].x) << a.unit_shift;
     uint64_t* sp = img64 + w;
     if (VERIFY) {
       const uint32_t ri = r0 + j;
@@ -150,8 +150,9 @@ __device__ __forceinline__ void reloc_apply_offsets(const RelocArgs& a, RelocSta
 }
 
 // One staged tile's slots from size records (DC_PLAN_DEVICE_SCAN): a target's
-// offset is its lane group's base plus the exclusive prefix of the padded sizes
-// before it in its group.  The records are warp-striped (warp w owns a
+// offset is its lane group's base plus the exclusive prefix of the sizes before
+// it in its group (a record's size: the units from its target to the next block
+// of the lane).  The records are warp-striped (warp w owns a
 // contiguous run of 32 x ITEMS records, its lane L record 32k + L); warp-shuffle
 // scans run slice by slice inside each warp, then over the warps' totals.  The
 // prefixes are 32-bit: a group's offsets stay below 2^32 units (the plan starts
@@ -162,7 +163,7 @@ template <uint32_t THREADS, bool VERIFY>
 __device__ __forceinline__ void reloc_apply_scan(const RelocArgs& a, RelocStage& S, uint32_t r0, uint32_t nr,
                                                  uint32_t ng, uint32_t sh, uint32_t n8, uint64_t base) {
   constexpr uint32_t NW = THREADS / 32, ITEMS = RELOC_MAXREC / THREADS;
-  // per lane group: its base offset / 16 (x, y) and minus the size prefix at its
+  // per lane group: its base offset in units (x, y) and minus the size prefix at its
   // first record (z); per warp: its records' size total
   __shared__ uint4 gb[RELOC_MAXGROUPS];
   __shared__ uint32_t warp_sum[32];
@@ -191,8 +192,8 @@ __device__ __forceinline__ void reloc_apply_scan(const RelocArgs& a, RelocStage&
     ex[i] += wpre;
     const uint32_t j = wb + i * 32 + lane, g = r[i].y >> 16;
     if (j < nr && g < ng && S.grp[g].rec_begin - r0 == j) {  // the group's first record
-      const uint64_t b16 = S.grp[g].base16;
-      gb[g] = make_uint4((uint32_t)b16, (uint32_t)(b16 >> 32), 0u - ex[i], 0u);
+      const uint64_t gbase = S.grp[g].base;
+      gb[g] = make_uint4((uint32_t)gbase, (uint32_t)(gbase >> 32), 0u - ex[i], 0u);
     }
   }
   __syncthreads();  // every group's base and start prefix are in shared memory
@@ -207,7 +208,7 @@ __device__ __forceinline__ void reloc_apply_scan(const RelocArgs& a, RelocStage&
       continue;
     }
     const uint4 G = gb[g];
-    const uint64_t off = ((((uint64_t)G.y << 32) | G.x) + (uint32_t)(ex[i] + G.z)) * 16;
+    const uint64_t off = ((((uint64_t)G.y << 32) | G.x) + (uint32_t)(ex[i] + G.z)) << a.unit_shift;
     uint64_t* sp = img64 + w;
     if (VERIFY) {
       const uint32_t ri = r0 + j;
@@ -249,7 +250,7 @@ __device__ __forceinline__ void issue_tile(const RelocArgs& a, RelocSmem& sm, ui
 // two-stage pipeline: while the CTA rewrites the slots of one staged tile,
 // the bulk copies of the next are in flight, and the producer has the header
 // after that in a register.  A slot's target lies at its lane group's base
-// plus its offset in the group (both in 16-byte units): the record's own
+// plus its offset in the group (both in record units): the record's own
 // offset, or with DC_PLAN_DEVICE_SCAN a prefix sum of the records' sizes.  The
 // rewritten staged tile goes back by one bulk store.  The loop's exits are
 // uniform across the CTA; every wait has an iteration limit.
@@ -493,7 +494,8 @@ __device__ __forceinline__ void leaf_next_seg(const LeafArgs& a, LeafNext* n) {
 // The producer (thread 0) stages sub-tile w (units [w, w+1) * LSUB, in leaf
 // tile w / 2) in stage s.  A leaf tile inside one segment comes by bulk copies
 // (its x and y units are contiguous and 16-byte aligned, the last one inside
-// its block's 16-byte padding); a tile across segments goes to the direct path,
+// its block's padding); a tile across segments, or in a segment off a 16-byte
+// boundary, goes to the direct path,
 // whole, from its first half (its second half is then empty); w past the end
 // marks the end.  hdr[2s] = (w, mode, units), hdr[2s+1] = the destination of
 // the sub-tile's first unit and the elements left from it.
@@ -508,7 +510,9 @@ __device__ __forceinline__ void leaf_issue(const LeafArgs& a, uint4* xd, uint4* 
     return;
   }
   const uint64_t u0 = w * LSUB, u1 = min(u0 + LSUB, a.units);
-  if (n.lo != n.hi || n.lo >= a.nseg) {  // across segments: the direct path takes the whole tile once
+  // across segments, or in a segment that does not start on 16 bytes (a
+  // packed arena's short head): the direct path takes the whole tile once
+  if (n.lo != n.hi || n.lo >= a.nseg || ((n.g.x | (KIND == DC_OP_AXPY_HALF ? n.g.y : 0)) & 15)) {
     hdr[0] = make_uint4((uint32_t)w, (uint32_t)(w >> 32), (w & 1) ? 3u : 0u, 0);
     mbar_arrive_tx(bar, 0);
     return;

@@ -5,7 +5,8 @@
 // block (the root struct, each non-empty array, each non-empty child-struct
 // array) with the pointer slot that refers to it.  The blocks are then laid out
 // in lanes (all struct blocks first, then one lane per ARRAY field), each block
-// on a 16-byte boundary, which fixes the arena and the relocation table.
+// on a 16-byte boundary (small arrays closer with DC_PLAN_PACK_SMALL), which
+// fixes the arena and the relocation table.
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
@@ -270,6 +271,104 @@ struct Walker {
 
 }  // namespace
 
+// Block offsets and the relocation tables (the second half of dc_plan; run
+// again by dc_plan_set_flags when DC_PLAN_PACK_SMALL changes).  Lanes follow
+// each other in the arena, each starting on 16 bytes; every block starts on 16
+// bytes, except that with DC_PLAN_PACK_SMALL an array block of fewer than
+// DC_PACK_BYTES bytes starts at the next multiple of its element alignment (8
+// bytes for f64, else 4): arrays of a few elements then lie back to back.  The
+// relocation records hold offsets in units of the smallest block alignment: 16
+// bytes, or 4 with packing.
+dc_status layout(dc_plan_s* p) {
+  const bool pack = (p->flags & DC_PLAN_PACK_SMALL) != 0;
+  const uint32_t shift = pack ? 2 : 4, unit = 1u << shift;
+  p->unit_shift = shift;
+  const uint64_t nb = p->blocks.size();
+  const uint32_t nl = p->schema.nlanes;
+  const std::vector<uint64_t>& lane_start = p->lane_start;
+  uint64_t off = 0;
+  for (uint32_t l = 0; l < nl; l++) {
+    off = round_up(off, 16);
+    for (uint64_t i = lane_start[l]; i < lane_start[l + 1]; i++) {
+      HostBlock& b = p->blocks[i];
+      uint64_t al = 16;
+      if (pack && l > 0 && b.bytes < DC_PACK_BYTES)
+        al = p->schema.fields[b.type][b.field].elem_kind == DC_E_F64 ? 8 : 4;
+      off = round_up(off, al);
+      b.off = off;
+      off += b.bytes;
+      if (round_up(b.bytes, unit) >> shift > 0xFFFFFFFFull)
+        return fail(DC_EINVAL, "block of %llu bytes: larger than 2^32 record units", (unsigned long long)b.bytes);
+    }
+  }
+  p->data_bytes = round_up(off, 16);
+  p->struct_bytes = p->nstruct_blocks ? p->blocks[p->nstruct_blocks - 1].off +
+                                            round_up(p->blocks[p->nstruct_blocks - 1].bytes, 16)
+                                      : 0;
+  if (p->struct_bytes / 8 > 0xFFFFFFFFull) return fail(DC_EINVAL, "struct lane larger than 32 GiB");
+
+  Trace phase("dc_plan", "reloc_tables");
+  // Relocation tables: tile t covers the struct-lane bytes [t, t+1) * RELOC_SPAN;
+  // its records are, lane by lane, the consecutive blocks whose slots lie there.
+  const uint64_t ntiles = (p->struct_bytes + RELOC_SPAN - 1) / RELOC_SPAN;
+  const uint64_t nr = p->roots.size();
+  std::vector<uint64_t> cur(lane_start.begin(), lane_start.end() - 1), last(nl, 0);
+  cur[0] += nr;  // the roots are pointed at by no slot
+  auto slot = [&](uint64_t b) { return p->blocks[p->blocks[b].parent].off + p->blocks[b].slot_off; };
+  p->rrec.clear();
+  p->rseg.clear();
+  p->rtiles.clear();
+  p->rec_host.clear();
+  p->rec_off.clear();
+  p->rec_size.clear();
+  p->rec_size.reserve(nb - nr);
+  p->rrec.reserve(nb - nr);
+  p->rec_host.reserve(nb - nr);
+  p->rec_off.reserve(nb - nr);
+  for (uint64_t t = 0; t < ntiles; t++) {
+    const uint32_t tr0 = (uint32_t)p->rrec.size(), tg0 = (uint32_t)p->rseg.size();
+    const uint64_t hi = (t + 1) * RELOC_SPAN;
+    for (uint32_t l = 0; l < nl; l++) {
+      // a record holds its target's offset from the group base in 32 bits of
+      // units: a target 2^32 units or more past the base starts a new group
+      uint64_t base = 0;
+      bool open = false;
+      for (; cur[l] < lane_start[l + 1] && slot(cur[l]) < hi; cur[l]++) {
+        const HostBlock& b = p->blocks[cur[l]];
+        const uint64_t sl = slot(cur[l]);
+        if (b.parent == NONE || sl < last[l] || sl % 8)
+          return fail(DC_EINVAL, "internal: lane %u is not in slot order at block %llu", l,
+                      (unsigned long long)cur[l]);
+        last[l] = sl + 8;
+        const uint64_t u = b.off >> shift;
+        if (!open || u - base > 0xFFFFFFFFull) {
+          base = u;
+          open = true;
+          p->rseg.push_back(RelocSeg{base, (uint32_t)p->rrec.size(), 0});
+        }
+        const uint64_t g = p->rseg.size() - 1 - tg0;  // checked against RELOC_MAXGROUPS below
+        const uint64_t w = (sl - t * RELOC_SPAN) / 8;  // < RELOC_MAXREC
+        p->rrec.push_back(RelocRec{(uint32_t)(u - base), (uint32_t)(w | std::min<uint64_t>(g, 0xFFFF) << 16)});
+        p->rec_host.push_back((uint64_t)(uintptr_t)b.host);
+        p->rec_off.push_back(b.off);
+        // the scan form's size: the distance to the next block of the lane (the
+        // block's bytes and the padding after it), < 2^32 units (checked above)
+        const uint64_t next = cur[l] + 1 < lane_start[l + 1] ? p->blocks[cur[l] + 1].off : round_up(b.off + b.bytes, unit);
+        p->rec_size.push_back((uint32_t)((next - b.off) >> shift));
+      }
+    }
+    if (p->rseg.size() - tg0 > RELOC_MAXGROUPS)
+      return fail(DC_EINVAL, "relocation tile %llu needs more than %u lane groups", (unsigned long long)t,
+                  RELOC_MAXGROUPS);
+    const uint32_t nrt = (uint32_t)p->rrec.size() - tr0, ngt = (uint32_t)p->rseg.size() - tg0;
+    if (nrt) p->rtiles.push_back(RelocTile{(uint32_t)t, tr0, tg0, nrt | ngt << 16});
+  }
+  p->rseg.push_back(RelocSeg{0, (uint32_t)p->rrec.size(), 0});
+  for (uint32_t l = 0; l < nl; l++)
+    if (cur[l] != lane_start[l + 1]) return fail(DC_EINVAL, "internal: lane %u has slots outside the struct lane", l);
+  return DC_OK;
+}
+
 dc_status build_plan(const dc_schema* schema, const void* const* roots, uint64_t nroots, dc_plan_s* p) {
   if (!roots || nroots == 0) return fail(DC_EINVAL, "no root");
   dc_status st = copy_schema(schema, &p->schema);
@@ -346,16 +445,13 @@ dc_status build_plan(const dc_schema* schema, const void* const* roots, uint64_t
   std::vector<uint32_t> new_id(nb);
   for (uint32_t l = 0; l < nl; l++)
     for (size_t j = 0; j < lanes[l].size(); j++) new_id[lanes[l][j]] = (uint32_t)(lane_start[l] + j);
-  // gather the blocks in arena order, each at the next 16-byte boundary
+  // gather the blocks in arena order
   p->blocks.clear();
   p->blocks.reserve(nb);
-  uint64_t off = 0;
   for (uint32_t l = 0; l < nl; l++)
     for (uint32_t old : lanes[l]) {
       HostBlock b = E[old];
       if (b.parent != NONE) b.parent = new_id[b.parent];
-      b.off = off;
-      off += round_up(b.bytes, 16);
       p->blocks.push_back(b);
     }
   lanes.clear();
@@ -363,67 +459,11 @@ dc_status build_plan(const dc_schema* schema, const void* const* roots, uint64_t
     if (t != NONE) t = new_id[t];
   p->roots.clear();
   for (uint32_t r : root_ids) p->roots.push_back(new_id[r]);
-  p->data_bytes = off;
-  p->struct_bytes = p->nstruct_blocks ? p->blocks[p->nstruct_blocks - 1].off +
-                                            round_up(p->blocks[p->nstruct_blocks - 1].bytes, 16)
-                                      : 0;
-  if (p->struct_bytes / 8 > 0xFFFFFFFFull) return fail(DC_EINVAL, "struct lane larger than 32 GiB");
-
-  phase.emplace("dc_plan", "reloc_tables");
-  // Relocation tables: tile t covers the struct-lane bytes [t, t+1) * RELOC_SPAN;
-  // its records are, lane by lane, the consecutive blocks whose slots lie there.
-  const uint64_t ntiles = (p->struct_bytes + RELOC_SPAN - 1) / RELOC_SPAN;
-  const uint64_t nr = p->roots.size();
-  std::vector<uint64_t> cur(lane_start.begin(), lane_start.end() - 1), last(nl, 0);
-  cur[0] += nr;  // the roots are pointed at by no slot
-  auto slot = [&](uint64_t b) { return p->blocks[p->blocks[b].parent].off + p->blocks[b].slot_off; };
-  p->rrec.clear();
-  p->rseg.clear();
-  p->rtiles.clear();
-  p->rec_host.clear();
-  p->rec_off.clear();
-  p->rec_size16.clear();
-  p->rec_size16.reserve(nb - nr);
-  p->rrec.reserve(nb - nr);
-  p->rec_host.reserve(nb - nr);
-  p->rec_off.reserve(nb - nr);
-  for (uint64_t t = 0; t < ntiles; t++) {
-    const uint32_t tr0 = (uint32_t)p->rrec.size(), tg0 = (uint32_t)p->rseg.size();
-    const uint64_t hi = (t + 1) * RELOC_SPAN;
-    for (uint32_t l = 0; l < nl; l++) {
-      // a record holds its target's offset from the group base in 32 bits: a
-      // target 2^32 units or more past the base starts a new group
-      uint64_t base16 = 0;
-      bool open = false;
-      for (; cur[l] < lane_start[l + 1] && slot(cur[l]) < hi; cur[l]++) {
-        const HostBlock& b = p->blocks[cur[l]];
-        const uint64_t sl = slot(cur[l]);
-        if (b.parent == NONE || sl < last[l] || sl % 8)
-          return fail(DC_EINVAL, "internal: lane %u is not in slot order at block %llu", l,
-                      (unsigned long long)cur[l]);
-        last[l] = sl + 8;
-        if (!open || b.off / 16 - base16 > 0xFFFFFFFFull) {
-          base16 = b.off / 16;
-          open = true;
-          p->rseg.push_back(RelocSeg{base16, (uint32_t)p->rrec.size(), 0});
-        }
-        const uint64_t g = p->rseg.size() - 1 - tg0;  // checked against RELOC_MAXGROUPS below
-        const uint64_t w = (sl - t * RELOC_SPAN) / 8;  // < RELOC_MAXREC
-        p->rrec.push_back(RelocRec{(uint32_t)(b.off / 16 - base16), (uint32_t)(w | std::min<uint64_t>(g, 0xFFFF) << 16)});
-        p->rec_host.push_back((uint64_t)(uintptr_t)b.host);
-        p->rec_off.push_back(b.off);
-        p->rec_size16.push_back((uint32_t)(round_up(b.bytes, 16) / 16));  // < 2^32: blocks stay below 64 GiB
-      }
-    }
-    if (p->rseg.size() - tg0 > RELOC_MAXGROUPS)
-      return fail(DC_EINVAL, "relocation tile %llu needs more than %u lane groups", (unsigned long long)t,
-                  RELOC_MAXGROUPS);
-    const uint32_t nrt = (uint32_t)p->rrec.size() - tr0, ngt = (uint32_t)p->rseg.size() - tg0;
-    if (nrt) p->rtiles.push_back(RelocTile{(uint32_t)t, tr0, tg0, nrt | ngt << 16});
+  p->lane_start = lane_start;
+  {
+    dc_status st = layout(p);
+    if (st) return st;
   }
-  p->rseg.push_back(RelocSeg{0, (uint32_t)p->rrec.size(), 0});
-  for (uint32_t l = 0; l < nl; l++)
-    if (cur[l] != lane_start[l + 1]) return fail(DC_EINVAL, "internal: lane %u has slots outside the struct lane", l);
   p->null_slots.clear();
   for (auto& ns : w.null_slots) p->null_slots.push_back(p->blocks[new_id[ns.first]].off + ns.second);
   std::sort(p->null_slots.begin(), p->null_slots.end());

@@ -42,11 +42,13 @@ DevLayout make_layout(const dc_plan_s* p) {
   o = align256(o + std::max<uint64_t>(1, p->rtiles.size()) * sizeof(RelocTile));
   L.ctrl = o;
   o = align256(o + CTRL_WORDS * 4);
-  L.seg_cap = std::max<uint64_t>(1, p->nstructs);
+  // one leaf segment per selected struct, or with DC_PLAN_PACK_SMALL up to 8 for an
+  // array off a 16-byte boundary (a head shorter than a vector, or pieces of one)
+  L.seg_cap = std::max<uint64_t>(1, p->nstructs) * ((p->flags & DC_PLAN_PACK_SMALL) ? 8 : 1);
   L.seg = o;
   o = align256(o + L.seg_cap * sizeof(Segment));
   // every segment has at least one 16-byte unit and lives in the data region
-  L.tseg_cap = p->data_bytes / 16 / LEAF_TILE + 2;
+  L.tseg_cap = (p->data_bytes / 16 + L.seg_cap) / LEAF_TILE + 2;
   L.tseg = o;
   o = align256(o + L.tseg_cap * 4);
   L.cseg = o;
@@ -281,7 +283,20 @@ dc_status dc_plan_forest(const dc_schema* schema, const void* const* roots, uint
 
 dc_status dc_plan_set_flags(dc_plan_t p, uint32_t flags) {
   if (!p) return fail(DC_EINVAL, "plan is NULL");
-  p->flags = flags | (debug_on() ? DC_PLAN_VERIFY : 0u);
+  const uint32_t before = p->flags;
+  flags |= debug_on() ? DC_PLAN_VERIFY : 0u;
+  if ((before ^ flags) & DC_PLAN_PACK_SMALL) {  // another layout: offsets and tables again
+    if (p->dev) return fail(DC_ESTATE, "DC_PLAN_PACK_SMALL changes the layout: set it before dc_bind_device");
+    p->flags = flags;
+    dc_status st = layout(p);
+    if (st) {
+      p->flags = before;
+      layout(p);
+      return st;
+    }
+    return DC_OK;
+  }
+  p->flags = flags;
   return DC_OK;
 }
 
@@ -404,7 +419,7 @@ dc_status dc_bind_device(dc_plan_t p, void* dev, uint64_t bytes, dc_stream_t str
   std::vector<RelocRec> size_rec;  // DC_PLAN_DEVICE_SCAN: the same records with sizes for offsets
   if (nrec && p->rec_scan) {
     size_rec.resize(nrec);
-    for (uint64_t i = 0; i < nrec; i++) size_rec[i] = RelocRec{p->rec_size16[i], p->rrec[i].where};
+    for (uint64_t i = 0; i < nrec; i++) size_rec[i] = RelocRec{p->rec_size[i], p->rrec[i].where};
   }
   if (nrec) {
     DC_CUDA(cudaMemcpyAsync(p->dev + p->L.rec, p->rec_scan ? size_rec.data() : p->rrec.data(), nrec * sizeof(RelocRec),
@@ -602,12 +617,41 @@ dc_status dc::build_leaf_table(dc_plan_s* p, const dc_op* op, cudaStream_t s) {
     if (nseg) {  // x (and y) continue the previous segment after at most its padding: one stream
       Segment& g = seg[nseg - 1];
       const uint64_t end = g.x + g.n * esz;
-      if (x >= end && x - end < 16 && (x - g.x) % esz == 0 && (!axpy || y - g.y == x - g.x)) {
+      if (x >= end && x - end < 16 && (x - g.x) % esz == 0 && (!axpy || y - g.y == x - g.x) && g.x % 16 == 0 &&
+          (!axpy || g.y % 16 == 0)) {
         g.n = (x - g.x) / esz + bx.count;
         continue;
       }
     }
-    seg[nseg++] = Segment{x, y, bx.count, 0};
+    // A segment streams in 16-byte vectors from its start, which must lie on 16
+    // bytes (a DC_PLAN_PACK_SMALL arena has arrays that do not): the elements
+    // before the next boundary become a segment of their own, shorter than a
+    // vector, which the kernels update element by element; if x and y are not
+    // on the same side of a boundary, the whole (small) array goes that way.
+    uint64_t n = bx.count, xx = x, yy = y;
+    const uint64_t epu = 16 / esz;
+    if (xx % 16 || (axpy && yy % 16)) {
+      if (!axpy || xx % 16 == yy % 16) {
+        const uint64_t head = std::min<uint64_t>(n, (16 - xx % 16) / esz);
+        if (nseg >= p->L.seg_cap) return fail(DC_EINVAL, "segment table larger than planned");
+        seg[nseg++] = Segment{xx, yy, head, 0};
+        xx += head * esz;
+        yy += axpy ? head * esz : 0;
+        n -= head;
+      } else {
+        for (; n; n -= std::min<uint64_t>(n, epu - 1)) {
+          const uint64_t c = std::min<uint64_t>(n, epu - 1);
+          if (nseg >= p->L.seg_cap) return fail(DC_EINVAL, "segment table larger than planned");
+          seg[nseg++] = Segment{xx, yy, c, 0};
+          xx += c * esz;
+          yy += c * esz;
+        }
+      }
+    }
+    if (n) {
+      if (nseg >= p->L.seg_cap) return fail(DC_EINVAL, "segment table larger than planned");
+      seg[nseg++] = Segment{xx, yy, n, 0};
+    }
   }
   for (uint64_t i = 0; i < nseg; i++) {
     seg[i].ubeg = units;
@@ -664,6 +708,7 @@ RelocArgs dc::reloc_args(const dc_plan_s* p) {
   a.ntiles = (uint32_t)p->L.ntiles;
   a.verify = (p->flags & DC_PLAN_VERIFY) ? 1u : 0u;
   a.scan = p->rec_scan ? 1u : 0u;
+  a.unit_shift = p->unit_shift;
   return a;
 }
 

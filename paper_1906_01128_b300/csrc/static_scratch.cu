@@ -101,6 +101,7 @@ extern "C" dc_status dc_relocate_static(dc_plan_t p, void* dev_data, uint64_t da
   a.ntiles = (uint32_t)ntiles;
   a.verify = 0;
   a.scan = 0;  // the offsets the plan assigned
+  a.unit_shift = p->unit_shift;
   DC_CUDA(launch_relocate(a, cs, sms));
   if (dev_status)
     DC_CUDA(cudaMemcpyAsync(dev_status, s + OFF_CTRL + CTRL_ERR * 4, 4, cudaMemcpyDeviceToDevice, cs));

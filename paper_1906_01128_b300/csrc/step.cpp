@@ -7,8 +7,9 @@
 // and y into the arena and the updated x straight back to the host.  The host
 // -> device and device -> host traffic of the leaf arrays thus overlap on the
 // link instead of following each other.  Needs a DC_PLAN_MAP_HOST plan whose
-// selected arrays start on 16-byte host addresses; otherwise the call runs
-// dc_deep_copy, dc_update_leaves and dc_copy_back in turn (same results).
+// selected arrays start on 16-byte host addresses and on 16 bytes in the arena;
+// otherwise the call runs dc_deep_copy, dc_update_leaves and dc_copy_back in
+// turn (same results).
 //
 // The pass runs in tile groups (up to STEP_GROUPS launches): the host
 // marshals the array pieces that group g+1 reads from the pinned arena and
@@ -38,6 +39,7 @@ dc_status build_step(dc_plan_s* p, const dc_op* op, bool direct, cudaStream_t s)
     mark[k.bx] = 1;
     if (axpy && k.by != NONE) mark[k.by] = 1;
     if ((uintptr_t)p->blocks[k.bx].host % 16 || (axpy && (uintptr_t)p->blocks[k.by].host % 16)) p->step_fused = false;
+    if (p->blocks[k.bx].off % 16 || (axpy && p->blocks[k.by].off % 16)) p->step_fused = false;  // packed arenas
   }
   std::vector<uint32_t> rest, xy, x;
   for (uint32_t b = 0; b < nb; b++) (mark[b] ? xy : rest).push_back(b);

@@ -6,7 +6,9 @@
 // group's base plus the record's offset equal to the plan's own offset of the
 // target block, the slot the record names being the one that points at that
 // block, and the running sum of the records' sizes within each group equal to
-// the record's offset (what the device-scan relocation computes).
+// the record's offset (what the device-scan relocation computes).  With `pack`
+// the plan is laid out again with DC_PLAN_PACK_SMALL (as dc_plan_set_flags does)
+// and every block's alignment is checked against the packing rule.
 #include <cstdio>
 #include <unordered_map>
 
@@ -24,12 +26,35 @@ extern "C" const char* shim_message() { return g_msg; }
 
 // Returns the dc_status of planning, 1000 when a table check fails (message in
 // shim_message()), else 0; out[0..5] = blocks, records, groups, listed tiles, data bytes, struct bytes.
-extern "C" int shim_plan(const dc_schema* schema, const void* const* roots, uint64_t nroots, uint64_t* out) {
+extern "C" int shim_plan(const dc_schema* schema, const void* const* roots, uint64_t nroots, int pack,
+                         uint64_t* out) {
   dc_plan_s* p = new dc_plan_s;
   int st = dc::build_plan(schema, roots, nroots, p);
+  if (!st && pack) {
+    p->flags |= DC_PLAN_PACK_SMALL;
+    st = dc::layout(p);
+  }
   if (st) {
     delete p;
     return st;
+  }
+  const uint32_t shift = p->unit_shift;
+  if (shift != (pack ? 2u : 4u)) {
+    delete p;
+    return bad("record unit", shift, pack);
+  }
+  for (size_t i = 0; i < p->blocks.size(); i++) {  // the layout rule, block by block
+    const dc::HostBlock& b = p->blocks[i];
+    const bool small = pack && b.lane > 0 && b.bytes < DC_PACK_BYTES;
+    const uint64_t al = !small ? 16 : p->schema.fields[b.type][b.field].elem_kind == DC_E_F64 ? 8 : 4;
+    const bool lane_first = i == 0 || p->blocks[i - 1].lane != b.lane;
+    uint64_t want = i ? p->blocks[i - 1].off + p->blocks[i - 1].bytes : 0;  // the previous block's end
+    if (lane_first) want = (want + 15) / 16 * 16;                             // a lane starts on 16 bytes
+    want = (want + al - 1) / al * al;
+    if (b.off != want) {
+      delete p;
+      return bad("block offset breaks the layout rule", i, b.off);
+    }
   }
   out[0] = p->blocks.size();
   out[1] = p->rrec.size();
@@ -58,11 +83,11 @@ extern "C" int shim_plan(const dc_schema* schema, const void* const* roots, uint
       uint64_t prefix = 0;  // the device-scan form: sizes summed from the group's first record
       for (uint32_t i = G.rec_begin; i < p->rseg[g + 1].rec_begin; i++) {
         const dc::RelocRec& R = p->rrec[i];
-        if (prefix != R.off16) {
-          rc = bad("prefix of the group's sizes differs from the record's offset", prefix, R.off16);
+        if (prefix != R.off) {
+          rc = bad("prefix of the group's sizes differs from the record's offset", prefix, R.off);
           break;
         }
-        prefix += p->rec_size16[i];
+        prefix += p->rec_size[i];
         const uint64_t slot = lo + (uint64_t)(R.where & 0xFFFFu) * 8;
         if (slot + 8 > hi) {
           rc = bad("slot outside its tile", slot, T.t);
@@ -72,8 +97,8 @@ extern "C" int shim_plan(const dc_schema* schema, const void* const* roots, uint
           rc = bad("record names another lane group", R.where >> 16, g - T.g0);
           break;
         }
-        if ((G.base16 + R.off16) * 16 != p->rec_off[i]) {
-          rc = bad("base + offset differs from the plan's offset", (G.base16 + R.off16) * 16, p->rec_off[i]);
+        if ((G.base + R.off) << shift != p->rec_off[i]) {
+          rc = bad("base + offset differs from the plan's offset", (G.base + R.off) << shift, p->rec_off[i]);
           break;
         }
         // the slot is the one that points at the block at that offset

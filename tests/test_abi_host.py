@@ -205,6 +205,83 @@ def test_host_model_of_relocation_passes_the_oracle_check():
         t.free()
 
 
+# ---- DC_PLAN_PACK_SMALL: small arrays at their element alignment --------------
+
+PACK = 64  # DC_PACK_BYTES
+
+
+def lane_elem_kinds(schema):
+    """The element kind of each array lane: lane 1 + i is the i-th ARRAY field
+    in (type, field) order, as the plan numbers them."""
+    kinds = [None]
+    for t in schema.types:
+        for f in t.fields:
+            if f.kind == tg.ARRAY:
+                kinds.append(f.elem_kind)
+    return kinds
+
+
+def packed_offsets(schema, blocks):
+    """Offsets under the packing rule, block by block in arena order: every lane
+    starts on 16 bytes; an array block of fewer than 64 bytes starts on 8 bytes
+    (f64) or 4, every other block on 16; blocks follow each other otherwise."""
+    kinds = lane_elem_kinds(schema)
+    offs, end, lane = [], 0, None
+    for b in blocks:
+        if b["lane"] != lane:
+            end, lane = (end + 15) // 16 * 16, b["lane"]
+        al = 16
+        if b["lane"] > 0 and b["bytes"] < PACK:
+            al = 8 if kinds[b["lane"]] == tg.F64 else 4
+        end = (end + al - 1) // al * al
+        offs.append(end)
+        end += b["bytes"]
+    return offs, (end + 15) // 16 * 16
+
+
+def test_packed_layout_closed_form():
+    # 21 nodes of 10 fp32 per array (the pointer-heavy workload's n): the struct
+    # lane holds 32 B per node, each array lane 40 B per node back to back
+    t = tg.node_tree(3, 4, 10, seed=61)
+    n = 21
+    p = dc.Plan(t.schema, t.root, flags=dc.PLAN_PACK_SMALL)
+    r16 = lambda x: (x + 15) // 16 * 16  # noqa: E731
+    assert p.info["data_bytes"] == r16(r16(32 * n + 40 * n) + 40 * n)
+    pos = sorted(b["offset"] for b in p.blocks() if b["lane"] == 1)
+    assert pos == [32 * n + 40 * i for i in range(n)]
+    # the same plan unpacked again: 48-byte slots
+    p.set_flags(0)
+    assert p.info["data_bytes"] == 32 * n + 2 * 48 * n
+    p.destroy()
+    t.free()
+
+
+def test_packed_layout_follows_its_rule_and_relocates():
+    trees = list(trees_for_tests())
+    trees.append(tg.node_tree(4, 5, tg.uniform(0, 30), seed=62))  # arrays on both sides of 64 bytes
+    trees.append(tg.dense_tree(4, 5, 3, seed=63))  # 40-byte f64 arrays
+    rng = random.Random(64)
+    for i in range(60):
+        s, levels, rules = tg.random_schema(rng)
+        trees.append(tg.Tree(s, levels, rules, seed=3000 + i))
+    smaller = 0
+    for t in trees:
+        p = dc.Plan(t.schema, t.root, flags=dc.PLAN_PACK_SMALL)
+        blocks = p.blocks()
+        offs, data = packed_offsets(t.schema, blocks)
+        assert [b["offset"] for b in blocks] == offs, t.name
+        assert p.info["data_bytes"] == data, t.name
+        c = oracle.count(t.schema, t.root)
+        assert p.info["data_bytes"] <= (c["padded_bytes"] + 15 * len(lane_elem_kinds(t.schema))) // 16 * 16 + 16
+        smaller += p.info["data_bytes"] < c["padded_bytes"]
+        ok, msg, seen = oracle.check_image(t.schema, t.root, host_image(p, BASE), BASE, pack_below=PACK)
+        assert ok, (t.name, msg)
+        assert (seen["nblocks"], seen["payload_bytes"]) == (c["nblocks"], c["payload_bytes"])
+        p.destroy()
+        t.free()
+    assert smaller >= 5  # arenas with several small arrays in a lane get shorter
+
+
 def test_resolve_offset_agrees_with_an_image_walk():
     rng = random.Random(5)
     t = tg.node_tree(4, 5, tg.uniform(1, 40), seed=11)

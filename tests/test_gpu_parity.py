@@ -26,8 +26,15 @@ def ops_pair(kind=dc.OP_AXPY_HALF, sel=dc.SEL_ALL, type_=0, x=2, y=3, scale=1.0,
             oracle.Op(kind, sel, type_, x, y, scale, list(path)))
 
 
+PACK_BELOW = 64  # DC_PACK_BYTES: a packed plan's small arrays may start on their element alignment
+
+
+def pack_of(plan):
+    return PACK_BELOW if plan.flags & dc.PLAN_PACK_SMALL else 0
+
+
 def image_ok(plan, schema, root_tree):
-    ok, msg, seen = oracle.check_image(schema, root_tree, plan.image(), plan.device_base)
+    ok, msg, seen = oracle.check_image(schema, root_tree, plan.image(), plan.device_base, pack_below=pack_of(plan))
     assert ok, msg
     return seen
 
@@ -419,7 +426,7 @@ def forest_parity(ntrees, t_max, mode, flags=0, seed=4):
         plan.sync()
         img, base = plan.image(), plan.device_base
         for i, t in enumerate(src):  # every tree of the arena is its source's replica
-            ok, msg, _ = oracle.check_image(s, t.root, img, base, plan.root_offset(i))
+            ok, msg, _ = oracle.check_image(s, t.root, img, base, plan.root_offset(i), pack_below=pack_of(plan))
             assert ok, (i, msg)
         if mode == "fused":
             plan.relocate_update(dop)
@@ -729,3 +736,93 @@ def test_selective_deep_copy_of_a_chain(case, flags):
     plan.destroy()
     src.free()
     ref.free()
+
+
+
+# ---- DC_PLAN_PACK_SMALL: arrays below 64 bytes at their element alignment -------------
+
+PACKED_CASES = {
+    # the pointer-heavy tree at full size: 2.2M arrays of 10 fp32 back to back
+    "reloc_stress": (lambda: tg.workload("reloc_stress"), {}),
+    # arrays on both sides of 64 bytes, empty ones, one-element ones
+    "ragged_small": (lambda: tg.node_tree(4, 6, tg.uniform(0, 30), seed=71), {}),
+    "tiny_segments": (lambda: tg.node_tree(5, 12, tg.uniform(1, 9), seed=13), {}),
+    # fp64 arrays below 64 bytes: 8-byte starts
+    "node64_small": (lambda: node64_tree(3, 7, tg.uniform(0, 12), seed=72), {}),
+    # the Dense tree with 5 doubles per level, Listing 2's scaling on the last level
+    "dense_f64_scale": (lambda: tg.dense_tree(4, 5, 3, seed=73), dict(kind=dc.OP_SCALE, type_=3, x=1, scale=1.1)),
+    # one struct's small arrays by a chain: a segment that starts off a 16-byte boundary
+    "chain_small": (lambda: tg.node_tree(4, 6, tg.uniform(1, 20), seed=74),
+                    dict(sel=dc.SEL_CHAIN, path=[(NODE_LEAF, 5), (NODE_LEAF, 2)])),
+}
+
+
+@pytest.mark.parametrize("case", sorted(PACKED_CASES))
+def test_packed_small_arrays(case, monkeypatch):
+    """A packed plan's arena (oracle image check with the packing rule) and
+    every update path on it against the oracle: the bulk-copy leaf kernel
+    (with the device-side slot check), the pointer chase, the device-scan
+    relocation, the persistent fused launch at each CTA size, the round trip
+    (which takes its three-call path) and the direct-load leaf kernel."""
+    make, kw = PACKED_CASES[case]
+    P = dc.PLAN_PACK_SMALL
+    full_parity(make, kw, repeat=2, flags=P, verify=True)
+    full_parity(make, kw, mode="chase", flags=P)
+    full_parity(make, kw, flags=P | dc.PLAN_DEVICE_SCAN)
+    step_parity(make, kw, P | dc.PLAN_MAP_HOST)
+    src, ref = make(), make()
+    s = src.schema
+    plan = dc.Plan(s, src.root, flags=P)
+    plan.bind()
+    dop, oop = ops_pair(**kw)
+    cp = oracle.deep_copy(s, ref.root)
+    plan.deep_copy()
+    for threads in (128, 256, 512):  # each launch relocates again and updates once more
+        plan.set_split(dop, threads, 2)
+        plan.relocate_update(dop)
+        plan.sync()
+        oracle.update(s, cp.root, oop)
+        image_ok(plan, s, cp.root)
+    plan.destroy()
+    src.free()
+    ref.free()
+    monkeypatch.setenv("DC_LEAF_TMA", "0")
+    full_parity(make, kw, flags=P)
+
+
+def test_packed_random_schemas_and_forest():
+    rng = random.Random(7373)
+    for i in range(60):
+        schema, levels, rules = tg.random_schema(rng)
+        full_parity(lambda: tg.Tree(schema, levels, rules, seed=700 + i), None, flags=dc.PLAN_PACK_SMALL)
+    forest_parity(300, 256 << 10, "fused", flags=dc.PLAN_PACK_SMALL)
+
+
+def test_packed_static_relocation_matches_dc_relocate():
+    # dc_relocate_static reads the same unit-scaled tables
+    t = tg.node_tree(4, 16, tg.uniform(1, 40), seed=21)
+    plan = dc.Plan(t.schema, t.root, flags=dc.PLAN_PACK_SMALL)
+    buf = plan.bind()
+    n = plan.info["data_bytes"]
+    img = np.zeros(n, dtype=np.uint8)
+    for b in plan.blocks():
+        if b["bytes"]:
+            img[b["offset"]:b["offset"] + b["bytes"]] = np.frombuffer(ctypes.string_at(b["host"], b["bytes"]),
+                                                                     dtype=np.uint8)
+    image = torch.from_numpy(img).cuda()
+    buf[:n].copy_(image)
+    plan.relocate()
+    plan.sync()
+    want = buf[:n].cpu()
+    ok, msg, _ = oracle.check_image(t.schema, t.root, want.numpy(), buf.data_ptr(), pack_below=PACK_BELOW)
+    assert ok, msg
+    buf[:n].copy_(image)
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    rc = dc.lib.dc_relocate_static(plan._h, buf.data_ptr(), n, status.data_ptr(),
+                                   torch.cuda.current_stream().cuda_stream)
+    assert rc == 0, dc.lib.dc_last_error()
+    torch.cuda.synchronize()
+    assert status.item() == 0
+    assert torch.equal(buf[:n].cpu(), want)
+    plan.destroy()
+    t.free()

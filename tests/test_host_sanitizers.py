@@ -30,14 +30,14 @@ DRIVER = textwrap.dedent(r'''
     from paper_1906_01128_b300 import schema_struct
     lib = ctypes.CDLL(SO)
     lib.shim_plan.restype = ctypes.c_int
-    lib.shim_plan.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]
+    lib.shim_plan.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p]
     lib.shim_message.restype = ctypes.c_char_p
 
-    def plan(schema, roots):
+    def plan(schema, roots, pack=0):
         cs, keep = schema_struct(schema)
         arr = (ctypes.c_void_p * len(roots))(*roots)
         out = (ctypes.c_uint64 * 6)()
-        rc = lib.shim_plan(ctypes.byref(cs), arr, len(roots), out)
+        rc = lib.shim_plan(ctypes.byref(cs), arr, len(roots), pack, out)
         if rc == 1000:
             raise SystemExit("table check: " + lib.shim_message().decode())
         return rc, list(out)
@@ -51,12 +51,14 @@ DRIVER = textwrap.dedent(r'''
         trees.append(tg.Tree(s, levels, rules, seed=2000 + i))
     n = 0
     for t in trees:
-        rc, out = plan(t.schema, [t.root])
-        assert rc == 0, (t.name, rc)
+        for pack in (0, 1):  # 16-byte blocks, and small arrays packed at their element alignment
+            rc, out = plan(t.schema, [t.root], pack)
+            assert rc == 0, (t.name, pack, rc)
         n += out[0]
     forest = tg.batched(40, seed=9, t_max=256 << 10)
-    rc, out = plan(forest[0].schema, [t.root for t in forest])
-    assert rc == 0, rc
+    for pack in (0, 1):
+        rc, out = plan(forest[0].schema, [t.root for t in forest], pack)
+        assert rc == 0, rc
     # targets 64 GiB and more past their lane group's base (reserved address space, never read)
     far = tg.ReservedChain(7, 2 ** 31 - 2)
     rc, out = plan(far.schema, [far.root])
