@@ -249,7 +249,8 @@ __device__ __forceinline__ void issue_tile(const RelocArgs& a, RelocSmem& sm, ui
 // Every listed relocation tile i = blockIdx.x + k * gridDim.x, through a
 // two-stage pipeline: while the CTA rewrites the slots of one staged tile,
 // the bulk copies of the next are in flight, and the producer has the header
-// after that in a register.  A slot's target lies at its lane group's base
+// after that in a register.  A stage is refilled one step after its store,
+// just after the next stage's wait.  A slot's target lies at its lane group's base
 // plus its offset in the group (both in record units): the record's own
 // offset, or with DC_PLAN_DEVICE_SCAN a prefix sum of the records' sizes.  The
 // rewritten staged tile goes back by one bulk store.  The loop's exits are
@@ -279,6 +280,7 @@ __device__ __forceinline__ void reloc_tiles(const RelocArgs& a, RelocSmem& sm) {
     if (in != NONE) hn = __ldg(hdrs + in);
   }
   const uint64_t base = reinterpret_cast<uint64_t>(a.arena);
+  uint32_t pend = NONE;  // (producer) the stage stored at the end of the last step, not yet refilled
   for (uint32_t k = 0;; k++) {
     const uint32_t s = k % RSTAGES, parity = (k / RSTAGES) & 1;
     const bool late = !mbar_wait(&sm.bar[s], parity, a.wait_limit);
@@ -287,10 +289,24 @@ __device__ __forceinline__ void reloc_tiles(const RelocArgs& a, RelocSmem& sm) {
         atomicOr(err, ERR_TIMEOUT);
         for (uint32_t q = 0; q < RSTAGES; q++) {
           const uint32_t kq = k + q;
-          mbar_wait(&sm.bar[kq % RSTAGES], (kq / RSTAGES) & 1, WAIT_LIMIT);
+          if (kq % RSTAGES != pend) mbar_wait(&sm.bar[kq % RSTAGES], (kq / RSTAGES) & 1, WAIT_LIMIT);
         }
       }
       break;
+    }
+    // The stage stored at the end of the last step is refilled here, once every
+    // thread has seen this step's stage complete: its bulk store has had the
+    // whole wait to read it, so the producer rarely waits here, and the other
+    // warps no longer wait for the store and the refill at a barrier.
+    if (tid == 0 && pend != NONE) {
+      bulk_wait_read();
+      issue_tile(a, sm, pend, in, hn);
+      if (in != NONE) {
+        in += gridDim.x;
+        in = in < a.ntiles ? in : NONE;
+        if (in != NONE) hn = __ldg(hdrs + in);  // used at the next refill
+      }
+      pend = NONE;
     }
     const uint4 h = sm.hdr[s];
     if (h.x == NONE) break;  // uniform: every thread reads the same header
@@ -307,16 +323,8 @@ __device__ __forceinline__ void reloc_tiles(const RelocArgs& a, RelocSmem& sm) {
     }
     __syncthreads();  // nobody reads stage s any more
     if (tid == 0) {
-      if (nr) {
-        bulk_store(a.arena + lo, S.img, (uint32_t)(hi - lo));
-        bulk_wait_read();  // the store has read stage s: refill it
-      }
-      issue_tile(a, sm, s, in, hn);
-      if (in != NONE) {
-        in += gridDim.x;
-        in = in < a.ntiles ? in : NONE;
-        if (in != NONE) hn = __ldg(hdrs + in);  // used at the next refill
-      }
+      if (nr) bulk_store(a.arena + lo, S.img, (uint32_t)(hi - lo));
+      pend = s;  // refilled after the next step's wait
     }
   }
   if (tid == 0) bulk_wait_all();
