@@ -164,13 +164,15 @@ typedef struct {
                              caller that starts inside such a page range and runs past
                              its end fails. */
 #define DC_MAP_MIN_BYTES (64u << 10)
-#define DC_PLAN_DEVICE_SCAN 4u /* the relocation computes every target's arena offset on
-                             the device: its records carry the targets' padded sizes,
-                             and warp-shuffle prefix sums over them, added to each lane
-                             group's base, give the offsets.  Without it (the default)
-                             the records carry the offsets the plan's layout assigned,
-                             which is faster; the device image is the same.  Read at
-                             dc_bind_device; dc_relocate_static ignores it. */
+#define DC_PLAN_DEVICE_SCAN 4u /* the relocation computes the targets' arena offsets on
+                             the device from their padded sizes: a tile's records are
+                             cut into slices of 32, each slice's first record carries
+                             its own offset, the others the size of the record before
+                             them, and one segmented warp-shuffle prefix sum per slice,
+                             added to each lane group's base, gives the offsets.
+                             Without it (the default) every record carries the offset
+                             the plan's layout assigned; the device image is the same.
+                             Read at dc_bind_device; dc_relocate_static ignores it. */
 #define DC_PLAN_PACK_SMALL 8u /* lay array blocks of fewer than DC_PACK_BYTES bytes out
                              at their element alignment (8 bytes for f64, else 4)
                              instead of on 16 bytes, so that many small arrays lie

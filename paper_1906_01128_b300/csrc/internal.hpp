@@ -52,14 +52,23 @@ const char* last_error();
 // Offsets in the relocation tables are in record units: 16 bytes, or 4 bytes
 // for DC_PLAN_PACK_SMALL plans (the plan's unit_shift: 4 or 2).
 // One pointer slot: the target block's arena offset in units relative to its
-// lane group's base (or, DC_PLAN_DEVICE_SCAN, the target's size in units), and
-// where the slot is: its 8-byte word within the tile (low 16 bits) and its lane
-// group's index within the tile (high 16 bits).
+// lane group's base (DC_PLAN_DEVICE_SCAN records, below, hold sizes instead),
+// and where the slot is: its 8-byte word within the tile (low 16 bits) and its
+// lane group's index within the tile (high 16 bits).
 struct RelocRec {
   uint32_t off;
   uint32_t where;
 };
 static_assert(sizeof(RelocRec) == 8, "RelocRec is 8 bytes");
+// DC_PLAN_DEVICE_SCAN records.  A tile's records are cut into slices of 32
+// (tile-relative indexes 32k .. 32k + 31), one warp scan each.  A record that
+// starts a slice or a lane group is a head: `off` holds its own offset from
+// the group's base (0 at a group's first record) and `where` has SCAN_HEAD
+// set; any other record holds the size in units of the record before it (the
+// units from that target to the next block of the lane).  A target's offset is
+// then the sum of `off` from its segment's head to itself.
+constexpr uint32_t SCAN_HEAD = 0x8000u;  // above the slot word (< 1024, one per 8 bytes of a tile)
+constexpr uint32_t SCAN_SLICE = 32;
 // One (tile, lane) group: the arena offset in units of its first target block
 // and the index of its first record; the plan starts a new group where a target
 // lies 2^32 units or more past the base.  The table ends with a group whose
@@ -362,6 +371,8 @@ struct dc_uvm_s {
 namespace dc {
 // Block offsets and relocation tables from the blocks in lane order (plan.cpp).
 dc_status layout(dc_plan_s* p);
+// The DC_PLAN_DEVICE_SCAN form of the plan's records (plan.cpp), one per record into `out`.
+void scan_records(const dc_plan_s* p, RelocRec* out);
 dc_status build_plan(const dc_schema* schema, const void* const* roots, uint64_t nroots, dc_plan_s* p);
 // Resolve a chain over the plan tables to (block, byte offset in block, type
 // of the struct reached or NONE when the last step was an ARRAY step, element).

@@ -149,66 +149,40 @@ __device__ __forceinline__ void reloc_apply_offsets(const RelocArgs& a, RelocSta
   }
 }
 
-// One staged tile's slots from size records (DC_PLAN_DEVICE_SCAN): a target's
-// offset is its lane group's base plus the exclusive prefix of the sizes before
-// it in its group (a record's size: the units from its target to the next block
-// of the lane).  The records are warp-striped (warp w owns a
-// contiguous run of 32 x ITEMS records, its lane L record 32k + L); warp-shuffle
-// scans run slice by slice inside each warp, then over the warps' totals.  The
-// prefixes are 32-bit: a group's offsets stay below 2^32 units (the plan starts
-// a new group otherwise), so a difference of two prefixes modulo 2^32 is exact.
-// Every thread reaches both barriers (the call is uniform across the CTA).  Its
-// shared arrays exist only in the kernels built with this form.
+// One staged tile's slots from scan records (DC_PLAN_DEVICE_SCAN): the
+// records are cut into slices of 32, slice k to warp k % NW, and each warp
+// scans its slice with shuffles, segmented at the heads (a slice's first
+// record, and a lane group's first).  A head holds its own offset from its
+// group's base; any other record holds the size of the record before it, so a
+// target's offset is the sum from its segment's head to itself: the inclusive
+// prefix minus the exclusive prefix at the head (32-bit: a group's offsets stay
+// below 2^32 units, so the difference is exact modulo 2^32).  The slices are
+// independent, so the tile needs no barrier beyond the offset form's, and
+// record j goes to thread j % THREADS as there.
 template <uint32_t THREADS, bool VERIFY>
 __device__ __forceinline__ void reloc_apply_scan(const RelocArgs& a, RelocStage& S, uint32_t r0, uint32_t nr,
                                                  uint32_t ng, uint32_t sh, uint32_t n8, uint64_t base) {
   constexpr uint32_t NW = THREADS / 32, ITEMS = RELOC_MAXREC / THREADS;
-  // per lane group: its base offset in units (x, y) and minus the size prefix at its
-  // first record (z); per warp: its records' size total
-  __shared__ uint4 gb[RELOC_MAXGROUPS];
-  __shared__ uint32_t warp_sum[32];
-  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, wb = warp * 32 * ITEMS;
-  uint2 r[ITEMS];
-#pragma unroll
-  for (uint32_t i = 0; i < ITEMS; i++) {
-    const uint32_t j = wb + i * 32 + lane;
-    r[i] = j < nr ? S.rec[sh + j] : make_uint2(0, 0);
-  }
-  uint32_t ex[ITEMS];
-  uint32_t carry = 0;
-#pragma unroll
-  for (uint32_t i = 0; i < ITEMS; i++) {
-    const uint32_t incl = warp_incl_scan32(r[i].x, lane);
-    ex[i] = carry + incl - r[i].x;
-    carry += __shfl_sync(0xffffffffu, incl, 31);
-  }
-  if (lane == 0) warp_sum[warp] = carry;
-  __syncthreads();
-  uint32_t wt = lane < NW ? warp_sum[lane] : 0u;
-  wt = warp_incl_scan32(wt, lane);
-  const uint32_t wpre = warp ? __shfl_sync(0xffffffffu, wt, (warp - 1) & 31) : 0u;
-#pragma unroll
-  for (uint32_t i = 0; i < ITEMS; i++) {
-    ex[i] += wpre;
-    const uint32_t j = wb + i * 32 + lane, g = r[i].y >> 16;
-    if (j < nr && g < ng && S.grp[g].rec_begin - r0 == j) {  // the group's first record
-      const uint64_t gbase = S.grp[g].base;
-      gb[g] = make_uint4((uint32_t)gbase, (uint32_t)(gbase >> 32), 0u - ex[i], 0u);
-    }
-  }
-  __syncthreads();  // every group's base and start prefix are in shared memory
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint64_t* img64 = reinterpret_cast<uint64_t*>(S.img);
 #pragma unroll
   for (uint32_t i = 0; i < ITEMS; i++) {
-    const uint32_t j = wb + i * 32 + lane;
+    const uint32_t j0 = (i * NW + warp) * 32;  // the slice's first record
+    if (j0 >= nr) break;                        // uniform across the warp
+    const uint32_t j = j0 + lane;
+    const uint2 rr = j < nr ? S.rec[sh + j] : make_uint2(0, 0);
+    // lane 0 starts the slice: a head whatever its record says
+    const uint32_t heads = __ballot_sync(0xffffffffu, (rr.y & SCAN_HEAD) != 0) | 1u;
+    const uint32_t incl = warp_incl_scan32(rr.x, lane);
+    const uint32_t head = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));  // the last head at or below
+    const uint32_t off32 = incl - __shfl_sync(0xffffffffu, incl - rr.x, head);
     if (j >= nr) continue;
-    const uint32_t w = r[i].y & 0xFFFFu, g = r[i].y >> 16;
+    const uint32_t w = rr.y & (SCAN_HEAD - 1), g = rr.y >> 16;
     if (w >= n8 || g >= ng) {
       atomicOr(&a.ctrl[CTRL_ERR], ERR_BOUNDS);
       continue;
     }
-    const uint4 G = gb[g];
-    const uint64_t off = ((((uint64_t)G.y << 32) | G.x) + (uint32_t)(ex[i] + G.z)) << a.unit_shift;
+    const uint64_t off = (S.grp[g].base + off32) << a.unit_shift;
     uint64_t* sp = img64 + w;
     if (VERIFY) {
       const uint32_t ri = r0 + j;

@@ -369,6 +369,17 @@ dc_status layout(dc_plan_s* p) {
   return DC_OK;
 }
 
+void scan_records(const dc_plan_s* p, RelocRec* out) {
+  for (const RelocTile& T : p->rtiles) {
+    const uint32_t ng = T.counts >> 16;
+    for (uint32_t g = T.g0; g < T.g0 + ng; g++)
+      for (uint32_t i = p->rseg[g].rec_begin; i < p->rseg[g + 1].rec_begin; i++) {
+        const bool head = (i - T.r0) % SCAN_SLICE == 0 || i == p->rseg[g].rec_begin;
+        out[i] = head ? RelocRec{p->rrec[i].off, p->rrec[i].where | SCAN_HEAD} : RelocRec{p->rec_size[i - 1], p->rrec[i].where};
+      }
+  }
+}
+
 dc_status build_plan(const dc_schema* schema, const void* const* roots, uint64_t nroots, dc_plan_s* p) {
   if (!roots || nroots == 0) return fail(DC_EINVAL, "no root");
   dc_status st = copy_schema(schema, &p->schema);

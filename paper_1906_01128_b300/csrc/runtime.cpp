@@ -416,10 +416,10 @@ dc_status dc_bind_device(dc_plan_t p, void* dev, uint64_t bytes, dc_stream_t str
   p->dev_bytes = bytes;
   const uint64_t nrec = p->rrec.size();
   p->rec_scan = (p->flags & DC_PLAN_DEVICE_SCAN) != 0;
-  std::vector<RelocRec> size_rec;  // DC_PLAN_DEVICE_SCAN: the same records with sizes for offsets
+  std::vector<RelocRec> size_rec;  // DC_PLAN_DEVICE_SCAN: slice heads' offsets and sizes
   if (nrec && p->rec_scan) {
     size_rec.resize(nrec);
-    for (uint64_t i = 0; i < nrec; i++) size_rec[i] = RelocRec{p->rec_size[i], p->rrec[i].where};
+    scan_records(p, size_rec.data());
   }
   if (nrec) {
     DC_CUDA(cudaMemcpyAsync(p->dev + p->L.rec, p->rec_scan ? size_rec.data() : p->rrec.data(), nrec * sizeof(RelocRec),

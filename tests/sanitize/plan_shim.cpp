@@ -5,12 +5,15 @@
 // every slot inside its tile, each record in the lane group it names, each
 // group's base plus the record's offset equal to the plan's own offset of the
 // target block, the slot the record names being the one that points at that
-// block, and the running sum of the records' sizes within each group equal to
-// the record's offset (what the device-scan relocation computes).  With `pack`
+// block, the running sum of the records' sizes within each group equal to the
+// record's offset, and the device-scan records (slice heads with offsets, the
+// rest with their predecessors' sizes), summed per slice from each head as the
+// device-scan relocation does, equal to the same offsets.  With `pack`
 // the plan is laid out again with DC_PLAN_PACK_SMALL (as dc_plan_set_flags does)
 // and every block's alignment is checked against the packing rule.
 #include <cstdio>
 #include <unordered_map>
+#include <vector>
 
 #include "internal.hpp"
 
@@ -113,6 +116,29 @@ extern "C" int shim_plan(const dc_schema* schema, const void* const* roots, uint
     if (rc) break;
   }
   if (!rc && seen != p->rrec.size()) rc = bad("records outside every tile", seen, p->rrec.size());
+  // The device-scan records, summed the way the kernel does (per tile, slices of
+  // 32 records, each sum restarting at a head), give back every record's offset.
+  std::vector<dc::RelocRec> sr(p->rrec.size());
+  if (!rc) dc::scan_records(p, sr.data());
+  for (const dc::RelocTile& T : p->rtiles) {
+    if (rc) break;
+    const uint32_t nr = T.counts & 0xFFFFu;
+    uint32_t sum = 0;
+    for (uint32_t j = 0; j < nr; j++) {
+      const dc::RelocRec& R = sr[T.r0 + j];
+      const bool head = (R.where & dc::SCAN_HEAD) != 0;
+      if ((j % dc::SCAN_SLICE == 0) != (head && j % dc::SCAN_SLICE == 0) ||
+          (R.where & ~dc::SCAN_HEAD) != p->rrec[T.r0 + j].where) {
+        rc = bad("scan record's head flag or slot word", T.r0 + j, R.where);
+        break;
+      }
+      sum = head ? R.off : sum + R.off;
+      if (sum != p->rrec[T.r0 + j].off) {
+        rc = bad("the scan records' segmented sum differs from the record's offset", sum, p->rrec[T.r0 + j].off);
+        break;
+      }
+    }
+  }
   delete p;
   return rc;
 }

@@ -139,13 +139,45 @@ def test_direct_load_leaf_kernel(case, monkeypatch):
 
 
 def test_device_scan_relocation():
-    """DC_PLAN_DEVICE_SCAN: the relocation derives every offset from the targets'
-    sizes with warp-shuffle prefix sums; the device image and the results are
+    """DC_PLAN_DEVICE_SCAN: the relocation derives the offsets from the targets'
+    sizes with segmented warp-shuffle prefix sums; the device image and the results are
     the oracle's, as with the default offset records (dense: two tiles; a
     ragged tree of ~13,000 blocks: 18 tiles and lane groups of uneven runs)."""
     full_parity(lambda: tg.workload("dense"), {}, flags=dc.PLAN_DEVICE_SCAN)
     full_parity(lambda: tg.node_tree(4, 16, tg.uniform(1, 40), seed=21), {}, verify=True,
                 flags=dc.PLAN_DEVICE_SCAN)
+
+
+def test_device_scan_random_schemas():
+    """Scan records on random schemas (several array and child lanes per struct):
+    lane groups start at every position of a 32-record slice, so the warp scans'
+    segments begin mid-slice; the device-side slot check compares every offset."""
+    rng = random.Random(5151)
+    for i in range(40):
+        schema, levels, rules = tg.random_schema(rng)
+        full_parity(lambda: tg.Tree(schema, levels, rules, seed=900 + i), None, verify=True,
+                    flags=dc.PLAN_DEVICE_SCAN)
+
+
+@pytest.mark.parametrize("threads", [128, 256, 512])
+def test_device_scan_fused_launch_each_cta_size(threads):
+    # the scan form inside the persistent launch: 4, 8 and 16 warps share a tile's slices
+    src, ref = tg.node_tree(4, 16, tg.uniform(1, 40), seed=21), tg.node_tree(4, 16, tg.uniform(1, 40), seed=21)
+    s = src.schema
+    plan = dc.Plan(s, src.root, flags=dc.PLAN_DEVICE_SCAN)
+    plan.bind()
+    dop, oop = ops_pair()
+    cp = oracle.deep_copy(s, ref.root)
+    plan.deep_copy()
+    plan.set_split(dop, threads, 2)
+    for _ in range(2):  # each launch relocates again and updates once more
+        plan.relocate_update(dop)
+        plan.sync()
+        oracle.update(s, cp.root, oop)
+        image_ok(plan, s, cp.root)
+    plan.destroy()
+    src.free()
+    ref.free()
 
 
 def test_reloc_stress_device_scan():
