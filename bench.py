@@ -944,7 +944,8 @@ def main():
     # the same step as two launches: each kernel on its own
     t_reloc, t_leaf = timed_loop([plan.relocate, lambda: plan.update(op)], "dc_two_launch_step")
     plan.sync()
-    # the same relocation with size records: offsets from warp-shuffle prefix sums on the device
+    # the same relocation with scan records: offsets from segmented warp-shuffle prefix sums of the
+    # targets' sizes on the device, one per 32-record slice
     plan_scan = dc.Plan(s, tree.root, flags=dc.PLAN_DEVICE_SCAN)
     plan_scan.bind()
     plan_scan.deep_copy()
@@ -1214,7 +1215,7 @@ def main():
                                "batched_frac": round(reloc_bytes / reloc_batch["offset"] / 1e9 / hbm, 4),
                                "batched_copies": reloc_batch["copies"]} if reloc_batch else {})},
             "relocation_device_scan": {
-                "kernel": "relocate_kernel, DC_PLAN_DEVICE_SCAN (offsets from prefix sums of the targets' sizes)",
+                "kernel": "relocate_kernel, DC_PLAN_DEVICE_SCAN (offsets from segmented warp prefix sums of the targets' sizes, one per 32-record slice seeded with its first offset)",
                 "avg_launch_us": round(statistics.mean(t_reloc_scan) * 1e6, 2),
                 "median_launch_us": round(statistics.median(t_reloc_scan) * 1e6, 2),
                 "frac": round(reloc_bytes / statistics.mean(t_reloc_scan) / 1e9 / hbm, 4),

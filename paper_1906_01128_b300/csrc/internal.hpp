@@ -276,7 +276,7 @@ struct dc_plan_s {
   std::vector<uint32_t> rec_size;        // per record: units to the next block of the lane (DC_PLAN_DEVICE_SCAN)
   std::vector<uint64_t> lane_start;      // lane l's blocks are [lane_start[l], lane_start[l+1])
   uint32_t unit_shift = 4;               // the tables' units: 16 bytes, or 4 with DC_PLAN_PACK_SMALL
-  bool rec_scan = false;                 // the bound buffer holds size records
+  bool rec_scan = false;                 // the bound buffer holds scan records (DC_PLAN_DEVICE_SCAN)
   uint64_t struct_bytes = 0;             // bytes of the struct lane (lane 0)
   std::vector<uint64_t> null_slots;      // arena offsets of slots with count 0 but a non-NULL host value
   std::vector<uint32_t> roots;           // arena index of each tree's root struct block

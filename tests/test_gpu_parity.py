@@ -503,7 +503,7 @@ def test_forest_of_uneven_trees(mode):
 
 @pytest.mark.parametrize("mode", ["fused", "split-128-1"])
 def test_forest_fused_launch_with_device_scan(mode):
-    # the persistent relocation + update launch with size records
+    # the persistent relocation + update launch with scan records
     forest_parity(300, 256 << 10, mode, flags=dc.PLAN_DEVICE_SCAN)
 
 
