@@ -413,6 +413,51 @@ def relocation_batches(torch, dc, schema, root, info, steps, barrier):
     return out
 
 
+def pointer_heavy_relocation(torch, dc, tg, steps, warmup, flush, barrier, hbm):
+    """relocate_kernel on the pointer-heavy tree (1,118,481 nodes, 2,306,867 slots in 4,370 tiles),
+    offset records and device scan, for the default line: CUDA events around single launches, each
+    after the L2 flush (outside the events), and back-to-back launches over copies of the arena
+    (relocation_batches).  The tree is the reloc_stress workload's."""
+    t = tg.workload("reloc_stress")
+    out = {"workload": WORKLOADS["reloc_stress"]}
+    info = None
+    for name, flags in (("offset", 0), ("device_scan", dc.PLAN_DEVICE_SCAN)):
+        p = dc.Plan(t.schema, t.root, flags=flags)
+        p.bind()
+        p.deep_copy()
+        p.sync()
+        info = p.info
+        nbytes = info["nrelocs"] * 20 + info["nblocks"] * 16
+        for _ in range(warmup):
+            flush()
+            p.relocate()
+        barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        queue_ahead(torch, 1000 + 500 * steps)
+        for e0, e1 in ev:
+            flush()
+            e0.record()
+            p.relocate()
+            e1.record()
+        torch.cuda.synchronize()
+        ts = [e0.elapsed_time(e1) * 1e-3 for e0, e1 in ev]
+        p.sync()
+        p.destroy()
+        avg = statistics.mean(ts)
+        out[name] = {"avg_launch_us": round(avg * 1e6, 2), "median_launch_us": round(statistics.median(ts) * 1e6, 2),
+                     "achieved_gbs": round(nbytes / avg / 1e9, 1), "frac": round(nbytes / avg / 1e9 / hbm, 4)}
+    out["algorithmic_bytes"] = nbytes
+    out["bytes_moved"] = info["reloc_table_bytes"] + 2 * info["struct_bytes"]
+    rb = relocation_batches(torch, dc, t.schema, t.root, info, steps, barrier)
+    if rb:
+        for name in ("offset", "device_scan"):
+            out[name]["batched_us"] = round(rb[name] * 1e6, 2)
+            out[name]["batched_frac"] = round(nbytes / rb[name] / 1e9 / hbm, 4)
+        out["batched_copies"] = rb["copies"]
+    t.free()
+    return out
+
+
 def link_peaks(torch, nbytes=256 << 20, reps=5):
     """Pinned cudaMemcpyAsync peaks: each direction alone (best of `reps` at 256 MiB), both
     directions at once on two streams (an H2D of 2x and a D2H of 1x the bytes, the round trip's
@@ -840,6 +885,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batched", action="store_true", help="default line: skip the batched summary")
     ap.add_argument("--no-served", action="store_true", help="default line: skip the served summary")
+    ap.add_argument("--no-pointer-heavy", action="store_true",
+                    help="default line: skip the relocation of the pointer-heavy tree")
     ap.add_argument("--split", default="", help="THREADS,CTAS_PER_SM for the fused step (dc_set_split) instead "
                     "of dc_autotune, e.g. 256,4: repeats a launch shape, as for an ncu capture")
     args = ap.parse_args()
@@ -976,6 +1023,11 @@ def main():
     # pair around the batch: a launch of a few microseconds is below the event timer's
     # resolution on its own (single-launch times come in steps of about 2 us).
     reloc_batch = relocation_batches(torch, dc, s, tree.root, info, args.steps, barrier)
+    # the default workload's relocation is a few hundred slots (launch-bound): its line also
+    # carries the relocation of the pointer-heavy tree
+    heavy = None
+    if args.workload == "dense" and not args.no_pointer_heavy:
+        heavy = pointer_heavy_relocation(torch, dc, tg, args.steps, args.warmup, flush, barrier, peaks()[0])
 
     # ---- the headline: the deep copy on the default plan (marshal, H2D, relocation) ----
     for _ in range(args.warmup):
@@ -1222,6 +1274,7 @@ def main():
                 **({"batched_us": round(reloc_batch["device_scan"] * 1e6, 2),
                     "batched_frac": round(reloc_bytes / reloc_batch["device_scan"] / 1e9 / hbm, 4)}
                    if reloc_batch else {})},
+            "relocation_pointer_heavy": heavy,
             "packed": packed and {**packed,
                                   "step_frac": round(fused_bytes / (packed["step_avg_us"] * 1e-6) / 1e9 / hbm, 4),
                                   "leaf_frac": round(leaf_bytes / (packed["leaf_avg_us"] * 1e-6) / 1e9 / hbm, 4)},
