@@ -292,9 +292,9 @@ dc_status dc_plan_set_flags(dc_plan_t p, uint32_t flags) {
     if (st) {
       p->flags = before;
       layout(p);
-      return st;
     }
-    return DC_OK;
+    p->L = make_layout(p);  // the device regions follow the data bytes and the segment capacity
+    return st;
   }
   p->flags = flags;
   return DC_OK;

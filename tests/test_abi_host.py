@@ -250,8 +250,16 @@ def test_packed_layout_closed_form():
     pos = sorted(b["offset"] for b in p.blocks() if b["lane"] == 1)
     assert pos == [32 * n + 40 * i for i in range(n)]
     # the same plan unpacked again: 48-byte slots
+    packed_device = p.info["device_bytes"]
     p.set_flags(0)
     assert p.info["data_bytes"] == 32 * n + 2 * 48 * n
+    # the device layout follows each re-layout: the unpacked plan's matches a fresh plan's, and the
+    # packed one differs (fewer data bytes, up to eight leaf segments per struct)
+    fresh = dc.Plan(t.schema, t.root)
+    assert p.info["device_bytes"] == fresh.info["device_bytes"] != packed_device
+    p.set_flags(dc.PLAN_PACK_SMALL)
+    assert p.info["device_bytes"] == packed_device
+    fresh.destroy()
     p.destroy()
     t.free()
 
