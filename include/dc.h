@@ -149,6 +149,8 @@ typedef struct {
                               the data region: the relocation reads and writes this range */
   uint64_t reloc_table_bytes; /* the relocation's tables (8 B per slot, 16 B per lane group
                                  of a tile, 16 B per tile that holds a slot) */
+  uint64_t staging_bytes;  /* the span staging area when dc_deep_copy stages by host spans
+                              (DC_PLAN_SPANS), else 0 */
 } dc_plan_info;
 
 /* Plan flags (dc_plan_set_flags, before dc_bind_device). */
@@ -187,6 +189,25 @@ typedef struct {
                              takes its three-call path when a selected array is not
                              on 16 bytes in the arena. */
 #define DC_PACK_BYTES 64u
+#define DC_PLAN_SPANS 16u /* stage the deep copy by host spans even where the plan's own
+                             rule would not (that rule: at least DC_SPAN_MIN_BLOCKS
+                             staged blocks averaging under DC_SPAN_MAX_MEAN bytes, whose
+                             spans hold at most 5/4 of their bytes).  A span is a run of
+                             staged blocks in host memory with gaps of under 1 KiB
+                             between them; dc_deep_copy copies each span whole into the
+                             pinned arena (the gap bytes included: they lie on pages
+                             that also hold the tree's blocks, are read, moved to the
+                             device and never used), moves the spans by DMA to a
+                             staging region of the device buffer, and one kernel launch
+                             places every block at its arena offset.  The device buffer
+                             then holds the staging region too (dc_plan_info's
+                             staging_bytes); the pinned arena is the larger of the data
+                             region and the staging area.  Ignored with DC_PLAN_MAP_HOST;
+                             set it before dc_bind_device.  The environment variable
+                             DC_SPANS=0, read at dc_plan, turns the plan's own rule
+                             off. */
+#define DC_SPAN_MIN_BLOCKS 1024u
+#define DC_SPAN_MAX_MEAN 4096u
 
 /* dc_plan — walk the host structure from `host_root` (one struct of
  * schema->root_type) and lay out its device arena (Algorithm 1's first step,

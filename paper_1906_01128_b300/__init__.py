@@ -32,6 +32,7 @@ PLAN_VERIFY = 1
 PLAN_MAP_HOST = 2
 PLAN_DEVICE_SCAN = 4
 PLAN_PACK_SMALL = 8
+PLAN_SPANS = 16
 COPY_ALL_ARRAYS = 1
 
 STATUS = {0: "DC_OK", 1: "DC_EINVAL", 2: "DC_ENOMEM", 3: "DC_ECUDA", 4: "DC_EALIAS", 5: "DC_ECYCLE",
@@ -74,7 +75,8 @@ class _Op(ctypes.Structure):
 class _Info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("data_bytes", "device_bytes", "payload_bytes", "nblocks",
                                                "nrelocs", "nstructs", "nstruct_blocks", "root_offset",
-                                               "ntrees", "struct_bytes", "reloc_table_bytes")]
+                                               "ntrees", "struct_bytes", "reloc_table_bytes",
+                                               "staging_bytes")]
 
 
 class _Request(ctypes.Structure):

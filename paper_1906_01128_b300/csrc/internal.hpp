@@ -253,7 +253,19 @@ struct DevLayout {
   uint64_t mva = 0, mvat = 0, mvb = 0, mvbt = 0, bk = 0, bkt = 0;  // move tables + their tile tables
   uint64_t sta = 0, stat = 0, stb = 0, stbt = 0, sts = 0, stst = 0;  // fused-step tables
   uint64_t seg_cap = 0, tseg_cap = 0, step_cap = 0, walk_cap = 0, ntiles = 0, tab_cap = 0;
+  // span staging (dc_plan_s::span_mode): the staged host spans, the move table that
+  // places their blocks in the arena, and its tile table (0 bytes without span staging)
+  uint64_t spn = 0, spd = 0, spdt = 0, spd_cap = 0, spdt_cap = 0;
 };
+
+// One host span: staged blocks close together in host memory (gaps under
+// SPAN_GAP bytes), copied as one range; `stage` is its offset in the staging
+// area, with the host address's phase modulo 16.
+struct HostSpan {
+  const uint8_t* host;
+  uint64_t bytes, stage;
+};
+constexpr uint64_t SPAN_GAP = 1024;  // a gap of less than a page: every page a span touches holds a block byte
 
 struct OpKey {
   int32_t kind = -1, sel = -1;
@@ -330,6 +342,18 @@ struct dc_plan_s {
   bool has_arena_blocks = false;       // some blocks live in a host arena (moved directly)
   Moves h2d;
   uint64_t h2d_int_nd = 0, h2d_int_units = 0, h2d_frag_nd = 0, h2d_frag_units = 0;
+  // Span staging: a deep copy of many small blocks copies whole host spans (the
+  // blocks and the gaps between them) into the pinned staging area, moves them
+  // to the device staging region by DMA, and places every block in the arena
+  // with one move-kernel launch (the host copies stream instead of handling
+  // each block).
+  std::vector<dc::HostSpan> spans;    // host order
+  uint64_t span_bytes = 0;            // staging area bytes
+  bool span_worth = false;            // the plan's blocks favour span staging
+  bool span_mode = false;             // dc_deep_copy stages by spans
+  Moves h2d_span;                     // frags: the spans, at their staging offsets
+  std::vector<uint64_t> span_nulls;   // NULL-slot fix-ups, as staging offsets (sorted)
+  uint64_t span_nd = 0, span_units = 0;
   uint64_t back_key = ~0ull;          // generation of the block list `back` was built for (0 = all arrays)
   Moves back;
   uint64_t bk_nd = 0, bk_units = 0;
@@ -394,15 +418,26 @@ uint64_t interior_bytes(const HostBlock& b);
 void plan_moves(const dc_plan_s* p, const std::vector<uint32_t>& list, dc_plan_s::Moves* m, bool host_order = true,
                 uint64_t chunk_bytes = 0, bool stage_all = false);
 // Marshal a chunked move list (plan_moves with host_order false) into the
-// pinned arena and queue each chunk's DMA to the device as it completes.
-dc_status send_staged(dc_plan_s* p, const dc_plan_s::Moves& m, cudaStream_t s);
+// pinned arena, zero the NULL slots `nulls` (offsets in the list's destination
+// range, sorted) and queue each chunk's DMA to `dev` + offset as it completes.
+dc_status send_staged(dc_plan_s* p, const dc_plan_s::Moves& m, const std::vector<uint64_t>& nulls, uint8_t* dev,
+                      cudaStream_t s);
 void plan_transfers(dc_plan_s* p);
+// Pieces, units, runs and (unless host_order) chunks of m->frags.
+void split_moves(dc_plan_s::Moves* m, bool host_order, uint64_t chunk_bytes);
+// The host spans of the staged blocks and whether span staging pays (at planning).
+void plan_spans(dc_plan_s* p);
+// span_mode from the plan's flags and span_worth (at planning and flag changes).
+void choose_spans(dc_plan_s* p);
+// Bytes of the pinned arena: the data region, or the span staging area if larger.
+uint64_t pin_arena_bytes(const dc_plan_s* p);
 void release_transfers(dc_plan_s* p);
 dc_status upload_h2d_tables(dc_plan_s* p, cudaStream_t s);
 dc_status transfer_to_device(dc_plan_s* p, cudaStream_t s);
 dc_status transfer_back(dc_plan_s* p, const std::vector<uint32_t>& list, uint64_t key, cudaStream_t s);
+// tile_cap: the tile table's capacity in entries (0: the plan's tseg_cap).
 dc_status upload(dc_plan_s* p, const std::vector<MoveDesc>& d, uint64_t desc_off, uint64_t tile_off, uint64_t cap,
-                 uint64_t* nd, uint64_t* units, cudaStream_t s);
+                 uint64_t* nd, uint64_t* units, cudaStream_t s, uint64_t tile_cap = 0);
 void push_desc(std::vector<MoveDesc>* d, uint64_t src, uint64_t dst, uint64_t bytes);
 dc_status launch_table(dc_plan_s* p, uint64_t desc_off, uint64_t tile_off, uint64_t nd, uint64_t units,
                        cudaStream_t s);

@@ -72,6 +72,16 @@ DevLayout make_layout(const dc_plan_s* p) {
   L.walk_cap = (uint64_t)p->max_depth + 2;
   L.walk = o;
   o = align256(o + L.walk_cap * sizeof(ChaseStep) + 16);
+  if (p->span_mode) {  // the staged spans, and one move descriptor per staged block
+    L.spn = o;
+    o = align256(o + p->span_bytes);
+    L.spd_cap = nb;
+    L.spd = o;
+    o = align256(o + L.spd_cap * sizeof(MoveDesc));
+    L.spdt_cap = (p->data_bytes / 16 + nb) / LEAF_TILE + 2;  // every block rounds up to a 16-byte unit
+    L.spdt = o;
+    o = align256(o + L.spdt_cap * 4);
+  }
   L.total = o;
   return L;
 }
@@ -275,6 +285,8 @@ dc_status dc_plan_forest(const dc_schema* schema, const void* const* roots, uint
     delete p;
     return st;
   }
+  plan_spans(p);
+  choose_spans(p);
   p->L = make_layout(p);
   if (debug_on()) p->flags |= DC_PLAN_VERIFY;
   *out = p;
@@ -293,8 +305,16 @@ dc_status dc_plan_set_flags(dc_plan_t p, uint32_t flags) {
       p->flags = before;
       layout(p);
     }
+    choose_spans(p);
     p->L = make_layout(p);  // the device regions follow the data bytes and the segment capacity
     return st;
+  }
+  if ((before ^ flags) & (DC_PLAN_MAP_HOST | DC_PLAN_SPANS)) {  // span staging on or off
+    if (p->dev) return fail(DC_ESTATE, "DC_PLAN_MAP_HOST and DC_PLAN_SPANS are set before dc_bind_device");
+    p->flags = flags;
+    choose_spans(p);
+    p->L = make_layout(p);
+    return DC_OK;
   }
   p->flags = flags;
   return DC_OK;
@@ -322,6 +342,7 @@ dc_status dc_plan_info_get(dc_plan_t p, dc_plan_info* out) {
   out->struct_bytes = p->struct_bytes;
   out->reloc_table_bytes =
       p->rrec.size() * sizeof(RelocRec) + p->rseg.size() * sizeof(RelocSeg) + p->rtiles.size() * sizeof(RelocTile);
+  out->staging_bytes = p->span_mode ? p->span_bytes : 0;
   return DC_OK;
 }
 
@@ -385,18 +406,18 @@ dc_status dc_bind_device(dc_plan_t p, void* dev, uint64_t bytes, dc_stream_t str
   DC_CUDA(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device));
   if (p->h2d_done) DC_CUDA(cudaEventSynchronize(p->h2d_done));
   if (!p->pinned) {
-    cudaError_t e = host_alloc((void**)&p->pinned, std::max<uint64_t>(p->data_bytes, 16), cudaHostAllocMapped);
+    const uint64_t pin = pin_arena_bytes(p);
+    cudaError_t e = host_alloc((void**)&p->pinned, std::max<uint64_t>(pin, 16), cudaHostAllocMapped);
     if (e != cudaSuccess) {
       p->pinned = nullptr;
-      return fail(DC_ENOMEM, "pinned arena of %llu bytes: %s", (unsigned long long)p->data_bytes,
-                  cudaGetErrorString(e));
+      return fail(DC_ENOMEM, "pinned arena of %llu bytes: %s", (unsigned long long)pin, cudaGetErrorString(e));
     }
     DC_CUDA(cudaHostGetDevicePointer((void**)&p->pinned_dev, p->pinned, 0));
     // padding between blocks stays zero: the marshal writes blocks only
     Pool& pool = pool_of(p);
-    const uint64_t n = (p->data_bytes + (64ull << 20) - 1) / (64ull << 20);
+    const uint64_t n = (pin + (64ull << 20) - 1) / (64ull << 20);
     pool.parallel_for(n, [&](uint64_t i) {
-      uint64_t lo = i * (64ull << 20), hi = std::min<uint64_t>(p->data_bytes, lo + (64ull << 20));
+      uint64_t lo = i * (64ull << 20), hi = std::min<uint64_t>(pin, lo + (64ull << 20));
       memset(p->pinned + lo, 0, hi - lo);
     });
   }
@@ -450,7 +471,7 @@ dc_status dc_bind_device(dc_plan_t p, void* dev, uint64_t bytes, dc_stream_t str
 
 }  // extern "C"
 
-uint64_t dc::pinned_need(const dc_plan_s* p) { return round_up(p->data_bytes, 256) + tab_total(p->L); }
+uint64_t dc::pinned_need(const dc_plan_s* p) { return round_up(pin_arena_bytes(p), 256) + tab_total(p->L); }
 
 dc_status dc::bind_borrowed(dc_plan_s* p, void* dev, uint64_t bytes, uint8_t* pinned, uint8_t* pinned_dev,
                             cudaStream_t s) {
@@ -458,7 +479,7 @@ dc_status dc::bind_borrowed(dc_plan_s* p, void* dev, uint64_t bytes, uint8_t* pi
   p->borrowed_pinned = true;
   p->pinned = pinned;
   p->pinned_dev = pinned_dev;
-  p->pin_tab = pinned + round_up(p->data_bytes, 256);
+  p->pin_tab = pinned + round_up(pin_arena_bytes(p), 256);
   p->pin_tab_bytes = tab_total(p->L);
   return dc_bind_device(p, dev, bytes, s);
 }
@@ -468,7 +489,7 @@ dc_status dc::lend_pinned(dc_plan_s* p, uint8_t* pinned, uint8_t* pinned_dev) {
   if (p->flags & DC_PLAN_MAP_HOST) return fail(DC_ESTATE, "mapped plans keep the pinned range they were bound with");
   p->pinned = pinned;
   p->pinned_dev = pinned_dev;
-  p->pin_tab = pinned + round_up(p->data_bytes, 256);
+  p->pin_tab = pinned + round_up(pin_arena_bytes(p), 256);
   p->step_key = OpKey();  // the round trip's device tables hold pinned addresses: rebuild them
   return DC_OK;
 }
@@ -551,7 +572,7 @@ dc_status dc_deep_copy_selected(dc_plan_t p, const dc_op* op, dc_stream_t stream
     p->sel_key = key;
   }
   if ((st = wait_event(p->h2d_done))) return st;  // an earlier transfer may still read the pinned arena
-  if ((st = send_staged(p, p->sel, s))) return st;
+  if ((st = send_staged(p, p->sel, p->null_slots, p->dev, s))) return st;
   DC_CUDA(cudaEventRecord(p->h2d_done, s));
   RelocArgs a = reloc_args(p);
   a.tiles = reinterpret_cast<const RelocTile*>(p->dev + p->L.seltile);

@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 
@@ -79,6 +80,13 @@ void plan_moves(const dc_plan_s* p, const std::vector<uint32_t>& list, dc_plan_s
       m->frags.push_back({B.off, B.bytes, host});
     }
   }
+  split_moves(m, host_order, chunk_bytes);
+}
+
+// The second half of planning a transfer: m->frags split into pieces and work
+// units, the runs of the destination range, and (arena order) DMA chunks.
+void split_moves(dc_plan_s::Moves* m, bool host_order, uint64_t chunk_bytes) {
+  if (!chunk_bytes) chunk_bytes = CHUNK_BYTES;
   for (const auto& f : m->frags)
     for (uint64_t o = 0; o < f.len; o += PIECE_BYTES)
       m->pieces.push_back({f.off + o, std::min(PIECE_BYTES, f.len - o), f.host + o});
@@ -124,6 +132,79 @@ void plan_moves(const dc_plan_s* p, const std::vector<uint32_t>& list, dc_plan_s
   }
 }
 
+namespace {
+
+// The struct block that holds arena offset `off` (a slot of a struct block).
+uint64_t struct_block_at(const dc_plan_s* p, uint64_t off) {
+  auto it = std::upper_bound(p->blocks.begin(), p->blocks.begin() + p->nstruct_blocks, off,
+                             [](uint64_t o, const HostBlock& hb) { return o < hb.off; });
+  return (uint64_t)(it - p->blocks.begin()) - 1;
+}
+
+// Per block: 1 if it is a struct block with a NULL-slot fix-up (such blocks go
+// through the pinned arena even when they live in a host arena).
+std::vector<uint8_t> null_fixups(const dc_plan_s* p) {
+  std::vector<uint8_t> fixup(p->blocks.size(), 0);
+  for (uint64_t off : p->null_slots) fixup[struct_block_at(p, off)] = 1;
+  return fixup;
+}
+
+// The span holding host address h (spans are in host order, h inside one).
+const HostSpan& span_at(const dc_plan_s* p, const uint8_t* h) {
+  auto it = std::upper_bound(p->spans.begin(), p->spans.end(), h,
+                             [](const uint8_t* a, const HostSpan& sp) { return a < sp.host; });
+  return *(it - 1);
+}
+
+}  // namespace
+
+void plan_spans(dc_plan_s* p) {
+  p->spans.clear();
+  p->span_bytes = 0;
+  p->span_worth = false;
+  const std::vector<uint8_t> fixup = null_fixups(p);
+  std::vector<std::pair<const uint8_t*, uint64_t>> hb;  // the blocks a full deep copy stages
+  uint64_t staged = 0;
+  for (uint64_t b = 0; b < p->blocks.size(); b++) {
+    const HostBlock& B = p->blocks[b];
+    if ((!fixup[b] && in_host_arena(B.host, B.bytes, nullptr)) || !B.bytes) continue;
+    hb.push_back({B.host, B.bytes});
+    staged += B.bytes;
+  }
+  std::sort(hb.begin(), hb.end());
+  for (const auto& x : hb) {
+    if (!p->spans.empty()) {
+      HostSpan& S = p->spans.back();
+      const uint8_t* end = S.host + S.bytes;
+      if (x.first >= end && (uint64_t)(x.first - end) < SPAN_GAP) {  // blocks never overlap
+        S.bytes = (uint64_t)(x.first + x.second - S.host);
+        continue;
+      }
+    }
+    p->spans.push_back({x.first, x.second, 0});
+  }
+  uint64_t o = 0;
+  for (HostSpan& S : p->spans) {  // each span keeps its host address's phase modulo 16
+    o = round_up(o, 16) + ((uintptr_t)S.host & 15);
+    S.stage = o;
+    o += S.bytes;
+  }
+  p->span_bytes = round_up(o, 16);
+  const char* v = getenv("DC_SPANS");
+  const bool rule = !(v && v[0] == '0');
+  p->span_worth = rule && hb.size() >= DC_SPAN_MIN_BLOCKS && staged < (uint64_t)DC_SPAN_MAX_MEAN * hb.size() &&
+                  p->span_bytes * 4 <= staged * 5;
+}
+
+void choose_spans(dc_plan_s* p) {
+  p->span_mode = !(p->flags & DC_PLAN_MAP_HOST) && !p->spans.empty() &&
+                 ((p->flags & DC_PLAN_SPANS) || p->span_worth);
+}
+
+uint64_t pin_arena_bytes(const dc_plan_s* p) {
+  return std::max(p->data_bytes, p->span_mode ? p->span_bytes : 0);
+}
+
 void plan_transfers(dc_plan_s* p) {
   const uint64_t nb = p->blocks.size();
   p->ilo.assign(nb, 0);
@@ -131,12 +212,7 @@ void plan_transfers(dc_plan_s* p) {
   p->idev.assign(nb, 0);
   {  // blocks in a host arena: the GPU reads and writes them in place (struct
      // blocks with NULL-slot fix-ups excepted: those go through the pinned arena)
-    std::vector<uint8_t> fixup(nb, 0);
-    for (uint64_t off : p->null_slots) {
-      auto it = std::upper_bound(p->blocks.begin(), p->blocks.begin() + p->nstruct_blocks, off,
-                                 [](uint64_t o, const HostBlock& hb) { return o < hb.off; });
-      fixup[(it - p->blocks.begin()) - 1] = 1;
-    }
+    const std::vector<uint8_t> fixup = null_fixups(p);
     for (uint32_t b = 0; b < nb; b++) {
       uint64_t dev;
       const HostBlock& B = p->blocks[b];
@@ -170,6 +246,19 @@ void plan_transfers(dc_plan_s* p) {
   std::vector<uint32_t> all(nb);
   for (uint32_t b = 0; b < nb; b++) all[b] = b;
   plan_moves(p, all, &p->h2d, (p->flags & DC_PLAN_MAP_HOST) != 0);  // staged copies go chunk by chunk
+  p->h2d_span = dc_plan_s::Moves();
+  p->span_nulls.clear();
+  if (p->span_mode) {  // the spans move instead, in staging order, chunk by chunk
+    for (const HostSpan& S : p->spans) p->h2d_span.frags.push_back({S.stage, S.bytes, const_cast<uint8_t*>(S.host)});
+    split_moves(&p->h2d_span, false, 0);
+    for (uint64_t off : p->null_slots) {  // where each NULL-slot fix-up lies in the staging area
+      const HostBlock& B = p->blocks[struct_block_at(p, off)];
+      const uint8_t* h = B.host + (off - B.off);
+      const HostSpan& S = span_at(p, h);
+      p->span_nulls.push_back(S.stage + (uint64_t)(h - S.host));
+    }
+    std::sort(p->span_nulls.begin(), p->span_nulls.end());
+  }
   p->transfers_ready = true;
 }
 
@@ -182,14 +271,14 @@ void release_transfers(dc_plan_s* p) {
 // sources are pageable vectors: cudaMemcpyAsync returns once it has staged
 // them, so they may go away afterwards.
 dc_status upload(dc_plan_s* p, const std::vector<MoveDesc>& d, uint64_t desc_off, uint64_t tile_off, uint64_t cap,
-                 uint64_t* nd, uint64_t* units, cudaStream_t s) {
+                 uint64_t* nd, uint64_t* units, cudaStream_t s, uint64_t tile_cap) {
   *nd = d.size();
   *units = d.empty() ? 0 : d.back().ubeg + (d.back().bytes + 15) / 16;
   if (d.empty()) return DC_OK;
   if (d.size() > cap) return fail(DC_EINVAL, "move table larger than planned");
   std::vector<uint32_t> tiles;
   const uint64_t ntiles = (*units + LEAF_TILE - 1) / LEAF_TILE;
-  if (ntiles + 1 > p->L.tseg_cap) return fail(DC_EINVAL, "move tile table larger than planned");
+  if (ntiles + 1 > (tile_cap ? tile_cap : p->L.tseg_cap)) return fail(DC_EINVAL, "move tile table larger than planned");
   for (uint64_t t = 0, k = 0; t < ntiles; t++) {
     while (k + 1 < d.size() && d[k + 1].ubeg <= t * LEAF_TILE) k++;
     tiles.push_back((uint32_t)k);
@@ -294,7 +383,14 @@ dc_status upload_h2d_tables(dc_plan_s* p, cudaStream_t s) {
   d.clear();
   if (p->flags & DC_PLAN_MAP_HOST)  // the staged bytes also move by kernel, from the mapped pinned arena
     for (const auto& r : p->h2d.runs) push_desc(&d, (uint64_t)(uintptr_t)p->pinned_dev + r.lo, base + r.lo, r.hi - r.lo);
-  return upload(p, d, p->L.mvb, p->L.mvbt, p->L.tab_cap, &p->h2d_frag_nd, &p->h2d_frag_units, s);
+  st = upload(p, d, p->L.mvb, p->L.mvbt, p->L.tab_cap, &p->h2d_frag_nd, &p->h2d_frag_units, s);
+  if (st || !p->span_mode) return st;
+  d.clear();  // span staging: every staged block from its place in the staging region to the arena
+  for (const auto& f : p->h2d.frags) {
+    const HostSpan& S = span_at(p, f.host);
+    push_desc(&d, base + p->L.spn + S.stage + (uint64_t)(f.host - S.host), base + f.off, f.len);
+  }
+  return upload(p, d, p->L.spd, p->L.spdt, p->L.spd_cap, &p->span_nd, &p->span_units, s, p->L.spdt_cap);
 }
 
 dc_status transfer_to_device(dc_plan_s* p, cudaStream_t s) {
@@ -311,43 +407,55 @@ dc_status transfer_to_device(dc_plan_s* p, cudaStream_t s) {
     }
     return launch_table(p, p->L.mvb, p->L.mvbt, p->h2d_frag_nd, p->h2d_frag_units, s);
   }
-  return send_staged(p, m, s);
+  if (p->span_mode) {  // the spans into the staging region, then every block to its place
+    st = send_staged(p, p->h2d_span, p->span_nulls, p->dev + p->L.spn, s);
+    if (st) return st;
+    return launch_table(p, p->L.spd, p->L.spdt, p->span_nd, p->span_units, s);
+  }
+  return send_staged(p, m, p->null_slots, p->dev, s);
 }
 
 // Algorithm 1's contiguous buffer.  The pool's threads take the work units in
-// arena order without stopping at chunk ends; the thread that finishes a
-// chunk's last unit zeroes the chunk's NULL slots and queues its DMA, so the
-// link starts on a chunk as soon as its bytes are in the pinned arena.
-dc_status send_staged(dc_plan_s* p, const dc_plan_s::Moves& m, cudaStream_t s) {
+// destination order (the arena's, or the span staging area's) without stopping
+// at chunk ends; each unit zeroes the NULL slots in its range after its copies,
+// and the thread that finishes a chunk's last unit queues the chunk's DMA to
+// `dev`, so the link starts on a chunk as soon as its bytes are in the pinned
+// arena.
+dc_status send_staged(dc_plan_s* p, const dc_plan_s::Moves& m, const std::vector<uint64_t>& nulls, uint8_t* dev,
+                      cudaStream_t s) {
   Trace tr("dc_deep_copy", "marshal+copies");
   const size_t nc = m.chunks.size();
   if (!nc) return DC_OK;
   std::vector<uint32_t> unit_chunk(m.units.size());
   std::unique_ptr<std::atomic<uint64_t>[]> left(new std::atomic<uint64_t>[nc]);
-  std::vector<size_t> nbeg(nc + 1, p->null_slots.size());
-  for (size_t c = 0, ns = 0; c < nc; c++) {
+  for (size_t c = 0; c < nc; c++) {
     const auto& ch = m.chunks[c];
     for (uint64_t u = ch.ufirst; u < ch.ulast; u++) unit_chunk[u] = (uint32_t)c;
     left[c].store(ch.ulast - ch.ufirst);
-    const uint64_t lo = m.pieces[m.units[ch.ufirst].first].off;  // chunk c's bytes start here
-    while (ns < p->null_slots.size() && p->null_slots[ns] < lo) ns++;
-    nbeg[c] = ns;
   }
   std::atomic<int> failed{0};
   cudaError_t first = cudaSuccess;
   auto finish_chunk = [&](size_t c) {
-    for (size_t k = nbeg[c]; k < nbeg[c + 1]; k++) memset(p->pinned + p->null_slots[k], 0, 8);
     const auto& ch = m.chunks[c];
     for (uint64_t k = ch.cfirst; k < ch.clast; k++) {
-      const cudaError_t e = cudaMemcpyAsync(p->dev + m.copies[k].lo, p->pinned + m.copies[k].lo,
+      const cudaError_t e = cudaMemcpyAsync(dev + m.copies[k].lo, p->pinned + m.copies[k].lo,
                                             m.copies[k].hi - m.copies[k].lo, cudaMemcpyHostToDevice, s);
       if (e != cudaSuccess && failed.exchange(1) == 0) first = e;
     }
   };
   auto unit = [&](uint64_t u) {
-    for (uint64_t k = m.units[u].first; k < m.units[u].last; k++) {
+    const uint64_t k0 = m.units[u].first, k1 = m.units[u].last;
+    for (uint64_t k = k0; k < k1; k++) {
       const auto& pc = m.pieces[k];
       copy_block(p->pinned + pc.off, pc.host, pc.len);
+    }
+    // the NULL-slot fix-ups of the unit's range, clipped to it: a slot that
+    // straddles two units is zeroed by each for its own bytes, after its copy
+    const uint64_t lo = m.pieces[k0].off, hi = m.pieces[k1 - 1].off + m.pieces[k1 - 1].len;
+    for (auto it = std::lower_bound(nulls.begin(), nulls.end(), lo >= 7 ? lo - 7 : 0); it != nulls.end() && *it < hi;
+         ++it) {
+      const uint64_t a = std::max(*it, lo), b = std::min(*it + 8, hi);
+      if (b > a) memset(p->pinned + a, 0, b - a);
     }
     const uint32_t c = unit_chunk[u];
     if (left[c].fetch_sub(1, std::memory_order_acq_rel) == 1) finish_chunk(c);

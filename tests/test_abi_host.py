@@ -290,6 +290,72 @@ def test_packed_layout_follows_its_rule_and_relocates():
     assert smaller >= 5  # arenas with several small arrays in a lane get shorter
 
 
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64)
+
+
+class BumpAllocator:
+    """Blocks for treegen from one buffer: each 16-byte aligned, `gap` bytes after the last."""
+
+    def __init__(self, nbytes, gap):
+        self.buf = (ctypes.c_uint8 * (nbytes + 64))()
+        self.next = (ctypes.addressof(self.buf) + 15) // 16 * 16
+        self.end = ctypes.addressof(self.buf) + nbytes
+        self.gap, self.blocks = gap, []
+        self.fn = ALLOC_FN(self._alloc)
+
+    def _alloc(self, ctx, nbytes, align):
+        a = (self.next + max(align, 16) - 1) // max(align, 16) * max(align, 16)
+        if a + nbytes > self.end:
+            return None
+        self.next = a + nbytes + self.gap
+        if nbytes:
+            self.blocks.append((a, nbytes))
+        return a
+
+    @property
+    def alloc(self):
+        return (ctypes.cast(self.fn, ctypes.c_void_p).value, None)
+
+
+def test_span_staging_plan_rule_and_closed_forms(monkeypatch):
+    # 1,885 nodes of 10 fp32 per array: 3,928 blocks, 40-byte arrays
+    r16 = lambda x: (x + 15) // 16 * 16  # noqa: E731
+
+    def tree(gap):
+        a = BumpAllocator(16 << 20, gap)
+        return tg.node_tree(4, 12, 10, seed=71, nthreads=1, alloc=a.alloc), a
+
+    def staging(t, flags=0):
+        p = dc.Plan(t.schema, t.root, flags=flags)
+        out = (p.info["staging_bytes"], p.info["device_bytes"])
+        p.destroy()
+        return out
+
+    # back to back (48-byte spacing of 40-byte arrays: 1.2x the bytes): one span, chosen by the rule
+    t, a = tree(0)
+    lo, hi = min(x for x, _ in a.blocks), max(x + n for x, n in a.blocks)
+    assert len(a.blocks) == 3928
+    st, dev = staging(t)
+    assert st == r16(hi - lo)
+    assert staging(t, dc.PLAN_MAP_HOST | dc.PLAN_SPANS)[0] == 0  # mapped plans never stage by spans
+    monkeypatch.setenv("DC_SPANS", "0")  # the rule off; the flag still applies
+    assert staging(t)[0] == 0 and staging(t, dc.PLAN_SPANS) == (st, dev)
+    monkeypatch.delenv("DC_SPANS")
+    # the device buffer also holds the staging region and one move descriptor per block
+    assert dev >= staging(t, dc.PLAN_MAP_HOST)[1] + st + 32 * len(a.blocks)
+    # 32-byte gaps: still one span, but 2x the bytes, so only the flag stages by spans
+    t2, a2 = tree(32)
+    lo2, hi2 = min(x for x, _ in a2.blocks), max(x + n for x, n in a2.blocks)
+    assert staging(t2)[0] == 0 and staging(t2, dc.PLAN_SPANS)[0] == r16(hi2 - lo2)
+    # gaps of 2,000 bytes (over the 1 KiB merge limit): one span per block
+    t3, a3 = tree(2000)
+    assert staging(t3, dc.PLAN_SPANS)[0] == sum(r16(n) for _, n in a3.blocks)
+    # few large blocks (the dense workload): never by the rule
+    d = tg.workload("dense")
+    assert staging(d)[0] == 0 and staging(d, dc.PLAN_SPANS)[0] >= d.payload_bytes
+    d.free()
+
+
 def test_resolve_offset_agrees_with_an_image_walk():
     rng = random.Random(5)
     t = tg.node_tree(4, 5, tg.uniform(1, 40), seed=11)

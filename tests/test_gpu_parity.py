@@ -645,13 +645,13 @@ def test_fused_launch_every_kind_and_width(case, threads):
 
 # ---- host arenas (allocation requests served from one pinned buffer) -----------------
 
-def arena_case(make_tree, op_kw, mode, arena_bytes):
+def arena_case(make_tree, op_kw, mode, arena_bytes, flags=0):
     arena = dc.HostArena(arena_bytes)
     src = make_tree(arena.allocator)  # every block of the source tree comes from the arena
     ref = make_tree(None)
     assert arena.used >= src.payload_bytes
     s = src.schema
-    plan = dc.Plan(s, src.root)
+    plan = dc.Plan(s, src.root, flags=flags)
     plan.bind()
     dop, oop = ops_pair(**op_kw)
     if mode == "calls":
@@ -680,6 +680,88 @@ def test_trees_built_in_a_host_arena(mode):
     arena_case(lambda a: tg.node_tree(5, 12, tg.uniform(1, 9), seed=13, alloc=a), {}, mode, 64 << 20)
     arena_case(lambda a: tg.node_tree(64, 1, 1024, 1 << 20, seed=3, alloc=a),
                dict(sel=dc.SEL_CHAIN, path=tg.leaf_path(64)), mode, 64 << 20)
+    # host-arena blocks move in place: with DC_PLAN_SPANS nothing is left to stage
+    arena_case(lambda a: tg.node_tree(5, 12, tg.uniform(1, 9), seed=13, alloc=a), {}, mode, 64 << 20,
+               flags=dc.PLAN_SPANS)
+
+
+# ---- span staging: host spans copied whole, every block placed by one device launch ----
+
+SPAN_CASES = {
+    "ragged": (lambda: tg.node_tree(4, 6, tg.uniform(0, 3000), seed=8), {}),
+    "small_arrays": (lambda: tg.node_tree(5, 8, tg.uniform(1, 30), seed=41), {}),
+    "listing1_f64": (lambda: tg.listing1_tree(3001, seed=33), dict(type_=2, x=1, y=2)),
+    "deep_chain": (lambda: tg.node_tree(64, 1, 1024, 1 << 18, seed=3), dict(sel=dc.SEL_CHAIN, path=tg.leaf_path(64))),
+}
+
+
+@pytest.mark.parametrize("case", sorted(SPAN_CASES))
+def test_span_staging(case):
+    """DC_PLAN_SPANS on trees the rule would stage block by block: the device image, the
+    updates and the copy back equal the oracle's, with the slot check, on a packed plan
+    and with the device scan."""
+    make, kw = SPAN_CASES[case]
+    t = make()
+    p = dc.Plan(t.schema, t.root, flags=dc.PLAN_SPANS)
+    assert p.info["staging_bytes"] >= t.payload_bytes  # the spans hold every staged block
+    p.destroy()
+    t.free()
+    full_parity(make, kw, flags=dc.PLAN_SPANS, verify=True, repeat=2)
+    full_parity(make, None, flags=dc.PLAN_SPANS)
+    full_parity(make, kw, flags=dc.PLAN_SPANS | dc.PLAN_PACK_SMALL, verify=True)
+    full_parity(make, kw, flags=dc.PLAN_SPANS | dc.PLAN_DEVICE_SCAN)
+
+
+def test_span_staging_null_slots_and_random_schemas():
+    # count-0 slots with a non-NULL host value are zeroed in the staging area
+    full_parity(HandTree, {}, flags=dc.PLAN_SPANS)
+    full_parity(HandTree, None, flags=dc.PLAN_SPANS)
+    rng = random.Random(6161)
+    for i in range(40):
+        schema, levels, rules = tg.random_schema(rng)
+        full_parity(lambda: tg.Tree(schema, levels, rules, seed=1100 + i), None, flags=dc.PLAN_SPANS, verify=True)
+
+
+def test_span_staging_by_the_rule_on_the_pointer_heavy_tree(monkeypatch):
+    """The 1.1M-node tree of 40-byte arrays stages by spans on the default plan: repeated
+    deep copies, the update, the copy back, the round trip and a selective deep copy on
+    one plan; with DC_SPANS=0 the same tree stages block by block."""
+    src, ref = tg.workload("reloc_stress"), tg.workload("reloc_stress")
+    s = src.schema
+    plan = dc.Plan(s, src.root)
+    assert plan.info["staging_bytes"] > 0
+    plan.bind()
+    dop, oop = ops_pair()
+    cp = oracle.deep_copy(s, ref.root)
+    for _ in range(2):
+        plan.deep_copy()
+        plan.sync()
+        image_ok(plan, s, src.root)
+    plan.update(dop)
+    oracle.update(s, cp.root, oop)
+    plan.copy_back()
+    oracle.copy_back(s, cp.root, ref.root, oop)
+    assert oracle.trees_equal(s, src.root, ref.root)[0]
+    plan.roundtrip(dop)  # deep copy + update + copy back, from the updated host tree
+    oracle.update(s, cp.root, oop)
+    oracle.copy_back(s, cp.root, ref.root, oop)
+    assert oracle.trees_equal(s, src.root, ref.root)[0]
+    path = tg.leaf_path(6)
+    dchain, _ = ops_pair(sel=dc.SEL_CHAIN, path=path)
+    plan.deep_copy_selected(dchain)  # block by block, into the same pinned arena
+    plan.sync()
+    ok, msg = oracle.check_chain_image(s, src.root, plan.image(), plan.device_base, path, 2, 3)
+    assert ok, msg
+    plan.destroy()
+    src.free()
+    ref.free()
+    monkeypatch.setenv("DC_SPANS", "0")
+    t = tg.workload("reloc_stress")
+    p = dc.Plan(t.schema, t.root)
+    assert p.info["staging_bytes"] == 0
+    p.destroy()
+    t.free()
+    full_parity(lambda: tg.workload("reloc_stress"), {}, verify=True)
 
 
 # ---- the pointerchain transfer scheme: only the op's arrays move ----------------------
