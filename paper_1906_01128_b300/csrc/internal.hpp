@@ -172,6 +172,27 @@ struct MoveArgs {
   uint64_t units;
 };
 
+// One piece of a staged block for the span placement (place_kernel): `src`
+// holds the piece's offset in the staging region (low 60 bits) and the zero
+// bytes written after it (high 4 bits, < 16); `dst` holds its arena offset
+// (high 48 bits) and the bytes written there minus one (low 16 bits).  A piece
+// writes its bytes and then zeros up to its 16-byte slot end where the arena
+// leaves room, so that writes fill whole sectors.  Pieces are in arena order.
+struct PlaceDesc {
+  uint64_t src, dst;
+};
+static_assert(sizeof(PlaceDesc) == 16, "PlaceDesc is 16 bytes");
+constexpr uint64_t PLACE_PIECE = 32768;  // bytes of a piece at most (the rest of a block is further pieces)
+
+struct PlaceArgs {
+  const PlaceDesc* d;
+  uint64_t nd;
+  const uint8_t* stage;     // the staging region
+  uint8_t* arena;
+  uint64_t stage_bytes, data_bytes;
+  uint32_t* err;            // ERR_BOUNDS for a piece outside either region
+};
+
 // One selected struct of a fused round trip (dc_roundtrip): its x and y blocks in the
 // arena (xd, yd), their element count, the unit prefix, and for each of x and
 // y where its bytes live on the host side: the host address, the mapped
@@ -209,6 +230,7 @@ cudaError_t launch_relocate(const RelocArgs& a, cudaStream_t s, int sm_count);
 cudaError_t launch_leaf(const LeafArgs& a, cudaStream_t s, int sm_count);
 cudaError_t launch_chase(const ChaseArgs& a, cudaStream_t s, int sm_count);
 cudaError_t launch_move(const MoveArgs& a, cudaStream_t s, int sm_count);
+cudaError_t launch_place(const PlaceArgs& a, cudaStream_t s, int sm_count);
 // threads: 128, 256 or 512 per CTA; ctas_per_sm: 0 = as many as fit.  With
 // max_per_sm set, launches nothing and reports how many CTAs fit on an SM.
 cudaError_t launch_fused(const RelocArgs& r, const LeafArgs& l, uint32_t threads, uint32_t ctas_per_sm, int sm_count,
@@ -253,9 +275,9 @@ struct DevLayout {
   uint64_t mva = 0, mvat = 0, mvb = 0, mvbt = 0, bk = 0, bkt = 0;  // move tables + their tile tables
   uint64_t sta = 0, stat = 0, stb = 0, stbt = 0, sts = 0, stst = 0;  // fused-step tables
   uint64_t seg_cap = 0, tseg_cap = 0, step_cap = 0, walk_cap = 0, ntiles = 0, tab_cap = 0;
-  // span staging (dc_plan_s::span_mode): the staged host spans, the move table that
-  // places their blocks in the arena, and its tile table (0 bytes without span staging)
-  uint64_t spn = 0, spd = 0, spdt = 0, spd_cap = 0, spdt_cap = 0;
+  // span staging (dc_plan_s::span_mode): the staged host spans and the placement
+  // table that puts their blocks in the arena (0 bytes without span staging)
+  uint64_t spn = 0, spd = 0, spd_cap = 0;
 };
 
 // One host span: staged blocks close together in host memory (gaps under
@@ -353,7 +375,7 @@ struct dc_plan_s {
   bool span_mode = false;             // dc_deep_copy stages by spans
   Moves h2d_span;                     // frags: the spans, at their staging offsets
   std::vector<uint64_t> span_nulls;   // NULL-slot fix-ups, as staging offsets (sorted)
-  uint64_t span_nd = 0, span_units = 0;
+  uint64_t span_nd = 0;                // pieces in the placement table
   uint64_t back_key = ~0ull;          // generation of the block list `back` was built for (0 = all arrays)
   Moves back;
   uint64_t bk_nd = 0, bk_units = 0;

@@ -749,6 +749,72 @@ __global__ void __launch_bounds__(LEAF_THREADS) move_kernel(MoveArgs a) {
   }
 }
 
+// ---- span placement: staged blocks from the staging region to the arena ----------
+
+// Bytes [o, o + n) of a piece (o a multiple of 16, n <= 16) from s to d; the
+// bytes at or past `valid` are written as zeros.  16-byte vectors when both
+// sides allow it (the staging region then holds the whole 16 bytes), else
+// 8-, 4- or 1-byte steps over the valid bytes.
+__device__ __forceinline__ void place_chunk(const uint8_t* s, uint8_t* d, uint32_t o, uint32_t n, uint32_t valid) {
+  const uint64_t al = reinterpret_cast<uint64_t>(s + o) | reinterpret_cast<uint64_t>(d + o);
+  if (n == 16 && (al & 15) == 0) {
+    uint4 v = *reinterpret_cast<const uint4*>(s + o);
+    if (valid < o + 16) {  // zeros after the block's bytes (its slot's padding)
+      uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (uint32_t q = 0; q < 4; q++) {
+        const uint32_t b0 = o + 4 * q;  // bytes [b0, b0 + 4) of the piece
+        const uint32_t keep = valid <= b0 ? 0u : valid >= b0 + 4 ? 4u : valid - b0;
+        w[q] = keep == 4 ? w[q] : keep == 0 ? 0u : (w[q] & ((1u << (8 * keep)) - 1));
+      }
+      v = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    *reinterpret_cast<uint4*>(d + o) = v;
+    return;
+  }
+  const uint32_t e = o + n, ve = valid < e ? (valid > o ? valid : o) : e;  // [o, ve) copied, [ve, e) zeroed
+  uint32_t k = o;
+  if ((al & 7) == 0)
+    for (; k + 8 <= ve; k += 8) *reinterpret_cast<uint64_t*>(d + k) = *reinterpret_cast<const uint64_t*>(s + k);
+  if ((al & 3) == 0)
+    for (; k + 4 <= ve; k += 4) *reinterpret_cast<uint32_t*>(d + k) = *reinterpret_cast<const uint32_t*>(s + k);
+  for (; k < ve; k++) d[k] = s[k];
+  for (; k < e; k++) d[k] = 0;
+}
+
+// Every piece of the placement table, warp by warp: each lane loads one
+// descriptor (16 coalesced bytes) and copies its piece itself when it writes
+// at most 64 bytes; larger pieces are copied by the whole warp, one after
+// another, 16 bytes per lane.  The pieces are in arena order, so a warp's
+// writes of small pieces fall in a few consecutive lines.
+__global__ void __launch_bounds__(LEAF_THREADS) place_kernel(PlaceArgs a) {
+  constexpr uint32_t WPB = LEAF_THREADS / 32;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t nwarps = (uint64_t)gridDim.x * WPB;
+  for (uint64_t w = (uint64_t)blockIdx.x * WPB + (threadIdx.x >> 5); w * 32 < a.nd; w += nwarps) {  // uniform per warp
+    const uint64_t i = w * 32 + lane;
+    PlaceDesc g{0, 0};
+    if (i < a.nd) g = a.d[i];
+    const uint64_t so = g.src & ((1ull << 60) - 1), dso = g.dst >> 16;
+    const uint32_t pad = (uint32_t)(g.src >> 60), wlen = (uint32_t)(g.dst & 0xFFFFu) + 1, len = wlen - pad;
+    bool ok = i < a.nd;
+    if (ok && (pad >= wlen || so + len > a.stage_bytes || dso + wlen > a.data_bytes)) {
+      atomicOr(a.err, ERR_BOUNDS);
+      ok = false;
+    }
+    if (ok && wlen <= 64)
+      for (uint32_t o = 0; o < wlen; o += 16) place_chunk(a.stage + so, a.arena + dso, o, min(16u, wlen - o), len);
+    uint32_t big = __ballot_sync(0xffffffffu, ok && wlen > 64);
+    while (big) {
+      const int j = __ffs(big) - 1;
+      big &= big - 1;
+      const uint64_t bso = __shfl_sync(0xffffffffu, so, j), bdo = __shfl_sync(0xffffffffu, dso, j);
+      const uint32_t bw = __shfl_sync(0xffffffffu, wlen, j), bl = __shfl_sync(0xffffffffu, len, j);
+      for (uint32_t o = lane * 16; o < bw; o += 32 * 16) place_chunk(a.stage + bso, a.arena + bdo, o, min(16u, bw - o), bl);
+    }
+  }
+}
+
 // ---- fused step: host -> update -> arena + host --------------------------------
 
 // Device-visible address of byte `off` of a block whose host copy is split in a
@@ -1026,6 +1092,16 @@ cudaError_t launch_move(const MoveArgs& a, cudaStream_t s, int sm_count) {
   uint64_t tiles = (a.units + LEAF_TILE - 1) / LEAF_TILE;
   uint32_t grid = (uint32_t)std::min<uint64_t>(tiles, (uint64_t)sm_count * occ);
   move_kernel<<<grid, LEAF_THREADS, 0, s>>>(a);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_place(const PlaceArgs& a, cudaStream_t s, int sm_count) {
+  if (a.nd == 0) return cudaSuccess;
+  const int occ = occupancy(place_kernel, LEAF_THREADS, 0);
+  const uint64_t blocks = (a.nd + LEAF_THREADS - 1) / LEAF_THREADS;  // one descriptor per thread at a time
+  const uint32_t grid = (uint32_t)std::min<uint64_t>(blocks, (uint64_t)sm_count * occ);
+  place_kernel<<<grid, LEAF_THREADS, 0, s>>>(a);
   count_launch();
   return cudaGetLastError();
 }

@@ -72,15 +72,12 @@ DevLayout make_layout(const dc_plan_s* p) {
   L.walk_cap = (uint64_t)p->max_depth + 2;
   L.walk = o;
   o = align256(o + L.walk_cap * sizeof(ChaseStep) + 16);
-  if (p->span_mode) {  // the staged spans, and one move descriptor per staged block
+  if (p->span_mode) {  // the staged spans, and the placement table (a piece per PLACE_PIECE bytes of a block)
     L.spn = o;
     o = align256(o + p->span_bytes);
-    L.spd_cap = nb;
+    L.spd_cap = nb + p->data_bytes / PLACE_PIECE + 1;
     L.spd = o;
-    o = align256(o + L.spd_cap * sizeof(MoveDesc));
-    L.spdt_cap = (p->data_bytes / 16 + nb) / LEAF_TILE + 2;  // every block rounds up to a 16-byte unit
-    L.spdt = o;
-    o = align256(o + L.spdt_cap * 4);
+    o = align256(o + L.spd_cap * sizeof(PlaceDesc));
   }
   L.total = o;
   return L;

@@ -385,12 +385,28 @@ dc_status upload_h2d_tables(dc_plan_s* p, cudaStream_t s) {
     for (const auto& r : p->h2d.runs) push_desc(&d, (uint64_t)(uintptr_t)p->pinned_dev + r.lo, base + r.lo, r.hi - r.lo);
   st = upload(p, d, p->L.mvb, p->L.mvbt, p->L.tab_cap, &p->h2d_frag_nd, &p->h2d_frag_units, s);
   if (st || !p->span_mode) return st;
-  d.clear();  // span staging: every staged block from its place in the staging region to the arena
-  for (const auto& f : p->h2d.frags) {
-    const HostSpan& S = span_at(p, f.host);
-    push_desc(&d, base + p->L.spn + S.stage + (uint64_t)(f.host - S.host), base + f.off, f.len);
+  // span staging: every staged block from its place in the staging region to the
+  // arena, in pieces of at most PLACE_PIECE bytes; the last piece also zeroes the
+  // block's slot up to 16 bytes where the next block does not start before that
+  std::vector<PlaceDesc> pd;
+  const uint64_t nb = p->blocks.size();
+  for (uint64_t b = 0; b < nb; b++) {
+    const HostBlock& B = p->blocks[b];
+    if (p->ihi[b] > p->ilo[b] || !B.bytes) continue;  // moved in place (a host arena)
+    const HostSpan& S = span_at(p, B.host);
+    const uint64_t src = S.stage + (uint64_t)(B.host - S.host), end = B.off + B.bytes;
+    const uint64_t next = b + 1 < nb ? p->blocks[b + 1].off : p->data_bytes;
+    const uint64_t pad = std::min(round_up(end, 16), std::max(next, end)) - end;
+    for (uint64_t o = 0; o < B.bytes; o += PLACE_PIECE) {
+      const uint64_t n = std::min(PLACE_PIECE, B.bytes - o), z = o + n == B.bytes ? pad : 0;
+      pd.push_back({(src + o) | (z << 60), (B.off + o) << 16 | (n + z - 1)});
+    }
   }
-  return upload(p, d, p->L.spd, p->L.spdt, p->L.spd_cap, &p->span_nd, &p->span_units, s, p->L.spdt_cap);
+  if (pd.size() > p->L.spd_cap) return fail(DC_EINVAL, "placement table larger than planned");
+  p->span_nd = pd.size();
+  if (!pd.empty())
+    DC_CUDA(cudaMemcpyAsync(p->dev + p->L.spd, pd.data(), pd.size() * sizeof(PlaceDesc), cudaMemcpyHostToDevice, s));
+  return DC_OK;
 }
 
 dc_status transfer_to_device(dc_plan_s* p, cudaStream_t s) {
@@ -410,7 +426,16 @@ dc_status transfer_to_device(dc_plan_s* p, cudaStream_t s) {
   if (p->span_mode) {  // the spans into the staging region, then every block to its place
     st = send_staged(p, p->h2d_span, p->span_nulls, p->dev + p->L.spn, s);
     if (st) return st;
-    return launch_table(p, p->L.spd, p->L.spdt, p->span_nd, p->span_units, s);
+    PlaceArgs a;
+    a.d = reinterpret_cast<const PlaceDesc*>(p->dev + p->L.spd);
+    a.nd = p->span_nd;
+    a.stage = p->dev + p->L.spn;
+    a.arena = p->dev;
+    a.stage_bytes = p->L.spd - p->L.spn;  // the region, rounded up: 16-byte reads of a piece's last vector stay inside
+    a.data_bytes = p->data_bytes;
+    a.err = reinterpret_cast<uint32_t*>(p->dev + p->L.ctrl) + CTRL_ERR;
+    DC_CUDA(launch_place(a, s, p->sm_count));
+    return DC_OK;
   }
   return send_staged(p, m, p->null_slots, p->dev, s);
 }

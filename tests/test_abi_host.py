@@ -341,8 +341,8 @@ def test_span_staging_plan_rule_and_closed_forms(monkeypatch):
     monkeypatch.setenv("DC_SPANS", "0")  # the rule off; the flag still applies
     assert staging(t)[0] == 0 and staging(t, dc.PLAN_SPANS) == (st, dev)
     monkeypatch.delenv("DC_SPANS")
-    # the device buffer also holds the staging region and one move descriptor per block
-    assert dev >= staging(t, dc.PLAN_MAP_HOST)[1] + st + 32 * len(a.blocks)
+    # the device buffer also holds the staging region and a 16-byte placement piece per block
+    assert dev >= staging(t, dc.PLAN_MAP_HOST)[1] + st + 16 * len(a.blocks)
     # 32-byte gaps: still one span, but 2x the bytes, so only the flag stages by spans
     t2, a2 = tree(32)
     lo2, hi2 = min(x for x, _ in a2.blocks), max(x + n for x, n in a2.blocks)

@@ -712,6 +712,28 @@ def test_span_staging(case):
     full_parity(make, kw, flags=dc.PLAN_SPANS | dc.PLAN_DEVICE_SCAN)
 
 
+@pytest.mark.parametrize("flags", [0, dc.PLAN_PACK_SMALL])
+def test_span_placement_zeroes_the_slots_padding(flags):
+    """The placement writes each block and then zeros up to its 16-byte slot end (or the
+    next block), so after a deep copy by spans every byte of the data region outside the
+    blocks is zero, whatever the buffer held before; the blocks equal the oracle's."""
+    for make, _ in SPAN_CASES.values():
+        t = make()
+        plan = dc.Plan(t.schema, t.root, flags=dc.PLAN_SPANS | flags)
+        buf = plan.bind()
+        n = plan.info["data_bytes"]
+        buf[:n].fill_(0xAB)
+        plan.deep_copy()
+        plan.sync()
+        image_ok(plan, t.schema, t.root)
+        img = plan.image()[:n].copy()
+        for b in plan.blocks():
+            img[b["offset"]:b["offset"] + b["bytes"]] = 0
+        assert not img.any(), int(np.flatnonzero(img)[0])
+        plan.destroy()
+        t.free()
+
+
 def test_span_staging_null_slots_and_random_schemas():
     # count-0 slots with a non-NULL host value are zeroed in the staging area
     full_parity(HandTree, {}, flags=dc.PLAN_SPANS)
