@@ -26,6 +26,9 @@
 //                    arena in 16-byte units (the deep copy's transfer and the
 //                    copy back, one launch for every block instead of one DMA
 //                    per block).
+//   place_kernel     span staging's placement: every staged block from its
+//                    place among the host spans moved to the device to its
+//                    arena offset, one descriptor per block piece.
 //   stream_kernel    the fused step: reads x and y of the selected structs from
 //                    host memory (mapped caller pages or the mapped pinned
 //                    arena), applies the leaf update, writes x and y into the
