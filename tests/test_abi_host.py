@@ -14,6 +14,7 @@ import pytest
 
 import oracle
 import treegen as tg
+from bump import BumpAllocator
 import paper_1906_01128_b300 as dc
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -288,33 +289,6 @@ def test_packed_layout_follows_its_rule_and_relocates():
         p.destroy()
         t.free()
     assert smaller >= 5  # arenas with several small arrays in a lane get shorter
-
-
-ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64)
-
-
-class BumpAllocator:
-    """Blocks for treegen from one buffer: each 16-byte aligned, `gap` bytes after the last."""
-
-    def __init__(self, nbytes, gap):
-        self.buf = (ctypes.c_uint8 * (nbytes + 64))()
-        self.next = (ctypes.addressof(self.buf) + 15) // 16 * 16
-        self.end = ctypes.addressof(self.buf) + nbytes
-        self.gap, self.blocks = gap, []
-        self.fn = ALLOC_FN(self._alloc)
-
-    def _alloc(self, ctx, nbytes, align):
-        a = (self.next + max(align, 16) - 1) // max(align, 16) * max(align, 16)
-        if a + nbytes > self.end:
-            return None
-        self.next = a + nbytes + self.gap
-        if nbytes:
-            self.blocks.append((a, nbytes))
-        return a
-
-    @property
-    def alloc(self):
-        return (ctypes.cast(self.fn, ctypes.c_void_p).value, None)
 
 
 def test_span_staging_plan_rule_and_closed_forms(monkeypatch):

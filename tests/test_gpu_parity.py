@@ -14,6 +14,7 @@ import torch
 
 import oracle
 import treegen as tg
+from bump import BumpAllocator
 import paper_1906_01128_b300 as dc
 
 pytestmark = pytest.mark.gpu
@@ -738,6 +739,8 @@ def test_span_staging_null_slots_and_random_schemas():
     # count-0 slots with a non-NULL host value are zeroed in the staging area
     full_parity(HandTree, {}, flags=dc.PLAN_SPANS)
     full_parity(HandTree, None, flags=dc.PLAN_SPANS)
+    # a forest of 300 uneven trees: their spans, then one persistent relocation + update launch
+    forest_parity(300, 256 << 10, "fused", flags=dc.PLAN_SPANS)
     rng = random.Random(6161)
     for i in range(40):
         schema, levels, rules = tg.random_schema(rng)
@@ -748,7 +751,8 @@ def test_span_staging_by_the_rule_on_the_pointer_heavy_tree(monkeypatch):
     """The 1.1M-node tree of 40-byte arrays stages by spans on the default plan: repeated
     deep copies, the update, the copy back, the round trip and a selective deep copy on
     one plan; with DC_SPANS=0 the same tree stages block by block."""
-    src, ref = tg.workload("reloc_stress"), tg.workload("reloc_stress")
+    bump = BumpAllocator(200 << 20)  # a compact host layout, whatever the process heap looks like
+    src, ref = tg.workload("reloc_stress", alloc=bump.alloc), tg.workload("reloc_stress")
     s = src.schema
     plan = dc.Plan(s, src.root)
     assert plan.info["staging_bytes"] > 0
@@ -777,6 +781,7 @@ def test_span_staging_by_the_rule_on_the_pointer_heavy_tree(monkeypatch):
     plan.destroy()
     src.free()
     ref.free()
+    del bump
     monkeypatch.setenv("DC_SPANS", "0")
     t = tg.workload("reloc_stress")
     p = dc.Plan(t.schema, t.root)

@@ -14,6 +14,7 @@ import torch
 
 import oracle
 import treegen as tg
+from bump import BumpAllocator
 import paper_1906_01128_b300 as dc
 
 pytestmark = pytest.mark.gpu
@@ -68,6 +69,33 @@ def test_same_results_alone_and_in_the_mix(slots, budget_mb):
         assert ok, ("mix", k, msg)
         ok, msg = oracle.trees_equal(s, alone[k].root, ref[k].root)
         assert ok, ("alone", k, msg)
+
+
+def test_served_trees_staged_by_host_spans():
+    """Trees of 1,244 blocks with 40-byte arrays: each request's plan stages its deep copy by host
+    spans, into the pinned staging the server lends it; with evictions and re-touches every host
+    tree still ends bit-identical to the oracle's replay."""
+    nkeys, nreq = 32, 100
+    # the mix's trees from one bump buffer, so that each lies together in host memory (in a
+    # process whose heap is fragmented, malloc scatters small blocks and the rule stages block by block)
+    bump = BumpAllocator(nkeys * (128 << 10))
+    mix = [tg.node_tree(4, 8, 10, seed=300 + k, alloc=bump.alloc) for k in range(nkeys)]
+    ref = [tg.node_tree(4, 8, 10, seed=300 + k) for k in range(nkeys)]
+    s = mix[0].schema
+    p = dc.Plan(s, mix[0].root)
+    assert p.info["staging_bytes"] > 0 and p.info["nblocks"] == 1244
+    p.destroy()
+    reqs = request_stream(nkeys, nreq, seed=11, span_s=0.05)
+    pool = torch.empty(4 << 20, dtype=torch.uint8, device="cuda")
+    srv = dc.Server(s, pool, pinned_bytes=16 << 20, slots=4)
+    srv.run([(k, mix[k].root, a, r) for k, a, r in reqs])
+    st = srv.stats
+    assert st["served"] == nreq and st["failed"] == 0 and st["evictions"] > 0 and st["resident_hits"] > 0
+    srv.destroy()
+    oracle_replay(ref, reqs)
+    for k in range(nkeys):
+        ok, msg = oracle.trees_equal(s, mix[k].root, ref[k].root)
+        assert ok, (k, msg)
 
 
 def test_request_larger_than_the_budget_fails_alone():
