@@ -749,8 +749,9 @@ def test_span_staging_null_slots_and_random_schemas():
 
 def test_span_staging_by_the_rule_on_the_pointer_heavy_tree(monkeypatch):
     """The 1.1M-node tree of 40-byte arrays stages by spans on the default plan: repeated
-    deep copies, the update, the copy back, the round trip and a selective deep copy on
-    one plan; with DC_SPANS=0 the same tree stages block by block."""
+    deep copies, the update, the copy back, the round trip, the selected-arrays round trip
+    and a selective deep copy on one plan; with DC_SPANS=0 the same tree stages block by
+    block."""
     bump = BumpAllocator(200 << 20)  # a compact host layout, whatever the process heap looks like
     src, ref = tg.workload("reloc_stress", alloc=bump.alloc), tg.workload("reloc_stress")
     s = src.schema
@@ -769,6 +770,10 @@ def test_span_staging_by_the_rule_on_the_pointer_heavy_tree(monkeypatch):
     oracle.copy_back(s, cp.root, ref.root, oop)
     assert oracle.trees_equal(s, src.root, ref.root)[0]
     plan.roundtrip(dop)  # deep copy + update + copy back, from the updated host tree
+    oracle.update(s, cp.root, oop)
+    oracle.copy_back(s, cp.root, ref.root, oop)
+    assert oracle.trees_equal(s, src.root, ref.root)[0]
+    plan.roundtrip_selected(dop)  # only the op's arrays, through the pinned arena at their arena offsets
     oracle.update(s, cp.root, oop)
     oracle.copy_back(s, cp.root, ref.root, oop)
     assert oracle.trees_equal(s, src.root, ref.root)[0]
