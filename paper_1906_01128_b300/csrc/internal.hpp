@@ -369,9 +369,12 @@ struct dc_plan_s {
   // to the device staging region by DMA, and places every block in the arena
   // with one move-kernel launch (the host copies stream instead of handling
   // each block).
-  std::vector<dc::HostSpan> spans;    // host order
+  std::vector<dc::HostSpan> spans;    // host order (built on first need)
   uint64_t span_bytes = 0;            // staging area bytes
-  bool span_worth = false;            // the plan's blocks favour span staging
+  uint64_t span_nstaged = 0, span_staged = 0;  // the blocks a full deep copy stages, and their bytes
+  bool span_rule = false;             // their count and mean size allow span staging
+  bool spans_built = false;
+  bool span_worth = false;            // ... and their spans hold at most 5/4 of their bytes
   bool span_mode = false;             // dc_deep_copy stages by spans
   Moves h2d_span;                     // frags: the spans, at their staging offsets
   std::vector<uint64_t> span_nulls;   // NULL-slot fix-ups, as staging offsets (sorted)
@@ -447,7 +450,7 @@ dc_status send_staged(dc_plan_s* p, const dc_plan_s::Moves& m, const std::vector
 void plan_transfers(dc_plan_s* p);
 // Pieces, units, runs and (unless host_order) chunks of m->frags.
 void split_moves(dc_plan_s::Moves* m, bool host_order, uint64_t chunk_bytes);
-// The host spans of the staged blocks and whether span staging pays (at planning).
+// The staged blocks' count and bytes, and whether the span rule may fire (at planning).
 void plan_spans(dc_plan_s* p);
 // span_mode from the plan's flags and span_worth (at planning and flag changes).
 void choose_spans(dc_plan_s* p);

@@ -162,14 +162,33 @@ void plan_spans(dc_plan_s* p) {
   p->spans.clear();
   p->span_bytes = 0;
   p->span_worth = false;
+  p->spans_built = false;
+  p->span_nstaged = p->span_staged = 0;
   const std::vector<uint8_t> fixup = null_fixups(p);
-  std::vector<std::pair<const uint8_t*, uint64_t>> hb;  // the blocks a full deep copy stages
-  uint64_t staged = 0;
+  for (uint64_t b = 0; b < p->blocks.size(); b++) {  // the blocks a full deep copy stages
+    const HostBlock& B = p->blocks[b];
+    if ((!fixup[b] && in_host_arena(B.host, B.bytes, nullptr)) || !B.bytes) continue;
+    p->span_nstaged++;
+    p->span_staged += B.bytes;
+  }
+  const char* v = getenv("DC_SPANS");
+  p->span_rule = !(v && v[0] == '0') && p->span_nstaged >= DC_SPAN_MIN_BLOCKS &&
+                 p->span_staged < (uint64_t)DC_SPAN_MAX_MEAN * p->span_nstaged;
+}
+
+namespace {
+
+// The spans themselves (a sort of the staged blocks by host address), built
+// the first time span staging is asked for or the rule's counts allow it.
+void build_spans(dc_plan_s* p) {
+  p->spans_built = true;
+  const std::vector<uint8_t> fixup = null_fixups(p);
+  std::vector<std::pair<const uint8_t*, uint64_t>> hb;
+  hb.reserve(p->span_nstaged);
   for (uint64_t b = 0; b < p->blocks.size(); b++) {
     const HostBlock& B = p->blocks[b];
     if ((!fixup[b] && in_host_arena(B.host, B.bytes, nullptr)) || !B.bytes) continue;
     hb.push_back({B.host, B.bytes});
-    staged += B.bytes;
   }
   std::sort(hb.begin(), hb.end());
   for (const auto& x : hb) {
@@ -190,15 +209,17 @@ void plan_spans(dc_plan_s* p) {
     o += S.bytes;
   }
   p->span_bytes = round_up(o, 16);
-  const char* v = getenv("DC_SPANS");
-  const bool rule = !(v && v[0] == '0');
-  p->span_worth = rule && hb.size() >= DC_SPAN_MIN_BLOCKS && staged < (uint64_t)DC_SPAN_MAX_MEAN * hb.size() &&
-                  p->span_bytes * 4 <= staged * 5;
+  p->span_worth = p->span_rule && p->span_bytes * 4 <= p->span_staged * 5;
 }
 
+}  // namespace
+
 void choose_spans(dc_plan_s* p) {
-  p->span_mode = !(p->flags & DC_PLAN_MAP_HOST) && !p->spans.empty() &&
-                 ((p->flags & DC_PLAN_SPANS) || p->span_worth);
+  p->span_mode = false;
+  if ((p->flags & DC_PLAN_MAP_HOST) || !p->span_nstaged) return;
+  if (!(p->flags & DC_PLAN_SPANS) && !p->span_rule) return;  // no sort where the rule cannot fire
+  if (!p->spans_built) build_spans(p);
+  p->span_mode = !p->spans.empty() && ((p->flags & DC_PLAN_SPANS) || p->span_worth);
 }
 
 uint64_t pin_arena_bytes(const dc_plan_s* p) {
