@@ -6,7 +6,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 SO = os.path.join(HERE, "libdc.so")
-SOURCES = ["kernels.cu", "plan.cpp", "runtime.cpp", "transfer.cpp", "step.cpp", "tune.cpp", "server.cpp", "arena.cpp", "static_scratch.cu", "trace.cpp", "debug.cpp", "partition.cpp"]
+SOURCES = ["kernels.cu", "plan.cpp", "runtime.cpp", "transfer.cpp", "step.cpp", "tune.cpp", "server.cpp", "arena.cpp", "spans.cpp", "static_scratch.cu", "trace.cpp", "debug.cpp", "partition.cpp"]
 HEADERS = ["internal.hpp", "pool.hpp", "trace.hpp"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 

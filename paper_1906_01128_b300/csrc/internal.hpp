@@ -456,6 +456,15 @@ void plan_spans(dc_plan_s* p);
 void choose_spans(dc_plan_s* p);
 // Bytes of the pinned arena: the data region, or the span staging area if larger.
 uint64_t pin_arena_bytes(const dc_plan_s* p);
+// The placement table of a span-staged plan (spans.cpp): one PlaceDesc per piece, arena order.
+void build_place_table(const dc_plan_s* p, std::vector<PlaceDesc>* out);
+// The plan's NULL-slot fix-ups as offsets in the span staging area, sorted (spans.cpp).
+std::vector<uint64_t> span_null_offsets(const dc_plan_s* p);
+// The struct block holding arena offset `off`; per block, 1 for a struct block with a
+// NULL-slot fix-up; the span holding host address h (spans.cpp).
+uint64_t struct_block_at(const dc_plan_s* p, uint64_t off);
+std::vector<uint8_t> null_fixups(const dc_plan_s* p);
+const HostSpan& span_at(const dc_plan_s* p, const uint8_t* h);
 void release_transfers(dc_plan_s* p);
 dc_status upload_h2d_tables(dc_plan_s* p, cudaStream_t s);
 dc_status transfer_to_device(dc_plan_s* p, cudaStream_t s);

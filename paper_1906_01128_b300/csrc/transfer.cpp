@@ -4,8 +4,7 @@
 //   staged (default)  every block is marshalled into the plan's pinned arena
 //                     (Algorithm 1: one contiguous buffer) by host threads and
 //                     sent by DMA in chunks, each chunk as soon as it is
-//                     marshalled; the copy back is one move-kernel launch into
-//                     the (mapped) pinned arena plus a host scatter.
+//                     marshalled.
 //   mapped (DC_PLAN_MAP_HOST)  the whole pages strictly inside each large
 //                     array are page-locked in place, and one move-kernel launch
 //                     reads them straight from the caller's memory (one
@@ -15,7 +14,9 @@
 //                     are marshalled meanwhile and moved by a second launch.
 //                     The copy back writes array interiors straight back.
 // Only pages wholly inside an array are registered, so no other object's bytes
-// are ever page-locked.
+// are ever page-locked.  A staged plan of many small blocks copies whole host
+// spans instead of single blocks (span staging, spans.cpp); the staged copy back
+// is a DMA into the pinned arena in chunks and a host scatter per chunk.
 #include <immintrin.h>
 
 #include <algorithm>
@@ -132,100 +133,6 @@ void split_moves(dc_plan_s::Moves* m, bool host_order, uint64_t chunk_bytes) {
   }
 }
 
-namespace {
-
-// The struct block that holds arena offset `off` (a slot of a struct block).
-uint64_t struct_block_at(const dc_plan_s* p, uint64_t off) {
-  auto it = std::upper_bound(p->blocks.begin(), p->blocks.begin() + p->nstruct_blocks, off,
-                             [](uint64_t o, const HostBlock& hb) { return o < hb.off; });
-  return (uint64_t)(it - p->blocks.begin()) - 1;
-}
-
-// Per block: 1 if it is a struct block with a NULL-slot fix-up (such blocks go
-// through the pinned arena even when they live in a host arena).
-std::vector<uint8_t> null_fixups(const dc_plan_s* p) {
-  std::vector<uint8_t> fixup(p->blocks.size(), 0);
-  for (uint64_t off : p->null_slots) fixup[struct_block_at(p, off)] = 1;
-  return fixup;
-}
-
-// The span holding host address h (spans are in host order, h inside one).
-const HostSpan& span_at(const dc_plan_s* p, const uint8_t* h) {
-  auto it = std::upper_bound(p->spans.begin(), p->spans.end(), h,
-                             [](const uint8_t* a, const HostSpan& sp) { return a < sp.host; });
-  return *(it - 1);
-}
-
-}  // namespace
-
-void plan_spans(dc_plan_s* p) {
-  p->spans.clear();
-  p->span_bytes = 0;
-  p->span_worth = false;
-  p->spans_built = false;
-  p->span_nstaged = p->span_staged = 0;
-  const std::vector<uint8_t> fixup = null_fixups(p);
-  for (uint64_t b = 0; b < p->blocks.size(); b++) {  // the blocks a full deep copy stages
-    const HostBlock& B = p->blocks[b];
-    if ((!fixup[b] && in_host_arena(B.host, B.bytes, nullptr)) || !B.bytes) continue;
-    p->span_nstaged++;
-    p->span_staged += B.bytes;
-  }
-  const char* v = getenv("DC_SPANS");
-  p->span_rule = !(v && v[0] == '0') && p->span_nstaged >= DC_SPAN_MIN_BLOCKS &&
-                 p->span_staged < (uint64_t)DC_SPAN_MAX_MEAN * p->span_nstaged;
-}
-
-namespace {
-
-// The spans themselves (a sort of the staged blocks by host address), built
-// the first time span staging is asked for or the rule's counts allow it.
-void build_spans(dc_plan_s* p) {
-  p->spans_built = true;
-  const std::vector<uint8_t> fixup = null_fixups(p);
-  std::vector<std::pair<const uint8_t*, uint64_t>> hb;
-  hb.reserve(p->span_nstaged);
-  for (uint64_t b = 0; b < p->blocks.size(); b++) {
-    const HostBlock& B = p->blocks[b];
-    if ((!fixup[b] && in_host_arena(B.host, B.bytes, nullptr)) || !B.bytes) continue;
-    hb.push_back({B.host, B.bytes});
-  }
-  std::sort(hb.begin(), hb.end());
-  for (const auto& x : hb) {
-    if (!p->spans.empty()) {
-      HostSpan& S = p->spans.back();
-      const uint8_t* end = S.host + S.bytes;
-      if (x.first >= end && (uint64_t)(x.first - end) < SPAN_GAP) {  // blocks never overlap
-        S.bytes = (uint64_t)(x.first + x.second - S.host);
-        continue;
-      }
-    }
-    p->spans.push_back({x.first, x.second, 0});
-  }
-  uint64_t o = 0;
-  for (HostSpan& S : p->spans) {  // each span keeps its host address's phase modulo 16
-    o = round_up(o, 16) + ((uintptr_t)S.host & 15);
-    S.stage = o;
-    o += S.bytes;
-  }
-  p->span_bytes = round_up(o, 16);
-  p->span_worth = p->span_rule && p->span_bytes * 4 <= p->span_staged * 5;
-}
-
-}  // namespace
-
-void choose_spans(dc_plan_s* p) {
-  p->span_mode = false;
-  if ((p->flags & DC_PLAN_MAP_HOST) || !p->span_nstaged) return;
-  if (!(p->flags & DC_PLAN_SPANS) && !p->span_rule) return;  // no sort where the rule cannot fire
-  if (!p->spans_built) build_spans(p);
-  p->span_mode = !p->spans.empty() && ((p->flags & DC_PLAN_SPANS) || p->span_worth);
-}
-
-uint64_t pin_arena_bytes(const dc_plan_s* p) {
-  return std::max(p->data_bytes, p->span_mode ? p->span_bytes : 0);
-}
-
 void plan_transfers(dc_plan_s* p) {
   const uint64_t nb = p->blocks.size();
   p->ilo.assign(nb, 0);
@@ -272,13 +179,7 @@ void plan_transfers(dc_plan_s* p) {
   if (p->span_mode) {  // the spans move instead, in staging order, chunk by chunk
     for (const HostSpan& S : p->spans) p->h2d_span.frags.push_back({S.stage, S.bytes, const_cast<uint8_t*>(S.host)});
     split_moves(&p->h2d_span, false, 0);
-    for (uint64_t off : p->null_slots) {  // where each NULL-slot fix-up lies in the staging area
-      const HostBlock& B = p->blocks[struct_block_at(p, off)];
-      const uint8_t* h = B.host + (off - B.off);
-      const HostSpan& S = span_at(p, h);
-      p->span_nulls.push_back(S.stage + (uint64_t)(h - S.host));
-    }
-    std::sort(p->span_nulls.begin(), p->span_nulls.end());
+    p->span_nulls = span_null_offsets(p);
   }
   p->transfers_ready = true;
 }
@@ -406,23 +307,8 @@ dc_status upload_h2d_tables(dc_plan_s* p, cudaStream_t s) {
     for (const auto& r : p->h2d.runs) push_desc(&d, (uint64_t)(uintptr_t)p->pinned_dev + r.lo, base + r.lo, r.hi - r.lo);
   st = upload(p, d, p->L.mvb, p->L.mvbt, p->L.tab_cap, &p->h2d_frag_nd, &p->h2d_frag_units, s);
   if (st || !p->span_mode) return st;
-  // span staging: every staged block from its place in the staging region to the
-  // arena, in pieces of at most PLACE_PIECE bytes; the last piece also zeroes the
-  // block's slot up to 16 bytes where the next block does not start before that
   std::vector<PlaceDesc> pd;
-  const uint64_t nb = p->blocks.size();
-  for (uint64_t b = 0; b < nb; b++) {
-    const HostBlock& B = p->blocks[b];
-    if (p->ihi[b] > p->ilo[b] || !B.bytes) continue;  // moved in place (a host arena)
-    const HostSpan& S = span_at(p, B.host);
-    const uint64_t src = S.stage + (uint64_t)(B.host - S.host), end = B.off + B.bytes;
-    const uint64_t next = b + 1 < nb ? p->blocks[b + 1].off : p->data_bytes;
-    const uint64_t pad = std::min(round_up(end, 16), std::max(next, end)) - end;
-    for (uint64_t o = 0; o < B.bytes; o += PLACE_PIECE) {
-      const uint64_t n = std::min(PLACE_PIECE, B.bytes - o), z = o + n == B.bytes ? pad : 0;
-      pd.push_back({(src + o) | (z << 60), (B.off + o) << 16 | (n + z - 1)});
-    }
-  }
+  build_place_table(p, &pd);
   if (pd.size() > p->L.spd_cap) return fail(DC_EINVAL, "placement table larger than planned");
   p->span_nd = pd.size();
   if (!pd.empty())

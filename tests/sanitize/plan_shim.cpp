@@ -12,6 +12,7 @@
 // the plan is laid out again with DC_PLAN_PACK_SMALL (as dc_plan_set_flags does)
 // and every block's alignment is checked against the packing rule.
 #include <cstdio>
+#include <cstring>
 #include <unordered_map>
 #include <vector>
 
@@ -138,6 +139,101 @@ extern "C" int shim_plan(const dc_schema* schema, const void* const* roots, uint
         break;
       }
     }
+  }
+  delete p;
+  return rc;
+}
+
+// Span staging on the CPU: plan with `flags` (DC_PLAN_PACK_SMALL lays the plan
+// out again), then check the spans (host order, gaps of SPAN_GAP or more between
+// them, staging offsets in order with their host address's phase modulo 16)
+// and the placement table (pieces in arena order that cover every staged block
+// exactly, read inside the staging area, and pad only up to the block's 16-byte
+// slot end or the next block).  With `emulate`, copy the spans into a staging
+// buffer as the deep copy does (reading the gaps: only for trees whose blocks
+// share one allocation), zero the NULL-slot fix-ups, apply the table to an
+// arena image filled with 0xAB, and check every block's bytes and that every
+// other byte of the data region is zero.  out[0..3] = span staging on, staging
+// bytes, spans, pieces.  Returns 1000 on a failed check (message in
+// shim_message()), else the planning status.
+extern "C" int shim_spans(const dc_schema* schema, const void* const* roots, uint64_t nroots, uint32_t flags,
+                          int emulate, uint64_t* out) {
+  dc_plan_s* p = new dc_plan_s;
+  int st = dc::build_plan(schema, roots, nroots, p);
+  if (!st && (flags & DC_PLAN_PACK_SMALL)) {
+    p->flags |= DC_PLAN_PACK_SMALL;
+    st = dc::layout(p);
+  }
+  if (st) {
+    delete p;
+    return st;
+  }
+  dc::plan_spans(p);
+  p->flags |= flags;
+  dc::choose_spans(p);
+  out[0] = p->span_mode;
+  out[1] = p->span_bytes;
+  out[2] = p->spans.size();
+  out[3] = 0;
+  if (!p->span_mode) {
+    delete p;
+    return 0;
+  }
+  int rc = 0;
+  for (size_t i = 0; i < p->spans.size() && !rc; i++) {
+    const dc::HostSpan& S = p->spans[i];
+    if (S.stage % 16 != (uint64_t)(uintptr_t)S.host % 16 || S.stage + S.bytes > p->span_bytes)
+      rc = bad("span's staging offset", i, S.stage);
+    else if (i && (S.host < p->spans[i - 1].host + p->spans[i - 1].bytes ||
+                   (uint64_t)(S.host - (p->spans[i - 1].host + p->spans[i - 1].bytes)) < dc::SPAN_GAP ||
+                   S.stage < p->spans[i - 1].stage + p->spans[i - 1].bytes))
+      rc = bad("spans out of order or closer than the merge gap", i, S.stage);
+  }
+  std::vector<dc::PlaceDesc> pd;
+  dc::build_place_table(p, &pd);
+  out[3] = pd.size();
+  size_t k = 0;
+  const uint64_t nb = p->blocks.size();
+  for (uint64_t b = 0; b < nb && !rc; b++) {  // the pieces of each block, in arena order
+    const dc::HostBlock& B = p->blocks[b];
+    const dc::HostSpan& S = dc::span_at(p, B.host);
+    if (B.host < S.host || B.host + B.bytes > S.host + S.bytes) {
+      rc = bad("block outside its span", b, B.off);
+      break;
+    }
+    const uint64_t end = B.off + B.bytes, next = b + 1 < nb ? p->blocks[b + 1].off : p->data_bytes;
+    for (uint64_t o = 0; o < B.bytes && !rc; k++) {
+      if (k >= pd.size()) {
+        rc = bad("placement table ends early", b, o);
+        break;
+      }
+      const uint64_t src = pd[k].src & ((1ull << 60) - 1), pad = pd[k].src >> 60, dst = pd[k].dst >> 16;
+      const uint64_t w = (pd[k].dst & 0xFFFFu) + 1, n = w - pad;
+      const bool last = o + n == B.bytes;
+      if (dst != B.off + o || src != S.stage + (uint64_t)(B.host - S.host) + o || n > dc::PLACE_PIECE ||
+          src + n > p->span_bytes)
+        rc = bad("piece's source or destination", b, o);
+      else if (pad >= 16 || (!last && pad) || (last && dst + w != std::min(dc::round_up(end, 16), next)))
+        rc = bad("piece's padding", b, pad);
+      o += n;
+    }
+  }
+  if (!rc && k != pd.size()) rc = bad("placement table has extra pieces", k, pd.size());
+  if (!rc && emulate) {
+    std::vector<uint8_t> stage(p->span_bytes, 0), img(p->data_bytes, 0xAB);
+    for (const dc::HostSpan& S : p->spans) memcpy(stage.data() + S.stage, S.host, S.bytes);
+    for (uint64_t o : dc::span_null_offsets(p)) memset(stage.data() + o, 0, 8);
+    for (const dc::PlaceDesc& d : pd) {
+      const uint64_t src = d.src & ((1ull << 60) - 1), pad = d.src >> 60, dst = d.dst >> 16;
+      const uint64_t w = (d.dst & 0xFFFFu) + 1;
+      memcpy(img.data() + dst, stage.data() + src, w - pad);
+      memset(img.data() + dst + (w - pad), 0, pad);
+    }
+    std::vector<uint8_t> want(p->data_bytes, 0);  // the blocks' bytes, NULL slots zeroed; zero elsewhere
+    for (const dc::HostBlock& B : p->blocks) memcpy(want.data() + B.off, B.host, B.bytes);
+    for (uint64_t o : p->null_slots) memset(want.data() + o, 0, 8);
+    for (uint64_t i = 0; i < p->data_bytes && !rc; i++)
+      if (img[i] != want[i]) rc = bad("emulated arena byte", i, img[i]);
   }
   delete p;
   return rc;

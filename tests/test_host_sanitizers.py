@@ -9,7 +9,10 @@ undefined behaviour aborts the child.  The shim also checks the relocation
 tables the way the relocation kernel reads them (every slot inside its tile,
 each record in the group it names, each group's base plus the record's offset
 equal to the plan's offset of the target block, and the record's slot being
-the one that points at that block)."""
+the one that points at that block).  For span staging it checks the spans and
+the placement table on every tree, and on trees from one bump buffer emulates
+the whole staged path (span copies, NULL-slot fix-ups, placement) against the
+blocks' own bytes."""
 import os
 import shutil
 import subprocess
@@ -24,7 +27,7 @@ CSRC = os.path.join(ROOT, "paper_1906_01128_b300", "csrc")
 CUDA = "/usr/local/cuda"
 
 DRIVER = textwrap.dedent(r'''
-    import ctypes, random, sys
+    import ctypes, os, random, sys
     sys.path.insert(0, ROOT)
     import treegen as tg
     from paper_1906_01128_b300 import schema_struct
@@ -66,7 +69,50 @@ DRIVER = textwrap.dedent(r'''
     # planning errors: the same tree twice in a forest (alias), a NULL root in a forest
     rc, _ = plan(forest[0].schema, [forest[0].root, forest[0].root])
     assert rc != 0
-    print("planned", len(trees) + 1, "trees,", n, "blocks")
+    # span staging: the spans and the placement table of every tree above (their blocks are
+    # malloc'd, so nothing reads between them), then the whole staged path emulated on trees
+    # whose blocks come from one bump buffer (gaps of 0 to 2,000 bytes: one span or many)
+    lib.shim_spans.restype = ctypes.c_int
+    lib.shim_spans.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
+                               ctypes.c_void_p]
+
+    def spans(schema, roots, flags, emulate):
+        cs, keep = schema_struct(schema)
+        arr = (ctypes.c_void_p * len(roots))(*roots)
+        out = (ctypes.c_uint64 * 4)()
+        rc = lib.shim_spans(ctypes.byref(cs), arr, len(roots), flags, emulate, out)
+        if rc == 1000:
+            raise SystemExit("span check: " + lib.shim_message().decode())
+        return rc, list(out)
+
+    SPANS, PACK = 16, 8
+    for t in trees:
+        for fl in (SPANS, SPANS | PACK):
+            rc, out = spans(t.schema, [t.root], fl, 0)
+            assert rc == 0 and out[0] == 1, (t.name, fl, rc, out)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from bump import BumpAllocator
+    keep_alive = []
+    rng = random.Random(12)
+    for i in range(30):
+        s, levels, rules = tg.random_schema(rng)
+        sized = tg.Tree(s, levels, rules, seed=2100 + i)  # for the buffer's size
+        gap = rng.choice([0, 8, 48, 2000])
+        nb = sized.payload_bytes + (1 << 20)
+        sized.free()
+        b = BumpAllocator(nb + 40000 * (gap + 32), gap)
+        t = tg.Tree(s, levels, rules, seed=2100 + i, alloc=b.alloc)
+        keep_alive.append(b)
+        for fl in (SPANS, SPANS | PACK):
+            rc, out = spans(t.schema, [t.root], fl, 1)
+            assert rc == 0 and out[0] == 1, (i, fl, rc, out)
+    b = BumpAllocator(16 << 20)
+    t = tg.node_tree(4, 8, 10, seed=300, alloc=b.alloc)  # 1,244 blocks of 40-byte arrays: by the rule
+    rc, out = spans(t.schema, [t.root], 0, 1)
+    assert rc == 0 and out[0] == 1 and out[2] == 1, out
+    rc, out = spans(t.schema, [t.root], PACK, 1)
+    assert rc == 0 and out[0] == 1, out
+    print("planned", len(trees) + 1, "trees,", n, "blocks; span staging checked")
 ''')
 
 
@@ -77,7 +123,8 @@ def test_plan_under_asan_and_ubsan(tmp_path):
     so = str(tmp_path / "libplan_asan.so")
     cmd = [gxx, "-std=c++17", "-O1", "-g", "-fsanitize=address,undefined", "-fno-sanitize-recover=all",
            "-fno-omit-frame-pointer", "-shared", "-fPIC", f"-I{CUDA}/include", f"-I{CSRC}",
-           os.path.join(CSRC, "plan.cpp"), os.path.join(CSRC, "trace.cpp"),
+           os.path.join(CSRC, "plan.cpp"), os.path.join(CSRC, "trace.cpp"), os.path.join(CSRC, "spans.cpp"),
+           os.path.join(CSRC, "arena.cpp"), os.path.join(CSRC, "debug.cpp"),
            os.path.join(HERE, "sanitize", "plan_shim.cpp"),
            f"-L{CUDA}/lib64", "-lcudart", f"-Wl,-rpath,{CUDA}/lib64", "-o", so]
     subprocess.run(cmd, check=True, capture_output=True, text=True)
