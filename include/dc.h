@@ -257,7 +257,8 @@ DC_API dc_status dc_plan_destroy(dc_plan_t plan);
  * info.device_bytes bytes, 256-byte aligned (a torch CUDA uint8 tensor
  * qualifies).  Uploads the block table and clears the scratch on `stream`
  * (blocking).  The plan's first bind also allocates its pinned staging arena:
- * info.data_bytes of page-locked host memory.
+ * info.data_bytes of page-locked host memory (or info.staging_bytes, if larger,
+ * for a plan staged by host spans).
  * Errors: DC_EBUDGET, DC_EINVAL (misaligned), DC_ENOMEM, DC_ECUDA. */
 DC_API dc_status dc_bind_device(dc_plan_t plan, void* dev_buffer, uint64_t bytes, dc_stream_t stream);
 
@@ -268,7 +269,11 @@ DC_API dc_status dc_bind_device(dc_plan_t plan, void* dev_buffer, uint64_t bytes
  * contiguous buffer) by the plan's host threads, which take work units of
  * about 256 KiB in arena order; each 16 MiB chunk of the arena goes by DMA as
  * soon as its last unit is marshalled, while the threads go on with the next
- * chunks (the call returns once every chunk is queued); with DC_PLAN_MAP_HOST
+ * chunks (the call returns once every chunk is queued).  A plan staged by host
+ * spans (DC_PLAN_SPANS, or the plan's own rule for many small blocks) copies
+ * whole spans the same way into the staging area, sends them to the device
+ * buffer's staging region, and one kernel launch puts every block at its arena
+ * offset before the relocation.  With DC_PLAN_MAP_HOST
  * the interiors of large arrays are
  * read straight from the caller's pages by one kernel launch (one transfer
  * per effective-address array, as in the paper's pointerchain scheme,
