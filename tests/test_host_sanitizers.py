@@ -136,3 +136,32 @@ def test_plan_under_asan_and_ubsan(tmp_path):
     r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, (r.stdout[-3000:], r.stderr[-3000:])
     assert "planned" in r.stdout
+
+
+def test_thread_pool_under_tsan(tmp_path):
+    """The host pool with several callers' jobs in flight at once (the server's slots share one
+    pool): every item runs exactly once and every call returns after its own items, under
+    ThreadSanitizer."""
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("no g++")
+    so = str(tmp_path / "libpool_tsan.so")
+    cmd = [gxx, "-std=c++17", "-O1", "-g", "-fsanitize=thread", "-shared", "-fPIC", f"-I{CSRC}",
+           os.path.join(HERE, "sanitize", "pool_shim.cpp"), "-lpthread", "-o", so]
+    subprocess.run(cmd, check=True, capture_output=True, text=True)
+    tsan = subprocess.run([gxx, "-print-file-name=libtsan.so"], capture_output=True, text=True).stdout.strip()
+    code = textwrap.dedent(f"""
+        import ctypes, sys
+        lib = ctypes.CDLL({so!r})
+        lib.pool_stress.restype = ctypes.c_int
+        lib.pool_stress.argtypes = [ctypes.c_uint, ctypes.c_uint, ctypes.c_uint, ctypes.c_uint64]
+        lib.pool_message.restype = ctypes.c_char_p
+        for threads, callers, jobs, seed in ((4, 1, 200, 1), (4, 6, 120, 2), (8, 8, 80, 3), (2, 3, 150, 4)):
+            rc = lib.pool_stress(threads, callers, jobs, seed)
+            if rc:
+                sys.exit("pool: " + lib.pool_message().decode())
+        print("pool ok")
+    """)
+    env = dict(os.environ, LD_PRELOAD=tsan, TSAN_OPTIONS="halt_on_error=1 report_signal_unsafe=0")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and "pool ok" in r.stdout, (r.stdout[-3000:], r.stderr[-3000:])
