@@ -9,11 +9,13 @@
 // those items.
 //
 // Waking sleeping threads costs tens of microseconds on a virtual machine, so
-// workers spin for a short while (SPIN rounds of a pause instruction) after
+// workers spin for a while (SPIN rounds of a yield to the scheduler) after
 // their last item before they sleep, and a caller spins the same way for its
 // job's items to finish: back-to-back jobs (a transfer's chunks) then start
-// within a few microseconds.  Jobs of one or two items run on the calling
-// thread alone.
+// within a few microseconds.  The spin yields rather than pauses because the
+// server's slot threads share the cores with the workers: a pausing worker
+// holds a core a slot thread is waiting for (DC_POOL_YIELD=0 builds the pause
+// form).  Jobs of one or two items run on the calling thread alone.
 #pragma once
 
 #include <algorithm>
@@ -25,7 +27,10 @@
 #include <thread>
 #include <vector>
 
-#if defined(DC_POOL_YIELD) && DC_POOL_YIELD
+#ifndef DC_POOL_YIELD
+#define DC_POOL_YIELD 1
+#endif
+#if DC_POOL_YIELD
 #define DC_POOL_PAUSE() std::this_thread::yield()
 #elif defined(__x86_64__) || defined(__i386__)
 #include <immintrin.h>
@@ -41,7 +46,7 @@ class Pool {
 #ifndef DC_POOL_SPIN
 #define DC_POOL_SPIN 4096
 #endif
-  static constexpr unsigned SPIN = DC_POOL_SPIN;  // pause rounds before sleeping (tens of microseconds)
+  static constexpr unsigned SPIN = DC_POOL_SPIN;  // spin rounds before sleeping
   static constexpr uint64_t TAKE = 2;              // items a worker takes from one job before moving on
 
   explicit Pool(unsigned nthreads) {
