@@ -735,6 +735,37 @@ def test_span_placement_zeroes_the_slots_padding(flags):
         t.free()
 
 
+@pytest.mark.parametrize("min_align", [8])
+def test_span_staging_of_blocks_off_16_byte_boundaries(min_align):
+    """Host blocks at 8-byte aligned addresses (a packing allocator's): the staging area
+    keeps each span's phase, so the placement reads off 16 bytes and takes its 8-, 4- and 1-byte
+    steps, for small pieces (one lane) and large ones (a warp)."""
+    for make_kw in (dict(levels=4, fanout=8, length=10), dict(levels=3, fanout=6, length=tg.uniform(1, 3000))):
+        def make(alloc=None):
+            return tg.node_tree(make_kw["levels"], make_kw["fanout"], make_kw["length"], seed=77, alloc=alloc)
+        bump = BumpAllocator(64 << 20, gap=4, min_align=min_align)
+        src, ref = make(bump.alloc), make()
+        s = src.schema
+        assert any(a % 16 for a, _ in bump.blocks)
+        for flags in (dc.PLAN_SPANS, dc.PLAN_SPANS | dc.PLAN_PACK_SMALL):
+            plan = dc.Plan(s, src.root, flags=flags | dc.PLAN_VERIFY)
+            plan.bind()
+            plan.deep_copy()
+            plan.sync()
+            image_ok(plan, s, src.root)
+            dop, oop = ops_pair()
+            plan.update(dop)
+            plan.copy_back()
+            cp = oracle.deep_copy(s, ref.root)
+            oracle.update(s, cp.root, oop)
+            oracle.copy_back(s, cp.root, ref.root, oop)
+            ok, msg = oracle.trees_equal(s, src.root, ref.root)
+            assert ok, msg
+            plan.destroy()
+        src.free()
+        ref.free()
+
+
 def test_span_staging_null_slots_and_random_schemas():
     # count-0 slots with a non-NULL host value are zeroed in the staging area
     full_parity(HandTree, {}, flags=dc.PLAN_SPANS)

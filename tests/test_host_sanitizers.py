@@ -106,6 +106,14 @@ DRIVER = textwrap.dedent(r'''
         for fl in (SPANS, SPANS | PACK):
             rc, out = spans(t.schema, [t.root], fl, 1)
             assert rc == 0 and out[0] == 1, (i, fl, rc, out)
+    for al in (8,):  # blocks off 16-byte boundaries: the staging keeps each span's phase
+        b = BumpAllocator(32 << 20, gap=4, min_align=al)
+        keep_alive.append(b)
+        t = tg.node_tree(3, 6, tg.uniform(1, 3000), seed=77, alloc=b.alloc)
+        assert any(a % 16 for a, _ in b.blocks)
+        for fl in (SPANS, SPANS | PACK):
+            rc, out = spans(t.schema, [t.root], fl, 1)
+            assert rc == 0 and out[0] == 1, (al, fl, rc, out)
     b = BumpAllocator(16 << 20)
     t = tg.node_tree(4, 8, 10, seed=300, alloc=b.alloc)  # 1,244 blocks of 40-byte arrays: by the rule
     rc, out = spans(t.schema, [t.root], 0, 1)
