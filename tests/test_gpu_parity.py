@@ -766,6 +766,46 @@ def test_span_staging_of_blocks_off_16_byte_boundaries(min_align):
         ref.free()
 
 
+def test_span_staging_with_part_of_the_tree_in_a_host_arena():
+    """Every other block from a library host arena (moved in place, never staged) and the rest
+    from one bump buffer (staged by host spans): the placement table skips the arena's blocks and
+    the image, the update and the copy back equal the oracle's, with spans forced and by default."""
+    from bump import ALLOC_FN
+    for flags in (dc.PLAN_SPANS, 0):
+        arena = dc.HostArena(64 << 20)
+        bump = BumpAllocator(64 << 20)
+        turn = [0]
+
+        def alternate(ctx, nbytes, align):
+            turn[0] += 1
+            return arena.alloc(nbytes, max(align, 16)) if turn[0] % 2 else bump._alloc(None, nbytes, align)
+
+        fn = ALLOC_FN(alternate)
+        mk = lambda alloc=None: tg.node_tree(4, 8, tg.uniform(1, 300), seed=91, alloc=alloc)  # noqa: E731
+        src, ref = mk((ctypes.cast(fn, ctypes.c_void_p).value, None)), mk()
+        s = src.schema
+        assert arena.used > 0 and bump.blocks
+        plan = dc.Plan(s, src.root, flags=flags | dc.PLAN_VERIFY)
+        if flags:
+            assert plan.info["staging_bytes"] > 0
+        plan.bind()
+        plan.deep_copy()
+        plan.sync()
+        image_ok(plan, s, src.root)
+        dop, oop = ops_pair()
+        plan.update(dop)
+        plan.copy_back()
+        cp = oracle.deep_copy(s, ref.root)
+        oracle.update(s, cp.root, oop)
+        oracle.copy_back(s, cp.root, ref.root, oop)
+        ok, msg = oracle.trees_equal(s, src.root, ref.root)
+        assert ok, msg
+        plan.destroy()
+        src.free()
+        ref.free()
+        arena.destroy()
+
+
 def test_span_staging_null_slots_and_random_schemas():
     # count-0 slots with a non-NULL host value are zeroed in the staging area
     full_parity(HandTree, {}, flags=dc.PLAN_SPANS)
