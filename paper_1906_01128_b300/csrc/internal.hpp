@@ -177,7 +177,7 @@ struct MoveArgs {
 // bytes written after it (high 4 bits, < 16); `dst` holds its arena offset
 // (high 48 bits) and the bytes written there minus one (low 16 bits).  A piece
 // writes its bytes and then zeros up to its 16-byte slot end where the arena
-// leaves room, so that writes fill whole sectors.  Pieces are in arena order.
+// leaves room, so that writes fill whole sectors.  Pieces are in staging order.
 struct PlaceDesc {
   uint64_t src, dst;
 };
@@ -456,7 +456,7 @@ void plan_spans(dc_plan_s* p);
 void choose_spans(dc_plan_s* p);
 // Bytes of the pinned arena: the data region, or the span staging area if larger.
 uint64_t pin_arena_bytes(const dc_plan_s* p);
-// The placement table of a span-staged plan (spans.cpp): one PlaceDesc per piece, arena order.
+// The placement table of a span-staged plan (spans.cpp): one PlaceDesc per piece, staging order.
 void build_place_table(const dc_plan_s* p, std::vector<PlaceDesc>* out);
 // The plan's NULL-slot fix-ups as offsets in the span staging area, sorted (spans.cpp).
 std::vector<uint64_t> span_null_offsets(const dc_plan_s* p);

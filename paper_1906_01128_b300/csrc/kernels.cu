@@ -788,8 +788,9 @@ __device__ __forceinline__ void place_chunk(const uint8_t* s, uint8_t* d, uint32
 // Every piece of the placement table, warp by warp: each lane loads one
 // descriptor (16 coalesced bytes) and copies its piece itself when it writes
 // at most 64 bytes; larger pieces are copied by the whole warp, one after
-// another, 16 bytes per lane.  The pieces are in arena order, so a warp's
-// writes of small pieces fall in a few consecutive lines.
+// another, 16 bytes per lane.  The pieces are in staging order, so a warp
+// reads consecutive bytes, and its writes of small pieces fall in a few runs
+// of consecutive slots (one per lane of the arena).
 __global__ void __launch_bounds__(LEAF_THREADS) place_kernel(PlaceArgs a) {
   constexpr uint32_t WPB = LEAF_THREADS / 32;
   const uint32_t lane = threadIdx.x & 31;

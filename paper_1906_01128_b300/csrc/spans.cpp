@@ -131,6 +131,11 @@ void build_place_table(const dc_plan_s* p, std::vector<PlaceDesc>* out) {
       out->push_back({(src + o) | (z << 60), (B.off + o) << 16 | (n + z - 1)});
     }
   }
+  // in staging order: a warp then reads consecutive bytes, and its writes go to a
+  // few runs of consecutive slots, one per lane (no two pieces write the same byte)
+  std::sort(out->begin(), out->end(), [](const PlaceDesc& a, const PlaceDesc& b) {
+    return (a.src & ((1ull << 60) - 1)) < (b.src & ((1ull << 60) - 1));
+  });
 }
 
 }  // namespace dc

@@ -11,6 +11,7 @@
 // device-scan relocation does, equal to the same offsets.  With `pack`
 // the plan is laid out again with DC_PLAN_PACK_SMALL (as dc_plan_set_flags does)
 // and every block's alignment is checked against the packing rule.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <unordered_map>
@@ -147,8 +148,8 @@ extern "C" int shim_plan(const dc_schema* schema, const void* const* roots, uint
 // Span staging on the CPU: plan with `flags` (DC_PLAN_PACK_SMALL lays the plan
 // out again), then check the spans (host order, gaps of SPAN_GAP or more between
 // them, staging offsets in order with their host address's phase modulo 16)
-// and the placement table (pieces in arena order that cover every staged block
-// exactly, read inside the staging area, and pad only up to the block's 16-byte
+// and the placement table (pieces in staging order that, taken in arena order,
+// cover every staged block exactly, read inside the staging area, and pad only up to the block's 16-byte
 // slot end or the next block).  With `emulate`, copy the spans into a staging
 // buffer as the deep copy does (reading the gaps: only for trees whose blocks
 // share one allocation), zero the NULL-slot fix-ups, apply the table to an
@@ -192,6 +193,9 @@ extern "C" int shim_spans(const dc_schema* schema, const void* const* roots, uin
   std::vector<dc::PlaceDesc> pd;
   dc::build_place_table(p, &pd);
   out[3] = pd.size();
+  for (size_t i = 1; i < pd.size() && !rc; i++)  // staging order
+    if ((pd[i].src & ((1ull << 60) - 1)) < (pd[i - 1].src & ((1ull << 60) - 1))) rc = bad("pieces not in staging order", i, 0);
+  std::sort(pd.begin(), pd.end(), [](const dc::PlaceDesc& a, const dc::PlaceDesc& b) { return a.dst < b.dst; });
   size_t k = 0;
   const uint64_t nb = p->blocks.size();
   for (uint64_t b = 0; b < nb && !rc; b++) {  // the pieces of each block, in arena order
