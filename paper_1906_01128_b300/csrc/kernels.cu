@@ -785,8 +785,45 @@ __device__ __forceinline__ void place_chunk(const uint8_t* s, uint8_t* d, uint32
   for (; k < e; k++) d[k] = 0;
 }
 
+// Word x holding bytes [b, b + 4) of a piece, with the bytes at or past `valid` zeroed.
+__device__ __forceinline__ uint32_t keep_below(uint32_t x, uint32_t b, uint32_t valid) {
+  return valid >= b + 4 ? x : valid <= b ? 0u : (x & ((1u << (8 * (valid - b))) - 1));
+}
+
+// A piece that writes more than 64 bytes, by a whole warp, 16 bytes per lane at
+// a time (rare in a span-staged plan, so kept out of line).
+__device__ __noinline__ void place_big(const uint8_t* s, uint8_t* d, uint32_t wlen, uint32_t valid, uint32_t lane) {
+  for (uint32_t o = lane * 16; o < wlen; o += 32 * 16) place_chunk(s, d, o, min(16u, wlen - o), valid);
+}
+
+// A piece that writes at most 64 bytes, by one lane: with both sides on 16
+// bytes and whole vectors, every load is issued before the first store (a
+// store could alias a later load, so chunk by chunk each load would wait for
+// the store before it); else chunk by chunk.
+__device__ __forceinline__ void place_small(const uint8_t* s, uint8_t* d, uint32_t wlen, uint32_t valid) {
+  const uint64_t al = reinterpret_cast<uint64_t>(s) | reinterpret_cast<uint64_t>(d);
+  if ((al & 15) == 0 && (wlen & 15) == 0) {
+    uint4 v[4];
+#pragma unroll
+    for (uint32_t q = 0; q < 4; q++)
+      if (16 * q < wlen) v[q] = *reinterpret_cast<const uint4*>(s + 16 * q);
+#pragma unroll
+    for (uint32_t q = 0; q < 4; q++) {
+      if (16 * q < wlen) {
+        // zeros after the block's bytes (its slot's padding)
+        const uint32_t b0 = 16 * q;
+        const uint4 o = make_uint4(keep_below(v[q].x, b0, valid), keep_below(v[q].y, b0 + 4, valid),
+                                   keep_below(v[q].z, b0 + 8, valid), keep_below(v[q].w, b0 + 12, valid));
+        *reinterpret_cast<uint4*>(d + b0) = o;
+      }
+    }
+    return;
+  }
+  for (uint32_t o = 0; o < wlen; o += 16) place_chunk(s, d, o, min(16u, wlen - o), valid);
+}
+
 // Every piece of the placement table, warp by warp: each lane loads one
-// descriptor (16 coalesced bytes) and copies its piece itself when it writes
+// descriptor (16 coalesced bytes, a round ahead) and copies its piece itself when it writes
 // at most 64 bytes; larger pieces are copied by the whole warp, one after
 // another, 16 bytes per lane.  The pieces are in staging order, so a warp
 // reads consecutive bytes, and its writes of small pieces fall in a few runs
@@ -795,10 +832,13 @@ __global__ void __launch_bounds__(LEAF_THREADS) place_kernel(PlaceArgs a) {
   constexpr uint32_t WPB = LEAF_THREADS / 32;
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t nwarps = (uint64_t)gridDim.x * WPB;
-  for (uint64_t w = (uint64_t)blockIdx.x * WPB + (threadIdx.x >> 5); w * 32 < a.nd; w += nwarps) {  // uniform per warp
-    const uint64_t i = w * 32 + lane;
-    PlaceDesc g{0, 0};
-    if (i < a.nd) g = a.d[i];
+  uint64_t w = (uint64_t)blockIdx.x * WPB + (threadIdx.x >> 5);
+  PlaceDesc gn{0, 0};  // the lane's descriptor for the next round, loaded a round ahead
+  if (w * 32 + lane < a.nd) gn = a.d[w * 32 + lane];
+  for (; w * 32 < a.nd; w += nwarps) {  // uniform per warp
+    const uint64_t i = w * 32 + lane, inext = (w + nwarps) * 32 + lane;
+    const PlaceDesc g = gn;
+    if (inext < a.nd) gn = a.d[inext];
     const uint64_t so = g.src & ((1ull << 60) - 1), dso = g.dst >> 16;
     const uint32_t pad = (uint32_t)(g.src >> 60), wlen = (uint32_t)(g.dst & 0xFFFFu) + 1, len = wlen - pad;
     bool ok = i < a.nd;
@@ -806,15 +846,14 @@ __global__ void __launch_bounds__(LEAF_THREADS) place_kernel(PlaceArgs a) {
       atomicOr(a.err, ERR_BOUNDS);
       ok = false;
     }
-    if (ok && wlen <= 64)
-      for (uint32_t o = 0; o < wlen; o += 16) place_chunk(a.stage + so, a.arena + dso, o, min(16u, wlen - o), len);
+    if (ok && wlen <= 64) place_small(a.stage + so, a.arena + dso, wlen, len);
     uint32_t big = __ballot_sync(0xffffffffu, ok && wlen > 64);
     while (big) {
       const int j = __ffs(big) - 1;
       big &= big - 1;
       const uint64_t bso = __shfl_sync(0xffffffffu, so, j), bdo = __shfl_sync(0xffffffffu, dso, j);
       const uint32_t bw = __shfl_sync(0xffffffffu, wlen, j), bl = __shfl_sync(0xffffffffu, len, j);
-      for (uint32_t o = lane * 16; o < bw; o += 32 * 16) place_chunk(a.stage + bso, a.arena + bdo, o, min(16u, bw - o), bl);
+      place_big(a.stage + bso, a.arena + bdo, bw, bl, lane);
     }
   }
 }
