@@ -67,6 +67,7 @@ NCU_TRAFFIC = {
     ("dense", 128, 4): (452_980_480, "profiles/fused_kernel_dense.md"),
     ("reloc_stress", 128, 4): (196_291_200, "profiles/relocate_kernel_reloc_stress.md"),
     ("deep", 128, 4): (751_002_368, "profiles/fused_kernel_deep_batched.md"),
+    ("batched", 128, 4): (7_017_168_384, "profiles/fused_kernel_deep_batched.md"),
 }
 
 
