@@ -469,9 +469,8 @@ void release_transfers(dc_plan_s* p);
 dc_status upload_h2d_tables(dc_plan_s* p, cudaStream_t s);
 dc_status transfer_to_device(dc_plan_s* p, cudaStream_t s);
 dc_status transfer_back(dc_plan_s* p, const std::vector<uint32_t>& list, uint64_t key, cudaStream_t s);
-// tile_cap: the tile table's capacity in entries (0: the plan's tseg_cap).
 dc_status upload(dc_plan_s* p, const std::vector<MoveDesc>& d, uint64_t desc_off, uint64_t tile_off, uint64_t cap,
-                 uint64_t* nd, uint64_t* units, cudaStream_t s, uint64_t tile_cap = 0);
+                 uint64_t* nd, uint64_t* units, cudaStream_t s);
 void push_desc(std::vector<MoveDesc>* d, uint64_t src, uint64_t dst, uint64_t bytes);
 dc_status launch_table(dc_plan_s* p, uint64_t desc_off, uint64_t tile_off, uint64_t nd, uint64_t units,
                        cudaStream_t s);

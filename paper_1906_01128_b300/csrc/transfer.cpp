@@ -193,14 +193,14 @@ void release_transfers(dc_plan_s* p) {
 // sources are pageable vectors: cudaMemcpyAsync returns once it has staged
 // them, so they may go away afterwards.
 dc_status upload(dc_plan_s* p, const std::vector<MoveDesc>& d, uint64_t desc_off, uint64_t tile_off, uint64_t cap,
-                 uint64_t* nd, uint64_t* units, cudaStream_t s, uint64_t tile_cap) {
+                 uint64_t* nd, uint64_t* units, cudaStream_t s) {
   *nd = d.size();
   *units = d.empty() ? 0 : d.back().ubeg + (d.back().bytes + 15) / 16;
   if (d.empty()) return DC_OK;
   if (d.size() > cap) return fail(DC_EINVAL, "move table larger than planned");
   std::vector<uint32_t> tiles;
   const uint64_t ntiles = (*units + LEAF_TILE - 1) / LEAF_TILE;
-  if (ntiles + 1 > (tile_cap ? tile_cap : p->L.tseg_cap)) return fail(DC_EINVAL, "move tile table larger than planned");
+  if (ntiles + 1 > p->L.tseg_cap) return fail(DC_EINVAL, "move tile table larger than planned");
   for (uint64_t t = 0, k = 0; t < ntiles; t++) {
     while (k + 1 < d.size() && d[k + 1].ubeg <= t * LEAF_TILE) k++;
     tiles.push_back((uint32_t)k);
