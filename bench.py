@@ -417,8 +417,9 @@ def relocation_batches(torch, dc, schema, root, info, steps, barrier):
 def pointer_heavy_relocation(torch, dc, tg, steps, warmup, flush, barrier, hbm):
     """relocate_kernel on the pointer-heavy tree (1,118,481 nodes, 2,306,867 slots in 4,370 tiles),
     offset records and device scan, for the default line: CUDA events around single launches, each
-    after the L2 flush (outside the events), and back-to-back launches over copies of the arena
-    (relocation_batches).  The tree is the reloc_stress workload's."""
+    after the L2 flush (outside the events), back-to-back launches over copies of the arena
+    (relocation_batches), and one launch over a forest of four such trees.  The tree is the
+    reloc_stress workload's."""
     t = tg.workload("reloc_stress")
     out = {"workload": WORKLOADS["reloc_stress"]}
     info = None
@@ -455,6 +456,33 @@ def pointer_heavy_relocation(torch, dc, tg, steps, warmup, flush, barrier, hbm):
             out[name]["batched_us"] = round(rb[name] * 1e6, 2)
             out[name]["batched_frac"] = round(nbytes / rb[name] / 1e9 / hbm, 4)
         out["batched_copies"] = rb["copies"]
+    # four such trees as one forest plan, relocated by one launch (after the flush): the kernel's
+    # rate without a launch's ramp and tail per tree
+    more = [tg.workload("reloc_stress", seed=100 + i) for i in range(3)]
+    for name, flags in (("offset", 0), ("device_scan", dc.PLAN_DEVICE_SCAN)):
+        p = dc.Plan(t.schema, [t.root] + [m.root for m in more], flags=flags)
+        p.bind()
+        p.deep_copy()
+        p.sync()
+        fbytes = p.info["nrelocs"] * 20 + p.info["nblocks"] * 16
+        for _ in range(warmup):
+            flush()
+            p.relocate()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        queue_ahead(torch, 1000 + 500 * steps)
+        for e0, e1 in ev:
+            flush()
+            e0.record()
+            p.relocate()
+            e1.record()
+        torch.cuda.synchronize()
+        tf = statistics.mean([e0.elapsed_time(e1) * 1e-3 for e0, e1 in ev])
+        p.sync()
+        p.destroy()
+        out[name]["forest4_us_per_tree"] = round(tf * 1e6 / 4, 2)
+        out[name]["forest4_frac"] = round(fbytes / tf / 1e9 / hbm, 4)
+    for m in more:
+        m.free()
     t.free()
     return out
 
