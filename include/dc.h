@@ -205,7 +205,8 @@ typedef struct {
                              region and the staging area.  Ignored with DC_PLAN_MAP_HOST;
                              set it before dc_bind_device.  The environment variable
                              DC_SPANS=0, read at dc_plan, turns the plan's own rule
-                             off. */
+                             off: a program run under a memory checker (AddressSanitizer
+                             and the like) would report the reads between allocations. */
 #define DC_SPAN_MIN_BLOCKS 1024u
 #define DC_SPAN_MAX_MEAN 4096u
 
